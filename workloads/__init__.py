@@ -1,0 +1,155 @@
+"""Seeded synthetic workloads shared by the oracle, the tests and ``bench.py``.
+
+This module only *describes* inputs: mesh sizes, subdomain cuts, material
+constants, boundary-condition masks, load schedules, tolerances and the seeded
+random draws of the irregular-partition workload.  It holds none of the
+method's arithmetic (no strains, stresses, stiffness, loads or solves), so that
+both the CUDA path and the CPU oracle can take their inputs from here without
+sharing any of the computation.
+
+Material (Sec. 5, numerical experiments): E = 206 900, nu = 0.29,
+sigma_y = 450, H_m = 10 000.  The paper's benchmark geometry (a plate with a
+hole meshed by Ansys and partitioned by Metis) is not available, so seeded
+unit-cube hex meshes with box subdomains stand in for it.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+import random
+
+# Sec. 5: material parameters of the benchmark body.
+MATERIAL = {"young": 206900.0, "poisson": 0.29, "sigma_y": 450.0, "hardening": 10000.0}
+
+# Face names and their (axis, side) pairs; side 0 = low end, 1 = high end.
+FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+
+def equal_cuts(n_elements: int, n_parts: int) -> tuple:
+    """Cut positions splitting ``n_elements`` into ``n_parts`` equal boxes."""
+    if n_elements % n_parts:
+        raise ValueError("equal split needs n_elements divisible by n_parts")
+    a = n_elements // n_parts
+    return tuple(a * i for i in range(n_parts + 1))
+
+
+def irregular_cuts(n_elements: int, rng: random.Random, lo: int = 4, hi: int = 12) -> tuple:
+    """Seeded irregular 1-D partition with segment lengths in [lo, hi].
+
+    While more than ``hi`` elements remain, draw a length uniformly from
+    {lo .. min(hi, rem - lo)}; the last segment takes the remainder, which
+    then lies in [lo, hi].
+    """
+    cuts = [0]
+    rem = n_elements
+    while rem > hi:
+        length = rng.randint(lo, min(hi, rem - lo))
+        cuts.append(cuts[-1] + length)
+        rem -= length
+    cuts.append(n_elements)
+    return tuple(cuts)
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic problem: a box of hex8 elements cut into box subdomains."""
+
+    name: str
+    nel: tuple                       # elements per axis (nx, ny, nz)
+    cuts: tuple                      # per axis, the subdomain cut positions
+    length: tuple = (1.0, 1.0, 1.0)  # box edge lengths
+    material: dict = field(default_factory=lambda: dict(MATERIAL))
+    # Dirichlet mask per face: bit c set = displacement component c fixed.
+    dirichlet: dict = field(default_factory=lambda: {"z0": 7})
+    traction_face: str = "z1"
+    traction_dir: tuple = (1.0, 0.0, 0.0)
+    n_steps: int = 10
+    load_factor: float = 1.5         # final load = load_factor x first-yield load
+    newton_tol: float = 1e-10
+    pcg_rtol: float = 1e-12
+    newton_maxit: int = 30
+    pcg_maxit: int = 2000
+
+    @property
+    def n_sub(self) -> int:
+        return (len(self.cuts[0]) - 1) * (len(self.cuts[1]) - 1) * (len(self.cuts[2]) - 1)
+
+    def dirichlet_masks(self) -> tuple:
+        """Six masks in FACES order."""
+        return tuple(int(self.dirichlet.get(f, 0)) for f in FACES)
+
+    def load_fractions(self, n_steps: int | None = None) -> list:
+        """Linear ramp: step k (1-based) carries load_factor * k / n_steps."""
+        n = self.n_steps if n_steps is None else n_steps
+        return [self.load_factor * k / self.n_steps for k in range(1, n + 1)]
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def cube(name: str, n: int, parts: int, **kw) -> Workload:
+    c = equal_cuts(n, parts)
+    return Workload(name=name, nel=(n, n, n), cuts=(c, c, c), **kw)
+
+
+# Tolerances: in the decomposed Newton of Algorithm 4 the Newton criterion
+# cannot fall below roughly 0.03..0.4 x the dual PCG tolerance (the dual
+# right-hand side always carries the O(1) interface forces), so a Newton
+# tolerance is paired with a PCG tolerance at least ~100x tighter:
+# (1e-10, 1e-12) for parity runs, (1e-6, 1e-8) for timed runs.
+# 12^3 hex8, 2x2x2 subdomains of 6^3, 10 steps to 1.5x first yield.
+CUBE12 = cube("cube12_2x2x2", 12, 2, n_steps=10, newton_tol=1e-10, pcg_rtol=1e-12)
+# 64^3 hex8, 8x8x8 subdomains of 8^3, 20 steps to 1.5x first yield, timed at 1e-8 dual residual.
+CUBE64 = cube("cube64_8x8x8", 64, 8, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
+# 96^3 hex8, 12^3 subdomains of 8^3.
+CUBE96 = cube("cube96_12x12x12", 96, 12, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
+# 128^3 hex8, 16^3 subdomains of 8^3, cyclic load (40 steps).
+CUBE128 = cube("cube128_16x16x16", 128, 16, n_steps=40, newton_tol=1e-6, pcg_rtol=1e-8)
+
+# Small cases for pins and parity tests.
+TINY_1x1x2 = Workload(name="tiny2_1x1x2", nel=(2, 2, 2), cuts=((0, 2), (0, 2), (0, 1, 2)), n_steps=4)
+SMALL4 = cube("small4_2x2x2", 4, 2, n_steps=4)
+SMALL6_RAGGED = Workload(name="small_ragged", nel=(5, 4, 6), cuts=((0, 2, 5), (0, 4), (0, 3, 4, 6)),
+                         length=(1.0, 0.8, 1.2), n_steps=4)
+
+WORKLOADS = {w.name: w for w in (CUBE12, CUBE64, CUBE96, CUBE128, TINY_1x1x2, SMALL4, SMALL6_RAGGED)}
+
+
+def irregular_cube80(seed: int = 0, n: int = 80) -> Workload:
+    """80^3 cube with a seeded tensor-product partition into boxes of 4..12 elements."""
+    rng = random.Random(seed)
+    cuts = tuple(irregular_cuts(n, rng) for _ in range(3))
+    return Workload(name=f"cube80_irregular_s{seed}", nel=(n, n, n), cuts=cuts, n_steps=20)
+
+
+def irregular_cases(seed: int = 0, n_cases: int = 16) -> list:
+    """Seeded material/load cases: sigma_y ~ U[300,600], H ~ U[1e3,2e4], traction angle ~ U[0, 2pi)."""
+    import math
+    rng = random.Random(seed + 1000003)
+    cases = []
+    for _ in range(n_cases):
+        sy = rng.uniform(300.0, 600.0)
+        hm = rng.uniform(1e3, 2e4)
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        cases.append({"sigma_y": sy, "hardening": hm, "traction_dir": (math.cos(th), math.sin(th), 0.0)})
+    return cases
+
+
+def seeded_vector(n: int, seed: int, dtype="float64"):
+    """Deterministic standard-normal vector (numpy) for operator parity tests."""
+    import numpy as np
+    return np.random.default_rng(seed).standard_normal(n).astype(dtype)
+
+
+def seeded_gauss_point_inputs(n: int, seed: int, scale_strain: float = 1e-3, scale_stress: float = 100.0):
+    """Seeded (sigma_k, kappa_k, eta) triples for material-point parity tests.
+
+    sigma_k ~ N(0, scale_stress) per component, kappa_k ~ U[0, 1e-3],
+    eta ~ N(0, scale_strain) per component.  A spread that puts points on both
+    sides of the yield surface for the Sec. 5 material.
+    """
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sig = rng.standard_normal((n, 6)) * scale_stress
+    kap = rng.uniform(0.0, 1e-3, size=n)
+    eta = rng.standard_normal((n, 6)) * scale_strain
+    return sig, kap, eta
