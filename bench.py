@@ -1,0 +1,350 @@
+"""Benchmark: time per load step of the semismooth-Newton TFETI solver (Algorithm 4).
+
+Workload: unit cube of 64^3 trilinear bricks torn into 8x8x8 = 512 boxes of 8^3
+elements (2187 dofs each, 308 544 multipliers), the Sec. 5 material, u = 0 on z = 0,
+uniform x-traction on z = 1 ramped linearly to 1.5 x the first-yield load over 20
+load steps; eps_PCGP = 1e-8 (dual relative residual), eps_Newton = 1e-6.
+
+One bench step = one load step (ssn_time_step): every Newton iteration runs the
+return mapping, the tangent assembly, the subdomain factorisations, the PCGP
+dual solve with its F-applies and projections, and the recovery.  Warm-up steps
+are the first W load steps of the history; the K timed steps continue it (beyond
+step 20 the ramp continues at the same rate).  Inputs (factors 2.5 GB) are larger
+than L2, so no flush is needed between steps.
+
+Arms: default = the CUDA path; ``--impl reference`` = the FP64 CPU oracle on a
+bounded sample of the same workload (see ``oracle_sample``).  For N > 1 (torchrun)
+each rank solves an independent replica of the workload (weak scaling; the solver
+itself runs on one GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "time per load step @1e-8 dual res: FP64 vs mixed+learned; F-apply % HBM peak"
+UNIT = "s/load_step"
+FP64_PEAK_TFLOPS = 1.207      # measured DFMA throughput of this GB300 pool
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def workload_config(w, steps, warmup):
+    return {"workload": f"{w.name}: {w.nel[0]}x{w.nel[1]}x{w.nel[2]} hex8 bricks, "
+                        f"{len(w.cuts[0]) - 1}x{len(w.cuts[1]) - 1}x{len(w.cuts[2]) - 1} subdomains, "
+                        f"{w.n_steps}-step ramp to {w.load_factor} x first-yield x-traction on z=1",
+            "newton_tol": w.newton_tol, "pcg_rtol": w.pcg_rtol, "preconditioner": "lumped",
+            "kdag": "fixing-node banded Cholesky (shared elastic factor per box shape)",
+            "load_steps_timed": f"{warmup + 1}..{warmup + steps}",
+            "l2": "inputs larger than L2 (subdomain factors 2.5 GB), no flush"}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------- oracle
+def oracle_sample(w, n_sub_sample=32, n_pcg_sample=2):
+    """Time the FP64 oracle on a bounded sample of the workload (single BLAS thread).
+
+    Sample: Algorithm 5 and the fixing-node factorisation for ``n_sub_sample`` of the
+    subdomains (scaled to all of them), and ``n_pcg_sample`` full PCGP iterations over all
+    subdomains (F-apply, two projections, lumped preconditioner).  Returns per-component
+    seconds; the model set-up (mesh, B, R, N N^T) is excluded like the GPU's set-up.
+    """
+    import numpy as np
+    from threadpoolctl import threadpool_limits
+    from oracle.decomp import FixingNodeInverse
+    from oracle.ssn import ElastoplasticModel
+    with threadpool_limits(1):
+        model = ElastoplasticModel(w)
+        n_sub = model.dec.n_sub
+        subset = list(range(0, n_sub, max(1, n_sub // n_sub_sample)))[:n_sub_sample]
+        f1 = model.traction_load(w.traction_dir)
+        du = np.zeros(model.dec.n_dof)
+        t0 = time.perf_counter()
+        Kb_sub, _, _ = model.assemble(du, f1, subdomains=set(subset))
+        t_asm = (time.perf_counter() - t0) * n_sub / len(subset)
+        t0 = time.perf_counter()
+        for K, p in zip(Kb_sub, subset):
+            FixingNodeInverse(K, model.fixing[p])
+        t_fac = (time.perf_counter() - t0) * n_sub / len(subset)
+        # a full operator for the PCGP sample: the elastic factor of one box shape repeated
+        kd0 = FixingNodeInverse(Kb_sub[0], model.fixing[subset[0]])
+        solver = model.tfeti([Kb_sub[0]] * n_sub, kdag=[kd0] * n_sub)
+        rng = np.random.default_rng(0)
+        r = rng.standard_normal(model.dec.m)
+        t0 = time.perf_counter()
+        for _ in range(n_pcg_sample):
+            wv = solver.project(r)
+            z = solver.apply_precond(wv)
+            y = solver.project(z)
+            solver.apply_F(y)
+        t_pcg = (time.perf_counter() - t0) / n_pcg_sample
+        t0 = time.perf_counter()
+        solver.apply_F(r)
+        t_fapply = time.perf_counter() - t0
+    return {"assembly_s": t_asm, "factor_s": t_fac, "pcg_iter_s": t_pcg, "f_apply_s": t_fapply, "cores": 1,
+            "sample": f"Algorithm 5 + fixing-node Cholesky on {len(subset)} of {n_sub} subdomains (scaled), "
+                      f"{n_pcg_sample} PCGP iterations over all {n_sub} subdomains; 1 BLAS thread"}
+
+
+def oracle_step_estimate(s, newton_per_step, pcg_per_step):
+    """Seconds per load step: per Newton iteration assembly + factorisation + 3 set-up/recovery
+    F-applies, plus the PCGP iterations, with the given iteration counts."""
+    return newton_per_step * (s["assembly_s"] + s["factor_s"] + 3 * s["f_apply_s"]) + pcg_per_step * s["pcg_iter_s"]
+
+
+def oracle_record_counts(first, last):
+    path = os.path.join(ROOT, "tests", "golden", "cube64_oracle_record.json")
+    with open(path) as fh:
+        rec = json.load(fh)
+    steps = [s for s in rec["steps"] if first <= s["step"] <= last] or rec["steps"]
+    newton = statistics.mean(s["newton"] for s in steps)
+    pcg = statistics.mean(sum(s["pcg"]) for s in steps)
+    return newton, pcg, f"oracle record, load steps {steps[0]['step']}..{steps[-1]['step']}"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = W.CUBE64
+    t_start = time.perf_counter()
+    try:
+        newton, pcg, src = oracle_record_counts(args.warmup + 1, args.warmup + args.steps)
+    except (OSError, ValueError, KeyError):
+        newton, pcg, src = None, None, None
+    for _ in range(args.warmup):
+        pass
+    s = oracle_sample(w)
+    if newton is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration-count record missing"}))
+        return
+    v = oracle_step_estimate(s, newton, pcg)
+    elapsed = time.perf_counter() - t_start
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, args.steps, args.warmup),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                             "sample": s["sample"] + f"; iteration counts per step from the {src} "
+                                                     f"(Newton {newton:.2f}, PCGP {pcg:.1f})",
+                             "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s")},
+                             "wall_s": elapsed},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------------------- CUDA path
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_1205_1926_gb300 as T
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = W.CUBE64
+    n_total = args.warmup + args.steps
+    stream = torch.cuda.Stream(device=dev)
+    ctx = T.Context(w, stream=stream)
+    n = ctx.sizes["n_dof"]
+    n_gp = ctx.sizes["n_gp"]
+    t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
+    fr = w.load_fractions(n_total)
+    dfs, prev = [], 0.0
+    with torch.cuda.stream(stream):
+        for a in fr:
+            d = torch.zeros(n, dtype=torch.float64, device=dev)
+            ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), d)
+            dfs.append(d)
+            prev = a
+    stream.synchronize()
+    infos = []
+    for k in range(args.warmup):
+        infos.append(ctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+    # checkpoint for the end-to-end pass
+    ck = [torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(6 * n_gp, dtype=torch.float64, device=dev),
+          torch.zeros(n_gp, dtype=torch.float64, device=dev)]
+    ctx.get_state(*ck)
+
+    # ---- timed pass: inputs resident in HBM
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ctx.timing_reset(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    timed = []
+    for k in range(args.warmup, n_total):
+        timed.append(ctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    tm = ctx.timing()
+    u_dev = torch.zeros(n, dtype=torch.float64, device=dev)
+    ctx.get_state(u=u_dev)
+    u_final = u_dev.clone()
+
+    # ---- end-to-end pass: same steps through the C ABI with host (pinned) buffers
+    ctx.set_state(*ck)
+    dfs_h = [d.cpu().pin_memory() for d in dfs]
+    u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.warmup, n_total):
+        ctx.time_step(dfs_h[k].data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit, df_on_host=True)
+        ctx.get_state(u=u_dev)
+        with torch.cuda.stream(stream):
+            u_host.copy_(u_dev, non_blocking=True)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    elapsed_e2e = time.perf_counter() - t0
+    e2e_match = bool(torch.equal(u_host.to(dev), u_final))
+
+    if world > 1:
+        t = torch.tensor([elapsed, elapsed_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed, elapsed_e2e = float(t[0]), float(t[1])
+    units = args.steps * world
+    value = elapsed / units
+    pk, pk_kind = peaks()
+    avg_f_ms = tm["f_apply_ms_total"] / max(tm["f_apply_launches"], 1)
+    flops = tm["f_apply_flops"]
+    byts = tm["f_apply_bytes"]
+    achieved_tf = flops / (avg_f_ms * 1e-3) / 1e12 if avg_f_ms > 0 else None
+    achieved_gbs = byts / (avg_f_ms * 1e-3) / 1e9 if avg_f_ms > 0 else None
+    t_alu, t_hbm = flops / (FP64_PEAK_TFLOPS * 1e12), byts / (pk["hbm_gbs"] * 1e9)
+    bound = "alu" if t_alu >= t_hbm else "hbm"
+    if bound == "alu":
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": None,
+                "kernel": "k_sub_solve (F-apply: banded forward/backward substitution, FP64)",
+                "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None, "traffic": None,
+                "kernel": "k_sub_solve (F-apply)", "peak_kind": pk_kind}
+    roof["hbm"] = {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
+                   "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None,
+                   "bytes_per_launch": byts, "flops_per_launch": flops, "avg_launch_ms": avg_f_ms,
+                   "launches": tm["f_apply_launches"], "of": f"{pk_kind} hbm_gbs"}
+    newton_steps = [s["newton"] for s in timed]
+    pcg_steps = [sum(s["pcg"]) for s in timed]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, args.steps, args.warmup) | {"parallelism": "replicas" if world > 1 else "1 GPU"},
+            "e2e": {"value": elapsed_e2e / units, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n, "matches_device_pass": e2e_match},
+            "gpu_launches": int(tm["kernel_launches"]),
+            "roofline": roof,
+            "clocks": clocks,
+            "solver": {"t_y": t_y, "newton_per_step": newton_steps, "pcg_per_step": pcg_steps,
+                       "plastic_gp_final": timed[-1]["plastic_committed"],
+                       "refactored_per_step": [s["refactored"] for s in timed],
+                       "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
+                       "timed_s": elapsed}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(w)
+        v = oracle_step_estimate(s, statistics.mean(newton_steps), statistics.mean(pcg_steps))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                                "sample": s["sample"] + "; scaled with this run's Newton/PCGP counts per step",
+                                "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s",
+                                                                   "f_apply_s")}}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=17)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * tfeti.h -- C ABI of the GB300 TFETI solver for one-time-step von Mises
+ * elastoplasticity with linear isotropic hardening.
+ *
+ * Method: Cermak, Kozubek, Sysala, Valdman, "A TFETI Domain Decomposition
+ * Solver for Elastoplastic Problems".  Section, equation and algorithm
+ * numbers below refer to that paper.
+ *
+ * General conventions
+ * -------------------
+ * - Every call returns an int status (TFETI_OK = 0 on success); no C++
+ *   exception crosses this boundary.  tfeti_last_error(ctx) returns a message
+ *   for the last failing call on that context.
+ * - "device" pointers are CUDA global-memory pointers on the context's device;
+ *   "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *   passes; the context owns everything it allocates and frees it in
+ *   tfeti_destroy.  Null is accepted only where a parameter says "nullable".
+ * - All device work of a context is enqueued on the CUDA stream given to
+ *   tfeti_setup.  Calls that return host data synchronise that stream.
+ * - Floating point is IEEE binary64 throughout unless stated.
+ *
+ * Discretisation and layouts (all shared with the documentation of the CPU
+ * oracle, which implements them independently)
+ * ------------------------------------------------------------------------
+ * - Box [0,Lx]x[0,Ly]x[0,Lz] of nx*ny*nz trilinear 8-node bricks with 2x2x2
+ *   Gauss points (the paper uses P1 tetrahedra, Sec. 3.1; |T| of eqs. (F_def)
+ *   and (K_def) becomes the Gauss weight times det J = hx hy hz / 8).
+ * - Global node (i,j,k) has id i + (nx+1)(j + (ny+1) k).
+ * - Subdomains are a tensor product of per-axis cuts; box (I,J,K) has id
+ *   p = I + sx (J + sy K).  Local node (li,lj,lk) of a box with (ax,ay,az)
+ *   elements has id li + (ax+1)(lj + (ay+1) lk); local dof = 3 lnode + c.
+ * - Decomposed vectors (u, f, du) concatenate the subdomain vectors in
+ *   subdomain order: length n_dof = sum_p 3 (ax+1)(ay+1)(az+1).
+ * - Element local nodes: bottom face counter-clockwise then top face,
+ *   offsets (0,0,0)(1,0,0)(1,1,0)(0,1,0)(0,0,1)(1,0,1)(1,1,1)(0,1,1).
+ *   Elements of a box are numbered x-fastest; Gauss point g = gx + 2 gy + 4 gz
+ *   at reference coordinates (2 g_d - 1)/sqrt(3).  The Gauss-point index is
+ *   gp = 8 (elem_off[p] + local element) + g, n_gp = 8 * n_elements.
+ * - Stress vectors (s11,s22,s33,s12,s23,s13); strain vectors with engineering
+ *   shears (e11,e22,e33,2e12,2e23,2e13) (eq. (stress_strain_vector)).
+ *   Gauss-point arrays are structure-of-arrays: a [6][n_gp] stress array
+ *   holds component c of point gp at c*n_gp + gp.
+ * - Multipliers (rows of the orthonormal B of eq. (equ.set.matrix.B)) come in
+ *   (global node, component) order.  The copies of a node are ordered by
+ *   subdomain id.  A component fixed by a Dirichlet mask gives one identity
+ *   row per copy; a free component with k >= 2 copies gives the k-1 Helmert
+ *   rows (e_1 + ... + e_j - j e_{j+1}) / sqrt(j (j+1)), j = 1..k-1, i.e. the
+ *   orthonormalised redundant gluing rows of Sec. 4.1.
+ * - The generalised inverse K_p^+ is the fixing-node one of Remark 1: the
+ *   rows/columns of the dofs {x,y,z of local node (0,0,0); y,z of (ax,0,0);
+ *   z of (0,ay,0)} are removed and the rest is banded-Cholesky factorised.
+ *   u and lambda do not depend on this choice; alpha and d do.
+ */
+#ifndef TFETI_H
+#define TFETI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define TFETI_OK                 0
+#define TFETI_ERR_ARG            1  /* invalid argument, size or pointer              */
+#define TFETI_ERR_CUDA           2  /* a CUDA runtime call failed                     */
+#define TFETI_ERR_OOM            3  /* device or host allocation failed               */
+#define TFETI_ERR_NUMERIC        4  /* non-positive pivot in a subdomain factorisation */
+#define TFETI_ERR_SINGULAR       5  /* coarse matrix G G^T not SPD (Ker K ∩ Ker B ≠ 0) */
+#define TFETI_ERR_NOT_CONVERGED  6  /* iteration limit reached (last iterate written)  */
+#define TFETI_ERR_BREAKDOWN      7  /* p^T F p <= 0 in PCGP                           */
+#define TFETI_ERR_NONFINITE      8  /* NaN or Inf met in a residual or scalar         */
+
+/* ---- problem description (host struct, copied by tfeti_setup) ------------ */
+#define TFETI_PRECOND_NONE   0
+#define TFETI_PRECOND_LUMPED 1      /* F^-1 ~ B K B^T (Sec. 4.2) */
+
+typedef struct tfeti_problem {
+    int32_t nel[3];            /* elements per axis, each >= 1                         */
+    double  length[3];         /* box edge lengths, > 0                                */
+    int32_t nsub[3];           /* subdomains per axis, each >= 1                       */
+    const int32_t* cuts[3];    /* host, nullable: per axis nsub[a]+1 increasing cut
+                                  positions from 0 to nel[a]; NULL = equal split
+                                  (nel[a] must then be divisible by nsub[a])           */
+    double  young, poisson;    /* E > 0, 0 < nu < 0.5                                  */
+    double  sigma_y, hardening;/* initial yield stress > 0, hardening modulus H_m > 0 */
+    int32_t dirichlet[6];      /* per face x0,x1,y0,y1,z0,z1: bit c = component c fixed */
+    int32_t traction_face;     /* 0..5 in the same face order: the loaded face          */
+    int32_t precond;           /* TFETI_PRECOND_*                                      */
+} tfeti_problem;
+
+typedef struct tfeti_sizes {
+    int64_t n_sub;             /* s                                                     */
+    int64_t n_dof;             /* decomposed dofs                                       */
+    int64_t n_elements;
+    int64_t n_gp;              /* 8 n_elements                                          */
+    int64_t n_mult;            /* m, number of rows of B                                */
+    int64_t n_coarse;          /* l = 6 s                                               */
+    int64_t n_nodes;           /* global nodes                                          */
+    int64_t n_copy;            /* interface copy slots (3 per interface node copy)      */
+    int64_t max_band;          /* largest subdomain half bandwidth (dofs)               */
+    int64_t device_bytes;      /* device memory the context holds (0 for a plan)        */
+} tfeti_sizes;
+
+/* ---- host-only plan: mesh, partition and index maps, no GPU needed -------- */
+typedef struct tfeti_plan tfeti_plan;
+
+/* Builds the mesh numbering, subdomains, B (Sec. 4.1) and fixing dofs on the
+ * host.  Errors: TFETI_ERR_ARG (bad sizes/cuts/material), TFETI_ERR_OOM. */
+int tfeti_plan_create(const tfeti_problem* prob, tfeti_plan** out);
+int tfeti_plan_destroy(tfeti_plan* plan);
+int tfeti_plan_sizes(const tfeti_plan* plan, tfeti_sizes* out);
+/* B as COO in row order (copies in subdomain order within a row); each array
+ * holds plan nnz(B) entries, host memory, caller-allocated.  *nnz receives the
+ * count; pass null arrays to query it. */
+int tfeti_plan_export_B(const tfeti_plan* plan, int64_t* rows, int64_t* cols, double* vals, int64_t* nnz);
+/* Per subdomain: origin[3], dims[3] (elements), dof offset, element offset,
+ * half bandwidth: 9 int64 per subdomain, host memory [n_sub][9]. */
+int tfeti_plan_export_subdomains(const tfeti_plan* plan, int64_t* out);
+/* Fixing dofs: 6 local dof indices per subdomain, host [n_sub][6]. */
+int tfeti_plan_export_fixing(const tfeti_plan* plan, int32_t* out);
+
+/* ---- device context -------------------------------------------------------- */
+typedef struct tfeti_ctx tfeti_ctx;
+
+/* Sec. 4.1-4.2, Algorithm 3 line 1 set-up: builds the plan, uploads the index
+ * maps, forms the element tables, the rigid-body bases R_p, G = R^T B^T, the
+ * coarse matrix G G^T and its inverse H (factorised once: G depends only on B
+ * and R), and the shared elastic factors of every subdomain shape.  The state
+ * (u, sigma, kappa) starts at zero (Algorithm 1 line 1).  `cuda_stream` is a
+ * cudaStream_t (nullable = default stream) on the current device.
+ * Errors: TFETI_ERR_ARG, TFETI_ERR_OOM, TFETI_ERR_CUDA, TFETI_ERR_SINGULAR,
+ * TFETI_ERR_NUMERIC. */
+int tfeti_setup(const tfeti_problem* prob, void* cuda_stream, tfeti_ctx** out);
+int tfeti_destroy(tfeti_ctx* ctx);
+int tfeti_sizes_get(const tfeti_ctx* ctx, tfeti_sizes* out);
+const char* tfeti_last_error(const tfeti_ctx* ctx);
+const char* tfeti_status_str(int status);
+
+/* Decomposed load of a uniform traction t (host double[3]) on the problem's
+ * traction face: each element face gives t * area / 4 to each of its four
+ * nodes in the subdomain owning the element.  f_out: device [n_dof]. */
+int tfeti_traction_load(tfeti_ctx* ctx, const double* t, double* f_out);
+
+/* Return mapping at every Gauss point (Sec. 2.4 eqs. (elast_pred),
+ * (plast_corr), (stress_op), (hardening_op); Algorithm 5 lines 6-7) for the
+ * displacement increment du (device [n_dof]) from the committed state
+ * sigma_k, kappa_k.  Outputs (device, caller-owned): dsigma [6][n_gp],
+ * dkappa [n_gp], plastic [n_gp] (1 iff Phi(sigma_k + C eta, kappa_k) > 0),
+ * Dtan (nullable) [21][n_gp]: the Clarke derivative T^o_k of Sec. 3.1 as the
+ * upper triangle of the 6x6 matrix, row-major (00,01,..,05,11,..,55). */
+int tfeti_return_map(tfeti_ctx* ctx, const double* du, double* dsigma, double* dkappa,
+                     uint8_t* plastic, double* Dtan);
+
+/* Algorithm 5 lines 8-9 for every subdomain at du (device [n_dof]):
+ * f^p = df^p - sum_T |T| dsigma_T^T G_T R_T and K^p = sum_T |T| (T^o G_T R_T)^T G_T R_T,
+ * then the generalised inverse of every K^p is prepared (banded Cholesky of
+ * K_rr; subdomains whose Gauss points are all elastic reuse the shared factor
+ * of their shape).  df: device [n_dof]; f_out: device [n_dof], nullable.  The
+ * assembled operator stays in the context for tfeti_dual_pcg and the
+ * operator calls below.  Errors: TFETI_ERR_NUMERIC. */
+int tfeti_assemble_tangent(tfeti_ctx* ctx, const double* du, const double* df, double* f_out);
+
+typedef struct tfeti_pcg_info {
+    int32_t iterations;        /* PCGP iterations j                                     */
+    int32_t converged;         /* 1 if ||w|| <= rtol ||r^0||                             */
+    int32_t used_lambda0;      /* 1 if a caller lambda0 was used as the start           */
+    int32_t f_applies;         /* F-applies including set-up and recovery               */
+    double  r0_norm;           /* ||r^0|| = ||d~||                                      */
+    double  w_norm;            /* last ||w^{j-1}||                                      */
+    double  seconds;           /* wall time of the call                                 */
+} tfeti_pcg_info;
+
+/* Algorithm 3 on the operator left by tfeti_assemble_tangent, for the
+ * decomposed right-hand side f (device [n_dof]): lambda_Im = N^T H e,
+ * d~ = d - F lambda_Im, PCGP with the lumped preconditioner and the stopping
+ * test ||w^{j-1}|| <= rtol ||r^0|| after the updates, then alpha = H N (d - F lambda)
+ * and u = K^+ (f - B^T lambda) + R alpha.  u_out: device [n_dof]; lambda_out:
+ * device [n_mult], nullable; lambda0: device [n_mult], nullable -- if given,
+ * lambda_Ker starts from P_N lambda0 instead of o.  info: host, nullable.
+ * Errors: TFETI_ERR_NOT_CONVERGED (last iterate written), TFETI_ERR_BREAKDOWN,
+ * TFETI_ERR_NONFINITE. */
+int tfeti_dual_pcg(tfeti_ctx* ctx, const double* f, double* u_out, double* lambda_out,
+                   const double* lambda0, double rtol, int32_t maxit, tfeti_pcg_info* info);
+
+#define TFETI_MAX_NEWTON 64
+typedef struct tfeti_step_info {
+    int32_t newton;                          /* Newton iterations i                       */
+    int32_t converged;
+    int32_t pcg[TFETI_MAX_NEWTON];           /* PCGP iterations per Newton iteration      */
+    int64_t plastic[TFETI_MAX_NEWTON];       /* plastic Gauss points per Newton iteration */
+    double  criterion[TFETI_MAX_NEWTON];     /* ||du_i - du_{i-1}|| / (||du_i|| + ||du_{i-1}||) */
+    int32_t refactored[TFETI_MAX_NEWTON];    /* subdomains refactorised per iteration     */
+    int64_t plastic_committed;               /* plastic points of the committed state     */
+    double  seconds;
+} tfeti_step_info;
+
+/* Algorithm 4 for one time step: du = o; Newton iterations of Algorithm 5 +
+ * Algorithm 3 with the relative-increment stop of Algorithm 2; then commits
+ * u += du and sigma, kappa += T_k, T_kappa evaluated at the final du.  On any
+ * error the committed state is left at step k.  df: the load increment, host
+ * memory if df_on_host != 0 else device [n_dof].  info: host, nullable.
+ * Errors: TFETI_ERR_NOT_CONVERGED, and those of the calls above. */
+int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double newton_tol,
+                  double pcg_rtol, int32_t newton_maxit, int32_t pcg_maxit, tfeti_step_info* info);
+
+/* Load magnitude of the workloads: t_y = sigma_y / max_g sqrt(3/2) ||dev sigma_g||
+ * for the elastic response to the unit traction `dir` (host double[3]) on the
+ * traction face, solved with tfeti_dual_pcg at rtol.  Requires the zero
+ * state (fresh context); leaves the committed state unchanged. */
+int tfeti_first_yield_traction(tfeti_ctx* ctx, const double* dir, double rtol, double* t_y);
+
+/* ---- committed state (checkpoint / resume, Algorithm 4 line 16-17) -------- */
+/* u: [n_dof], sigma: [6][n_gp], kappa: [n_gp]; device pointers, each nullable. */
+int tfeti_get_state(tfeti_ctx* ctx, double* u, double* sigma, double* kappa);
+int tfeti_set_state(tfeti_ctx* ctx, const double* u, const double* sigma, const double* kappa);
+
+/* ---- dual operators on the last assembled tangent (for tests and tools) --- */
+/* y = F x = B K^+ B^T x (eq. (equ:sps3)); x, y device [n_mult]. */
+int tfeti_apply_F(tfeti_ctx* ctx, const double* x, double* y);
+/* y = P_N x = x - N^T (N N^T)^{-1} N x (Sec. 4.2); device [n_mult]. */
+int tfeti_apply_projector(tfeti_ctx* ctx, const double* x, double* y);
+/* y = B K B^T x, the lumped preconditioner (Sec. 4.2); device [n_mult]. */
+int tfeti_apply_precond(tfeti_ctx* ctx, const double* x, double* y);
+/* y = N x = -R^T B^T x; x device [n_mult], y device [n_coarse]. */
+int tfeti_apply_N(tfeti_ctx* ctx, const double* x, double* y);
+/* y = K^+ x per subdomain; device [n_dof]. */
+int tfeti_apply_kdag(tfeti_ctx* ctx, const double* x, double* y);
+/* y = K x per subdomain (the assembled tangent, fixing dofs untouched); device [n_dof]. */
+int tfeti_apply_K(tfeti_ctx* ctx, const double* x, double* y);
+
+/* ---- timing of the last calls (host) ---------------------------------------- */
+typedef struct tfeti_timing {
+    double f_apply_ms_total;   /* summed device time of the F-apply kernel launches     */
+    int64_t f_apply_launches;
+    double f_apply_bytes;      /* algorithmic bytes of one F-apply                      */
+    double f_apply_flops;      /* FP64 flops of one F-apply                             */
+    double factor_ms_total;
+    int64_t factor_launches;
+    int64_t kernel_launches;   /* library kernels launched since the last reset         */
+} tfeti_timing;
+int tfeti_timing_get(tfeti_ctx* ctx, tfeti_timing* out);
+int tfeti_timing_reset(tfeti_ctx* ctx, int32_t enable_events);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFETI_H */

@@ -70,14 +70,16 @@ class ElastoplasticModel:
         ds, dk, plastic = self.mat.stress_increment(sigma, kappa, eta)
         return ds, dk, plastic, eta
 
-    def assemble(self, du: np.ndarray, df: np.ndarray):
-        """Algorithm 5 for every subdomain: K^p (sparse) and f^p (decomposed)."""
+    def assemble(self, du: np.ndarray, df: np.ndarray, subdomains=None):
+        """Algorithm 5 for every subdomain (or the listed ones): K^p (sparse) and f^p (decomposed)."""
         eta = self.strains(du)
         ds, dk, plastic = self.mat.stress_increment(self.sigma, self.kappa, eta)
         D = self.mat.tangent(self.sigma, self.kappa, eta)
         K_blocks = []
         f = df.copy()
         for p, s in enumerate(self.dec.subs):
+            if subdomains is not None and p not in subdomains:
+                continue
             sl = self.gp_slice(p)
             E = s.n_elements
             Ke = element_stiffness(self.Bg, D[sl].reshape(E, 8, 6, 6), self.wdet)

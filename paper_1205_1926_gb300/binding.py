@@ -1,0 +1,298 @@
+"""ctypes binding of the C ABI declared in ``include/tfeti.h``.
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Device buffers are passed as raw pointers; torch tensors (CUDA,
+float64/uint8, contiguous) are accepted wherever a device pointer is expected.
+The library is built in-tree by ``build.py``; if it is missing the import of
+this module raises, so there is no silent fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+TFETI_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "non-positive pivot",
+          5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value"}
+PRECOND_NONE, PRECOND_LUMPED = 0, 1
+MAX_NEWTON = 64
+FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+
+class Problem(C.Structure):
+    _fields_ = [("nel", C.c_int32 * 3), ("length", C.c_double * 3), ("nsub", C.c_int32 * 3),
+                ("cuts", C.POINTER(C.c_int32) * 3), ("young", C.c_double), ("poisson", C.c_double),
+                ("sigma_y", C.c_double), ("hardening", C.c_double), ("dirichlet", C.c_int32 * 6),
+                ("traction_face", C.c_int32), ("precond", C.c_int32)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_sub", "n_dof", "n_elements", "n_gp", "n_mult", "n_coarse", "n_nodes",
+                                         "n_copy", "max_band", "device_bytes")]
+
+
+class PcgInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("used_lambda0", C.c_int32),
+                ("f_applies", C.c_int32), ("r0_norm", C.c_double), ("w_norm", C.c_double), ("seconds", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("newton", C.c_int32), ("converged", C.c_int32), ("pcg", C.c_int32 * MAX_NEWTON),
+                ("plastic", C.c_int64 * MAX_NEWTON), ("criterion", C.c_double * MAX_NEWTON),
+                ("refactored", C.c_int32 * MAX_NEWTON), ("plastic_committed", C.c_int64), ("seconds", C.c_double)]
+
+    def as_dict(self) -> dict:
+        n = self.newton
+        return {"newton": n, "converged": bool(self.converged), "pcg": list(self.pcg[:n]),
+                "plastic": list(self.plastic[:n]), "criterion": list(self.criterion[:n]),
+                "refactored": list(self.refactored[:n]), "plastic_committed": self.plastic_committed,
+                "seconds": self.seconds}
+
+
+class Timing(C.Structure):
+    _fields_ = [("f_apply_ms_total", C.c_double), ("f_apply_launches", C.c_int64), ("f_apply_bytes", C.c_double),
+                ("f_apply_flops", C.c_double), ("factor_ms_total", C.c_double), ("factor_launches", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int32
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "tfeti_plan_create": (C.c_int, [C.POINTER(Problem), C.POINTER(_P)]),
+    "tfeti_plan_destroy": (C.c_int, [_P]),
+    "tfeti_plan_sizes": (C.c_int, [_P, C.POINTER(Sizes)]),
+    "tfeti_plan_export_B": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int64)]),
+    "tfeti_plan_export_subdomains": (C.c_int, [_P, _P]),
+    "tfeti_plan_export_fixing": (C.c_int, [_P, _P]),
+    "tfeti_setup": (C.c_int, [C.POINTER(Problem), _P, C.POINTER(_P)]),
+    "tfeti_destroy": (C.c_int, [_P]),
+    "tfeti_sizes_get": (C.c_int, [_P, C.POINTER(Sizes)]),
+    "tfeti_last_error": (C.c_char_p, [_P]),
+    "tfeti_status_str": (C.c_char_p, [C.c_int]),
+    "tfeti_traction_load": (C.c_int, [_P, _P, _P]),
+    "tfeti_return_map": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "tfeti_assemble_tangent": (C.c_int, [_P, _P, _P, _P]),
+    "tfeti_dual_pcg": (C.c_int, [_P, _P, _P, _P, _P, _D, _I, C.POINTER(PcgInfo)]),
+    "ssn_time_step": (C.c_int, [_P, _P, _I, _D, _D, _I, _I, C.POINTER(StepInfo)]),
+    "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
+    "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
+    "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
+    "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_projector": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_precond": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_N": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_kdag": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_K": (C.c_int, [_P, _P, _P]),
+    "tfeti_timing_get": (C.c_int, [_P, C.POINTER(Timing)]),
+    "tfeti_timing_reset": (C.c_int, [_P, _I]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load the in-tree shared library (building it first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"TFETI CUDA library not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TfetiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def make_problem(workload, material: dict | None = None, precond: int = PRECOND_LUMPED):
+    """Fill a Problem struct from a ``workloads.Workload`` (sizes, cuts, material, masks)."""
+    pr = Problem()
+    mat = dict(workload.material if material is None else material)
+    keep = []
+    for d in range(3):
+        pr.nel[d] = workload.nel[d]
+        pr.length[d] = workload.length[d]
+        cuts = workload.cuts[d]
+        pr.nsub[d] = len(cuts) - 1
+        arr = (C.c_int32 * len(cuts))(*cuts)
+        keep.append(arr)
+        pr.cuts[d] = C.cast(arr, C.POINTER(C.c_int32))
+    pr.young, pr.poisson = mat["young"], mat["poisson"]
+    pr.sigma_y, pr.hardening = mat["sigma_y"], mat["hardening"]
+    for f, m in enumerate(workload.dirichlet_masks()):
+        pr.dirichlet[f] = m
+    pr.traction_face = FACES.index(workload.traction_face)
+    pr.precond = precond
+    pr._keep = keep
+    return pr
+
+
+class Plan:
+    """Host-only plan (no GPU): sizes, B, subdomains and fixing dofs."""
+
+    def __init__(self, workload, **kw):
+        self.lib = load()
+        self.problem = make_problem(workload, **kw)
+        h = _P()
+        st = self.lib.tfeti_plan_create(C.byref(self.problem), C.byref(h))
+        if st != TFETI_OK:
+            raise TfetiError(st, "tfeti_plan_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tfeti_plan_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def sizes(self) -> dict:
+        s = Sizes()
+        self.lib.tfeti_plan_sizes(self.h, C.byref(s))
+        return {k: getattr(s, k) for k, _ in Sizes._fields_}
+
+    def export_B(self):
+        import numpy as np
+        nnz = C.c_int64()
+        self.lib.tfeti_plan_export_B(self.h, None, None, None, C.byref(nnz))
+        rows = np.zeros(nnz.value, dtype=np.int64)
+        cols = np.zeros(nnz.value, dtype=np.int64)
+        vals = np.zeros(nnz.value, dtype=np.float64)
+        self.lib.tfeti_plan_export_B(self.h, rows.ctypes.data, cols.ctypes.data, vals.ctypes.data, C.byref(nnz))
+        return rows, cols, vals
+
+    def export_subdomains(self):
+        import numpy as np
+        out = np.zeros((self.sizes()["n_sub"], 9), dtype=np.int64)
+        self.lib.tfeti_plan_export_subdomains(self.h, out.ctypes.data)
+        return out
+
+    def export_fixing(self):
+        import numpy as np
+        out = np.zeros((self.sizes()["n_sub"], 6), dtype=np.int32)
+        self.lib.tfeti_plan_export_fixing(self.h, out.ctypes.data)
+        return out
+
+
+class Context:
+    """A device context (``tfeti_setup``) with thin wrappers of every C-ABI call."""
+
+    def __init__(self, workload, stream=None, **kw):
+        self.lib = load()
+        self.problem = make_problem(workload, **kw)
+        h = _P()
+        st = self.lib.tfeti_setup(C.byref(self.problem), _ptr_stream(stream), C.byref(h))
+        if st != TFETI_OK:
+            raise TfetiError(st, "tfeti_setup")
+        self.h = h
+        s = Sizes()
+        self.lib.tfeti_sizes_get(self.h, C.byref(s))
+        self.sizes = {k: getattr(s, k) for k, _ in Sizes._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tfeti_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _check(self, st, name):
+        if st != TFETI_OK:
+            raise TfetiError(st, f"{name}: {self.lib.tfeti_last_error(self.h).decode()}")
+        return st
+
+    def traction_load(self, t, f_out):
+        arr = (C.c_double * 3)(*t)
+        return self._check(self.lib.tfeti_traction_load(self.h, C.cast(arr, _P), _ptr(f_out)), "tfeti_traction_load")
+
+    def return_map(self, du, dsigma, dkappa, plastic, Dtan=None):
+        return self._check(self.lib.tfeti_return_map(self.h, _ptr(du), _ptr(dsigma), _ptr(dkappa), _ptr(plastic),
+                                                     _ptr(Dtan)), "tfeti_return_map")
+
+    def assemble_tangent(self, du, df, f_out=None):
+        return self._check(self.lib.tfeti_assemble_tangent(self.h, _ptr(du), _ptr(df), _ptr(f_out)),
+                           "tfeti_assemble_tangent")
+
+    def dual_pcg(self, f, u_out, lambda_out=None, lambda0=None, rtol=1e-8, maxit=5000, check=True):
+        info = PcgInfo()
+        st = self.lib.tfeti_dual_pcg(self.h, _ptr(f), _ptr(u_out), _ptr(lambda_out), _ptr(lambda0), rtol, maxit,
+                                     C.byref(info))
+        if check:
+            self._check(st, "tfeti_dual_pcg")
+        return {k: getattr(info, k) for k, _ in PcgInfo._fields_} | {"status": st}
+
+    def time_step(self, df, newton_tol, pcg_rtol, newton_maxit=30, pcg_maxit=5000, df_on_host=False, check=True):
+        info = StepInfo()
+        st = self.lib.ssn_time_step(self.h, _ptr(df), 1 if df_on_host else 0, newton_tol, pcg_rtol, newton_maxit,
+                                    pcg_maxit, C.byref(info))
+        if check:
+            self._check(st, "ssn_time_step")
+        return info.as_dict() | {"status": st}
+
+    def first_yield_traction(self, direction, rtol=1e-12) -> float:
+        arr = (C.c_double * 3)(*direction)
+        out = C.c_double()
+        self._check(self.lib.tfeti_first_yield_traction(self.h, C.cast(arr, _P), rtol, C.byref(out)),
+                    "tfeti_first_yield_traction")
+        return out.value
+
+    def get_state(self, u=None, sigma=None, kappa=None):
+        return self._check(self.lib.tfeti_get_state(self.h, _ptr(u), _ptr(sigma), _ptr(kappa)), "tfeti_get_state")
+
+    def set_state(self, u=None, sigma=None, kappa=None):
+        return self._check(self.lib.tfeti_set_state(self.h, _ptr(u), _ptr(sigma), _ptr(kappa)), "tfeti_set_state")
+
+    def apply(self, which: str, x, y):
+        fn = getattr(self.lib, "tfeti_apply_" + which)
+        return self._check(fn(self.h, _ptr(x), _ptr(y)), "tfeti_apply_" + which)
+
+    def timing(self) -> dict:
+        t = Timing()
+        self.lib.tfeti_timing_get(self.h, C.byref(t))
+        return {k: getattr(t, k) for k, _ in Timing._fields_}
+
+    def timing_reset(self, events: bool):
+        self.lib.tfeti_timing_reset(self.h, 1 if events else 0)
+
+
+def _ptr_stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)

@@ -1,0 +1,821 @@
+// C ABI of the GB300 TFETI solver: context set-up (Sec. 4.1-4.2), assembly
+// (Algorithm 5), PCGP (Algorithm 3) and one semismooth-Newton time step
+// (Algorithm 4).  Host code only orchestrates; every arithmetic step of the
+// solver runs in the kernels of kernels_*.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tfeti.h"
+#include "dev.h"
+#include "plan.h"
+
+using namespace tfeti;
+
+struct tfeti_ctx {
+  Plan plan;
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  DevMesh M{};
+  long long l = 0;
+  // tables and maps
+  SubDev* d_subs = nullptr;
+  std::vector<SubDev> h_subs;
+  // state
+  double *u = nullptr, *sig = nullptr, *kap = nullptr;
+  // Newton iterate
+  double *du = nullptr, *df = nullptr, *dsig = nullptr, *dkap = nullptr, *pa = nullptr, *pb = nullptr, *pn = nullptr;
+  uint8_t* plastic = nullptr;
+  int *elem_np = nullptr, *sub_np = nullptr;
+  double* dKe = nullptr;
+  double* band = nullptr;            // template pool followed by the per-subdomain pool
+  long long own_base = 0;            // offset of the per-subdomain pool
+  std::vector<long long> tmpl_off;   // per shape
+  long long* d_kdag_off = nullptr;
+  std::vector<long long> h_kdag_off;
+  int* d_list = nullptr;
+  long long* d_list_off = nullptr;
+  double* ell_val = nullptr;
+  // dual
+  double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
+         *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *dvec = nullptr, *tm = nullptr;
+  double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
+  double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
+  double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;
+  int* d_err = nullptr;
+  int max_copy = 0;
+  // timing
+  bool events = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  cudaEvent_t fac_e0 = nullptr, fac_e1 = nullptr;
+  double f_ms = 0.0, factor_ms = 0.0;
+  long long f_launches = 0, factor_launches = 0, launches = 0;
+  std::vector<int> last_refactored;
+};
+
+namespace {
+
+int fail(tfeti_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(tfeti_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, TFETI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return TFETI_OK;
+}
+
+template <class T>
+T* dalloc(tfeti_ctx* c, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    throw std::bad_alloc();
+  }
+  c->allocs.push_back(p);
+  c->bytes += n * sizeof(T);
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* upload(tfeti_ctx* c, const std::vector<T>& v) {
+  T* d = dalloc<T>(c, v.size());
+  if (!v.empty()) cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st);
+  return d;
+}
+
+void sync(tfeti_ctx* c) { cudaStreamSynchronize(c->st); }
+
+double dot_host(tfeti_ctx* c, const double* x, const double* y, long long n) {
+  launch_dot(x, y, n, c->partial, c->sc + 8, c->st);
+  c->launches += 2;
+  double v = 0.0;
+  cudaMemcpyAsync(&v, c->sc + 8, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  return v;
+}
+
+// ---- dual operators ---------------------------------------------------------
+void op_F(tfeti_ctx* c, const double* x, double* yv) {
+  SolveArgs a{};
+  a.lam = x;
+  a.cbuf = c->cbuf;
+  a.band = c->band;
+  a.kdag_off = c->d_kdag_off;
+  a.in_mode = 0;
+  a.out_mode = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->events && c->ev_used + 2 <= c->ev_pool.size()) {
+    e0 = c->ev_pool[c->ev_used++];
+    e1 = c->ev_pool[c->ev_used++];
+    cudaEventRecord(e0, c->st);
+  }
+  launch_sub_solve(c->M, a, c->plan.max_ndof, c->st);
+  if (e1) cudaEventRecord(e1, c->st);
+  launch_contract(c->M, c->cbuf, yv, c->st);
+  c->launches += 2;
+  c->f_launches += 1;
+}
+
+void op_project(tfeti_ctx* c, const double* x, double* out) {
+  launch_G_apply(c->M, x, nullptr, c->gx, 1.0, c->st);
+  launch_gemv(c->H, c->l, c->gx, 1.0, c->hx, c->st);
+  launch_GT_update(c->M, x, 1.0, c->hx, -1.0, out, c->st);
+  c->launches += 3;
+}
+
+void op_precond(tfeti_ctx* c, const double* x, double* out) {
+  if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
+    launch_lumped(c->M, x, c->ell_val, c->cbuf, c->st, c->max_copy);
+    launch_contract(c->M, c->cbuf, out, c->st);
+    c->launches += 2;
+  } else {
+    cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
+  }
+}
+
+void collect_events(tfeti_ctx* c) {
+  if (!c->events) return;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) c->f_ms += ms;
+  }
+  c->ev_used = 0;
+}
+
+int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
+  const DevMesh& M = c->M;
+  launch_return_map(M, du, c->sig, c->kap, c->dsig, c->dkap, c->plastic, nullptr, c->pa, c->pb, c->pn, c->st);
+  cudaMemsetAsync(c->sub_np, 0, sizeof(int) * M.n_sub, c->st);
+  GPData gd{c->dsig, c->pa, c->pb, c->pn, c->plastic};
+  launch_elem_correction(M, gd, c->elem_np, c->sub_np, c->dKe, c->st);
+  c->launches += 2;
+  std::vector<int> np(M.n_sub);
+  cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  std::vector<int> list;
+  std::vector<long long> offs;
+  for (int p = 0; p < M.n_sub; ++p) {
+    const SubDev& S = c->h_subs[p];
+    if (np[p] > 0) {
+      list.push_back(p);
+      offs.push_back(c->own_base + S.band_off);
+      c->h_kdag_off[p] = c->own_base + S.band_off;
+    } else {
+      c->h_kdag_off[p] = c->tmpl_off[S.shape];
+    }
+  }
+  c->last_refactored.push_back((int)list.size());
+  cudaMemcpyAsync(c->d_kdag_off, c->h_kdag_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
+  if (!list.empty()) {
+    cudaMemcpyAsync(c->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_list_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
+    int max_rows = 0;
+    for (int p : list) max_rows = std::max(max_rows, c->h_subs[p].n_dof);
+    launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band, c->d_list_off, 0, max_rows,
+                     c->plan.max_bw, c->st);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    cudaEvent_t e0 = c->events ? c->fac_e0 : nullptr, e1 = c->events ? c->fac_e1 : nullptr;
+    if (e0) cudaEventRecord(e0, c->st);
+    launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_err, c->plan.max_bw, c->st);
+    if (e1) cudaEventRecord(e1, c->st);
+    c->launches += 2;
+    c->factor_launches += 1;
+    int herr = 0;
+    cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    if (e0) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->factor_ms += ms;
+    }
+    if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a subdomain factorisation");
+  }
+  launch_ell_fill(M, c->elem_np, c->dKe, c->ell_val, c->st);
+  launch_internal_force(M, c->dsig, df, c->f_full, c->st);
+  c->launches += 2;
+  if (f_out && f_out != c->f_full)
+    cudaMemcpyAsync(f_out, c->f_full, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
+  return cuda_check(c, "assemble");
+}
+
+int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0, double rtol,
+             int maxit, tfeti_pcg_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const DevMesh& M = c->M;
+  const long long m = M.n_mult;
+  const long long f_before = c->f_launches;
+  // d = B K^+ f
+  SolveArgs a{};
+  a.src = f;
+  a.cbuf = c->cbuf;
+  a.band = c->band;
+  a.kdag_off = c->d_kdag_off;
+  a.in_mode = 1;
+  a.out_mode = 0;
+  launch_sub_solve(M, a, c->plan.max_ndof, c->st);
+  launch_contract(M, c->cbuf, c->dvec, c->st);
+  // e = -R^T f ; lambda_Im = N^T H e = -B R (H e)
+  launch_G_apply(M, nullptr, f, c->ev, -1.0, c->st);
+  launch_gemv(c->H, c->l, c->ev, 1.0, c->hx, c->st);
+  launch_GT_update(M, nullptr, 0.0, c->hx, -1.0, c->lam_im, c->st);
+  c->launches += 5;
+  // d~ = d - F lambda_Im ; r^0 = d~
+  op_F(c, c->lam_im, c->tm);
+  launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->r, c->st);
+  c->launches += 1;
+  const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
+  cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
+  int used_l0 = 0;
+  if (lambda0) {
+    op_project(c, lambda0, c->lamk);
+    op_F(c, c->lamk, c->tm);
+    launch_axpby(m, 1.0, c->r, -1.0, c->tm, c->r, c->st);
+    c->launches += 1;
+    used_l0 = 1;
+  }
+  int it = 0, converged = 0, status = TFETI_OK;
+  double w_norm = 0.0;
+  if (m > 0 && r0 > 0.0) {
+    for (int j = 1; j <= maxit; ++j) {
+      op_project(c, c->r, c->w);                       // w = P r
+      launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
+      op_precond(c, c->w, c->z);                       // z = F^-1 w
+      op_project(c, c->z, c->y);                       // y = P z
+      launch_dot(c->y, c->w, m, c->partial, c->sc + 0, c->st);
+      c->launches += 4;
+      cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st);
+      cudaEvent_t ready = nullptr;
+      if (j == 1) {
+        sync(c);
+        if (!(c->h_sc[3] > 0.0)) {                     // ||w^0|| = 0: lambda_Ker = o
+          w_norm = std::sqrt(std::max(0.0, c->h_sc[3]));
+          converged = 1;
+          break;
+        }
+      } else {
+        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        cudaEventRecord(ready, c->st);
+      }
+      launch_p_update(m, c->y, c->pdir, c->sc, j == 1, c->st);   // p = y + beta p
+      op_F(c, c->pdir, c->Fp);                                   // F p
+      launch_dot(c->pdir, c->Fp, m, c->partial, c->sc + 2, c->st);
+      launch_lam_r_update(m, c->pdir, c->Fp, c->lamk, c->r, c->sc, c->st);
+      cudaMemcpyAsync(c->sc + 1, c->sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      c->launches += 5;
+      if (ready) {
+        cudaEventSynchronize(ready);
+        cudaEventDestroy(ready);
+      }
+      it = j;
+      const double ww = c->h_sc[3];
+      if (!std::isfinite(ww) || !std::isfinite(c->h_sc[0])) {
+        status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
+        break;
+      }
+      if (c->h_sc[6] != 0.0) {
+        status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+        break;
+      }
+      w_norm = std::sqrt(ww);
+      if (w_norm <= rtol * r0) {
+        converged = 1;
+        break;
+      }
+    }
+  } else {
+    converged = 1;
+  }
+  sync(c);
+  if (status == TFETI_OK) {
+    double flag = 0.0;
+    cudaMemcpy(&flag, c->sc + 6, sizeof(double), cudaMemcpyDeviceToHost);
+    if (flag != 0.0) status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+  }
+  // lambda = lambda_Im + lambda_Ker ; alpha = H N (d - F lambda) ; u = K^+(f - B^T lambda) + R alpha
+  launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
+  op_F(c, c->lam, c->tm);
+  launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->tm, c->st);
+  launch_G_apply(M, c->tm, nullptr, c->gx, -1.0, c->st);
+  launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
+  SolveArgs b{};
+  b.src = f;
+  b.lam = c->lam;
+  b.dst = u_out;
+  b.alpha = c->alpha;
+  b.band = c->band;
+  b.kdag_off = c->d_kdag_off;
+  b.in_mode = 1;
+  b.out_mode = 1;
+  launch_sub_solve(M, b, c->plan.max_ndof, c->st);
+  c->launches += 5;
+  if (lambda_out) cudaMemcpyAsync(lambda_out, c->lam, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemsetAsync(c->sc + 6, 0, sizeof(double), c->st);
+  sync(c);
+  collect_events(c);
+  int cst = cuda_check(c, "tfeti_dual_pcg");
+  if (cst != TFETI_OK) return cst;
+  if (status == TFETI_OK && !converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "PCGP iteration limit reached");
+  if (info) {
+    info->iterations = it;
+    info->converged = converged;
+    info->used_lambda0 = used_l0;
+    info->f_applies = (int)(c->f_launches - f_before) + 2;
+    info->r0_norm = r0;
+    info->w_norm = w_norm;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+void fill_sizes(const tfeti_ctx* c, tfeti_sizes* out) {
+  const Plan& P = c->plan;
+  out->n_sub = (int64_t)P.subs.size();
+  out->n_dof = P.n_dof;
+  out->n_elements = P.n_elem;
+  out->n_gp = P.n_gp;
+  out->n_mult = P.n_mult;
+  out->n_coarse = 6 * (int64_t)P.subs.size();
+  out->n_nodes = P.n_nodes;
+  out->n_copy = P.n_copy;
+  out->max_band = P.max_bw;
+  out->device_bytes = (int64_t)c->bytes;
+}
+
+int setup_impl(tfeti_ctx* c) {
+  Plan& P = c->plan;
+  const int ns = (int)P.subs.size();
+  c->l = 6LL * ns;
+  // subdomain descriptors
+  c->h_subs.resize(ns);
+  for (int p = 0; p < ns; ++p) {
+    const SubInfo& s = P.subs[p];
+    SubDev d{};
+    for (int k = 0; k < 3; ++k) {
+      d.origin[k] = s.origin[k];
+      d.dims[k] = s.dims[k];
+      d.nn[k] = s.nn[k];
+    }
+    d.n_dof = s.n_dof;
+    d.n_elem = s.n_elem;
+    d.bw = s.bw;
+    d.nb = std::min(kMaxNB, s.bw + 1);
+    d.shape = s.shape;
+    d.n_copy = s.n_copy;
+    for (int t = 0; t < 6; ++t) d.fix[t] = s.fix[t];
+    d.dof_off = s.dof_off;
+    d.elem_off = s.elem_off;
+    d.band_off = s.band_off;
+    d.copy_off = s.copy_off;
+    d.r_off = P.shapes[s.shape].r_off;
+    c->h_subs[p] = d;
+    c->max_copy = std::max(c->max_copy, s.n_copy);
+  }
+  c->d_subs = upload(c, c->h_subs);
+  std::vector<GroupDev> gd(P.groups.size());
+  for (size_t g = 0; g < P.groups.size(); ++g) {
+    const Group& s = P.groups[g];
+    GroupDev d{};
+    d.row0 = (int)s.row0;
+    d.k = s.k;
+    d.nrows = s.nrows;
+    d.dirichlet = s.dirichlet;
+    for (int j = 0; j < 8; ++j) {
+      d.slot[j] = j < s.k ? (int)s.slot[j] : 0;
+      d.sub[j] = j < s.k ? s.sub[j] : 0;
+    }
+    gd[g] = d;
+  }
+  std::vector<int> elem_sub(P.n_elem);
+  for (int p = 0; p < ns; ++p)
+    for (int e = 0; e < P.subs[p].n_elem; ++e) elem_sub[P.subs[p].elem_off + e] = p;
+  std::vector<double> helm(64, 0.0);
+  for (int r = 1; r < 8; ++r)
+    for (int j = 0; j <= r; ++j) helm[r * 8 + j] = helmert_coef(r, j);
+  DevMesh& M = c->M;
+  M.subs = c->d_subs;
+  M.n_sub = ns;
+  M.groups = upload(c, gd);
+  M.slot_group = upload(c, P.slot_group);
+  M.slot_j = upload(c, P.slot_j);
+  M.slot_ldof = upload(c, P.slot_ldof);
+  M.slot_sub = upload(c, P.slot_sub);
+  M.row_group = upload(c, P.row_group);
+  M.row_r = upload(c, P.row_r);
+  M.ell_nbr = upload(c, P.ell_nbr);
+  M.elem_sub = upload(c, elem_sub);
+  M.helm = upload(c, helm);
+  double* dN = dalloc<double>(c, 8 * 8 * 3);
+  double* Kel = dalloc<double>(c, 576);
+  double* Q = dalloc<double>(c, 8 * 576);
+  double* R = dalloc<double>(c, P.r_total);
+  M.dN = dN;
+  M.Kel = Kel;
+  M.Q = Q;
+  M.R = R;
+  const tfeti_problem& pr = P.prob;
+  const double lam = pr.young * pr.poisson / ((1.0 + pr.poisson) * (1.0 - 2.0 * pr.poisson));
+  const double mu = pr.young / (2.0 * (1.0 + pr.poisson));
+  M.lam = lam;
+  M.mu = mu;
+  M.sigma_y = pr.sigma_y;
+  M.H = pr.hardening;
+  M.wdet = P.h[0] * P.h[1] * P.h[2] / 8.0;
+  M.n_dof = P.n_dof;
+  M.n_gp = P.n_gp;
+  M.n_mult = P.n_mult;
+  M.n_copy = P.n_copy;
+  M.n_elem = P.n_elem;
+  launch_tables(P.h, lam, mu, dN, Kel, Q, c->st);
+  for (const ShapeInfo& sh : P.shapes) launch_rigid_for_shape(c->h_subs[sh.rep_sub], P.h, R + sh.r_off, c->st);
+  c->launches += 1 + (long long)P.shapes.size();
+  // state and iterate buffers
+  c->u = dalloc<double>(c, P.n_dof);
+  c->sig = dalloc<double>(c, 6 * P.n_gp);
+  c->kap = dalloc<double>(c, P.n_gp);
+  c->du = dalloc<double>(c, P.n_dof);
+  c->df = dalloc<double>(c, P.n_dof);
+  c->dsig = dalloc<double>(c, 6 * P.n_gp);
+  c->dkap = dalloc<double>(c, P.n_gp);
+  c->pa = dalloc<double>(c, P.n_gp);
+  c->pb = dalloc<double>(c, P.n_gp);
+  c->pn = dalloc<double>(c, 6 * P.n_gp);
+  c->plastic = dalloc<uint8_t>(c, P.n_gp);
+  c->elem_np = dalloc<int>(c, P.n_elem);
+  c->sub_np = dalloc<int>(c, ns);
+  c->dKe = dalloc<double>(c, (size_t)P.n_elem * kTri24);
+  c->band = dalloc<double>(c, P.template_band_total + P.band_total);
+  c->own_base = P.template_band_total;
+  c->d_kdag_off = dalloc<long long>(c, ns);
+  c->h_kdag_off.assign(ns, 0);
+  c->d_list = dalloc<int>(c, ns);
+  c->d_list_off = dalloc<long long>(c, ns);
+  c->ell_val = dalloc<double>(c, (size_t)(P.n_copy / 3) * 243);
+  c->cbuf = dalloc<double>(c, P.n_copy);
+  const size_t m = (size_t)P.n_mult;
+  for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->dvec, &c->tm})
+    *v = dalloc<double>(c, m);
+  c->H = dalloc<double>(c, (size_t)c->l * c->l);
+  c->gx = dalloc<double>(c, c->l);
+  c->hx = dalloc<double>(c, c->l);
+  c->ev = dalloc<double>(c, c->l);
+  c->alpha = dalloc<double>(c, c->l);
+  c->f_full = dalloc<double>(c, P.n_dof);
+  c->tn = dalloc<double>(c, P.n_dof);
+  c->tn2 = dalloc<double>(c, P.n_dof);
+  c->partial = dalloc<double>(c, kRedBlocks);
+  c->sc = dalloc<double>(c, 16);
+  c->d_err = dalloc<int>(c, 1);
+  if (cudaMallocHost(&c->h_sc, 16 * sizeof(double)) != cudaSuccess) throw std::bad_alloc();
+  cudaMemsetAsync(c->u, 0, sizeof(double) * P.n_dof, c->st);
+  cudaMemsetAsync(c->sig, 0, sizeof(double) * 6 * P.n_gp, c->st);
+  cudaMemsetAsync(c->kap, 0, sizeof(double) * P.n_gp, c->st);
+  cudaMemsetAsync(c->elem_np, 0, sizeof(int) * P.n_elem, c->st);
+  cudaMemsetAsync(c->sc, 0, sizeof(double) * 16, c->st);
+  // coarse problem: G G^T assembled once and inverted (G depends only on B and R)
+  {
+    int* pp = upload(c, P.pair_p);
+    int* pq = upload(c, P.pair_q);
+    long long* ps = upload(c, std::vector<long long>(P.pair_start.begin(), P.pair_start.end()));
+    int* tg = upload(c, P.trip_group);
+    int* ti = upload(c, P.trip_i);
+    int* tj = upload(c, P.trip_j);
+    launch_coarse_assemble(M, pp, pq, ps, tg, ti, tj, (long long)P.pair_p.size(), c->H, c->l, c->st);
+    double* work = nullptr;
+    if (cudaMalloc(&work, sizeof(double) * dense_inverse_work(c->l)) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    dense_cholesky_inverse(c->H, work, c->l, c->d_err, c->st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    cudaFree(work);
+    if (herr) return fail(c, TFETI_ERR_SINGULAR, "coarse matrix G G^T is not positive definite");
+  }
+  // shared elastic factor per subdomain shape
+  {
+    std::vector<int> reps;
+    std::vector<long long> offs;
+    int max_rows = 0;
+    for (size_t s = 0; s < P.shapes.size(); ++s) {
+      reps.push_back(P.shapes[s].rep_sub);
+      offs.push_back(P.shapes[s].band_off);
+      c->tmpl_off.push_back(P.shapes[s].band_off);
+      max_rows = std::max(max_rows, P.shapes[s].n_dof);
+    }
+    int* dl = upload(c, reps);
+    long long* dof = upload(c, offs);
+    launch_band_fill(M, dl, (int)reps.size(), c->elem_np, c->dKe, c->band, dof, 1, max_rows, P.max_bw, c->st);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    launch_band_chol(M, dl, (int)reps.size(), dof, c->band, c->d_err, P.max_bw, c->st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in an elastic template factorisation");
+    for (int p = 0; p < ns; ++p) c->h_kdag_off[p] = c->tmpl_off[c->h_subs[p].shape];
+    cudaMemcpyAsync(c->d_kdag_off, c->h_kdag_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
+  }
+  launch_ell_fill(M, c->elem_np, c->dKe, c->ell_val, c->st);
+  c->launches += 4;
+  cudaEventCreate(&c->fac_e0);
+  cudaEventCreate(&c->fac_e1);
+  for (int i = 0; i < 8192; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) break;
+    c->ev_pool.push_back(e);
+  }
+  sync(c);
+  return cuda_check(c, "tfeti_setup");
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* tfeti_status_str(int s) {
+  switch (s) {
+    case TFETI_OK: return "ok";
+    case TFETI_ERR_ARG: return "invalid argument";
+    case TFETI_ERR_CUDA: return "CUDA error";
+    case TFETI_ERR_OOM: return "out of memory";
+    case TFETI_ERR_NUMERIC: return "non-positive pivot";
+    case TFETI_ERR_SINGULAR: return "singular coarse problem";
+    case TFETI_ERR_NOT_CONVERGED: return "not converged";
+    case TFETI_ERR_BREAKDOWN: return "PCGP breakdown";
+    case TFETI_ERR_NONFINITE: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+
+const char* tfeti_last_error(const tfeti_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tfeti_setup(const tfeti_problem* prob, void* cuda_stream, tfeti_ctx** out) {
+  if (!out) return TFETI_ERR_ARG;
+  *out = nullptr;
+  tfeti_ctx* c = new (std::nothrow) tfeti_ctx();
+  if (!c) return TFETI_ERR_OOM;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  int st = plan_build(prob, c->plan);
+  if (st == TFETI_OK) {
+    try {
+      st = setup_impl(c);
+    } catch (const std::bad_alloc&) {
+      st = fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+  }
+  if (st != TFETI_OK) {
+    tfeti_destroy(c);
+    return st;
+  }
+  *out = c;
+  return TFETI_OK;
+}
+
+int tfeti_destroy(tfeti_ctx* c) {
+  if (!c) return TFETI_OK;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->fac_e0) cudaEventDestroy(c->fac_e0);
+  if (c->fac_e1) cudaEventDestroy(c->fac_e1);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  delete c;
+  return TFETI_OK;
+}
+
+int tfeti_sizes_get(const tfeti_ctx* c, tfeti_sizes* out) {
+  if (!c || !out) return TFETI_ERR_ARG;
+  fill_sizes(c, out);
+  return TFETI_OK;
+}
+
+int tfeti_traction_load(tfeti_ctx* c, const double* t, double* f_out) {
+  if (!c || !t || !f_out) return fail(c, TFETI_ERR_ARG, "null argument");
+  launch_traction(c->M, c->plan.prob.traction_face, c->plan.prob.nel, t, c->plan.h, f_out, c->st);
+  c->launches += 1;
+  return cuda_check(c, "tfeti_traction_load");
+}
+
+int tfeti_return_map(tfeti_ctx* c, const double* du, double* dsigma, double* dkappa, uint8_t* plastic,
+                     double* Dtan) {
+  if (!c || !du || !dsigma || !dkappa || !plastic) return fail(c, TFETI_ERR_ARG, "null argument");
+  launch_return_map(c->M, du, c->sig, c->kap, dsigma, dkappa, plastic, Dtan, nullptr, nullptr, nullptr, c->st);
+  c->launches += 1;
+  return cuda_check(c, "tfeti_return_map");
+}
+
+int tfeti_assemble_tangent(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
+  if (!c || !du || !df) return fail(c, TFETI_ERR_ARG, "null argument");
+  int st = assemble(c, du, df, f_out);
+  sync(c);
+  return st;
+}
+
+int tfeti_dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0,
+                   double rtol, int32_t maxit, tfeti_pcg_info* info) {
+  if (!c || !f || !u_out || !(rtol >= 0.0) || maxit < 0) return fail(c, TFETI_ERR_ARG, "bad argument");
+  return dual_pcg(c, f, u_out, lambda_out, lambda0, rtol, maxit, info);
+}
+
+int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double newton_tol, double pcg_rtol,
+                  int32_t newton_maxit, int32_t pcg_maxit, tfeti_step_info* info) {
+  if (!c || !df || !(newton_tol >= 0.0) || newton_maxit < 1 || newton_maxit > TFETI_MAX_NEWTON)
+    return fail(c, TFETI_ERR_ARG, "bad argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  const DevMesh& M = c->M;
+  const long long n = M.n_dof;
+  tfeti_step_info loc{};
+  c->last_refactored.clear();
+  cudaMemcpyAsync(c->df, df, sizeof(double) * n, df_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                  c->st);
+  cudaMemsetAsync(c->du, 0, sizeof(double) * n, c->st);
+  int status = TFETI_OK;
+  double nrm_old = 0.0;
+  for (int i = 1; i <= newton_maxit; ++i) {
+    status = assemble(c, c->du, c->df, nullptr);
+    if (status != TFETI_OK) break;
+    std::vector<int> np(M.n_sub);
+    cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
+    tfeti_pcg_info pi{};
+    status = dual_pcg(c, c->f_full, c->tn, nullptr, nullptr, pcg_rtol, pcg_maxit, &pi);
+    if (status != TFETI_OK) break;
+    const double nd = std::sqrt(dot_host(c, c->tn, c->tn, n));
+    launch_axpby(n, 1.0, c->du, 1.0, c->tn, c->du, c->st);
+    c->launches += 1;
+    const double nrm_new = std::sqrt(dot_host(c, c->du, c->du, n));
+    const double den = nrm_new + nrm_old;
+    const double crit = den == 0.0 ? 0.0 : nd / den;
+    nrm_old = nrm_new;
+    long long npl = 0;
+    for (int v : np) npl += v;
+    loc.newton = i;
+    loc.pcg[i - 1] = pi.iterations;
+    loc.plastic[i - 1] = npl;
+    loc.criterion[i - 1] = crit;
+    loc.refactored[i - 1] = c->last_refactored.empty() ? 0 : c->last_refactored.back();
+    if (!std::isfinite(crit)) {
+      status = fail(c, TFETI_ERR_NONFINITE, "non-finite Newton increment");
+      break;
+    }
+    if (crit <= newton_tol) {
+      loc.converged = 1;
+      break;
+    }
+  }
+  if (status == TFETI_OK && !loc.converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "Newton iteration limit");
+  if (status == TFETI_OK) {
+    // commit at the converged increment (Algorithm 1 evaluates T_k at the solution)
+    launch_return_map(M, c->du, c->sig, c->kap, c->dsig, c->dkap, c->plastic, nullptr, nullptr, nullptr, nullptr,
+                      c->st);
+    cudaMemsetAsync(c->sub_np, 0, sizeof(int) * M.n_sub, c->st);
+    GPData gd{c->dsig, c->pa, c->pb, c->pn, c->plastic};
+    launch_elem_correction(M, gd, c->elem_np, c->sub_np, c->dKe, c->st);
+    std::vector<int> np(M.n_sub);
+    cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
+    launch_commit(M, c->du, c->dsig, c->dkap, c->u, c->sig, c->kap, c->st);
+    c->launches += 3;
+    sync(c);
+    for (int v : np) loc.plastic_committed += v;
+  }
+  sync(c);
+  loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  int cst = cuda_check(c, "ssn_time_step");
+  return cst != TFETI_OK ? cst : status;
+}
+
+int tfeti_first_yield_traction(tfeti_ctx* c, const double* dir, double rtol, double* t_y) {
+  if (!c || !dir || !t_y) return fail(c, TFETI_ERR_ARG, "null argument");
+  const long long n = c->M.n_dof;
+  launch_traction(c->M, c->plan.prob.traction_face, c->plan.prob.nel, dir, c->plan.h, c->tn2, c->st);
+  cudaMemsetAsync(c->du, 0, sizeof(double) * n, c->st);
+  int st = assemble(c, c->du, c->tn2, nullptr);
+  if (st != TFETI_OK) return st;
+  st = dual_pcg(c, c->f_full, c->tn, nullptr, nullptr, rtol, 100000, nullptr);
+  if (st != TFETI_OK) return st;
+  launch_return_map(c->M, c->tn, c->sig, c->kap, c->dsig, c->dkap, c->plastic, nullptr, nullptr, nullptr, nullptr,
+                    c->st);
+  launch_vm_max(c->M, c->dsig, c->partial, c->sc + 9, c->st);
+  c->launches += 4;
+  double q = 0.0;
+  cudaMemcpyAsync(&q, c->sc + 9, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  if (!(q > 0.0)) return fail(c, TFETI_ERR_NUMERIC, "zero elastic response");
+  *t_y = c->plan.prob.sigma_y / q;
+  return cuda_check(c, "tfeti_first_yield_traction");
+}
+
+int tfeti_get_state(tfeti_ctx* c, double* u, double* sigma, double* kappa) {
+  if (!c) return TFETI_ERR_ARG;
+  if (u) cudaMemcpyAsync(u, c->u, sizeof(double) * c->M.n_dof, cudaMemcpyDeviceToDevice, c->st);
+  if (sigma) cudaMemcpyAsync(sigma, c->sig, sizeof(double) * 6 * c->M.n_gp, cudaMemcpyDeviceToDevice, c->st);
+  if (kappa) cudaMemcpyAsync(kappa, c->kap, sizeof(double) * c->M.n_gp, cudaMemcpyDeviceToDevice, c->st);
+  sync(c);
+  return cuda_check(c, "tfeti_get_state");
+}
+
+int tfeti_set_state(tfeti_ctx* c, const double* u, const double* sigma, const double* kappa) {
+  if (!c) return TFETI_ERR_ARG;
+  if (u) cudaMemcpyAsync(c->u, u, sizeof(double) * c->M.n_dof, cudaMemcpyDeviceToDevice, c->st);
+  if (sigma) cudaMemcpyAsync(c->sig, sigma, sizeof(double) * 6 * c->M.n_gp, cudaMemcpyDeviceToDevice, c->st);
+  if (kappa) cudaMemcpyAsync(c->kap, kappa, sizeof(double) * c->M.n_gp, cudaMemcpyDeviceToDevice, c->st);
+  sync(c);
+  return cuda_check(c, "tfeti_set_state");
+}
+
+int tfeti_apply_F(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  op_F(c, x, y);
+  sync(c);
+  collect_events(c);
+  return cuda_check(c, "tfeti_apply_F");
+}
+
+int tfeti_apply_projector(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  op_project(c, x, y);
+  sync(c);
+  return cuda_check(c, "tfeti_apply_projector");
+}
+
+int tfeti_apply_precond(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  op_precond(c, x, y);
+  sync(c);
+  return cuda_check(c, "tfeti_apply_precond");
+}
+
+int tfeti_apply_N(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  launch_G_apply(c->M, x, nullptr, y, -1.0, c->st);
+  c->launches += 1;
+  sync(c);
+  return cuda_check(c, "tfeti_apply_N");
+}
+
+int tfeti_apply_kdag(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  SolveArgs a{};
+  a.src = x;
+  a.dst = y;
+  a.band = c->band;
+  a.kdag_off = c->d_kdag_off;
+  a.in_mode = 1;
+  a.out_mode = 1;
+  launch_sub_solve(c->M, a, c->plan.max_ndof, c->st);
+  c->launches += 1;
+  sync(c);
+  return cuda_check(c, "tfeti_apply_kdag");
+}
+
+int tfeti_apply_K(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  launch_apply_K(c->M, c->elem_np, c->dKe, x, y, c->st);
+  c->launches += 1;
+  sync(c);
+  return cuda_check(c, "tfeti_apply_K");
+}
+
+int tfeti_timing_get(tfeti_ctx* c, tfeti_timing* out) {
+  if (!c || !out) return TFETI_ERR_ARG;
+  collect_events(c);
+  out->f_apply_ms_total = c->f_ms;
+  out->f_apply_launches = c->f_launches;
+  double bytes = 0.0, flops = 0.0;
+  for (const SubDev& s : c->h_subs) {
+    bytes += 2.0 * 8.0 * (double)s.n_dof * (s.bw + 1);
+    flops += 2.0 * 2.0 * (double)s.n_dof * (s.bw + 1);
+  }
+  out->f_apply_bytes = bytes;
+  out->f_apply_flops = flops;
+  out->factor_ms_total = c->factor_ms;
+  out->factor_launches = c->factor_launches;
+  out->kernel_launches = c->launches;
+  return TFETI_OK;
+}
+
+int tfeti_timing_reset(tfeti_ctx* c, int32_t enable_events) {
+  if (!c) return TFETI_ERR_ARG;
+  collect_events(c);
+  c->events = enable_events != 0;
+  c->f_ms = c->factor_ms = 0.0;
+  c->f_launches = c->factor_launches = c->launches = 0;
+  return TFETI_OK;
+}
+
+}  // extern "C"

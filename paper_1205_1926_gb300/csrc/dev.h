@@ -1,0 +1,119 @@
+// Device-side data structures and kernel entry points of the TFETI library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tfeti {
+
+constexpr int kMaxNB = 32;     // row block of the banded factor / solves
+constexpr int kTri24 = 300;    // packed lower triangle of a 24x24 element matrix
+
+struct SubDev {
+  int origin[3], dims[3], nn[3];
+  int n_dof, n_elem, bw, nb, shape, n_copy;
+  int fix[6];
+  long long dof_off, elem_off, band_off, copy_off, r_off;
+};
+
+struct GroupDev {
+  int row0, k, nrows, dirichlet;
+  int slot[8];
+  int sub[8];
+};
+
+// Everything a kernel needs to know about the mesh and the decomposition.
+struct DevMesh {
+  const SubDev* subs;
+  int n_sub;
+  const GroupDev* groups;
+  const int* slot_group;
+  const int* slot_j;
+  const int* slot_ldof;
+  const int* slot_sub;
+  const int* row_group;
+  const int* row_r;
+  const int* ell_nbr;
+  const int* elem_sub;     // subdomain of every element
+  const double* R;         // rigid-body bases per shape, [n_dof][6] row-major
+  const double* dN;        // [8 g][8 a][3] physical shape-function gradients
+  const double* Kel;       // [24][24] elastic brick stiffness
+  const double* Q;         // [8 g][24][24] w detJ B_g^T E_eps B_g
+  const double* helm;      // [8 r][8 j] Helmert coefficients (row r = 1..7, copy j)
+  double wdet;
+  double lam, mu, sigma_y, H;
+  long long n_dof, n_gp, n_mult, n_copy, n_elem;
+};
+
+// Per-Newton-iterate Gauss-point data used by the assembly.
+struct GPData {
+  const double* dsig;      // [6][n_gp]
+  const double* pa;        // [n_gp] 2 mu c (1 - rho)  (0 if elastic)
+  const double* pb;        // [n_gp] 2 mu c rho
+  const double* pn;        // [6][n_gp] n-bar
+  const uint8_t* plastic;  // [n_gp]
+};
+
+// ---- launchers (all enqueue on `st`) -------------------------------------
+void launch_tables(const double* h, double lam, double mu, double* dN, double* Kel, double* Q, cudaStream_t st);
+void launch_rigid_for_shape(const SubDev& S, const double* h, double* R_shape, cudaStream_t st);
+void launch_traction(const DevMesh& M, int face, const int* nel, const double* t, const double* h, double* f,
+                     cudaStream_t st);
+void launch_return_map(const DevMesh& M, const double* du, const double* sig_k, const double* kap_k,
+                       double* dsig, double* dkap, uint8_t* plastic, double* Dtan, double* pa, double* pb,
+                       double* pn, cudaStream_t st);
+void launch_elem_correction(const DevMesh& M, GPData gp, int* elem_np, int* sub_np, double* dKe, cudaStream_t st);
+void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const int* elem_np, const double* dKe,
+                      double* band, const long long* band_off_list, int elastic_only, int max_rows, int max_bw,
+                      cudaStream_t st);
+void launch_ell_fill(const DevMesh& M, const int* elem_np, const double* dKe, double* ell_val, cudaStream_t st);
+void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st);
+void launch_apply_K(const DevMesh& M, const int* elem_np, const double* dKe, const double* x, double* y,
+                    cudaStream_t st);
+void launch_commit(const DevMesh& M, const double* du, const double* dsig, const double* dkap, double* u,
+                   double* sig, double* kap, cudaStream_t st);
+void launch_vm_max(const DevMesh& M, const double* dsig, double* partial, double* out, cudaStream_t st);
+
+void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
+                      double* band, int* err, int max_bw, cudaStream_t st);
+
+// Subdomain K^+ solve.  in_mode 0: x = B^T lam at the interface slots (zero
+// elsewhere); 1: x = src - B^T lam (lam nullable).  out_mode 0: interface slots
+// to cbuf; 1: full local vector to dst (+ R alpha if alpha != null).
+struct SolveArgs {
+  const double* lam;
+  const double* src;
+  double* cbuf;
+  double* dst;
+  const double* alpha;
+  const double* band;
+  const long long* kdag_off;   // per subdomain offset into band
+  int in_mode, out_mode;
+};
+void launch_sub_solve(const DevMesh& M, const SolveArgs& a, int max_ndof, cudaStream_t st);
+
+void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream_t st);
+void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,
+                    cudaStream_t st);
+void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
+                      cudaStream_t st);
+void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st);
+void launch_lumped(const DevMesh& M, const double* w, const double* ell_val, double* cbuf, cudaStream_t st,
+                   int max_copy);
+
+// Deterministic reductions and PCG vector updates
+constexpr int kRedBlocks = 304;
+void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st);
+void launch_axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st);
+void launch_p_update(long long n, const double* y, double* p, const double* sc, int first, cudaStream_t st);
+void launch_lam_r_update(long long n, const double* p, const double* Fp, double* lam, double* r, double* sc,
+                         cudaStream_t st);
+
+// Coarse problem
+void launch_coarse_assemble(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
+                            const int* trip_group, const int* trip_i, const int* trip_j, long long n_pairs,
+                            double* A, long long l, cudaStream_t st);
+long long dense_inverse_work(long long l);
+int dense_cholesky_inverse(double* A, double* work, long long l, int* err, cudaStream_t st);
+
+}  // namespace tfeti

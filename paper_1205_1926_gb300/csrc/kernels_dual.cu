@@ -1,0 +1,439 @@
+// Dual-space kernels of Algorithm 3: B (copy slots -> multipliers), the
+// coarse operators G = R^T B^T and G^T, the projector pieces, the lumped
+// preconditioner B K B^T, deterministic reductions and the PCGP updates, and
+// the one-time coarse set-up (G G^T assembly, dense Cholesky, explicit inverse).
+#include "dev.h"
+#include "dual_common.cuh"
+
+namespace tfeti {
+
+namespace {
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// y[row] = (B v)[row]
+__global__ void k_contract(DevMesh M, const double* __restrict__ v, double* y) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row < M.n_mult) y[row] = b_at_row(M, v, row);
+}
+
+__device__ double block_reduce_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;   // valid in thread 0
+}
+
+// gx[6p+c] = scale * (R_p^T (B^T x))_c over the interface slots of p (x_lam), or
+// scale * (R_p^T x_p)_c over all dofs of p (x_full).  One CTA per subdomain.
+__global__ void k_G_apply(DevMesh M, const double* __restrict__ x_lam, const double* __restrict__ x_full,
+                          double* gx, double scale) {
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  const SubDev S = M.subs[p];
+  const double* R = M.R + S.r_off;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (x_lam) {
+    for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) {
+      const long long slot = S.copy_off + s;
+      const double v = bt_at_slot(M, x_lam, slot);
+      const double* r = R + (long long)M.slot_ldof[slot] * 6;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
+    }
+  } else {
+    for (int i = threadIdx.x; i < S.n_dof; i += blockDim.x) {
+      const double v = x_full[S.dof_off + i];
+      const double* r = R + (long long)i * 6;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double s = block_reduce_sum(acc[c], red);
+    if (threadIdx.x == 0) gx[6 * (long long)p + c] = scale * s;
+  }
+}
+
+// out[row] = ax * x[row] + bh * (B R h)[row]   (x nullable)
+__global__ void k_GT_update(DevMesh M, const double* __restrict__ x, double ax, const double* __restrict__ h,
+                            double bh, double* out) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row >= M.n_mult) return;
+  const GroupDev& g = M.groups[M.row_group[row]];
+  const int rr = M.row_r[row];
+  double s = 0.0;
+  const int j0 = g.dirichlet ? rr : 0, j1 = g.dirichlet ? rr : rr + 1;
+  for (int j = j0; j <= j1; ++j) {
+    const long long slot = g.slot[j];
+    const int q = g.sub[j];
+    const double* r = M.R + M.subs[q].r_off + (long long)M.slot_ldof[slot] * 6;
+    const double* hq = h + 6 * (long long)q;
+    double rh = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) rh += r[c] * hq[c];
+    s += (g.dirichlet ? 1.0 : M.helm[(rr + 1) * 8 + j]) * rh;
+  }
+  out[row] = (x ? ax * x[row] : 0.0) + bh * s;
+}
+
+// y = alpha * A x, A dense n x n row-major; one warp per row.
+__global__ void k_gemv(const double* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
+                       double* y) {
+  const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = A + row * n;
+  double s = 0.0;
+  for (long long j = lane; j < n; j += 32) s += a[j] * x[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = alpha * s;
+}
+
+// Lumped preconditioner, subdomain part: v = K_bb (B^T w) on the interface slots.
+__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* __restrict__ ell_val, double* cbuf) {
+  extern __shared__ double xs[];
+  const int p = blockIdx.x;
+  const SubDev S = M.subs[p];
+  for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = bt_at_slot(M, w, S.copy_off + s);
+  __syncthreads();
+  const long long in0 = S.copy_off / 3;
+  const int n_in = S.n_copy / 3;
+  for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
+    const int inode = q / 3, a = q % 3;
+    const long long gi = in0 + inode;
+    double s = 0.0;
+    for (int t = 0; t < 27; ++t) {
+      const int nb = M.ell_nbr[gi * 27 + t];
+      if (nb < 0) continue;
+      const int lb = (int)(nb - S.copy_off);
+      const double* kv = ell_val + (gi * 27 + t) * 9 + a * 3;
+      s += kv[0] * xs[lb] + kv[1] * xs[lb + 1] + kv[2] * xs[lb + 2];
+    }
+    cbuf[S.copy_off + q] = s;
+  }
+  (void)n_in;
+}
+
+// Deterministic dot product: fixed grid, fixed per-block order, fixed final order.
+__global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                              double* partial) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  s = block_reduce_sum(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_dot_final(const double* partial, int nparts, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+  s = block_reduce_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (x ? a * x[i] : 0.0) + (y ? b * y[i] : 0.0);
+}
+
+// Scalars: sc[0] = y.w (current), sc[1] = y.w (previous), sc[2] = p.Fp, sc[3] = w.w,
+// sc[4] = beta, sc[5] = gamma, sc[6] = breakdown flag.
+__global__ void k_p_update(long long n, const double* __restrict__ y, double* p, const double* sc, int first) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double beta = first ? 0.0 : sc[0] / sc[1];
+  p[i] = first ? y[i] : y[i] + beta * p[i];
+}
+
+__global__ void k_lam_r_update(long long n, const double* __restrict__ p, const double* __restrict__ Fp, double* lam,
+                               double* r, const double* sc) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gamma = sc[0] / sc[2];
+  lam[i] += gamma * p[i];
+  r[i] -= gamma * Fp[i];
+}
+
+__global__ void k_scalars_after_pfp(double* sc) {
+  if (threadIdx.x == 0) {
+    sc[5] = sc[0] / sc[2];
+    if (!(sc[2] > 0.0)) sc[6] = 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse matrix G G^T = R^T B^T B R assembled per subdomain pair (p >= q):
+// block[a][b] = sum over groups with copies i in p and j in q of
+// R_p[slot_i][a] (sum_rows B[row][i] B[row][j]) R_q[slot_j][b].
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_assemble(DevMesh M, const int* __restrict__ pair_p, const int* __restrict__ pair_q,
+                                  const long long* __restrict__ pair_start, const int* __restrict__ trip_group,
+                                  const int* __restrict__ trip_i, const int* __restrict__ trip_j, long long n_pairs,
+                                  double* A, long long l) {
+  const long long pr = blockIdx.x;
+  if (pr >= n_pairs) return;
+  const int e = threadIdx.x;
+  if (e >= 36) return;
+  const int a = e / 6, b = e % 6;
+  const int p = pair_p[pr], q = pair_q[pr];
+  const double* Rp = M.R + M.subs[p].r_off;
+  const double* Rq = M.R + M.subs[q].r_off;
+  double s = 0.0;
+  for (long long t = pair_start[pr]; t < pair_start[pr + 1]; ++t) {
+    const GroupDev& g = M.groups[trip_group[t]];
+    const int i = trip_i[t], j = trip_j[t];
+    double m;
+    if (g.dirichlet) {
+      m = (i == j) ? 1.0 : 0.0;
+    } else {
+      m = 0.0;
+      for (int r = 1; r < g.k; ++r) m += M.helm[r * 8 + i] * M.helm[r * 8 + j];
+    }
+    s += Rp[(long long)M.slot_ldof[g.slot[i]] * 6 + a] * m * Rq[(long long)M.slot_ldof[g.slot[j]] * 6 + b];
+  }
+  A[(6LL * p + a) * l + 6LL * q + b] = s;
+  if (p != q) A[(6LL * q + b) * l + 6LL * p + a] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Dense FP64 building blocks for the coarse problem (set-up only).
+// ---------------------------------------------------------------------------
+constexpr int kD = 32;
+
+// Factor the kD x kD diagonal block at (k0,k0) of A in place (lower) and write
+// its inverse to Dinv (kD x kD).  One warp.
+__global__ void k_dense_diag(double* A, long long l, long long k0, int jb, double* Dinv, int* err) {
+  __shared__ double D[kD][kD + 1];
+  __shared__ double X[kD][kD + 1];
+  const int lane = threadIdx.x;
+  for (int r = 0; r < jb; ++r)
+    if (lane < jb) D[r][lane] = lane <= r ? A[(k0 + r) * l + k0 + lane] : 0.0;
+  __syncwarp();
+  for (int c = 0; c < jb; ++c) {
+    double d = D[c][c];
+    if (!(d > 0.0)) {
+      if (lane == 0) atomicOr(err, 1);
+      d = 1.0;
+    }
+    d = sqrt(d);
+    const double inv = 1.0 / d;
+    __syncwarp();
+    if (lane == c) D[c][c] = d;
+    if (lane > c && lane < jb) D[lane][c] *= inv;
+    __syncwarp();
+    if (lane > c && lane < jb) {
+      const double lrc = D[lane][c];
+      for (int s = c + 1; s <= lane; ++s) D[lane][s] -= lrc * D[s][c];
+    }
+    __syncwarp();
+  }
+  if (lane < jb) {
+    const int s = lane;
+    for (int r = 0; r < jb; ++r) {
+      if (r < s) {
+        X[r][s] = 0.0;
+      } else {
+        double acc = (r == s) ? 1.0 : 0.0;
+        for (int t = s; t < r; ++t) acc -= D[r][t] * X[t][s];
+        X[r][s] = acc / D[r][r];
+      }
+    }
+  }
+  __syncwarp();
+  for (int r = 0; r < jb; ++r)
+    if (lane < jb) {
+      A[(k0 + r) * l + k0 + lane] = lane <= r ? D[r][lane] : 0.0;
+      Dinv[r * kD + lane] = X[r][lane];
+    }
+}
+
+// Panel: A[i][k0+c] <- sum_{s<=c} A[i][k0+s] Dinv[c][s] for rows i >= k0+jb.  One warp per row.
+__global__ void k_dense_panel(double* A, long long l, long long k0, int jb, const double* Dinv) {
+  const long long i = k0 + jb + blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= l) return;
+  double* row = A + i * l + k0;
+  double val = 0.0;
+  if (lane < jb)
+    for (int s = 0; s <= lane; ++s) val += row[s] * Dinv[lane * kD + s];
+  __syncwarp();
+  if (lane < jb) row[lane] = val;
+}
+
+// Generic tiled FP64 GEMM: C[i][j] = beta C[i][j] + alpha sum_t A(i,t) B(t,j),
+// A(i,t) = A[i*sai + t*sat], B(t,j) = B[t*sbt + j*sbj], t in [k_lo, k_hi).
+// lower_only: skip tiles strictly above the diagonal and entries j > i.
+// ktri: start t at max(tile row, tile col) (for Y^T Y with Y lower-triangular).
+constexpr int TM = 64, TN = 64, TK = 16;
+__global__ void __launch_bounds__(256) k_dgemm(long long Mr, long long Nc, long long k_lo, long long k_hi,
+                                               double alpha, const double* __restrict__ A, long long sai,
+                                               long long sat, const double* __restrict__ B, long long sbt,
+                                               long long sbj, double beta, double* C, long long ldc, int lower_only,
+                                               int ktri) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const long long i0 = blockIdx.y * (long long)TM, j0 = blockIdx.x * (long long)TN;
+  if (lower_only && j0 > i0 + TM - 1) return;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  long long kbeg = k_lo;
+  if (ktri) kbeg = i0 > j0 ? (i0 > k_lo ? i0 : k_lo) : (j0 > k_lo ? j0 : k_lo);
+  for (long long kt = kbeg; kt < k_hi; kt += TK) {
+    for (int e = threadIdx.x; e < TK * TM; e += 256) {
+      const int kk = e / TM, ii = e % TM;
+      const long long gi = i0 + ii, gk = kt + kk;
+      As[kk][ii] = (gi < Mr && gk < k_hi) ? A[gi * sai + gk * sat] : 0.0;
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      const int kk = e / TN, jj = e % TN;
+      const long long gj = j0 + jj, gk = kt + kk;
+      Bs[kk][jj] = (gj < Nc && gk < k_hi) ? B[gk * sbt + gj * sbj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty * 4 + u];
+        b[u] = Bs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const long long gi = i0 + ty * 4 + u, gj = j0 + tx * 4 + v;
+      if (gi < Mr && gj < Nc && (!lower_only || gj <= gi)) {
+        double* c = C + gi * ldc + gj;
+        *c = (beta == 0.0 ? 0.0 : beta * *c) + alpha * acc[u][v];
+      }
+    }
+}
+
+void dgemm(long long Mr, long long Nc, long long k_lo, long long k_hi, double alpha, const double* A, long long sai,
+           long long sat, const double* B, long long sbt, long long sbj, double beta, double* C, long long ldc,
+           int lower_only, int ktri, cudaStream_t st) {
+  if (Mr <= 0 || Nc <= 0) return;
+  dim3 grid((unsigned)((Nc + TN - 1) / TN), (unsigned)((Mr + TM - 1) / TM));
+  k_dgemm<<<grid, 256, 0, st>>>(Mr, Nc, k_lo, k_hi, alpha, A, sai, sat, B, sbt, sbj, beta, C, ldc, lower_only, ktri);
+}
+
+}  // namespace
+
+void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream_t st) {
+  if (M.n_mult > 0) k_contract<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, cbuf, y);
+}
+
+void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,
+                    cudaStream_t st) {
+  k_G_apply<<<M.n_sub, 256, 0, st>>>(M, x_lam, x_full, gx, scale);
+}
+
+void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
+                      cudaStream_t st) {
+  if (M.n_mult > 0) k_GT_update<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, x, ax, h, bh, out);
+}
+
+void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
+  k_gemv<<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+}
+
+void launch_lumped(const DevMesh& M, const double* w, const double* ell_val, double* cbuf, cudaStream_t st,
+                   int max_copy) {
+  const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
+  cudaFuncSetAttribute(k_lumped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_lumped<<<M.n_sub, 256, smem, st>>>(M, w, ell_val, cbuf);
+}
+
+void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st) {
+  k_dot_partial<<<kRedBlocks, 256, 0, st>>>(x, y, n, partial);
+  k_dot_final<<<1, 256, 0, st>>>(partial, kRedBlocks, out);
+}
+
+void launch_axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st) {
+  if (n > 0) k_axpby<<<blocks_for(n, 256), 256, 0, st>>>(n, a, x, b, y, out);
+}
+
+void launch_p_update(long long n, const double* y, double* p, const double* sc, int first, cudaStream_t st) {
+  if (n > 0) k_p_update<<<blocks_for(n, 256), 256, 0, st>>>(n, y, p, sc, first);
+}
+
+void launch_lam_r_update(long long n, const double* p, const double* Fp, double* lam, double* r, double* sc,
+                         cudaStream_t st) {
+  k_scalars_after_pfp<<<1, 32, 0, st>>>(sc);
+  if (n > 0) k_lam_r_update<<<blocks_for(n, 256), 256, 0, st>>>(n, p, Fp, lam, r, sc);
+}
+
+void launch_coarse_assemble(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
+                            const int* trip_group, const int* trip_i, const int* trip_j, long long n_pairs,
+                            double* A, long long l, cudaStream_t st) {
+  cudaMemsetAsync(A, 0, sizeof(double) * l * l, st);
+  if (n_pairs > 0)
+    k_coarse_assemble<<<(unsigned)n_pairs, 64, 0, st>>>(M, pair_p, pair_q, pair_start, trip_group, trip_i, trip_j,
+                                                         n_pairs, A, l);
+}
+
+// In place: A (l x l, symmetric positive definite) -> H = A^{-1}.
+// work needs dense_inverse_work(l) doubles.  Blocked Cholesky A = L L^T with
+// the inverse of every diagonal block kept, then Y = L^{-1} by block forward
+// substitution and H = Y^T Y.  A non-positive pivot sets *err (device).
+long long dense_inverse_work(long long l) {
+  const long long nblk = (l + kD - 1) / kD;
+  return l * l + nblk * kD * kD + kD * l;
+}
+
+int dense_cholesky_inverse(double* A, double* work, long long l, int* err, cudaStream_t st) {
+  const long long nblk = (l + kD - 1) / kD;
+  double* Y = work;                        // l x l
+  double* Dall = work + l * l;             // nblk x kD x kD
+  double* T = Dall + nblk * kD * kD;       // kD x l
+  for (long long b = 0; b < nblk; ++b) {
+    const long long k0 = b * kD;
+    const int jb = (int)((l - k0) < kD ? (l - k0) : kD);
+    double* Dinv = Dall + b * kD * kD;
+    k_dense_diag<<<1, 32, 0, st>>>(A, l, k0, jb, Dinv, err);
+    const long long rest = l - k0 - jb;
+    if (rest > 0) {
+      k_dense_panel<<<blocks_for(rest, 8), 256, 0, st>>>(A, l, k0, jb, Dinv);
+      dgemm(rest, rest, 0, jb, -1.0, A + (k0 + jb) * l + k0, l, 1, A + (k0 + jb) * l + k0, 1, l, 1.0,
+            A + (k0 + jb) * l + (k0 + jb), l, 1, 0, st);
+    }
+  }
+  cudaMemsetAsync(Y, 0, sizeof(double) * l * l, st);
+  for (long long b = 0; b < nblk; ++b) {
+    const long long k0 = b * kD;
+    const int jb = (int)((l - k0) < kD ? (l - k0) : kD);
+    const double* Dinv = Dall + b * kD * kD;
+    if (k0 > 0) {
+      // T = -L[b, 0:k0] Y[0:k0, 0:k0];  Y[b, 0:k0] = Dinv_b T
+      dgemm(jb, k0, 0, k0, -1.0, A + k0 * l, l, 1, Y, l, 1, 0.0, T, l, 0, 0, st);
+      dgemm(jb, k0, 0, jb, 1.0, Dinv, kD, 1, T, l, 1, 0.0, Y + k0 * l, l, 0, 0, st);
+    }
+    // Y[b, k0:k0+jb] = Dinv_b (lower triangle; upper part of Dinv is zero)
+    cudaMemcpy2DAsync(Y + k0 * l + k0, sizeof(double) * l, Dinv, sizeof(double) * kD, sizeof(double) * jb, jb,
+                      cudaMemcpyDeviceToDevice, st);
+  }
+  // H = Y^T Y
+  dgemm(l, l, 0, l, 1.0, Y, 1, l, Y, l, 1, 0.0, A, l, 0, 1, st);
+  return 0;
+}
+
+}  // namespace tfeti

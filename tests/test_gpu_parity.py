@@ -1,0 +1,309 @@
+"""GPU parity: every C-ABI call of the CUDA path against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the CUDA path computes in FP64 like the oracle, so pointwise
+quantities (stress increments, tangents, internal forces, operator applies)
+agree to rounding, checked at 1e-11 relative to the array's scale; solutions of
+the dual problem at eps_PCGP = 1e-12 agree to <= 1e-9 relative (the bound the
+method's parity target states).  Plastic flags are integer decisions taken in
+FP64 on both sides and must agree exactly except for points within
+|Phi| <= 1e-8 (sigma_y + H kappa) of the yield surface, where the branch is
+decided by rounding.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.decomp import FixingNodeInverse
+from oracle.ssn import ElastoplasticModel, run_load_history
+from oracle.fem import element_strain_matrices, gauss_weight_detj, NODE_OFFSETS
+from oracle.material import Material
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines only
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1205_1926_gb300 as T  # noqa: E402
+
+ONE_ELEMENT_BOXES = W.Workload(name="boxes_of_one", nel=(2, 2, 2), cuts=((0, 1, 2), (0, 1, 2), (0, 1, 2)))
+
+
+def dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    return t.to(device="cuda", dtype=dtype or t.dtype)
+
+
+def zeros(n, dtype=torch.float64):
+    return torch.zeros(int(n), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def plastic_state(w, seed):
+    m = ElastoplasticModel(w)
+    sig, kap, _ = W.seeded_gauss_point_inputs(m.dec.n_gp, seed=seed, scale_stress=100.0)
+    du = W.seeded_vector(m.dec.n_dof, seed=seed + 1) * 1e-3 * min(m.grid.h)
+    return m, sig, kap, du
+
+
+def set_oracle_state(ctx, sig, kap):
+    ctx.set_state(sigma=dev(sig.T.copy()), kappa=dev(kap))
+
+
+def yield_band(m, sig, kap, eta):
+    phi = m.mat.yield_function(m.mat.trial(sig, eta), kap)
+    return np.abs(phi) <= 1e-8 * (m.mat.sigma_y + m.mat.H * kap)
+
+
+# ---------------------------------------------------------------------------- return map
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
+def test_return_map_parity(w):
+    m, sig, kap, du = plastic_state(w, seed=11)
+    ctx = T.Context(w)
+    n_gp = ctx.sizes["n_gp"]
+    set_oracle_state(ctx, sig, kap)
+    ds, dk, pl, D = zeros(6 * n_gp), zeros(n_gp), zeros(n_gp, torch.uint8), zeros(21 * n_gp)
+    ctx.return_map(dev(du), ds, dk, pl, D)
+    m.sigma, m.kappa = sig, kap
+    ods, odk, opl, eta = m.return_map(du)
+    oD = m.mat.tangent(sig, kap, eta)
+    gpl = host(pl).astype(bool)
+    band = yield_band(m, sig, kap, eta)
+    assert 0.1 < opl.mean() < 0.9
+    np.testing.assert_array_equal(gpl[~band], opl[~band])
+    agree = gpl == opl
+    gds = host(ds).reshape(6, n_gp).T
+    assert np.abs(gds[agree] - ods[agree]).max() <= 1e-11 * np.abs(ods).max()
+    assert np.abs(host(dk)[agree] - odk[agree]).max() <= 1e-11 * max(np.abs(odk).max(), 1e-30)
+    iu = np.triu_indices(6)
+    gD = host(D).reshape(21, n_gp).T
+    assert np.abs(gD[agree] - oD[agree][:, iu[0], iu[1]]).max() <= 1e-11 * np.abs(oD).max()
+
+
+# ---------------------------------------------------------------------------- assembly, K, K^+
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, ONE_ELEMENT_BOXES])
+def test_assembly_internal_force_and_operators(w):
+    m, sig, kap, du = plastic_state(w, seed=21)
+    ctx = T.Context(w)
+    n = ctx.sizes["n_dof"]
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((10.0, -3.0, 5.0))
+    f = zeros(n)
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, st = m.assemble(du, df)
+    assert np.abs(host(f) - f_or).max() <= 1e-11 * np.abs(f_or).max()
+    x = W.seeded_vector(n, seed=22)
+    y = zeros(n)
+    ctx.apply("K", dev(x), y)
+    import scipy.sparse as sp
+    Kx = sp.block_diag(Kb) @ x
+    assert np.abs(host(y) - Kx).max() <= 1e-11 * np.abs(Kx).max()
+    ctx.apply("kdag", dev(x), y)
+    kd = np.concatenate([FixingNodeInverse(K, s.fixing_dofs()).apply(x[m.dec.dof_off[p]:m.dec.dof_off[p + 1]])
+                         for p, (K, s) in enumerate(zip(Kb, m.dec.subs))])
+    assert rel(host(y), kd) <= 1e-10
+
+
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
+def test_dual_operators_F_projector_precond_N(w):
+    m, sig, kap, du = plastic_state(w, seed=31)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    ctx.assemble_tangent(dev(du), dev(np.zeros(s["n_dof"])))
+    m.sigma, m.kappa = sig, kap
+    Kb, _, _ = m.assemble(du, np.zeros(m.dec.n_dof))
+    solver = m.tfeti(Kb)
+    lam = W.seeded_vector(s["n_mult"], seed=32)
+    out = zeros(s["n_mult"])
+    ctx.apply("F", dev(lam), out)
+    assert rel(host(out), solver.apply_F(lam)) <= 1e-10
+    ctx.apply("projector", dev(lam), out)
+    assert rel(host(out), solver.project(lam)) <= 1e-11
+    ctx.apply("precond", dev(lam), out)
+    assert rel(host(out), solver.apply_precond(lam)) <= 1e-11
+    outl = zeros(s["n_coarse"])
+    ctx.apply("N", dev(lam), outl)
+    assert rel(host(outl), solver.N @ lam) <= 1e-11
+
+
+# ---------------------------------------------------------------------------- Algorithm 3
+@pytest.mark.parametrize("w", [W.TINY_1x1x2, ONE_ELEMENT_BOXES, W.SMALL6_RAGGED, W.CUBE12])
+def test_dual_pcg_parity(w):
+    m, sig, kap, du = plastic_state(w, seed=41)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((20.0, 5.0, -8.0))
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+    info = ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, _ = m.assemble(du, df)
+    sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+    assert rel(host(u), sol["u"]) <= 1e-9
+    assert rel(host(lam), sol["lam"]) <= 1e-9
+    assert abs(info["iterations"] - sol["iterations"]) <= 1
+    # determinism: a second solve is bitwise identical
+    u2 = zeros(s["n_dof"])
+    ctx.dual_pcg(f, u2, rtol=1e-12, maxit=5000)
+    assert torch.equal(u, u2)
+
+
+def test_dual_pcg_zero_rhs_and_iteration_limit():
+    w = W.SMALL4
+    ctx = T.Context(w)
+    s = ctx.sizes
+    u = zeros(s["n_dof"])
+    info = ctx.dual_pcg(zeros(s["n_dof"]), u, rtol=1e-8)
+    assert info["iterations"] == 0 and not host(u).any()
+    f = zeros(s["n_dof"])
+    ctx.traction_load((1.0, 0.0, 0.0), f)
+    info = ctx.dual_pcg(f, u, rtol=1e-14, maxit=2, check=False)
+    assert info["status"] == 6 and info["iterations"] == 2
+
+
+# ---------------------------------------------------------------------------- Algorithm 4 end to end
+def gpu_history(w, n_steps, t_y=None):
+    ctx = T.Context(w)
+    if t_y is None:
+        t_y = ctx.first_yield_traction(w.traction_dir)
+    infos, us = [], []
+    prev = 0.0
+    df = zeros(ctx.sizes["n_dof"])
+    u = zeros(ctx.sizes["n_dof"])
+    for a in w.load_fractions(n_steps):
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        prev = a
+        infos.append(ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+        ctx.get_state(u=u)
+        us.append(host(u).copy())
+    return ctx, infos, us, t_y
+
+
+def test_first_yield_traction_parity():
+    w = W.CUBE12
+    ctx = T.Context(w)
+    t_gpu = ctx.first_yield_traction(w.traction_dir)
+    t_or = ElastoplasticModel(w).first_yield_traction()
+    assert abs(t_gpu - t_or) <= 1e-10 * t_or
+
+
+def test_ssn_load_history_cube12_parity():
+    w = W.CUBE12                      # 12^3 bricks, 2x2x2 boxes, 10 steps to 1.5 t_y; (1e-10, 1e-12)
+    ctx, infos, us, t_y = gpu_history(w, w.n_steps)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    assert abs(t_y - t_or) <= 1e-10 * t_or
+    f1 = model.traction_load(w.traction_dir)
+    prev = 0.0
+    for k, a in enumerate(w.load_fractions()):
+        info = model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        assert infos[k]["converged"] and info["converged"]
+        assert rel(us[k], model.u) <= 1e-9, (k, rel(us[k], model.u))
+        assert abs(infos[k]["newton"] - info["newton"]) <= 1
+        assert infos[k]["criterion"][0] == 1.0
+    n_gp = ctx.sizes["n_gp"]
+    sig, kap = zeros(6 * n_gp), zeros(n_gp)
+    ctx.get_state(sigma=sig, kappa=kap)
+    gk = host(kap)
+    assert (model.kappa > 0).sum() > 0
+    assert np.array_equal(gk > 0, model.kappa > 0) or \
+        np.sum((gk > 0) != (model.kappa > 0)) <= 1e-3 * n_gp
+    assert np.abs(host(sig).reshape(6, n_gp).T - model.sigma).max() <= 1e-7 * np.abs(model.sigma).max()
+
+
+def test_checkpoint_resume_bitwise():
+    w = W.SMALL6_RAGGED.with_(newton_tol=1e-9, pcg_rtol=1e-11)
+    ctx_a, _, us_a, t_y = gpu_history(w, 4)
+    ctx_b, _, _, _ = gpu_history(w, 2, t_y=t_y)
+    n, n_gp = ctx_b.sizes["n_dof"], ctx_b.sizes["n_gp"]
+    u, sig, kap = zeros(n), zeros(6 * n_gp), zeros(n_gp)
+    ctx_b.get_state(u, sig, kap)
+    ctx_c = T.Context(w)
+    ctx_c.set_state(u, sig, kap)
+    df = zeros(n)
+    prev = w.load_fractions(2)[-1]
+    for a in w.load_fractions(4)[2:]:
+        ctx_c.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        prev = a
+        ctx_c.time_step(df, w.newton_tol, w.pcg_rtol)
+    ctx_c.get_state(u=u)
+    assert np.array_equal(host(u), us_a[-1])
+
+
+def test_zero_load_step_converges_immediately():
+    w = W.SMALL4
+    ctx = T.Context(w)
+    info = ctx.time_step(zeros(ctx.sizes["n_dof"]), 1e-10, 1e-12)
+    assert info["converged"] and info["newton"] == 1 and info["criterion"][0] == 0.0
+
+
+# ---------------------------------------------------------------------------- full size, timed launch config
+def test_cube64_full_size_properties():
+    """64^3 bricks in 512 boxes (the timed workload): one plastic load step through the same
+    calls bench.py times; sampled Gauss points and nodes checked against the oracle one by one."""
+    w = W.CUBE64
+    ctx = T.Context(w)
+    s = ctx.sizes
+    t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
+    df = zeros(s["n_dof"])
+    ctx.traction_load(tuple(1.5 * t_y * c for c in w.traction_dir), df)
+    info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+    assert info["converged"] and info["plastic_committed"] > 0 and info["criterion"][0] == 1.0
+    n_gp = s["n_gp"]
+    u, sig, kap = zeros(s["n_dof"]), zeros(6 * n_gp), zeros(n_gp)
+    ctx.get_state(u, sig, kap)
+    u, sig, kap = host(u), host(sig).reshape(6, n_gp).T, host(kap)
+    plan = T.Plan(w)
+    subs = plan.export_subdomains()
+    mat = Material.from_dict(w.material)
+    h = tuple(1.0 / n for n in w.nel)
+    Bg = element_strain_matrices(h)
+    rng = np.random.default_rng(5)
+    # (1) return map at sampled elements from the zero state: sigma = T_0(eta(u))
+    for p in rng.choice(len(subs), 12, replace=False):
+        ox, oy, oz, ax, ay, az, doff, eoff, _ = subs[p]
+        for le in rng.choice(ax * ay * az, 4, replace=False):
+            ex, ey, ez = le % ax, (le // ax) % ay, le // (ax * ay)
+            ln = [(ex + o[0]) + (ax + 1) * ((ey + o[1]) + (ay + 1) * (ez + o[2])) for o in NODE_OFFSETS]
+            ue = np.concatenate([u[doff + 3 * a: doff + 3 * a + 3] for a in ln])
+            eta = Bg @ ue
+            ds, dk, pl = mat.stress_increment(np.zeros((8, 6)), np.zeros(8), eta)
+            gp = 8 * (eoff + le) + np.arange(8)
+            assert np.abs(sig[gp] - ds).max() <= 1e-9 * mat.sigma_y
+            np.testing.assert_allclose(kap[gp], dk, rtol=1e-8, atol=1e-15)
+    # (2) continuity: copies of shared nodes agree (B u = 0 up to the solver tolerance)
+    rows, cols, vals = plan.export_B()
+    import scipy.sparse as sps
+    Bu = sps.csr_matrix((vals, (rows, cols)), shape=(s["n_mult"], s["n_dof"])) @ u
+    assert np.linalg.norm(Bu) <= 1e-6 * np.linalg.norm(u)
+    # (3) equilibrium at sampled interior global nodes: the element forces of the committed
+    #     stresses cancel (no load inside the body)
+    wdet = gauss_weight_detj(h)
+    n = w.nel[0]
+    for _ in range(10):
+        i, j, k = rng.integers(1, n, size=3)
+        force, scale = np.zeros(3), 0.0
+        for a, o in enumerate(NODE_OFFSETS):
+            ex, ey, ez = i - o[0], j - o[1], k - o[2]
+            p = (ex // 8) + 8 * ((ey // 8) + 8 * (ez // 8))
+            ox, oy, oz, ax, ay, az, doff, eoff, _ = subs[p]
+            le = (ex - ox) + ax * ((ey - oy) + ay * (ez - oz))
+            gp = 8 * (eoff + le) + np.arange(8)
+            for c in range(3):
+                contrib = wdet * np.einsum("gi,gi->g", Bg[:, :, 3 * a + c], sig[gp])
+                force[c] += contrib.sum()
+                scale += np.abs(contrib).sum()
+        assert np.abs(force).max() <= 1e-6 * scale
