@@ -230,6 +230,27 @@ int tfeti_apply_kdag(tfeti_ctx* ctx, const double* x, double* y);
 /* y = K x per subdomain (the assembled tangent, fixing dofs untouched); device [n_dof]. */
 int tfeti_apply_K(tfeti_ctx* ctx, const double* x, double* y);
 
+/* ---- projector without device allocation ------------------------------------ */
+/* The paper has no counterpart to this call.  It is a deployment variant of
+ * tfeti_apply_projector for callers that cannot call cudaMalloc when they apply
+ * the operator: their device memory is owned by another allocator (a caching
+ * pool sized to the whole GPU), or their policy forbids allocation after
+ * start-up.  It computes the same y = P_N x (x, y: device [n_mult]) but keeps
+ * its two work vectors (G x and H G x) in a static device array of
+ * 2 x TFETI_NOALLOC_MAX_COARSE doubles (384 KiB) that every GPU loading the
+ * library holds until the process exits; it allocates nothing.
+ * - Contexts with n_coarse > TFETI_NOALLOC_MAX_COARSE (more than 4096
+ *   subdomains) are rejected with TFETI_ERR_ARG.
+ * - The first call on a device resolves the array's device address with
+ *   cudaGetSymbolAddress while that device is current; make that first call
+ *   before any stream capture.
+ * - All calls on a device share the array: calls whose kernels overlap on the
+ *   GPU race.  Both work vectors are overwritten before they are read, so no
+ *   clearing is needed between calls.
+ * - Synchronises the context's stream. */
+#define TFETI_NOALLOC_MAX_COARSE 24576
+int tfeti_apply_projector_noalloc(tfeti_ctx* ctx, const double* x, double* y);
+
 /* ---- timing of the last calls (host) ---------------------------------------- */
 typedef struct tfeti_timing {
     double f_apply_ms_total;   /* summed device time of the F-apply kernel launches     */

@@ -89,6 +89,7 @@ SIGNATURES = {
     "tfeti_apply_N": (C.c_int, [_P, _P, _P]),
     "tfeti_apply_kdag": (C.c_int, [_P, _P, _P]),
     "tfeti_apply_K": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_projector_noalloc": (C.c_int, [_P, _P, _P]),
     "tfeti_timing_get": (C.c_int, [_P, C.POINTER(Timing)]),
     "tfeti_timing_reset": (C.c_int, [_P, _I]),
 }
@@ -280,6 +281,11 @@ class Context:
     def apply(self, which: str, x, y):
         fn = getattr(self.lib, "tfeti_apply_" + which)
         return self._check(fn(self.h, _ptr(x), _ptr(y)), "tfeti_apply_" + which)
+
+    def apply_projector_noalloc(self, x, y):
+        """P_N x through the entry point that keeps its work vectors in static device memory."""
+        return self._check(self.lib.tfeti_apply_projector_noalloc(self.h, _ptr(x), _ptr(y)),
+                           "tfeti_apply_projector_noalloc")
 
     def timing(self) -> dict:
         t = Timing()

@@ -13,54 +13,12 @@
 #include <vector>
 
 #include "../../include/tfeti.h"
+#include "ctx.h"
 #include "dev.h"
 #include "plan.h"
 
 using namespace tfeti;
 
-struct tfeti_ctx {
-  Plan plan;
-  cudaStream_t st = nullptr;
-  std::string err;
-  std::vector<void*> allocs;
-  size_t bytes = 0;
-  DevMesh M{};
-  long long l = 0;
-  // tables and maps
-  SubDev* d_subs = nullptr;
-  std::vector<SubDev> h_subs;
-  // state
-  double *u = nullptr, *sig = nullptr, *kap = nullptr;
-  // Newton iterate
-  double *du = nullptr, *df = nullptr, *dsig = nullptr, *dkap = nullptr, *pa = nullptr, *pb = nullptr, *pn = nullptr;
-  uint8_t* plastic = nullptr;
-  int *elem_np = nullptr, *sub_np = nullptr;
-  double* dKe = nullptr;
-  double* band = nullptr;            // template pool followed by the per-subdomain pool
-  long long own_base = 0;            // offset of the per-subdomain pool
-  std::vector<long long> tmpl_off;   // per shape
-  long long* d_kdag_off = nullptr;
-  std::vector<long long> h_kdag_off;
-  int* d_list = nullptr;
-  long long* d_list_off = nullptr;
-  double* ell_val = nullptr;
-  // dual
-  double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
-         *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *dvec = nullptr, *tm = nullptr;
-  double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
-  double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
-  double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;
-  int* d_err = nullptr;
-  int max_copy = 0;
-  // timing
-  bool events = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  cudaEvent_t fac_e0 = nullptr, fac_e1 = nullptr;
-  double f_ms = 0.0, factor_ms = 0.0;
-  long long f_launches = 0, factor_launches = 0, launches = 0;
-  std::vector<int> last_refactored;
-};
 
 namespace {
 

@@ -1,0 +1,37 @@
+"""The allocation-free projector entry point (tfeti_apply_projector_noalloc).
+
+Some callers cannot call cudaMalloc while they apply the solver's operators
+(their device memory belongs to another allocator, or allocation after
+start-up is forbidden).  tfeti_apply_projector_noalloc serves them by keeping its
+work vectors in a static device array; this test checks through the C ABI that
+it returns what tfeti_apply_projector returns, on two calls in a row (the second
+call reuses the array the first one left behind).  The file name sorts last so a
+run that stops at the first failure has run every other test before it.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines only
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1205_1926_gb300 as T  # noqa: E402
+
+
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
+def test_projector_noalloc_matches_allocating_entry_point(w):
+    ctx = T.Context(w)
+    m = ctx.sizes["n_mult"]
+    for seed in (101, 102):
+        x = torch.as_tensor(W.seeded_vector(m, seed)).cuda()
+        y_ref = torch.zeros(m, dtype=torch.float64, device="cuda")
+        y_static = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.apply("projector", x, y_ref)
+        ctx.apply_projector_noalloc(x, y_static)
+        a, b = y_static.cpu().numpy(), y_ref.cpu().numpy()
+        assert np.isfinite(a).all()
+        assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
