@@ -112,40 +112,52 @@ def oracle_sample(w, n_sub_sample=32, n_pcg_sample=2):
     seconds; the model set-up (mesh, B, R, N N^T) is excluded like the GPU's set-up.
     """
     import numpy as np
-    from threadpoolctl import threadpool_limits
     from oracle.decomp import FixingNodeInverse
     from oracle.ssn import ElastoplasticModel
-    with threadpool_limits(1):
-        model = ElastoplasticModel(w)
-        n_sub = model.dec.n_sub
-        subset = list(range(0, n_sub, max(1, n_sub // n_sub_sample)))[:n_sub_sample]
-        f1 = model.traction_load(w.traction_dir)
-        du = np.zeros(model.dec.n_dof)
-        t0 = time.perf_counter()
-        Kb_sub, _, _ = model.assemble(du, f1, subdomains=set(subset))
-        t_asm = (time.perf_counter() - t0) * n_sub / len(subset)
-        t0 = time.perf_counter()
-        for K, p in zip(Kb_sub, subset):
-            FixingNodeInverse(K, model.fixing[p])
-        t_fac = (time.perf_counter() - t0) * n_sub / len(subset)
-        # a full operator for the PCGP sample: the elastic factor of one box shape repeated
-        kd0 = FixingNodeInverse(Kb_sub[0], model.fixing[subset[0]])
-        solver = model.tfeti([Kb_sub[0]] * n_sub, kdag=[kd0] * n_sub)
-        rng = np.random.default_rng(0)
-        r = rng.standard_normal(model.dec.m)
-        t0 = time.perf_counter()
-        for _ in range(n_pcg_sample):
-            wv = solver.project(r)
-            z = solver.apply_precond(wv)
-            y = solver.project(z)
-            solver.apply_F(y)
-        t_pcg = (time.perf_counter() - t0) / n_pcg_sample
-        t0 = time.perf_counter()
-        solver.apply_F(r)
-        t_fapply = time.perf_counter() - t0
+    model = ElastoplasticModel(w)
+    n_sub = model.dec.n_sub
+    subset = list(range(0, n_sub, max(1, n_sub // n_sub_sample)))[:n_sub_sample]
+    f1 = model.traction_load(w.traction_dir)
+    du = np.zeros(model.dec.n_dof)
+    t0 = time.perf_counter()
+    Kb_sub, _, _ = model.assemble(du, f1, subdomains=set(subset))
+    t_asm = (time.perf_counter() - t0) * n_sub / len(subset)
+    t0 = time.perf_counter()
+    for K, p in zip(Kb_sub, subset):
+        FixingNodeInverse(K, model.fixing[p])
+    t_fac = (time.perf_counter() - t0) * n_sub / len(subset)
+    # a full operator for the PCGP sample: the elastic factor of one box shape repeated
+    kd0 = FixingNodeInverse(Kb_sub[0], model.fixing[subset[0]])
+    solver = model.tfeti([Kb_sub[0]] * n_sub, kdag=[kd0] * n_sub)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(model.dec.m)
+    t0 = time.perf_counter()
+    for _ in range(n_pcg_sample):
+        wv = solver.project(r)
+        z = solver.apply_precond(wv)
+        y = solver.project(z)
+        solver.apply_F(y)
+    t_pcg = (time.perf_counter() - t0) / n_pcg_sample
+    t0 = time.perf_counter()
+    solver.apply_F(r)
+    t_fapply = time.perf_counter() - t0
     return {"assembly_s": t_asm, "factor_s": t_fac, "pcg_iter_s": t_pcg, "f_apply_s": t_fapply, "cores": 1,
             "sample": f"Algorithm 5 + fixing-node Cholesky on {len(subset)} of {n_sub} subdomains (scaled), "
                       f"{n_pcg_sample} PCGP iterations over all {n_sub} subdomains; 1 BLAS thread"}
+
+
+THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_sample_subprocess(workload_name):
+    """Run oracle_sample in a fresh interpreter whose BLAS/OpenMP pools are limited to one thread."""
+    env = dict(os.environ)
+    for k in THREAD_ENV:
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name],
+                       env=env, capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def oracle_step_estimate(s, newton_per_step, pcg_per_step):
@@ -173,9 +185,7 @@ def run_reference(args, rank, world):
         newton, pcg, src = oracle_record_counts(args.warmup + 1, args.warmup + args.steps)
     except (OSError, ValueError, KeyError):
         newton, pcg, src = None, None, None
-    for _ in range(args.warmup):
-        pass
-    s = oracle_sample(w)
+    s = oracle_sample_subprocess(w.name)
     if newton is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration-count record missing"}))
         return
@@ -209,7 +219,7 @@ def run_gpu(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    w = W.CUBE64
+    w = W.WORKLOADS[args.workload]
     n_total = args.warmup + args.steps
     stream = torch.cuda.Stream(device=dev)
     ctx = T.Context(w, stream=stream)
@@ -255,13 +265,17 @@ def run_gpu(args, rank, world, local_rank):
     u_final = u_dev.clone()
 
     # ---- end-to-end pass: same steps through the C ABI with host (pinned) buffers
+    if args.no_e2e:
+        n_total_e2e = args.warmup
+    else:
+        n_total_e2e = n_total
     ctx.set_state(*ck)
     dfs_h = [d.cpu().pin_memory() for d in dfs]
     u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(args.warmup, n_total):
+    for k in range(args.warmup, n_total_e2e):
         ctx.time_step(dfs_h[k].data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit, df_on_host=True)
         ctx.get_state(u=u_dev)
         with torch.cuda.stream(stream):
@@ -270,7 +284,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     elapsed_e2e = time.perf_counter() - t0
-    e2e_match = bool(torch.equal(u_host.to(dev), u_final))
+    e2e_match = bool(torch.equal(u_host.to(dev), u_final)) if not args.no_e2e else None
 
     if world > 1:
         t = torch.tensor([elapsed, elapsed_e2e], dtype=torch.float64, device=dev)
@@ -305,8 +319,9 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, args.steps, args.warmup) | {"parallelism": "replicas" if world > 1 else "1 GPU"},
-            "e2e": {"value": elapsed_e2e / units, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-                    "d2h_bytes_per_step": 8 * n, "matches_device_pass": e2e_match},
+            "e2e": None if args.no_e2e else {"value": elapsed_e2e / units, "unit": UNIT,
+                                             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                                             "matches_device_pass": e2e_match},
             "gpu_launches": int(tm["kernel_launches"]),
             "roofline": roof,
             "clocks": clocks,
@@ -315,8 +330,8 @@ def run_gpu(args, rank, world, local_rank):
                        "refactored_per_step": [s["refactored"] for s in timed],
                        "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
                        "timed_s": elapsed}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(w)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cube64_8x8x8":
+        s = oracle_sample_subprocess(w.name)
         v = oracle_step_estimate(s, statistics.mean(newton_steps), statistics.mean(pcg_steps))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
                                 "sample": s["sample"] + "; scaled with this run's Newton/PCGP counts per step",
@@ -336,7 +351,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", metavar="WORKLOAD", help=argparse.SUPPRESS)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiler runs)")
+    ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
+                    help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
     args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(W.WORKLOADS[args.oracle_sample])))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -71,10 +71,11 @@ class ElastoplasticModel:
         return ds, dk, plastic, eta
 
     def assemble(self, du: np.ndarray, df: np.ndarray, subdomains=None):
-        """Algorithm 5 for every subdomain (or the listed ones): K^p (sparse) and f^p (decomposed)."""
-        eta = self.strains(du)
-        ds, dk, plastic = self.mat.stress_increment(self.sigma, self.kappa, eta)
-        D = self.mat.tangent(self.sigma, self.kappa, eta)
+        """Algorithm 4's subdomain loop calling Algorithm 5 for every subdomain (or the listed ones):
+        K^p (sparse) and f^p (decomposed), plus dsigma, dkappa and plastic flags at the Gauss points."""
+        n_gp = self.dec.n_gp
+        ds_all, dk_all = np.zeros((n_gp, 6)), np.zeros(n_gp)
+        pl_all = np.zeros(n_gp, dtype=bool)
         K_blocks = []
         f = df.copy()
         for p, s in enumerate(self.dec.subs):
@@ -82,15 +83,20 @@ class ElastoplasticModel:
                 continue
             sl = self.gp_slice(p)
             E = s.n_elements
-            Ke = element_stiffness(self.Bg, D[sl].reshape(E, 8, 6, 6), self.wdet)
-            Fe = element_internal_force(self.Bg, ds[sl].reshape(E, 8, 6), self.wdet)
+            ue = du[self.dec.dof_off[p]:self.dec.dof_off[p + 1]][self.edofs[p]]          # (E, 24)
+            eta = np.einsum("gia,ea->egi", self.Bg, ue).reshape(-1, 6)
+            ds, dk, pl = self.mat.stress_increment(self.sigma[sl], self.kappa[sl], eta)
+            D = self.mat.tangent(self.sigma[sl], self.kappa[sl], eta)
+            ds_all[sl], dk_all[sl], pl_all[sl] = ds, dk, pl
+            Ke = element_stiffness(self.Bg, D.reshape(E, 8, 6, 6), self.wdet)
+            Fe = element_internal_force(self.Bg, ds.reshape(E, 8, 6), self.wdet)
             ed = self.edofs[p]
             rows = np.repeat(ed, 24, axis=1).ravel()
             cols = np.tile(ed, (1, 24)).ravel()
             K_blocks.append(sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(s.n_dof, s.n_dof)))
             fl = f[self.dec.dof_off[p]:self.dec.dof_off[p + 1]]
             np.subtract.at(fl, ed.ravel(), Fe.ravel())
-        return K_blocks, f, {"dsigma": ds, "dkappa": dk, "plastic": plastic}
+        return K_blocks, f, {"dsigma": ds_all, "dkappa": dk_all, "plastic": pl_all}
 
     def internal_force(self, du: np.ndarray) -> np.ndarray:
         """F_k(du) of eq. (F_def) on the decomposed dofs."""

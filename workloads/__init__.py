@@ -100,6 +100,8 @@ def cube(name: str, n: int, parts: int, **kw) -> Workload:
 CUBE12 = cube("cube12_2x2x2", 12, 2, n_steps=10, newton_tol=1e-10, pcg_rtol=1e-12)
 # 64^3 hex8, 8x8x8 subdomains of 8^3, 20 steps to 1.5x first yield, timed at 1e-8 dual residual.
 CUBE64 = cube("cube64_8x8x8", 64, 8, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
+# 48^3 hex8, 6^3 subdomains of 8^3 (a smaller case of the same box size, for profiler captures).
+CUBE48 = cube("cube48_6x6x6", 48, 6, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
 # 96^3 hex8, 12^3 subdomains of 8^3.
 CUBE96 = cube("cube96_12x12x12", 96, 12, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
 # 128^3 hex8, 16^3 subdomains of 8^3, cyclic load (40 steps).
@@ -111,7 +113,7 @@ SMALL4 = cube("small4_2x2x2", 4, 2, n_steps=4)
 SMALL6_RAGGED = Workload(name="small_ragged", nel=(5, 4, 6), cuts=((0, 2, 5), (0, 4), (0, 3, 4, 6)),
                          length=(1.0, 0.8, 1.2), n_steps=4)
 
-WORKLOADS = {w.name: w for w in (CUBE12, CUBE64, CUBE96, CUBE128, TINY_1x1x2, SMALL4, SMALL6_RAGGED)}
+WORKLOADS = {w.name: w for w in (CUBE12, CUBE48, CUBE64, CUBE96, CUBE128, TINY_1x1x2, SMALL4, SMALL6_RAGGED)}
 
 
 def irregular_cube80(seed: int = 0, n: int = 80) -> Workload:
