@@ -64,13 +64,60 @@ double dot_host(tfeti_ctx* c, const double* x, const double* y, long long n) {
   return v;
 }
 
+// Solve work items: elastic subdomains of one shape share the shape's template
+// factor and are grouped R to a CTA so that the items fit one wave of SMs;
+// subdomains with plastic points carry their own factor, one per CTA.
+void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
+  const int ns = (int)c->h_subs.size();
+  int n_pl = 0;
+  for (int v : plastic_count) n_pl += v > 0;
+  const int n_el = ns - n_pl;
+  int R = (n_el + std::max(1, c->n_sm - n_pl) - 1) / std::max(1, c->n_sm - n_pl);
+  R = std::max(1, std::min(R, c->rcap));
+  c->h_items.clear();
+  for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+    SolveItem it{};
+    it.fac = c->tmpl_fac_off[sh];
+    for (int p = 0; p < ns; ++p) {
+      if (plastic_count[p] > 0 || c->h_subs[p].shape != (int)sh) continue;
+      it.sub[it.count++] = p;
+      if (it.count == R) {
+        c->h_items.push_back(it);
+        it.count = 0;
+      }
+    }
+    if (it.count) c->h_items.push_back(it);
+  }
+  for (int p = 0; p < ns; ++p)
+    if (plastic_count[p] > 0) {
+      SolveItem it{};
+      it.fac = c->own_fac_base + c->plan.subs[p].fac_off;
+      it.count = 1;
+      it.sub[0] = p;
+      c->h_items.push_back(it);
+    }
+  c->n_items = (int)c->h_items.size();
+  cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
+                  c->st);
+}
+
+SolveArgs solve_args(tfeti_ctx* c) {
+  SolveArgs a{};
+  a.fac = c->fac;
+  a.items = c->d_items;
+  a.n_items = c->n_items;
+  a.err = c->d_err;
+  a.rec_max = c->rec_max;
+  a.npad = c->npad;
+  a.rcap = c->rcap;
+  return a;
+}
+
 // ---- dual operators ---------------------------------------------------------
 void op_F(tfeti_ctx* c, const double* x, double* yv) {
-  SolveArgs a{};
+  SolveArgs a = solve_args(c);
   a.lam = x;
   a.cbuf = c->cbuf;
-  a.band = c->band;
-  a.kdag_off = c->d_kdag_off;
   a.in_mode = 0;
   a.out_mode = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -79,7 +126,7 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
     e1 = c->ev_pool[c->ev_used++];
     cudaEventRecord(e0, c->st);
   }
-  launch_sub_solve(c->M, a, c->plan.max_ndof, c->st);
+  launch_sub_solve(c->M, a, c->solve_smem, c->st);
   if (e1) cudaEventRecord(e1, c->st);
   launch_contract(c->M, c->cbuf, yv, c->st);
   c->launches += 2;
@@ -95,7 +142,7 @@ void op_project(tfeti_ctx* c, const double* x, double* out) {
 
 void op_precond(tfeti_ctx* c, const double* x, double* out) {
   if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped(c->M, x, c->ell_val, c->cbuf, c->st, c->max_copy);
+    launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
     c->launches += 2;
   } else {
@@ -123,22 +170,27 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
   cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
   sync(c);
   std::vector<int> list;
-  std::vector<long long> offs;
+  std::vector<long long> offs, facs, kbbs;
   for (int p = 0; p < M.n_sub; ++p) {
     const SubDev& S = c->h_subs[p];
     if (np[p] > 0) {
       list.push_back(p);
       offs.push_back(c->own_base + S.band_off);
-      c->h_kdag_off[p] = c->own_base + S.band_off;
+      facs.push_back(c->own_fac_base + c->plan.subs[p].fac_off);
+      kbbs.push_back(c->own_kbb_base + c->plan.subs[p].kbb_off);
+      c->h_kbb_off[p] = kbbs.back();
     } else {
-      c->h_kdag_off[p] = c->tmpl_off[S.shape];
+      c->h_kbb_off[p] = c->plan.shapes[S.shape].kbb_off;
     }
   }
+  cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
   c->last_refactored.push_back((int)list.size());
-  cudaMemcpyAsync(c->d_kdag_off, c->h_kdag_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
+  build_items(c, np);
   if (!list.empty()) {
     cudaMemcpyAsync(c->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_list_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_list_fac, facs.data(), sizeof(long long) * facs.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_list_kbb, kbbs.data(), sizeof(long long) * kbbs.size(), cudaMemcpyHostToDevice, c->st);
     int max_rows = 0;
     for (int p : list) max_rows = std::max(max_rows, c->h_subs[p].n_dof);
     launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band, c->d_list_off, 0, max_rows,
@@ -146,7 +198,8 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
     cudaEvent_t e0 = c->events ? c->fac_e0 : nullptr, e1 = c->events ? c->fac_e1 : nullptr;
     if (e0) cudaEventRecord(e0, c->st);
-    launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_err, c->plan.max_bw, c->st);
+    launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_list_fac, c->fac, c->d_err,
+                     c->plan.max_bw, c->st);
     if (e1) cudaEventRecord(e1, c->st);
     c->launches += 2;
     c->factor_launches += 1;
@@ -160,7 +213,8 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     }
     if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a subdomain factorisation");
   }
-  launch_ell_fill(M, c->elem_np, c->dKe, c->ell_val, c->st);
+  if (!list.empty())
+    launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, 0, c->st);
   launch_internal_force(M, c->dsig, df, c->f_full, c->st);
   c->launches += 2;
   if (f_out && f_out != c->f_full)
@@ -175,14 +229,12 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   const long long m = M.n_mult;
   const long long f_before = c->f_launches;
   // d = B K^+ f
-  SolveArgs a{};
+  SolveArgs a = solve_args(c);
   a.src = f;
   a.cbuf = c->cbuf;
-  a.band = c->band;
-  a.kdag_off = c->d_kdag_off;
   a.in_mode = 1;
   a.out_mode = 0;
-  launch_sub_solve(M, a, c->plan.max_ndof, c->st);
+  launch_sub_solve(M, a, c->solve_smem, c->st);
   launch_contract(M, c->cbuf, c->dvec, c->st);
   // e = -R^T f ; lambda_Im = N^T H e = -B R (H e)
   launch_G_apply(M, nullptr, f, c->ev, -1.0, c->st);
@@ -267,23 +319,27 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->tm, c->st);
   launch_G_apply(M, c->tm, nullptr, c->gx, -1.0, c->st);
   launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
-  SolveArgs b{};
+  SolveArgs b = solve_args(c);
   b.src = f;
   b.lam = c->lam;
   b.dst = u_out;
   b.alpha = c->alpha;
-  b.band = c->band;
-  b.kdag_off = c->d_kdag_off;
   b.in_mode = 1;
   b.out_mode = 1;
-  launch_sub_solve(M, b, c->plan.max_ndof, c->st);
+  launch_sub_solve(M, b, c->solve_smem, c->st);
   c->launches += 5;
   if (lambda_out) cudaMemcpyAsync(lambda_out, c->lam, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   cudaMemsetAsync(c->sc + 6, 0, sizeof(double), c->st);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
   sync(c);
   collect_events(c);
   int cst = cuda_check(c, "tfeti_dual_pcg");
   if (cst != TFETI_OK) return cst;
+  if (herr & 2) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    return fail(c, TFETI_ERR_CUDA, "a factor-panel copy did not complete within its time limit");
+  }
   if (status == TFETI_OK && !converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "PCGP iteration limit reached");
   if (info) {
     info->iterations = it;
@@ -328,10 +384,15 @@ int setup_impl(tfeti_ctx* c) {
     d.n_dof = s.n_dof;
     d.n_elem = s.n_elem;
     d.bw = s.bw;
-    d.nb = std::min(kMaxNB, s.bw + 1);
+    d.nb = s.nb;
+    d.nblk = s.nblk;
+    d.rec = s.rec;
     d.shape = s.shape;
     d.n_copy = s.n_copy;
     for (int t = 0; t < 6; ++t) d.fix[t] = s.fix[t];
+    d.n_bnd = P.shapes[s.shape].n_bnd;
+    d.bnd_off = P.shapes[s.shape].bnd_off;
+    d.b2s_off = s.b2s_off;
     d.dof_off = s.dof_off;
     d.elem_off = s.elem_off;
     d.band_off = s.band_off;
@@ -371,7 +432,10 @@ int setup_impl(tfeti_ctx* c) {
   M.slot_sub = upload(c, P.slot_sub);
   M.row_group = upload(c, P.row_group);
   M.row_r = upload(c, P.row_r);
-  M.ell_nbr = upload(c, P.ell_nbr);
+  M.shape_bln = upload(c, P.shape_bln);
+  M.shape_tnbr = upload(c, P.shape_tnbr);
+  M.sub_b2s = upload(c, P.sub_b2s);
+  M.slot_bnd = upload(c, P.slot_bnd);
   M.elem_sub = upload(c, elem_sub);
   M.helm = upload(c, helm);
   double* dN = dalloc<double>(c, 8 * 8 * 3);
@@ -415,11 +479,31 @@ int setup_impl(tfeti_ctx* c) {
   c->dKe = dalloc<double>(c, (size_t)P.n_elem * kTri24);
   c->band = dalloc<double>(c, P.template_band_total + P.band_total);
   c->own_base = P.template_band_total;
-  c->d_kdag_off = dalloc<long long>(c, ns);
-  c->h_kdag_off.assign(ns, 0);
+  c->fac = dalloc<double>(c, P.template_fac_total + P.fac_total);
+  c->own_fac_base = P.template_fac_total;
+  c->d_items = dalloc<SolveItem>(c, ns);
   c->d_list = dalloc<int>(c, ns);
   c->d_list_off = dalloc<long long>(c, ns);
-  c->ell_val = dalloc<double>(c, (size_t)(P.n_copy / 3) * 243);
+  c->d_list_fac = dalloc<long long>(c, ns);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (const SubInfo& s : P.subs) c->rec_max = std::max(c->rec_max, s.rec);
+    c->npad = (P.max_ndof + 1) & ~1;
+    const long long room = (long long)max_smem - 1024 - 16LL * c->rec_max;   // static smem and barriers
+    c->rcap = (int)std::min<long long>(kMaxRHS, room / (8LL * c->npad));
+    if (c->rcap < 1) return fail(c, TFETI_ERR_ARG, "subdomain too large for the shared-memory solve");
+    c->solve_smem = sub_solve_smem(c->rec_max, c->npad, c->rcap);
+  }
+  c->kbb = dalloc<double>(c, P.kbb_template_total + P.kbb_total);
+  c->own_kbb_base = P.kbb_template_total;
+  c->d_kbb_off = dalloc<long long>(c, ns);
+  c->h_kbb_off.assign(ns, 0);
+  c->d_list_kbb = dalloc<long long>(c, ns);
+  for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
   for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->dvec, &c->tm})
@@ -466,27 +550,34 @@ int setup_impl(tfeti_ctx* c) {
   // shared elastic factor per subdomain shape
   {
     std::vector<int> reps;
-    std::vector<long long> offs;
+    std::vector<long long> offs, facs;
     int max_rows = 0;
     for (size_t s = 0; s < P.shapes.size(); ++s) {
       reps.push_back(P.shapes[s].rep_sub);
       offs.push_back(P.shapes[s].band_off);
+      facs.push_back(P.shapes[s].fac_off);
       c->tmpl_off.push_back(P.shapes[s].band_off);
+      c->tmpl_fac_off.push_back(P.shapes[s].fac_off);
       max_rows = std::max(max_rows, P.shapes[s].n_dof);
     }
     int* dl = upload(c, reps);
     long long* dof = upload(c, offs);
+    long long* dfac = upload(c, facs);
     launch_band_fill(M, dl, (int)reps.size(), c->elem_np, c->dKe, c->band, dof, 1, max_rows, P.max_bw, c->st);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    launch_band_chol(M, dl, (int)reps.size(), dof, c->band, c->d_err, P.max_bw, c->st);
+    launch_band_chol(M, dl, (int)reps.size(), dof, c->band, dfac, c->fac, c->d_err, P.max_bw, c->st);
     int herr = 0;
     cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     sync(c);
     if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in an elastic template factorisation");
-    for (int p = 0; p < ns; ++p) c->h_kdag_off[p] = c->tmpl_off[c->h_subs[p].shape];
-    cudaMemcpyAsync(c->d_kdag_off, c->h_kdag_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
+    build_items(c, std::vector<int>(ns, 0));
+    std::vector<long long> kt;
+    for (const ShapeInfo& sh : P.shapes) kt.push_back(sh.kbb_off);
+    long long* dkt = upload(c, kt);
+    launch_kbb_fill(M, dl, dkt, (int)reps.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, 1, c->st);
+    for (int p = 0; p < ns; ++p) c->h_kbb_off[p] = P.shapes[c->h_subs[p].shape].kbb_off;
+    cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
   }
-  launch_ell_fill(M, c->elem_np, c->dKe, c->ell_val, c->st);
   c->launches += 4;
   cudaEventCreate(&c->fac_e0);
   cudaEventCreate(&c->fac_e1);
@@ -728,14 +819,12 @@ int tfeti_apply_N(tfeti_ctx* c, const double* x, double* y) {
 
 int tfeti_apply_kdag(tfeti_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
-  SolveArgs a{};
+  SolveArgs a = solve_args(c);
   a.src = x;
   a.dst = y;
-  a.band = c->band;
-  a.kdag_off = c->d_kdag_off;
   a.in_mode = 1;
   a.out_mode = 1;
-  launch_sub_solve(c->M, a, c->plan.max_ndof, c->st);
+  launch_sub_solve(c->M, a, c->solve_smem, c->st);
   c->launches += 1;
   sync(c);
   return cuda_check(c, "tfeti_apply_kdag");
@@ -756,8 +845,10 @@ int tfeti_timing_get(tfeti_ctx* c, tfeti_timing* out) {
   out->f_apply_launches = c->f_launches;
   double bytes = 0.0, flops = 0.0;
   for (const SubDev& s : c->h_subs) {
-    bytes += 2.0 * 8.0 * (double)s.n_dof * (s.bw + 1);
-    flops += 2.0 * 2.0 * (double)s.n_dof * (s.bw + 1);
+    // two sweeps over the panels (nb x bw per block) and the inverted diagonal blocks
+    const double panel = (double)s.nblk * s.nb * s.bw, diag = (double)s.nblk * s.nb * (s.nb + 1) / 2.0;
+    bytes += 2.0 * 8.0 * (panel + (double)s.nblk * s.nb * s.nb);
+    flops += 2.0 * 2.0 * (panel + diag);
   }
   out->f_apply_bytes = bytes;
   out->f_apply_flops = flops;

@@ -31,11 +31,24 @@ struct tfeti_ctx {
   double* band = nullptr;            // template pool followed by the per-subdomain pool
   long long own_base = 0;            // offset of the per-subdomain pool
   std::vector<long long> tmpl_off;   // per shape
-  long long* d_kdag_off = nullptr;
-  std::vector<long long> h_kdag_off;
+  double* fac = nullptr;             // factor records: template pool followed by the per-subdomain pool
+  long long own_fac_base = 0;
+  std::vector<long long> tmpl_fac_off;   // per shape
+  tfeti::SolveItem* d_items = nullptr;   // solve work items (device), rebuilt after each assembly
+  std::vector<tfeti::SolveItem> h_items;
+  int n_items = 0;
+  int rec_max = 0, npad = 0, rcap = 1;
+  size_t solve_smem = 0;
+  int n_sm = 1;
   int* d_list = nullptr;
   long long* d_list_off = nullptr;
-  double* ell_val = nullptr;
+  long long* d_list_fac = nullptr;
+  double* kbb = nullptr;               // boundary 3x3 blocks: template pool then per-subdomain pool
+  long long own_kbb_base = 0;
+  long long* d_kbb_off = nullptr;      // per subdomain: template or own offset
+  std::vector<long long> h_kbb_off;
+  long long* d_list_kbb = nullptr;
+  int max_bnd = 0;
   // dual
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
          *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *dvec = nullptr, *tm = nullptr;

@@ -13,7 +13,22 @@ struct SubDev {
   int origin[3], dims[3], nn[3];
   int n_dof, n_elem, bw, nb, shape, n_copy;
   int fix[6];
+  int nblk, rec;              // factor row blocks; doubles per off-diagonal panel record
+  int n_bnd;                  // box-boundary nodes of its shape
   long long dof_off, elem_off, band_off, copy_off, r_off;
+  long long bnd_off;          // its shape's boundary tables (shape_bln, 27 x for shape_tnbr)
+  long long b2s_off;          // its boundary index -> first copy slot table
+};
+
+constexpr int kMaxRHS = 4;     // right-hand sides one solve CTA carries
+
+// One CTA of the subdomain solve: up to kMaxRHS subdomains of one shape that
+// share the factor record at `fac` (the elastic template) or a single
+// subdomain with its own factor.
+struct SolveItem {
+  long long fac;
+  int count;
+  int sub[kMaxRHS];
 };
 
 struct GroupDev {
@@ -33,7 +48,10 @@ struct DevMesh {
   const int* slot_sub;
   const int* row_group;
   const int* row_r;
-  const int* ell_nbr;
+  const int* shape_bln;     // box-boundary node -> local node, per shape
+  const int* shape_tnbr;    // [boundary node][27] neighbour boundary index or -1, per shape
+  const int* sub_b2s;       // boundary index -> first copy slot or -1, per subdomain
+  const int* slot_bnd;      // copy slot -> boundary index of its node
   const int* elem_sub;     // subdomain of every element
   const double* R;         // rigid-body bases per shape, [n_dof][6] row-major
   const double* dN;        // [8 g][8 a][3] physical shape-function gradients
@@ -66,7 +84,9 @@ void launch_elem_correction(const DevMesh& M, GPData gp, int* elem_np, int* sub_
 void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const int* elem_np, const double* dKe,
                       double* band, const long long* band_off_list, int elastic_only, int max_rows, int max_bw,
                       cudaStream_t st);
-void launch_ell_fill(const DevMesh& M, const int* elem_np, const double* dKe, double* ell_val, cudaStream_t st);
+// Boundary 3x3 blocks of K for the listed subdomains (elastic_only: the shape's elastic template).
+void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
+                     const int* elem_np, const double* dKe, double* kbb, int elastic_only, cudaStream_t st);
 void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st);
 void launch_apply_K(const DevMesh& M, const int* elem_np, const double* dKe, const double* x, double* y,
                     cudaStream_t st);
@@ -74,8 +94,11 @@ void launch_commit(const DevMesh& M, const double* du, const double* dsig, const
                    double* sig, double* kap, cudaStream_t st);
 void launch_vm_max(const DevMesh& M, const double* dsig, double* partial, double* out, cudaStream_t st);
 
+// Banded Cholesky of K_rr in the band workspace, writing the factor record
+// (off-diagonal panels M_b = L_bb^{-1} L_b,off and the inverted diagonal blocks).
 void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
-                      double* band, int* err, int max_bw, cudaStream_t st);
+                      double* band, const long long* fac_off_list, double* fac, int* err, int max_bw,
+                      cudaStream_t st);
 
 // Subdomain K^+ solve.  in_mode 0: x = B^T lam at the interface slots (zero
 // elsewhere); 1: x = src - B^T lam (lam nullable).  out_mode 0: interface slots
@@ -86,11 +109,17 @@ struct SolveArgs {
   double* cbuf;
   double* dst;
   const double* alpha;
-  const double* band;
-  const long long* kdag_off;   // per subdomain offset into band
+  const double* fac;           // factor pool
+  const SolveItem* items;
+  int n_items;
   int in_mode, out_mode;
+  int* err;                    // bit 2 set if a bounded wait on a panel copy gives up
+  int rec_max;                 // largest panel record of the launch (doubles, even)
+  int npad;                    // vector stride in shared memory (largest n, even)
+  int rcap;                    // vectors allocated per CTA (>= every item's count)
 };
-void launch_sub_solve(const DevMesh& M, const SolveArgs& a, int max_ndof, cudaStream_t st);
+void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
+size_t sub_solve_smem(int rec_max, int npad, int rcap);
 
 void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream_t st);
 void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,
@@ -98,8 +127,8 @@ void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full,
 void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
                       cudaStream_t st);
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st);
-void launch_lumped(const DevMesh& M, const double* w, const double* ell_val, double* cbuf, cudaStream_t st,
-                   int max_copy);
+void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
+                   cudaStream_t st, int max_copy);
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;

@@ -2,12 +2,19 @@
 // generalised-inverse apply K^+ x (Remark 1: fixing dofs replaced by identity
 // rows, forward and backward substitution).
 //
-// Band layout (per subdomain, n rows, half bandwidth bw, W = bw + 1):
-//   band[r*W + k] = L[r][r - bw + k], k = 0..bw.
-// After factorisation the lower triangle of every NB x NB diagonal block
-// [j0, j0+NB) holds the inverse of that block of L instead of L itself, so
-// that both substitutions become block-row GEMVs with no sequential
-// triangle inside a block.
+// Band workspace (per subdomain, n rows, half bandwidth bw, W = bw + 1):
+//   band[r*W + k] = K[r][r - bw + k] on input, L[r][r - bw + k] after factorisation.
+//
+// Factor record written by the factorisation and read by the solves, for row
+// blocks b of nb rows (r0 = b nb):
+//   panel b : M_b = L_bb^{-1} L_b,off, nb x bw, entry (t, j) = column r0 - bw + j
+//   dinv b  : L_bb^{-1}, nb x nb lower triangular
+// With L = D (I + N), D = blockdiag(L_bb), N_b = M_b:
+//   L^{-1} x = (I + N)^{-1} D^{-1} x   and   L^{-T} y = D^{-T} (I + N)^{-T} y,
+// so each step of the forward and backward block recurrences is one GEMV with
+// a panel, and the triangular blocks are applied in parallel before and after.
+#include <cstdint>
+
 #include "dev.h"
 #include "dual_common.cuh"
 
@@ -18,11 +25,14 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kNB1 = kMaxNB + 1;
 
-// One CTA factorises one subdomain band in place (right-looking, block
-// column of NB at a time: diagonal block Cholesky + its inverse, panel TRSM
-// through that inverse, SYRK update of the trailing band).
+// ---------------------------------------------------------------------------
+// Factorisation: one CTA per subdomain, right-looking by block columns of nb:
+// Cholesky of the diagonal block and its inverse, the factor-record panel of
+// the block row, panel TRSM through the inverse, SYRK update of the trailing band.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __restrict__ sub_list,
                                                          const long long* __restrict__ off_list, double* band,
+                                                         const long long* __restrict__ fac_list, double* fac_pool,
                                                          int* err) {
   extern __shared__ double sm[];
   double* Dm = sm;                       // [NB][NB+1] diagonal block -> its Cholesky factor
@@ -31,9 +41,11 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
   const int p = sub_list[blockIdx.x];
   const SubDev S = M.subs[p];
   double* A = band + off_list[blockIdx.x];
+  double* fac = fac_pool + fac_list[blockIdx.x];
+  double* dinv = fac + (long long)S.nblk * S.rec;
   const int n = S.n_dof, bw = S.bw, W = bw + 1, NB = S.nb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  for (int j0 = 0; j0 < n; j0 += NB) {
+  for (int j0 = 0, b = 0; j0 < n; j0 += NB, ++b) {
     const int jb = min(NB, n - j0);
     for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
       const int r = idx / jb, c = idx % jb;
@@ -59,7 +71,6 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
         }
         __syncwarp();
       }
-      // inverse of the lower-triangular factor, one column per lane
       if (lane < jb) {
         const int s = lane;
         for (int r = 0; r < jb; ++r) {
@@ -74,9 +85,23 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
-      const int r = idx / jb, c = idx % jb;
-      if (c <= r) A[(long long)(j0 + r) * W + c - r + bw] = Di[r * kNB1 + c];
+    // factor record of block row b: dinv and M_b = Di * L[b rows][r0-bw .. r0)
+    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+      const int t = idx / NB, q = idx % NB;
+      dinv[(long long)b * NB * NB + idx] = (t < jb && q < jb && q <= t) ? Di[t * kNB1 + q] : 0.0;
+    }
+    double* panel = fac + (long long)b * S.rec;
+    for (int idx = tid; idx < S.rec; idx += blockDim.x) {
+      double s = 0.0;
+      const int t = idx / bw, j = idx % bw;
+      const int c = j0 - bw + j;
+      if (idx < NB * bw && t < jb && c >= 0) {
+        for (int q = 0; q <= t; ++q) {
+          const int k = c - (j0 + q) + bw;
+          if (k >= 0) s += Di[t * kNB1 + q] * A[(long long)(j0 + q) * W + k];
+        }
+      }
+      panel[idx] = s;
     }
     const int i0 = j0 + jb;
     const int P = min(bw, n - i0);
@@ -120,93 +145,250 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
   }
 }
 
-// One CTA applies K_p^+ of one subdomain.
-__global__ void __launch_bounds__(kThreads) k_sub_solve(DevMesh M, SolveArgs a) {
-  extern __shared__ double x[];
-  const int p = blockIdx.x;
-  const SubDev S = M.subs[p];
-  const int n = S.n_dof, bw = S.bw, W = bw + 1, NB = S.nb;
-  double* acc = x + ((n + 1) & ~1);
-  const double* L = a.band + a.kdag_off[p];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  if (a.in_mode == 0) {
-    for (int i = tid; i < n; i += blockDim.x) x[i] = 0.0;
-    __syncthreads();
-    for (int s = tid; s < S.n_copy; s += blockDim.x) {
-      const long long slot = S.copy_off + s;
-      x[M.slot_ldof[slot]] = bt_at_slot(M, a.lam, slot);
-    }
-  } else {
-    for (int i = tid; i < n; i += blockDim.x) x[i] = a.src ? a.src[S.dof_off + i] : 0.0;
-    __syncthreads();
-    if (a.lam)
-      for (int s = tid; s < S.n_copy; s += blockDim.x) {
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies of factor panels into shared memory (1-D TMA,
+// completion tracked by an mbarrier) with bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after about 2^31 SM cycles (~1 s).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Subdomain solve: one CTA applies K^+ to up to kMaxRHS subdomains of one
+// shape that share a factor record.  Shared memory: two panel buffers
+// (nb x bw doubles each) filled one step ahead by bulk copies, the kMaxRHS
+// local vectors, two mbarriers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs a) {
+  extern __shared__ __align__(128) double sm[];
+  __shared__ int s_fail;
+  const SolveItem item = a.items[blockIdx.x];
+  const SubDev& S0 = M.subs[item.sub[0]];
+  const int n = S0.n_dof, bw = S0.bw, nb = S0.nb, nblk = S0.nblk, rec = S0.rec;
+  const int R = item.count;
+  const int npad = a.npad;                       // vector stride (largest n of the launch, even)
+  double* pan[2] = {sm, sm + a.rec_max};
+  double* vec = sm + 2 * a.rec_max;              // [rcap][npad]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(vec + a.rcap * npad);
+  const double* fac = a.fac + item.fac;
+  const double* dinv = fac + (long long)nblk * rec;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nsteps = 2 * nblk;
+  const uint32_t pbytes = (uint32_t)rec * 8u;
+
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // step k uses the panel of block k (forward, k < nblk) or 2 nblk - 1 - k (backward)
+  auto step_block = [nblk, nsteps](int k) { return k < nblk ? k : nsteps - 1 - k; };
+  if (tid == 0) {
+    bulk_copy(pan[0], fac, pbytes, &bar[0]);
+    bulk_copy(pan[1], fac + (long long)step_block(1) * rec, pbytes, &bar[1]);
+  }
+
+  // ---- right-hand sides
+  for (int r = 0; r < R; ++r) {
+    const SubDev& S = M.subs[item.sub[r]];
+    double* x = vec + r * npad;
+    if (a.in_mode == 0)
+      for (int i = tid; i < n; i += nt) x[i] = 0.0;
+    else
+      for (int i = tid; i < n; i += nt) x[i] = a.src ? a.src[S.dof_off + i] : 0.0;
+  }
+  __syncthreads();
+  for (int r = 0; r < R; ++r) {
+    const SubDev& S = M.subs[item.sub[r]];
+    double* x = vec + r * npad;
+    if (a.in_mode == 0) {
+      for (int s = tid; s < S.n_copy; s += nt) {
+        const long long slot = S.copy_off + s;
+        x[M.slot_ldof[slot]] = bt_at_slot(M, a.lam, slot);
+      }
+    } else if (a.lam) {
+      for (int s = tid; s < S.n_copy; s += nt) {
         const long long slot = S.copy_off + s;
         x[M.slot_ldof[slot]] -= bt_at_slot(M, a.lam, slot);
       }
+    }
   }
   __syncthreads();
-  if (tid < 6) x[S.fix[tid]] = 0.0;
+  if (tid < 6)
+    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = 0.0;
   __syncthreads();
-  // forward: L y = x, block rows of NB
-  for (int r0 = 0; r0 < n; r0 += NB) {
-    const int jb = min(NB, n - r0);
-    for (int t = warp; t < jb; t += nwarps) {
-      const int i = r0 + t;
-      const double* row = L + (long long)i * W - i + bw;   // row[c] = L[i][c]
-      double s = 0.0;
-      for (int c = max(0, i - bw) + lane; c < r0; c += 32) s += row[c] * x[c];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) acc[t] = x[i] - s;
-    }
-    __syncthreads();
-    if (tid < jb) {
-      const int i = r0 + tid;
-      const double* row = L + (long long)i * W - i + bw;
-      double s = 0.0;
-      for (int q = 0; q <= tid; ++q) s += row[r0 + q] * acc[q];
-      x[i] = s;
-    }
-    __syncthreads();
-  }
-  // backward: L^T z = y, block rows from the bottom
-  for (int r0 = ((n - 1) / NB) * NB; r0 >= 0; r0 -= NB) {
-    const int jb = min(NB, n - r0);
-    if (tid < jb) {
-      const int c = tid;
-      double s = 0.0;
-      for (int t = c; t < jb; ++t) s += L[(long long)(r0 + t) * W + c - t + bw] * x[r0 + t];
-      acc[c] = s;
-    }
-    __syncthreads();
-    if (tid < jb) x[r0 + tid] = acc[tid];
-    __syncthreads();
-    for (int c = max(0, r0 - bw) + tid; c < r0; c += blockDim.x) {
-      double s = 0.0;
-      for (int t = 0; t < jb; ++t) {
-        const int i = r0 + t;
-        if (c >= i - bw) s += L[(long long)i * W + c - i + bw] * x[i];
+
+  // ---- x' = D^{-1} x, block-diagonal, 256 rows at a time through registers
+  for (int base = 0; base < n; base += nt) {
+    const int i = base + tid;
+    double v[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+      const int b = i / nb, t = i - b * nb, r0 = b * nb;
+      const double* drow = dinv + (long long)b * nb * nb + t * nb;
+      for (int q = 0; q <= t; ++q) {
+        const double d = drow[q];
+#pragma unroll
+        for (int r = 0; r < kMaxRHS; ++r)
+          if (r < R) v[r] = fma(d, vec[r * npad + r0 + q], v[r]);
       }
-      x[c] -= s;
     }
     __syncthreads();
+    if (i < n)
+#pragma unroll
+      for (int r = 0; r < kMaxRHS; ++r)
+        if (r < R) vec[r * npad + i] = v[r];
+    __syncthreads();
   }
-  if (tid < 6) x[S.fix[tid]] = 0.0;
-  __syncthreads();
-  if (a.out_mode == 0) {
-    for (int s = tid; s < S.n_copy; s += blockDim.x) {
-      const long long slot = S.copy_off + s;
-      a.cbuf[slot] = x[M.slot_ldof[slot]];
-    }
-  } else {
-    const double* R = M.R + S.r_off;
-    for (int i = tid; i < n; i += blockDim.x) {
-      double v = x[i];
-      if (a.alpha) {
-        const double* al = a.alpha + 6 * (long long)p;
-        for (int c = 0; c < 6; ++c) v += R[(long long)i * 6 + c] * al[c];
+
+  // ---- block recurrences: forward y_b = x'_b - M_b y[r0-bw, r0), then backward
+  //      z'[r0-bw, r0) -= M_b^T z'_b for b = nblk-1 .. 0
+  const int g = lane >> 3, l = lane & 7;
+  int k_fail = -1;
+  for (int k = 0; k < nsteps; ++k) {
+    const int buf = k & 1;
+    const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
+    if (!ok) s_fail = 1;
+    const double* P = pan[buf];
+    const int b = step_block(k);
+    const int r0 = b * nb, jb = min(nb, n - r0);
+    const int c0 = r0 - bw, jlo = max(0, -c0);
+    if (ok) {
+      if (k < nblk) {
+        const int t = 4 * warp + g;                 // 8 warps x 4 rows = 32 rows
+        const bool act = t < jb;
+        double acc[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+        if (act) {
+          const double* prow = P + t * bw;
+          for (int j = l; j < bw; j += 8) {
+            if (j < jlo) continue;
+            const double mv = prow[j];
+            const int c = c0 + j;
+#pragma unroll
+            for (int r = 0; r < kMaxRHS; ++r)
+              if (r < R) acc[r] = fma(mv, vec[r * npad + c], acc[r]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxRHS; ++r) {
+          acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 4);
+          acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
+          acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+        }
+        if (act && l == 0)
+#pragma unroll
+          for (int r = 0; r < kMaxRHS; ++r)
+            if (r < R) vec[r * npad + r0 + t] -= acc[r];
+      } else {
+        // one (column, right-hand side) pair per thread: bw * R units spread evenly over the CTA
+        const int units = (bw - jlo) * R;
+        for (int u = tid; u < units; u += nt) {
+          const int j = jlo + u / R, r = u - (u / R) * R;
+          const int c = c0 + j;
+          const double* zr = vec + r * npad + r0;
+          double acc = 0.0;
+          for (int t = 0; t < jb; ++t) acc = fma(P[t * bw + j], zr[t], acc);
+          vec[r * npad + c] -= acc;
+        }
       }
-      a.dst[S.dof_off + i] = v;
+    }
+    __syncthreads();
+    if (s_fail) {
+      k_fail = k;
+      break;
+    }
+    if (tid == 0 && k + 2 < nsteps) bulk_copy(pan[buf], fac + (long long)step_block(k + 2) * rec, pbytes, &bar[buf]);
+  }
+  if (k_fail >= 0) {
+    // a panel copy never completed: report, give the copies still in flight (steps
+    // k_fail and k_fail + 1) a bounded time to land, and leave
+    if (tid == 0) {
+      atomicOr(a.err, 2);
+      mbar_wait(&bar[k_fail & 1], (uint32_t)((k_fail >> 1) & 1));
+      if (k_fail + 1 < nsteps) mbar_wait(&bar[(k_fail + 1) & 1], (uint32_t)(((k_fail + 1) >> 1) & 1));
+    }
+    return;
+  }
+
+  // ---- z = D^{-T} z'
+  for (int base = 0; base < n; base += nt) {
+    const int i = base + tid;
+    double v[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+      const int b = i / nb, t = i - b * nb, r0 = b * nb;
+      const int jb = min(nb, n - r0);
+      const double* dblk = dinv + (long long)b * nb * nb;
+      for (int s = t; s < jb; ++s) {
+        const double d = dblk[s * nb + t];
+#pragma unroll
+        for (int r = 0; r < kMaxRHS; ++r)
+          if (r < R) v[r] = fma(d, vec[r * npad + r0 + s], v[r]);
+      }
+    }
+    __syncthreads();
+    if (i < n)
+#pragma unroll
+      for (int r = 0; r < kMaxRHS; ++r)
+        if (r < R) vec[r * npad + i] = v[r];
+    __syncthreads();
+  }
+  if (tid < 6)
+    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = 0.0;
+  __syncthreads();
+
+  // ---- outputs
+  for (int r = 0; r < R; ++r) {
+    const int p = item.sub[r];
+    const SubDev& S = M.subs[p];
+    const double* x = vec + r * npad;
+    if (a.out_mode == 0) {
+      for (int s = tid; s < S.n_copy; s += nt) {
+        const long long slot = S.copy_off + s;
+        a.cbuf[slot] = x[M.slot_ldof[slot]];
+      }
+    } else {
+      const double* Rb = M.R + S.r_off;
+      for (int i = tid; i < n; i += nt) {
+        double v = x[i];
+        if (a.alpha) {
+          const double* al = a.alpha + 6 * (long long)p;
+          for (int c = 0; c < 6; ++c) v += Rb[(long long)i * 6 + c] * al[c];
+        }
+        a.dst[S.dof_off + i] = v;
+      }
     }
   }
 }
@@ -214,17 +396,22 @@ __global__ void __launch_bounds__(kThreads) k_sub_solve(DevMesh M, SolveArgs a) 
 }  // namespace
 
 void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
-                      double* band, int* err, int max_bw, cudaStream_t st) {
+                      double* band, const long long* fac_off_list, double* fac, int* err, int max_bw,
+                      cudaStream_t st) {
   if (n_list <= 0) return;
   const size_t smem = sizeof(double) * (2 * kMaxNB * kNB1 + (size_t)max_bw * kNB1);
   cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_band_chol<<<n_list, kThreads, smem, st>>>(M, sub_list, band_off_list, band, err);
+  k_band_chol<<<n_list, kThreads, smem, st>>>(M, sub_list, band_off_list, band, fac_off_list, fac, err);
 }
 
-void launch_sub_solve(const DevMesh& M, const SolveArgs& a, int max_ndof, cudaStream_t st) {
-  const size_t smem = sizeof(double) * ((size_t)((max_ndof + 1) & ~1) + kMaxNB);
-  cudaFuncSetAttribute(k_sub_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_sub_solve<<<M.n_sub, kThreads, smem, st>>>(M, a);
+size_t sub_solve_smem(int rec_max, int npad, int rcap) {
+  return sizeof(double) * (2 * (size_t)rec_max + (size_t)rcap * npad) + 2 * sizeof(uint64_t);
+}
+
+void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st) {
+  if (a.n_items <= 0) return;
+  cudaFuncSetAttribute(k_sub_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  k_sub_solve<<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
 }
 
 }  // namespace tfeti

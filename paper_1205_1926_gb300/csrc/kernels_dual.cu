@@ -98,28 +98,35 @@ __global__ void k_gemv(const double* __restrict__ A, long long n, const double* 
 }
 
 // Lumped preconditioner, subdomain part: v = K_bb (B^T w) on the interface slots.
-__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* __restrict__ ell_val, double* cbuf) {
+// K_bb comes from the subdomain's boundary blocks (kbb + kbb_off[p]): its shape's
+// elastic template or its own blocks when it has plastic points.
+__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* __restrict__ kbb,
+                         const long long* __restrict__ kbb_off, double* cbuf) {
   extern __shared__ double xs[];
   const int p = blockIdx.x;
   const SubDev S = M.subs[p];
   for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = bt_at_slot(M, w, S.copy_off + s);
   __syncthreads();
-  const long long in0 = S.copy_off / 3;
-  const int n_in = S.n_copy / 3;
+  const double* kb = kbb + kbb_off[p];
+  const int* tn = M.shape_tnbr + S.bnd_off * 27;
+  const int* b2s = M.sub_b2s + S.b2s_off;
   for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
-    const int inode = q / 3, a = q % 3;
-    const long long gi = in0 + inode;
+    const long long slot = S.copy_off + q;
+    const int b = M.slot_bnd[slot], a = q % 3;
+    const double* kv = kb + (long long)b * 243 + a * 3;
+    const int* nb = tn + b * 27;
     double s = 0.0;
+#pragma unroll 9
     for (int t = 0; t < 27; ++t) {
-      const int nb = M.ell_nbr[gi * 27 + t];
-      if (nb < 0) continue;
-      const int lb = (int)(nb - S.copy_off);
-      const double* kv = ell_val + (gi * 27 + t) * 9 + a * 3;
-      s += kv[0] * xs[lb] + kv[1] * xs[lb + 1] + kv[2] * xs[lb + 2];
+      const int nu = nb[t];
+      const int sl = nu >= 0 ? b2s[nu] : -1;
+      if (sl >= 0) {
+        const int lb = (int)(sl - S.copy_off);
+        s += kv[t * 9] * xs[lb] + kv[t * 9 + 1] * xs[lb + 1] + kv[t * 9 + 2] * xs[lb + 2];
+      }
     }
-    cbuf[S.copy_off + q] = s;
+    cbuf[slot] = s;
   }
-  (void)n_in;
 }
 
 // Deterministic dot product: fixed grid, fixed per-block order, fixed final order.
@@ -356,11 +363,11 @@ void launch_gemv(const double* A, long long n, const double* x, double alpha, do
   k_gemv<<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
 }
 
-void launch_lumped(const DevMesh& M, const double* w, const double* ell_val, double* cbuf, cudaStream_t st,
-                   int max_copy) {
+void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
+                   cudaStream_t st, int max_copy) {
   const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
   cudaFuncSetAttribute(k_lumped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_lumped<<<M.n_sub, 256, smem, st>>>(M, w, ell_val, cbuf);
+  k_lumped<<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
 }
 
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st) {

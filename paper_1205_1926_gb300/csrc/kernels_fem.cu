@@ -387,23 +387,23 @@ __global__ void k_band_fill(DevMesh M, const int* __restrict__ sub_list, const i
   band[band_off_list[item] + idx] = v;
 }
 
-// Lumped-preconditioner blocks: K[3i+a][3j+b] for interface nodes i, j of a subdomain.
-__global__ void k_ell_fill(DevMesh M, const int* elem_np, const double* dKe, double* ell_val) {
+// Lumped-preconditioner blocks of one subdomain (or its shape's elastic template):
+// K[3 ln(b) + a][3 ln(nu) + c] for every box-boundary node b and its 27 stencil neighbours nu.
+__global__ void k_kbb_fill(DevMesh M, const int* __restrict__ sub_list, const long long* __restrict__ dst_off,
+                           const int* elem_np, const double* dKe, double* kbb, int elastic_only) {
+  const int p = sub_list[blockIdx.y];
+  const SubDev& S = M.subs[p];
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long n_in = M.n_copy / 3;
-  if (idx >= n_in * 243) return;
-  const long long inode = idx / 243;
-  const int rem = (int)(idx % 243), t = rem / 9, a = (rem % 9) / 3, b = rem % 3;
-  const int nbr = M.ell_nbr[inode * 27 + t];
+  if (idx >= (long long)S.n_bnd * 243) return;
+  const int b = (int)(idx / 243), rem = (int)(idx % 243), t = rem / 9, a = (rem % 9) / 3, cc = rem % 3;
+  const int nu = M.shape_tnbr[(S.bnd_off + b) * 27 + t];
   double v = 0.0;
-  if (nbr >= 0) {
-    const long long slot = inode * 3;
-    const SubDev& S = M.subs[M.slot_sub[slot]];
-    const int r = M.slot_ldof[slot] + a;
-    const int c = M.slot_ldof[nbr] + b;
-    v = stiffness_entry(M, S, elem_np, dKe, r, c, false);
+  if (nu >= 0) {
+    const int r = 3 * M.shape_bln[S.bnd_off + b] + a;
+    const int c = 3 * M.shape_bln[S.bnd_off + nu] + cc;
+    v = stiffness_entry(M, S, elem_np, dKe, r, c, elastic_only != 0);
   }
-  ell_val[idx] = v;
+  kbb[dst_off[blockIdx.y] + idx] = v;
 }
 
 // f = df - F_k(du): internal force of eq. (F_def) gathered per dof.
@@ -533,9 +533,11 @@ void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const i
   k_band_fill<<<grid, 256, 0, st>>>(M, sub_list, elem_np, dKe, band, band_off_list, elastic_only);
 }
 
-void launch_ell_fill(const DevMesh& M, const int* elem_np, const double* dKe, double* ell_val, cudaStream_t st) {
-  const long long n = (M.n_copy / 3) * 243;
-  if (n > 0) k_ell_fill<<<blocks_for(n, 256), 256, 0, st>>>(M, elem_np, dKe, ell_val);
+void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
+                     const int* elem_np, const double* dKe, double* kbb, int elastic_only, cudaStream_t st) {
+  if (n_list <= 0) return;
+  dim3 grid(blocks_for((long long)max_bnd * 243, 256), n_list);
+  k_kbb_fill<<<grid, 256, 0, st>>>(M, sub_list, dst_off, elem_np, dKe, kbb, elastic_only);
 }
 
 void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st) {

@@ -104,19 +104,34 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
         int fx[6] = {3 * a, 3 * a + 1, 3 * a + 2, 3 * b + 1, 3 * b + 2, 3 * c + 2};
         std::sort(fx, fx + 6);
         for (int t = 0; t < 6; ++t) s.fix[t] = fx[t];
+        // factor blocks: 32 rows unless two panels of 32 x bw and one vector exceed 200 KB of shared memory
+        s.nb = std::min(32, s.bw + 1);
+        if ((2LL * s.nb * s.bw + s.n_dof) * 8 > 200 * 1024) s.nb = std::min(16, s.bw + 1);
+        s.nblk = (s.n_dof + s.nb - 1) / s.nb;
+        s.rec = ((s.nb * s.bw) + 1) & ~1;
+        s.fac_size = (int64_t)s.nblk * s.rec + (int64_t)s.nblk * s.nb * s.nb;
         plan.max_bw = std::max(plan.max_bw, s.bw);
         plan.max_ndof = std::max(plan.max_ndof, s.n_dof);
         plan.subs.push_back(s);
       }
   plan.n_dof = dof_off;
   plan.band_total = band_off;
-  int64_t tb = 0, rt = 0;
+  int64_t fo = 0;
+  for (auto& s : plan.subs) {
+    s.fac_off = fo;
+    fo += (s.fac_size + 1) & ~1LL;        // keep every record 16-byte aligned
+  }
+  plan.fac_total = fo;
+  int64_t tb = 0, rt = 0, tf = 0;
   for (auto& sh : plan.shapes) {
     sh.band_off = tb;
     tb += (int64_t)sh.n_dof * (sh.bw + 1);
     sh.r_off = rt;
     rt += (int64_t)sh.n_dof * 6;
+    sh.fac_off = tf;
+    tf += (plan.subs[sh.rep_sub].fac_size + 1) & ~1LL;
   }
+  plan.template_fac_total = tf;
   plan.template_band_total = tb;
   plan.r_total = rt;
   const int ns = (int)plan.subs.size();
@@ -226,27 +241,60 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
   for (int64_t sl = 0; sl < plan.n_copy; ++sl)
     if (plan.slot_group[sl] < 0) return bad(plan, "internal: copy slot without group"), TFETI_ERR_ARG;
 
-  // ---- lumped preconditioner stencil on interface nodes
-  plan.ell_nbr.assign((size_t)(plan.n_copy / 3) * 27, -1);
-  for (int p = 0; p < ns; ++p) {
-    const auto& s = plan.subs[p];
-    int ln = 0;
-    for (int lk = 0; lk < s.nn[2]; ++lk)
-      for (int lj = 0; lj < s.nn[1]; ++lj)
-        for (int li = 0; li < s.nn[0]; ++li, ++ln) {
-          int ii = iface_index[p][ln];
-          if (ii < 0) continue;
-          int64_t base = (s.copy_off / 3 + ii) * 27;
-          for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-              for (int dx = -1; dx <= 1; ++dx) {
-                int t = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-                int a = li + dx, b = lj + dy, c = lk + dz;
-                if (a < 0 || b < 0 || c < 0 || a >= s.nn[0] || b >= s.nn[1] || c >= s.nn[2]) continue;
-                int jj = iface_index[p][a + s.nn[0] * (b + s.nn[1] * c)];
-                if (jj >= 0) plan.ell_nbr[base + t] = (int32_t)(s.copy_off + 3 * jj);
-              }
-        }
+  // ---- lumped preconditioner tables (box-boundary nodes of each shape)
+  {
+    int64_t boff = 0, kt = 0;
+    for (auto& sh : plan.shapes) {
+      const int nx_ = sh.dims[0] + 1, ny_ = sh.dims[1] + 1, nz_ = sh.dims[2] + 1;
+      std::vector<int32_t> ln2b(nx_ * ny_ * nz_, -1);
+      sh.bnd_off = boff;
+      sh.n_bnd = 0;
+      for (int lk = 0; lk < nz_; ++lk)
+        for (int lj = 0; lj < ny_; ++lj)
+          for (int li = 0; li < nx_; ++li) {
+            const bool on = li == 0 || lj == 0 || lk == 0 || li == nx_ - 1 || lj == ny_ - 1 || lk == nz_ - 1;
+            if (!on) continue;
+            const int ln = li + nx_ * (lj + ny_ * lk);
+            ln2b[ln] = sh.n_bnd++;
+            plan.shape_bln.push_back(ln);
+          }
+      for (int b = 0; b < sh.n_bnd; ++b) {
+        const int ln = plan.shape_bln[boff + b];
+        const int li = ln % nx_, lj = (ln / nx_) % ny_, lk = ln / (nx_ * ny_);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int a = li + dx, bb = lj + dy, cc = lk + dz;
+              int v = -1;
+              if (a >= 0 && bb >= 0 && cc >= 0 && a < nx_ && bb < ny_ && cc < nz_) v = ln2b[a + nx_ * (bb + ny_ * cc)];
+              plan.shape_tnbr.push_back(v);
+            }
+      }
+      sh.kbb_off = kt;
+      kt += (int64_t)sh.n_bnd * 243;
+      boff += sh.n_bnd;
+    }
+    plan.kbb_template_total = kt;
+    plan.slot_bnd.assign(plan.n_copy, -1);
+    int64_t b2 = 0, kown = 0;
+    for (int p = 0; p < ns; ++p) {
+      auto& s = plan.subs[p];
+      const auto& sh = plan.shapes[s.shape];
+      s.b2s_off = b2;
+      s.kbb_off = kown;
+      kown += (int64_t)sh.n_bnd * 243;
+      for (int b = 0; b < sh.n_bnd; ++b) {
+        const int ln = plan.shape_bln[sh.bnd_off + b];
+        const int ii = iface_index[p][ln];
+        plan.sub_b2s.push_back(ii >= 0 ? (int32_t)(s.copy_off + 3 * ii) : -1);
+        if (ii >= 0)
+          for (int c = 0; c < 3; ++c) plan.slot_bnd[s.copy_off + 3 * ii + c] = b;
+      }
+      b2 += sh.n_bnd;
+    }
+    plan.kbb_total = kown;
+    for (int64_t sl = 0; sl < plan.n_copy; ++sl)
+      if (plan.slot_bnd[sl] < 0) return bad(plan, "internal: interface node off the box boundary"), TFETI_ERR_ARG;
   }
 
   // ---- coarse pairs: GG^T[p][q] (p >= q) = sum over groups with copies in p and q

@@ -23,6 +23,12 @@ struct SubInfo {
   int64_t copy_off;   // first interface copy slot
   int n_copy;         // interface copy slots (3 per interface node)
   int fix[6];         // fixing dofs (local)
+  int nb, nblk;       // factor block size and number of row blocks
+  int rec;            // doubles per off-diagonal panel record (nb * bw, rounded to even)
+  int64_t fac_off;    // offset (doubles) of this subdomain's factor record in the own pool
+  int64_t fac_size;   // doubles of one factor record: nblk * rec + nblk * nb * nb
+  int64_t b2s_off;    // offset into Plan::sub_b2s (n_bnd of its shape entries)
+  int64_t kbb_off;    // offset of its own boundary blocks in the per-subdomain pool
 };
 
 struct ShapeInfo {
@@ -31,6 +37,10 @@ struct ShapeInfo {
   int64_t band_off;   // template (elastic) band storage offset in the template pool
   int64_t r_off;      // offset of R (n_dof x 6, row-major) in the R pool
   int rep_sub;        // a subdomain of this shape
+  int64_t fac_off;    // offset of the shape's elastic factor record in the template pool
+  int n_bnd;          // nodes on the box boundary
+  int64_t bnd_off;    // offset into Plan::shape_bln (and 27 x into Plan::shape_tnbr)
+  int64_t kbb_off;    // offset of the shape's elastic boundary blocks in the template pool
 };
 
 // One (global node, component) with its copies.  rows = k (Dirichlet), k-1
@@ -52,6 +62,7 @@ struct Plan {
   int64_t n_nodes = 0, n_elem = 0, n_gp = 0, n_dof = 0, n_mult = 0, n_copy = 0;
   int max_bw = 0, max_ndof = 0;
   int64_t band_total = 0, template_band_total = 0, r_total = 0;
+  int64_t fac_total = 0, template_fac_total = 0;
   std::vector<SubInfo> subs;
   std::vector<ShapeInfo> shapes;
   std::vector<Group> groups;
@@ -59,9 +70,13 @@ struct Plan {
   std::vector<int32_t> slot_group, slot_j, slot_ldof, slot_sub;
   // per row: group index and row index within group
   std::vector<int32_t> row_group, row_r;
-  // lumped preconditioner structure: per interface node (3 slots), up to 27
-  // neighbour interface nodes of the same subdomain (slot base, or -1)
-  std::vector<int32_t> ell_nbr;   // [n_copy/3][27]: neighbour's first slot or -1
+  // lumped preconditioner structure.  Per shape: the box-boundary nodes (local
+  // node ids) and, for each, its 27 stencil neighbours as boundary indices (or -1).
+  // Per subdomain: boundary index -> first copy slot of that node (or -1).
+  // Per copy slot: the boundary index of its node.  Blocks of K are stored per
+  // boundary node and neighbour as 3x3 (27 x 9 doubles per boundary node).
+  std::vector<int32_t> shape_bln, shape_tnbr, sub_b2s, slot_bnd;
+  int64_t kbb_template_total = 0, kbb_total = 0;
   // coarse matrix pairs (p, q) with p >= q that share at least one group,
   // and per pair the list of (group, i, j) triples
   std::vector<int32_t> pair_p, pair_q;
