@@ -199,7 +199,7 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     cudaEvent_t e0 = c->events ? c->fac_e0 : nullptr, e1 = c->events ? c->fac_e1 : nullptr;
     if (e0) cudaEventRecord(e0, c->st);
     launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_list_fac, c->fac, c->d_err,
-                     c->plan.max_bw, c->st);
+                     c->plan.max_bw, c->n_sm, c->st);
     if (e1) cudaEventRecord(e1, c->st);
     c->launches += 2;
     c->factor_launches += 1;
@@ -565,7 +565,7 @@ int setup_impl(tfeti_ctx* c) {
     long long* dfac = upload(c, facs);
     launch_band_fill(M, dl, (int)reps.size(), c->elem_np, c->dKe, c->band, dof, 1, max_rows, P.max_bw, c->st);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    launch_band_chol(M, dl, (int)reps.size(), dof, c->band, dfac, c->fac, c->d_err, P.max_bw, c->st);
+    launch_band_chol(M, dl, (int)reps.size(), dof, c->band, dfac, c->fac, c->d_err, P.max_bw, c->n_sm, c->st);
     int herr = 0;
     cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     sync(c);

@@ -98,7 +98,7 @@ void launch_vm_max(const DevMesh& M, const double* dsig, double* partial, double
 // (off-diagonal panels M_b = L_bb^{-1} L_b,off and the inverted diagonal blocks).
 void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
                       double* band, const long long* fac_off_list, double* fac, int* err, int max_bw,
-                      cudaStream_t st);
+                      int n_sm, cudaStream_t st);
 
 // Subdomain K^+ solve.  in_mode 0: x = B^T lam at the interface slots (zero
 // elsewhere); 1: x = src - B^T lam (lam nullable).  out_mode 0: interface slots

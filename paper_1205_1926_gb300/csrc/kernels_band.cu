@@ -26,10 +26,72 @@ constexpr int kThreads = 256;
 constexpr int kNB1 = kMaxNB + 1;
 
 // ---------------------------------------------------------------------------
-// Factorisation: one CTA per subdomain, right-looking by block columns of nb:
-// Cholesky of the diagonal block and its inverse, the factor-record panel of
-// the block row, panel TRSM through the inverse, SYRK update of the trailing band.
+// Factorisation: a cluster of C CTAs per subdomain, right-looking by block
+// columns of nb.  Per block column every CTA factors the diagonal block and
+// inverts it (identical, deterministic results, no exchange needed); the CTAs
+// split the factor-record panel of the block row, the panel TRSM through the
+// inverse and the SYRK update of the trailing band.  Two cluster barriers per
+// block column order the global-memory band updates between the CTAs.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_sync_all() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// Cholesky of the jb x jb block D (lower, in shared memory) and its inverse X, all threads.
+__device__ void diag_factor_invert(double* D, double* X, int jb, int* err) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ double s_inv;
+  for (int c = 0; c < jb; ++c) {
+    if (tid == 0) {
+      double d = D[c * kNB1 + c];
+      if (!(d > 0.0)) {
+        atomicOr(err, 1);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      D[c * kNB1 + c] = d;
+      s_inv = 1.0 / d;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int r = c + 1 + tid; r < jb; r += nt) D[r * kNB1 + c] *= inv;
+    __syncthreads();
+    const int m = jb - c - 1;                 // trailing size
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = c + 1 + e / m, q = c + 1 + e % m;
+      if (q <= r) D[r * kNB1 + q] -= D[r * kNB1 + c] * D[q * kNB1 + c];
+    }
+    __syncthreads();
+  }
+  // X = L^{-1}: X = I, then for c: X[c][:] /= L[c][c]; X[r][:] -= L[r][c] X[c][:] for r > c
+  for (int e = tid; e < jb * jb; e += nt) X[(e / jb) * kNB1 + e % jb] = (e / jb == e % jb) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    const double inv = 1.0 / D[c * kNB1 + c];
+    for (int q = tid; q <= c; q += nt) X[c * kNB1 + q] *= inv;
+    __syncthreads();
+    const int m = jb - c - 1;
+    for (int e = tid; e < m * (c + 1); e += nt) {
+      const int r = c + 1 + e / (c + 1), q = e % (c + 1);
+      X[r * kNB1 + q] -= D[r * kNB1 + c] * X[c * kNB1 + q];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __restrict__ sub_list,
                                                          const long long* __restrict__ off_list, double* band,
                                                          const long long* __restrict__ fac_list, double* fac_pool,
@@ -38,110 +100,90 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
   double* Dm = sm;                       // [NB][NB+1] diagonal block -> its Cholesky factor
   double* Di = Dm + kMaxNB * kNB1;       // [NB][NB+1] inverse of the factor
   double* Lp = Di + kMaxNB * kNB1;       // [bw][NB+1] panel
-  const int p = sub_list[blockIdx.x];
+  const int C = (int)cluster_size(), q = (int)cluster_rank();
+  const int item = blockIdx.x / C;
+  const int p = sub_list[item];
   const SubDev S = M.subs[p];
-  double* A = band + off_list[blockIdx.x];
-  double* fac = fac_pool + fac_list[blockIdx.x];
+  double* A = band + off_list[item];
+  double* fac = fac_pool + fac_list[item];
   double* dinv = fac + (long long)S.nblk * S.rec;
   const int n = S.n_dof, bw = S.bw, W = bw + 1, NB = S.nb;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int j0 = 0, b = 0; j0 < n; j0 += NB, ++b) {
     const int jb = min(NB, n - j0);
-    for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+    for (int idx = tid; idx < jb * jb; idx += nt) {
       const int r = idx / jb, c = idx % jb;
       Dm[r * kNB1 + c] = (c <= r) ? A[(long long)(j0 + r) * W + c - r + bw] : 0.0;
     }
     __syncthreads();
-    if (warp == 0) {
-      for (int c = 0; c < jb; ++c) {
-        double d = Dm[c * kNB1 + c];
-        if (!(d > 0.0)) {
-          if (lane == 0) atomicOr(err, 1);
-          d = 1.0;
-        }
-        d = sqrt(d);
-        const double inv = 1.0 / d;
-        __syncwarp();
-        if (lane == c) Dm[c * kNB1 + c] = d;
-        if (lane > c && lane < jb) Dm[lane * kNB1 + c] *= inv;
-        __syncwarp();
-        if (lane > c && lane < jb) {
-          const double lrc = Dm[lane * kNB1 + c];
-          for (int s = c + 1; s <= lane; ++s) Dm[lane * kNB1 + s] -= lrc * Dm[s * kNB1 + c];
-        }
-        __syncwarp();
+    diag_factor_invert(Dm, Di, jb, err);
+    // factor record of block row b (split over the cluster): dinv and M_b = Di * L[b rows][j0-bw .. j0)
+    if (q == 0)
+      for (int idx = tid; idx < NB * NB; idx += nt) {
+        const int t = idx / NB, u = idx % NB;
+        dinv[(long long)b * NB * NB + idx] = (t < jb && u < jb && u <= t) ? Di[t * kNB1 + u] : 0.0;
       }
-      if (lane < jb) {
-        const int s = lane;
-        for (int r = 0; r < jb; ++r) {
-          if (r < s) {
-            Di[r * kNB1 + s] = 0.0;
-          } else {
-            double acc = (r == s) ? 1.0 : 0.0;
-            for (int t = s; t < r; ++t) acc -= Dm[r * kNB1 + t] * Di[t * kNB1 + s];
-            Di[r * kNB1 + s] = acc / Dm[r * kNB1 + r];
+    double* panel = fac + (long long)b * S.rec;
+    {
+      const int chunk = (S.rec + C - 1) / C;
+      const int lo = q * chunk, hi = min(S.rec, lo + chunk);
+      for (int idx = lo + tid; idx < hi; idx += nt) {
+        double v = 0.0;
+        const int t = idx / bw, j = idx % bw;
+        const int c = j0 - bw + j;
+        if (idx < NB * bw && t < jb && c >= 0) {
+          for (int u = 0; u <= t; ++u) {
+            const int k = c - (j0 + u) + bw;
+            if (k >= 0) v += Di[t * kNB1 + u] * A[(long long)(j0 + u) * W + k];
           }
         }
+        panel[idx] = v;
       }
-    }
-    __syncthreads();
-    // factor record of block row b: dinv and M_b = Di * L[b rows][r0-bw .. r0)
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-      const int t = idx / NB, q = idx % NB;
-      dinv[(long long)b * NB * NB + idx] = (t < jb && q < jb && q <= t) ? Di[t * kNB1 + q] : 0.0;
-    }
-    double* panel = fac + (long long)b * S.rec;
-    for (int idx = tid; idx < S.rec; idx += blockDim.x) {
-      double s = 0.0;
-      const int t = idx / bw, j = idx % bw;
-      const int c = j0 - bw + j;
-      if (idx < NB * bw && t < jb && c >= 0) {
-        for (int q = 0; q <= t; ++q) {
-          const int k = c - (j0 + q) + bw;
-          if (k >= 0) s += Di[t * kNB1 + q] * A[(long long)(j0 + q) * W + k];
-        }
-      }
-      panel[idx] = s;
     }
     const int i0 = j0 + jb;
     const int P = min(bw, n - i0);
-    if (P <= 0) {
+    if (P > 0) {
+      // panel TRSM, rows split over the cluster: L[i][j0+c] = sum_{s<=c} A[i][j0+s] Di[c][s]
+      const int rchunk = (P + C - 1) / C;
+      const int t0 = q * rchunk, t1 = min(P, t0 + rchunk);
+      for (int idx = tid; idx < (t1 - t0) * jb; idx += nt) {
+        const int t = t0 + idx / jb, c = idx % jb;
+        const int i = i0 + t, k = j0 + c - i + bw;
+        Lp[t * kNB1 + c] = (k >= 0) ? A[(long long)i * W + k] : 0.0;
+      }
       __syncthreads();
-      continue;
+      for (int idx = tid; idx < (t1 - t0) * jb; idx += nt) {
+        const int t = t0 + idx / jb, c = idx % jb;
+        double v = 0.0;
+        for (int s2 = 0; s2 <= c; ++s2) v += Lp[t * kNB1 + s2] * Di[c * kNB1 + s2];
+        const int i = i0 + t, k = j0 + c - i + bw;
+        if (k >= 0) A[(long long)i * W + k] = v;
+      }
     }
-    for (int idx = tid; idx < P * jb; idx += blockDim.x) {
-      const int t = idx / jb, c = idx % jb;
-      const int i = i0 + t, k = j0 + c - i + bw;
-      Lp[t * kNB1 + c] = (k >= 0) ? A[(long long)i * W + k] : 0.0;
+    cluster_sync_all();
+    if (P > 0) {
+      for (int idx = tid; idx < P * jb; idx += nt) {
+        const int t = idx / jb, c = idx % jb;
+        const int i = i0 + t, k = j0 + c - i + bw;
+        Lp[t * kNB1 + c] = (k >= 0) ? A[(long long)i * W + k] : 0.0;
+      }
+      __syncthreads();
+      // trailing update A[i][i'] -= sum_c L[i][c] L[i'][c], lower triangle split over the cluster
+      const int ntri = P * (P + 1) / 2;
+      const int tchunk = (ntri + C - 1) / C;
+      const int l0 = q * tchunk, l1 = min(ntri, l0 + tchunk);
+      for (int L = l0 + tid; L < l1; L += nt) {
+        int t = (int)((sqrtf(8.0f * (float)L + 1.0f) - 1.0f) * 0.5f);
+        while (t * (t + 1) / 2 > L) --t;
+        while ((t + 1) * (t + 2) / 2 <= L) ++t;
+        const int tp = L - t * (t + 1) / 2;
+        double v = 0.0;
+        for (int c = 0; c < jb; ++c) v += Lp[t * kNB1 + c] * Lp[tp * kNB1 + c];
+        const int i = i0 + t, ip = i0 + tp;
+        A[(long long)i * W + ip - i + bw] -= v;
+      }
     }
-    __syncthreads();
-    // panel: L[i][j0+c] = sum_{s<=c} A[i][j0+s] Di[c][s]
-    for (int t = warp; t < P; t += nwarps) {
-      double val = 0.0;
-      if (lane < jb)
-        for (int s = 0; s <= lane; ++s) val += Lp[t * kNB1 + s] * Di[lane * kNB1 + s];
-      __syncwarp();
-      if (lane < jb) Lp[t * kNB1 + lane] = val;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < P * jb; idx += blockDim.x) {
-      const int t = idx / jb, c = idx % jb;
-      const int i = i0 + t, k = j0 + c - i + bw;
-      if (k >= 0) A[(long long)i * W + k] = Lp[t * kNB1 + c];
-    }
-    // trailing update A[i][i'] -= sum_c L[i][c] L[i'][c] over the panel rows (i >= i')
-    const int ntri = P * (P + 1) / 2;
-    for (int L = tid; L < ntri; L += blockDim.x) {
-      int t = (int)((sqrtf(8.0f * (float)L + 1.0f) - 1.0f) * 0.5f);
-      while (t * (t + 1) / 2 > L) --t;
-      while ((t + 1) * (t + 2) / 2 <= L) ++t;
-      const int tp = L - t * (t + 1) / 2;
-      double s = 0.0;
-      for (int c = 0; c < jb; ++c) s += Lp[t * kNB1 + c] * Lp[tp * kNB1 + c];
-      const int i = i0 + t, ip = i0 + tp;
-      A[(long long)i * W + ip - i + bw] -= s;
-    }
-    __syncthreads();
+    cluster_sync_all();
   }
 }
 
@@ -397,11 +439,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
 
 void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
                       double* band, const long long* fac_off_list, double* fac, int* err, int max_bw,
-                      cudaStream_t st) {
+                      int n_sm, cudaStream_t st) {
   if (n_list <= 0) return;
   const size_t smem = sizeof(double) * (2 * kMaxNB * kNB1 + (size_t)max_bw * kNB1);
   cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_band_chol<<<n_list, kThreads, smem, st>>>(M, sub_list, band_off_list, band, fac_off_list, fac, err);
+  const bool big = cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                   cudaSuccess;
+  cudaGetLastError();
+  // cluster size: the largest power of two with n_list * C <= 2 * n_sm (at most 16, or 8 if
+  // non-portable cluster sizes are unavailable)
+  int C = 1;
+  const int cmax = big ? 16 : 8;
+  while (C < cmax && (long long)n_list * C * 2 <= 2LL * n_sm) C *= 2;
+  for (;;) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(n_list * C));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int max_clusters = 0;
+    if (C > 1 && (cudaOccupancyMaxActiveClusters(&max_clusters, k_band_chol, &cfg) != cudaSuccess ||
+                  max_clusters < 1)) {
+      cudaGetLastError();
+      C /= 2;
+      continue;
+    }
+    cudaLaunchKernelEx(&cfg, k_band_chol, M, sub_list, band_off_list, band, fac_off_list, fac, err);
+    return;
+  }
 }
 
 size_t sub_solve_smem(int rec_max, int npad, int rcap) {
