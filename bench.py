@@ -223,6 +223,8 @@ def run_gpu(args, rank, world, local_rank):
     n_total = args.warmup + args.steps
     stream = torch.cuda.Stream(device=dev)
     ctx = T.Context(w, stream=stream)
+    if args.precision == "mixed":
+        ctx.set_precision(True, args.inner_rtol)
     n = ctx.sizes["n_dof"]
     n_gp = ctx.sizes["n_gp"]
     t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
@@ -317,8 +319,10 @@ def run_gpu(args, rank, world, local_rank):
     pcg_steps = [sum(s["pcg"]) for s in timed]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args.steps, args.warmup) | {"parallelism": "replicas" if world > 1 else "1 GPU"},
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": workload_config(w, args.steps, args.warmup) | {
+                "parallelism": "replicas" if world > 1 else "1 GPU", "precision": args.precision,
+                "inner_rtol": args.inner_rtol if args.precision == "mixed" else None},
             "e2e": None if args.no_e2e else {"value": elapsed_e2e / units, "unit": UNIT,
                                              "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                                              "matches_device_pass": e2e_match},
@@ -326,6 +330,7 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": roof,
             "clocks": clocks,
             "solver": {"t_y": t_y, "newton_per_step": newton_steps, "pcg_per_step": pcg_steps,
+                       "outer_per_step": [sum(s["outer"]) for s in timed],
                        "plastic_gp_final": timed[-1]["plastic_committed"],
                        "refactored_per_step": [s["refactored"] for s in timed],
                        "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
@@ -353,6 +358,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", metavar="WORKLOAD", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiler runs)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
                     help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
     args = ap.parse_args()

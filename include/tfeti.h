@@ -170,6 +170,8 @@ typedef struct tfeti_pcg_info {
     double  r0_norm;           /* ||r^0|| = ||d~||                                      */
     double  w_norm;            /* last ||w^{j-1}||                                      */
     double  seconds;           /* wall time of the call                                 */
+    int32_t f32_applies;       /* F-applies with FP32 subdomain solves (mixed precision) */
+    int32_t outer_iterations;  /* FP64 refinement steps (mixed precision), else 0        */
 } tfeti_pcg_info;
 
 /* Algorithm 3 on the operator left by tfeti_assemble_tangent, for the
@@ -194,6 +196,7 @@ typedef struct tfeti_step_info {
     int32_t refactored[TFETI_MAX_NEWTON];    /* subdomains refactorised per iteration     */
     int64_t plastic_committed;               /* plastic points of the committed state     */
     double  seconds;
+    int32_t outer[TFETI_MAX_NEWTON];         /* FP64 refinement steps per Newton iteration */
 } tfeti_step_info;
 
 /* Algorithm 4 for one time step: du = o; Newton iterations of Algorithm 5 +
@@ -204,6 +207,20 @@ typedef struct tfeti_step_info {
  * Errors: TFETI_ERR_NOT_CONVERGED, and those of the calls above. */
 int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double newton_tol,
                   double pcg_rtol, int32_t newton_maxit, int32_t pcg_maxit, tfeti_step_info* info);
+
+/* Arithmetic of the dual solve.  TFETI_PRECISION_FP64 (default): Algorithm 3 in
+ * FP64.  TFETI_PRECISION_MIXED: the PCGP of Algorithm 3 runs as FP64 iterative
+ * refinement of the dual problem -- the true residual r = d~ - F lambda_Ker is
+ * formed with FP64 F-applies and corrected by inner PCGP solves (same projector
+ * and preconditioner, FP64 vectors) whose F-applies use FP32 subdomain solves
+ * with the factors rounded to FP32; each inner solve reduces its projected
+ * residual by inner_rtol (0 < inner_rtol < 1, e.g. 1e-3).  The stopping test
+ * ||P r|| <= rtol ||d~|| is applied to the FP64 residual, so both modes reach
+ * the same dual residual.  The paper has no mixed-precision variant; this is an
+ * implementation choice for GPUs whose FP64 rate is far below their FP32 rate. */
+#define TFETI_PRECISION_FP64  0
+#define TFETI_PRECISION_MIXED 1
+int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);
 
 /* Load magnitude of the workloads: t_y = sigma_y / max_g sqrt(3/2) ||dev sigma_g||
  * for the elastic response to the unit traction `dir` (host double[3]) on the

@@ -37,20 +37,22 @@ class Sizes(C.Structure):
 
 class PcgInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("used_lambda0", C.c_int32),
-                ("f_applies", C.c_int32), ("r0_norm", C.c_double), ("w_norm", C.c_double), ("seconds", C.c_double)]
+                ("f_applies", C.c_int32), ("r0_norm", C.c_double), ("w_norm", C.c_double), ("seconds", C.c_double),
+                ("f32_applies", C.c_int32), ("outer_iterations", C.c_int32)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("newton", C.c_int32), ("converged", C.c_int32), ("pcg", C.c_int32 * MAX_NEWTON),
                 ("plastic", C.c_int64 * MAX_NEWTON), ("criterion", C.c_double * MAX_NEWTON),
-                ("refactored", C.c_int32 * MAX_NEWTON), ("plastic_committed", C.c_int64), ("seconds", C.c_double)]
+                ("refactored", C.c_int32 * MAX_NEWTON), ("plastic_committed", C.c_int64), ("seconds", C.c_double),
+                ("outer", C.c_int32 * MAX_NEWTON)]
 
     def as_dict(self) -> dict:
         n = self.newton
         return {"newton": n, "converged": bool(self.converged), "pcg": list(self.pcg[:n]),
                 "plastic": list(self.plastic[:n]), "criterion": list(self.criterion[:n]),
                 "refactored": list(self.refactored[:n]), "plastic_committed": self.plastic_committed,
-                "seconds": self.seconds}
+                "seconds": self.seconds, "outer": list(self.outer[:n])}
 
 
 class Timing(C.Structure):
@@ -81,6 +83,7 @@ SIGNATURES = {
     "tfeti_dual_pcg": (C.c_int, [_P, _P, _P, _P, _P, _D, _I, C.POINTER(PcgInfo)]),
     "ssn_time_step": (C.c_int, [_P, _P, _I, _D, _D, _I, _I, C.POINTER(StepInfo)]),
     "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
+    "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
@@ -264,6 +267,10 @@ class Context:
         if check:
             self._check(st, "ssn_time_step")
         return info.as_dict() | {"status": st}
+
+    def set_precision(self, mixed: bool, inner_rtol: float = 1e-3):
+        """FP64 dual solve (default) or FP64-refined PCGP with FP32 inner F-applies."""
+        return self._check(self.lib.tfeti_set_precision(self.h, 1 if mixed else 0, inner_rtol), "tfeti_set_precision")
 
     def first_yield_traction(self, direction, rtol=1e-12) -> float:
         arr = (C.c_double * 3)(*direction)

@@ -67,14 +67,9 @@ double dot_host(tfeti_ctx* c, const double* x, const double* y, long long n) {
 // Solve work items: elastic subdomains of one shape share the shape's template
 // factor and are grouped R to a CTA so that the items fit one wave of SMs;
 // subdomains with plastic points carry their own factor, one per CTA.
-void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
+void build_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R, std::vector<SolveItem>& items) {
   const int ns = (int)c->h_subs.size();
-  int n_pl = 0;
-  for (int v : plastic_count) n_pl += v > 0;
-  const int n_el = ns - n_pl;
-  int R = (n_el + std::max(1, c->n_sm - n_pl) - 1) / std::max(1, c->n_sm - n_pl);
-  R = std::max(1, std::min(R, c->rcap));
-  c->h_items.clear();
+  items.clear();
   for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
     SolveItem it{};
     it.fac = c->tmpl_fac_off[sh];
@@ -82,11 +77,11 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
       if (plastic_count[p] > 0 || c->h_subs[p].shape != (int)sh) continue;
       it.sub[it.count++] = p;
       if (it.count == R) {
-        c->h_items.push_back(it);
+        items.push_back(it);
         it.count = 0;
       }
     }
-    if (it.count) c->h_items.push_back(it);
+    if (it.count) items.push_back(it);
   }
   for (int p = 0; p < ns; ++p)
     if (plastic_count[p] > 0) {
@@ -94,22 +89,40 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
       it.fac = c->own_fac_base + c->plan.subs[p].fac_off;
       it.count = 1;
       it.sub[0] = p;
-      c->h_items.push_back(it);
+      items.push_back(it);
     }
-  c->n_items = (int)c->h_items.size();
-  cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
-                  c->st);
 }
 
-SolveArgs solve_args(tfeti_ctx* c) {
+void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
+  const int ns = (int)c->h_subs.size();
+  int n_pl = 0;
+  for (int v : plastic_count) n_pl += v > 0;
+  const int n_el = ns - n_pl;
+  // FP64: one CTA per SM, so at most n_sm items; FP32: two CTAs per SM fit in shared memory
+  const int slots64 = std::max(1, c->n_sm - n_pl), slots32 = std::max(1, 2 * c->n_sm - n_pl);
+  const int R64 = std::max(1, std::min((n_el + slots64 - 1) / slots64, c->rcap));
+  const int R32 = std::max(1, std::min((n_el + slots32 - 1) / slots32, c->rcap32));
+  build_item_list(c, plastic_count, R64, c->h_items);
+  build_item_list(c, plastic_count, R32, c->h_items32);
+  c->n_items = (int)c->h_items.size();
+  c->n_items32 = (int)c->h_items32.size();
+  cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
+                  c->st);
+  cudaMemcpyAsync(c->d_items32, c->h_items32.data(), sizeof(SolveItem) * c->h_items32.size(),
+                  cudaMemcpyHostToDevice, c->st);
+}
+
+SolveArgs solve_args(tfeti_ctx* c, bool fp32 = false) {
   SolveArgs a{};
   a.fac = c->fac;
-  a.items = c->d_items;
-  a.n_items = c->n_items;
+  a.fac32 = c->fac32;
+  a.fp32 = fp32 ? 1 : 0;
+  a.items = fp32 ? c->d_items32 : c->d_items;
+  a.n_items = fp32 ? c->n_items32 : c->n_items;
   a.err = c->d_err;
   a.rec_max = c->rec_max;
   a.npad = c->npad;
-  a.rcap = c->rcap;
+  a.rcap = fp32 ? c->rcap32 : c->rcap;
   return a;
 }
 
@@ -131,6 +144,19 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
   launch_contract(c->M, c->cbuf, yv, c->st);
   c->launches += 2;
   c->f_launches += 1;
+}
+
+// F x with FP32 subdomain solves (inner iterations of the mixed-precision PCGP).
+void op_F32(tfeti_ctx* c, const double* x, double* yv) {
+  SolveArgs a = solve_args(c, true);
+  a.lam = x;
+  a.cbuf = c->cbuf;
+  a.in_mode = 0;
+  a.out_mode = 0;
+  launch_sub_solve(c->M, a, c->solve_smem32, c->st);
+  launch_contract(c->M, c->cbuf, yv, c->st);
+  c->launches += 2;
+  c->f32_launches += 1;
 }
 
 void op_project(tfeti_ctx* c, const double* x, double* out) {
@@ -212,6 +238,12 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
       c->factor_ms += ms;
     }
     if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a subdomain factorisation");
+    if (c->precision == TFETI_PRECISION_MIXED) {
+      long long len = 0;
+      for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
+      launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)list.size(), len, c->st);
+      c->launches += 1;
+    }
   }
   if (!list.empty())
     launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, 0, c->st);
@@ -222,12 +254,79 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
   return cuda_check(c, "assemble");
 }
 
+struct PcgOut {
+  int it = 0, converged = 0, status = TFETI_OK;
+  double w_norm = 0.0;
+};
+
+// The PCGP loop of Algorithm 3 on P F x = P r: x (in Ker N) and its residual r are
+// updated in place; stops after the updates of the iteration whose ||w^{j-1}|| =
+// ||P r^{j-1}|| <= tol_abs, or at maxit.  fp32: F-applies with FP32 subdomain solves.
+PcgOut pcg_core(tfeti_ctx* c, double* x, double* r, double tol_abs, int maxit, bool fp32) {
+  const long long m = c->M.n_mult;
+  PcgOut o;
+  for (int j = 1; j <= maxit; ++j) {
+    op_project(c, r, c->w);                          // w = P r
+    launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
+    op_precond(c, c->w, c->z);                       // z = F^-1 w
+    op_project(c, c->z, c->y);                       // y = P z
+    launch_dot(c->y, c->w, m, c->partial, c->sc + 0, c->st);
+    c->launches += 4;
+    cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st);
+    cudaEvent_t ready = nullptr;
+    if (j == 1) {
+      sync(c);
+      if (!(c->h_sc[3] > 0.0)) {                     // ||w^0|| = 0: nothing to do
+        o.w_norm = std::sqrt(std::max(0.0, c->h_sc[3]));
+        o.converged = 1;
+        break;
+      }
+    } else {
+      cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+      cudaEventRecord(ready, c->st);
+    }
+    launch_p_update(m, c->y, c->pdir, c->sc, j == 1, c->st);   // p = y + beta p
+    if (fp32) op_F32(c, c->pdir, c->Fp);
+    else op_F(c, c->pdir, c->Fp);                              // F p
+    launch_dot(c->pdir, c->Fp, m, c->partial, c->sc + 2, c->st);
+    launch_lam_r_update(m, c->pdir, c->Fp, x, r, c->sc, c->st);
+    cudaMemcpyAsync(c->sc + 1, c->sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    c->launches += 5;
+    if (ready) {
+      cudaEventSynchronize(ready);
+      cudaEventDestroy(ready);
+    }
+    o.it = j;
+    const double ww = c->h_sc[3];
+    if (!std::isfinite(ww) || !std::isfinite(c->h_sc[0])) {
+      o.status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
+      break;
+    }
+    if (c->h_sc[6] != 0.0) {
+      o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+      break;
+    }
+    o.w_norm = std::sqrt(ww);
+    if (o.w_norm <= tol_abs) {
+      o.converged = 1;
+      break;
+    }
+  }
+  sync(c);
+  if (o.status == TFETI_OK) {
+    double flag = 0.0;
+    cudaMemcpy(&flag, c->sc + 6, sizeof(double), cudaMemcpyDeviceToHost);
+    if (flag != 0.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+  }
+  return o;
+}
+
 int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0, double rtol,
              int maxit, tfeti_pcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   const DevMesh& M = c->M;
   const long long m = M.n_mult;
-  const long long f_before = c->f_launches;
+  const long long f_before = c->f_launches, f32_before = c->f32_launches;
   // d = B K^+ f
   SolveArgs a = solve_args(c);
   a.src = f;
@@ -246,6 +345,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->r, c->st);
   c->launches += 1;
   const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
+  cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);   // d~
   cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
   int used_l0 = 0;
   if (lambda0) {
@@ -255,63 +355,51 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     c->launches += 1;
     used_l0 = 1;
   }
-  int it = 0, converged = 0, status = TFETI_OK;
+  int it = 0, converged = 0, status = TFETI_OK, outer = 0;
   double w_norm = 0.0;
   if (m > 0 && r0 > 0.0) {
-    for (int j = 1; j <= maxit; ++j) {
-      op_project(c, c->r, c->w);                       // w = P r
-      launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
-      op_precond(c, c->w, c->z);                       // z = F^-1 w
-      op_project(c, c->z, c->y);                       // y = P z
-      launch_dot(c->y, c->w, m, c->partial, c->sc + 0, c->st);
-      c->launches += 4;
-      cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st);
-      cudaEvent_t ready = nullptr;
-      if (j == 1) {
-        sync(c);
-        if (!(c->h_sc[3] > 0.0)) {                     // ||w^0|| = 0: lambda_Ker = o
-          w_norm = std::sqrt(std::max(0.0, c->h_sc[3]));
+    if (c->precision == TFETI_PRECISION_MIXED) {
+      // FP64 iterative refinement of the dual problem: the true residual
+      // r = d~ - F lambda_Ker (FP64 F) is corrected by inner PCGP solves whose
+      // F-applies use FP32 subdomain solves; the stopping test is Algorithm 3's,
+      // on the FP64 residual.
+      for (outer = 0; outer < 100;) {
+        op_project(c, c->r, c->w);
+        const double wn = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
+        w_norm = wn;
+        if (!std::isfinite(wn)) {
+          status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
+          break;
+        }
+        if (wn <= rtol * r0) {
           converged = 1;
           break;
         }
-      } else {
-        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-        cudaEventRecord(ready, c->st);
+        if (it >= maxit) break;
+        cudaMemsetAsync(c->dlt, 0, sizeof(double) * m, c->st);
+        cudaMemcpyAsync(c->rin, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+        PcgOut in = pcg_core(c, c->dlt, c->rin, std::max(c->inner_rtol * wn, 0.5 * rtol * r0),
+                             std::min(maxit - it, 1000), true);
+        it += in.it;
+        ++outer;
+        if (in.status != TFETI_OK) {
+          status = in.status;
+          break;
+        }
+        launch_axpby(m, 1.0, c->lamk, 1.0, c->dlt, c->lamk, c->st);
+        op_F(c, c->lamk, c->tm);
+        launch_axpby(m, 1.0, c->dtil, -1.0, c->tm, c->r, c->st);   // r = d~ - F lambda_Ker
+        c->launches += 2;
       }
-      launch_p_update(m, c->y, c->pdir, c->sc, j == 1, c->st);   // p = y + beta p
-      op_F(c, c->pdir, c->Fp);                                   // F p
-      launch_dot(c->pdir, c->Fp, m, c->partial, c->sc + 2, c->st);
-      launch_lam_r_update(m, c->pdir, c->Fp, c->lamk, c->r, c->sc, c->st);
-      cudaMemcpyAsync(c->sc + 1, c->sc + 0, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-      c->launches += 5;
-      if (ready) {
-        cudaEventSynchronize(ready);
-        cudaEventDestroy(ready);
-      }
-      it = j;
-      const double ww = c->h_sc[3];
-      if (!std::isfinite(ww) || !std::isfinite(c->h_sc[0])) {
-        status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
-        break;
-      }
-      if (c->h_sc[6] != 0.0) {
-        status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
-        break;
-      }
-      w_norm = std::sqrt(ww);
-      if (w_norm <= rtol * r0) {
-        converged = 1;
-        break;
-      }
+    } else {
+      PcgOut o = pcg_core(c, c->lamk, c->r, rtol * r0, maxit, false);
+      it = o.it;
+      converged = o.converged;
+      status = o.status;
+      w_norm = o.w_norm;
     }
   } else {
     converged = 1;
-  }
-  sync(c);
-  if (status == TFETI_OK) {
-    double flag = 0.0;
-    cudaMemcpy(&flag, c->sc + 6, sizeof(double), cudaMemcpyDeviceToHost);
-    if (flag != 0.0) status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
   }
   // lambda = lambda_Im + lambda_Ker ; alpha = H N (d - F lambda) ; u = K^+(f - B^T lambda) + R alpha
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
@@ -346,6 +434,8 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     info->converged = converged;
     info->used_lambda0 = used_l0;
     info->f_applies = (int)(c->f_launches - f_before) + 2;
+    info->f32_applies = (int)(c->f32_launches - f32_before);
+    info->outer_iterations = outer;
     info->r0_norm = r0;
     info->w_norm = w_norm;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -479,9 +569,13 @@ int setup_impl(tfeti_ctx* c) {
   c->dKe = dalloc<double>(c, (size_t)P.n_elem * kTri24);
   c->band = dalloc<double>(c, P.template_band_total + P.band_total);
   c->own_base = P.template_band_total;
-  c->fac = dalloc<double>(c, P.template_fac_total + P.fac_total);
+  long long max_fac = 0;
+  for (const SubInfo& s : P.subs) max_fac = std::max<long long>(max_fac, s.fac_size);
+  c->fac = dalloc<double>(c, P.template_fac_total + P.fac_total + max_fac);   // slack for whole-record copies
+  c->fac32 = dalloc<float>(c, P.template_fac_total + P.fac_total + max_fac);
   c->own_fac_base = P.template_fac_total;
   c->d_items = dalloc<SolveItem>(c, ns);
+  c->d_items32 = dalloc<SolveItem>(c, ns);
   c->d_list = dalloc<int>(c, ns);
   c->d_list_off = dalloc<long long>(c, ns);
   c->d_list_fac = dalloc<long long>(c, ns);
@@ -496,7 +590,11 @@ int setup_impl(tfeti_ctx* c) {
     const long long room = (long long)max_smem - 1024 - 16LL * c->rec_max;   // static smem and barriers
     c->rcap = (int)std::min<long long>(kMaxRHS, room / (8LL * c->npad));
     if (c->rcap < 1) return fail(c, TFETI_ERR_ARG, "subdomain too large for the shared-memory solve");
-    c->solve_smem = sub_solve_smem(c->rec_max, c->npad, c->rcap);
+    c->solve_smem = sub_solve_smem(c->rec_max, c->npad, c->rcap, 8);
+    const long long room32 = (long long)max_smem - 1024 - 8LL * c->rec_max;
+    c->rcap32 = (int)std::min<long long>(kMaxRHS, room32 / (4LL * c->npad));
+    if (c->rcap32 < 1) c->rcap32 = 1;
+    c->solve_smem32 = sub_solve_smem(c->rec_max, c->npad, c->rcap32, 4);
   }
   c->kbb = dalloc<double>(c, P.kbb_template_total + P.kbb_total);
   c->own_kbb_base = P.kbb_template_total;
@@ -506,7 +604,8 @@ int setup_impl(tfeti_ctx* c) {
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
-  for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->dvec, &c->tm})
+  for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->dvec, &c->tm,
+                     &c->dtil, &c->dlt, &c->rin})
     *v = dalloc<double>(c, m);
   c->H = dalloc<double>(c, (size_t)c->l * c->l);
   c->gx = dalloc<double>(c, c->l);
@@ -570,6 +669,9 @@ int setup_impl(tfeti_ctx* c) {
     cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     sync(c);
     if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in an elastic template factorisation");
+    long long len = 0;
+    for (const ShapeInfo& sh : P.shapes) len = std::max<long long>(len, P.subs[sh.rep_sub].fac_size);
+    launch_fac_to_f32(c->fac, c->fac32, dfac, (int)reps.size(), len, c->st);
     build_items(c, std::vector<int>(ns, 0));
     std::vector<long long> kt;
     for (const ShapeInfo& sh : P.shapes) kt.push_back(sh.kbb_off);
@@ -714,6 +816,7 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
     for (int v : np) npl += v;
     loc.newton = i;
     loc.pcg[i - 1] = pi.iterations;
+    loc.outer[i - 1] = pi.outer_iterations;
     loc.plastic[i - 1] = npl;
     loc.criterion[i - 1] = crit;
     loc.refactored[i - 1] = c->last_refactored.empty() ? 0 : c->last_refactored.back();
@@ -746,6 +849,29 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
   if (info) *info = loc;
   int cst = cuda_check(c, "ssn_time_step");
   return cst != TFETI_OK ? cst : status;
+}
+
+int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
+  if (!c || (mode != TFETI_PRECISION_FP64 && mode != TFETI_PRECISION_MIXED) || !(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return fail(c, TFETI_ERR_ARG, "bad precision mode or inner tolerance");
+  if (mode == TFETI_PRECISION_MIXED && c->precision != TFETI_PRECISION_MIXED) {
+    // bring the FP32 copies of the per-subdomain factors in use up to date
+    std::vector<long long> offs;
+    long long len = 0;
+    for (const SolveItem& it : c->h_items)
+      if (it.fac >= c->own_fac_base) {
+        offs.push_back(it.fac);
+        len = std::max<long long>(len, c->plan.subs[it.sub[0]].fac_size);
+      }
+    if (!offs.empty()) {
+      cudaMemcpyAsync(c->d_list_fac, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
+      launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)offs.size(), len, c->st);
+      sync(c);
+    }
+  }
+  c->precision = mode;
+  c->inner_rtol = inner_rtol;
+  return cuda_check(c, "tfeti_set_precision");
 }
 
 int tfeti_first_yield_traction(tfeti_ctx* c, const double* dir, double rtol, double* t_y) {

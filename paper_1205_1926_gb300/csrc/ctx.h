@@ -32,6 +32,16 @@ struct tfeti_ctx {
   long long own_base = 0;            // offset of the per-subdomain pool
   std::vector<long long> tmpl_off;   // per shape
   double* fac = nullptr;             // factor records: template pool followed by the per-subdomain pool
+  float* fac32 = nullptr;            // the same records rounded to FP32 (mixed-precision inner solves)
+  std::vector<tfeti::SolveItem> h_items32;
+  tfeti::SolveItem* d_items32 = nullptr;
+  int n_items32 = 0;
+  int rcap32 = 1;
+  size_t solve_smem32 = 0;
+  int precision = 0;                 // TFETI_PRECISION_*
+  double inner_rtol = 1e-3;
+  double *dtil = nullptr, *dlt = nullptr, *rin = nullptr;
+  long long f32_launches = 0;
   long long own_fac_base = 0;
   std::vector<long long> tmpl_fac_off;   // per shape
   tfeti::SolveItem* d_items = nullptr;   // solve work items (device), rebuilt after each assembly

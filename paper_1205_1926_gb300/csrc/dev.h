@@ -109,7 +109,9 @@ struct SolveArgs {
   double* cbuf;
   double* dst;
   const double* alpha;
-  const double* fac;           // factor pool
+  const double* fac;           // factor pool (FP64)
+  const float* fac32;          // the same records rounded to FP32 (used when fp32 != 0)
+  int fp32;                    // 1: FP32 arithmetic (inner solves of the mixed-precision PCGP)
   const SolveItem* items;
   int n_items;
   int in_mode, out_mode;
@@ -119,7 +121,10 @@ struct SolveArgs {
   int rcap;                    // vectors allocated per CTA (>= every item's count)
 };
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
-size_t sub_solve_smem(int rec_max, int npad, int rcap);
+size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
+// FP32 copies of factor records (offsets in entries, same for both pools)
+void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_list, int n_list, long long len,
+                       cudaStream_t st);
 
 void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream_t st);
 void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,

@@ -233,22 +233,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // (nb x bw doubles each) filled one step ahead by bulk copies, the kMaxRHS
 // local vectors, two mbarriers.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs a) {
-  extern __shared__ __align__(128) double sm[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   __shared__ int s_fail;
   const SolveItem item = a.items[blockIdx.x];
   const SubDev& S0 = M.subs[item.sub[0]];
   const int n = S0.n_dof, bw = S0.bw, nb = S0.nb, nblk = S0.nblk, rec = S0.rec;
   const int R = item.count;
   const int npad = a.npad;                       // vector stride (largest n of the launch, even)
-  double* pan[2] = {sm, sm + a.rec_max};
-  double* vec = sm + 2 * a.rec_max;              // [rcap][npad]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(vec + a.rcap * npad);
-  const double* fac = a.fac + item.fac;
-  const double* dinv = fac + (long long)nblk * rec;
+  T* pan[2] = {sm, sm + a.rec_max};
+  T* vec = sm + 2 * a.rec_max;                   // [rcap][npad]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(vec + ((a.rcap * npad + 1) & ~1));
+  const T* fac = (sizeof(T) == 8 ? reinterpret_cast<const T*>(a.fac) : reinterpret_cast<const T*>(a.fac32)) + item.fac;
+  const T* dinv = fac + (long long)nblk * rec;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nsteps = 2 * nblk;
-  const uint32_t pbytes = (uint32_t)rec * 8u;
+  const uint32_t pbytes = (uint32_t)rec * (uint32_t)sizeof(T);
 
   if (tid == 0) {
     s_fail = 0;
@@ -267,42 +269,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   // ---- right-hand sides
   for (int r = 0; r < R; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
-    double* x = vec + r * npad;
+    T* x = vec + r * npad;
     if (a.in_mode == 0)
-      for (int i = tid; i < n; i += nt) x[i] = 0.0;
+      for (int i = tid; i < n; i += nt) x[i] = T(0);
     else
-      for (int i = tid; i < n; i += nt) x[i] = a.src ? a.src[S.dof_off + i] : 0.0;
+      for (int i = tid; i < n; i += nt) x[i] = a.src ? T(a.src[S.dof_off + i]) : T(0);
   }
   __syncthreads();
   for (int r = 0; r < R; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
-    double* x = vec + r * npad;
+    T* x = vec + r * npad;
     if (a.in_mode == 0) {
       for (int s = tid; s < S.n_copy; s += nt) {
         const long long slot = S.copy_off + s;
-        x[M.slot_ldof[slot]] = bt_at_slot(M, a.lam, slot);
+        x[M.slot_ldof[slot]] = T(bt_at_slot(M, a.lam, slot));
       }
     } else if (a.lam) {
       for (int s = tid; s < S.n_copy; s += nt) {
         const long long slot = S.copy_off + s;
-        x[M.slot_ldof[slot]] -= bt_at_slot(M, a.lam, slot);
+        x[M.slot_ldof[slot]] -= T(bt_at_slot(M, a.lam, slot));
       }
     }
   }
   __syncthreads();
   if (tid < 6)
-    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = 0.0;
+    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = T(0);
   __syncthreads();
 
   // ---- x' = D^{-1} x, block-diagonal, 256 rows at a time through registers
   for (int base = 0; base < n; base += nt) {
     const int i = base + tid;
-    double v[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+    T v[kMaxRHS] = {T(0), T(0), T(0), T(0)};
     if (i < n) {
       const int b = i / nb, t = i - b * nb, r0 = b * nb;
-      const double* drow = dinv + (long long)b * nb * nb + t * nb;
+      const T* drow = dinv + (long long)b * nb * nb + t * nb;
       for (int q = 0; q <= t; ++q) {
-        const double d = drow[q];
+        const T d = drow[q];
 #pragma unroll
         for (int r = 0; r < kMaxRHS; ++r)
           if (r < R) v[r] = fma(d, vec[r * npad + r0 + q], v[r]);
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     const int buf = k & 1;
     const bool ok = mbar_wait(&bar[buf], (uint32_t)((k >> 1) & 1));
     if (!ok) s_fail = 1;
-    const double* P = pan[buf];
+    const T* P = pan[buf];
     const int b = step_block(k);
     const int r0 = b * nb, jb = min(nb, n - r0);
     const int c0 = r0 - bw, jlo = max(0, -c0);
@@ -332,12 +334,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
       if (k < nblk) {
         const int t = 4 * warp + g;                 // 8 warps x 4 rows = 32 rows
         const bool act = t < jb;
-        double acc[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+        T acc[kMaxRHS] = {T(0), T(0), T(0), T(0)};
         if (act) {
-          const double* prow = P + t * bw;
+          const T* prow = P + t * bw;
           for (int j = l; j < bw; j += 8) {
             if (j < jlo) continue;
-            const double mv = prow[j];
+            const T mv = prow[j];
             const int c = c0 + j;
 #pragma unroll
             for (int r = 0; r < kMaxRHS; ++r)
@@ -360,8 +362,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
         for (int u = tid; u < units; u += nt) {
           const int j = jlo + u / R, r = u - (u / R) * R;
           const int c = c0 + j;
-          const double* zr = vec + r * npad + r0;
-          double acc = 0.0;
+          const T* zr = vec + r * npad + r0;
+          T acc = T(0);
           for (int t = 0; t < jb; ++t) acc = fma(P[t * bw + j], zr[t], acc);
           vec[r * npad + c] -= acc;
         }
@@ -388,13 +390,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   // ---- z = D^{-T} z'
   for (int base = 0; base < n; base += nt) {
     const int i = base + tid;
-    double v[kMaxRHS] = {0.0, 0.0, 0.0, 0.0};
+    T v[kMaxRHS] = {T(0), T(0), T(0), T(0)};
     if (i < n) {
       const int b = i / nb, t = i - b * nb, r0 = b * nb;
       const int jb = min(nb, n - r0);
-      const double* dblk = dinv + (long long)b * nb * nb;
+      const T* dblk = dinv + (long long)b * nb * nb;
       for (int s = t; s < jb; ++s) {
-        const double d = dblk[s * nb + t];
+        const T d = dblk[s * nb + t];
 #pragma unroll
         for (int r = 0; r < kMaxRHS; ++r)
           if (r < R) v[r] = fma(d, vec[r * npad + r0 + s], v[r]);
@@ -408,23 +410,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     __syncthreads();
   }
   if (tid < 6)
-    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = 0.0;
+    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = T(0);
   __syncthreads();
 
   // ---- outputs
   for (int r = 0; r < R; ++r) {
     const int p = item.sub[r];
     const SubDev& S = M.subs[p];
-    const double* x = vec + r * npad;
+    const T* x = vec + r * npad;
     if (a.out_mode == 0) {
       for (int s = tid; s < S.n_copy; s += nt) {
         const long long slot = S.copy_off + s;
-        a.cbuf[slot] = x[M.slot_ldof[slot]];
+        a.cbuf[slot] = double(x[M.slot_ldof[slot]]);
       }
     } else {
       const double* Rb = M.R + S.r_off;
       for (int i = tid; i < n; i += nt) {
-        double v = x[i];
+        double v = double(x[i]);
         if (a.alpha) {
           const double* al = a.alpha + 6 * (long long)p;
           for (int c = 0; c < 6; ++c) v += Rb[(long long)i * 6 + c] * al[c];
@@ -476,14 +478,36 @@ void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const l
   }
 }
 
-size_t sub_solve_smem(int rec_max, int npad, int rcap) {
-  return sizeof(double) * (2 * (size_t)rec_max + (size_t)rcap * npad) + 2 * sizeof(uint64_t);
+size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes) {
+  const size_t vec = ((size_t)rcap * npad + 1) & ~(size_t)1;
+  return (size_t)elem_bytes * (2 * (size_t)rec_max + vec) + 2 * sizeof(uint64_t);
 }
 
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st) {
   if (a.n_items <= 0) return;
-  cudaFuncSetAttribute(k_sub_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-  k_sub_solve<<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
+  if (a.fp32) {
+    cudaFuncSetAttribute(k_sub_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    k_sub_solve<float><<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
+  } else {
+    cudaFuncSetAttribute(k_sub_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    k_sub_solve<double><<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
+  }
+}
+
+namespace {
+__global__ void k_to_f32(const double* __restrict__ src, float* dst, const long long* __restrict__ off,
+                         long long len) {
+  const long long base = off[blockIdx.y];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    dst[base + i] = (float)src[base + i];
+}
+}  // namespace
+
+void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_list, int n_list, long long len,
+                       cudaStream_t st) {
+  if (n_list <= 0) return;
+  dim3 grid(64, n_list);
+  k_to_f32<<<grid, 256, 0, st>>>(fac, fac32, off_list, len);
 }
 
 }  // namespace tfeti

@@ -108,7 +108,7 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
         s.nb = std::min(32, s.bw + 1);
         if ((2LL * s.nb * s.bw + s.n_dof) * 8 > 200 * 1024) s.nb = std::min(16, s.bw + 1);
         s.nblk = (s.n_dof + s.nb - 1) / s.nb;
-        s.rec = ((s.nb * s.bw) + 1) & ~1;
+        s.rec = ((s.nb * s.bw) + 3) & ~3;                  // 16-byte records in FP64 and FP32
         s.fac_size = (int64_t)s.nblk * s.rec + (int64_t)s.nblk * s.nb * s.nb;
         plan.max_bw = std::max(plan.max_bw, s.bw);
         plan.max_ndof = std::max(plan.max_ndof, s.n_dof);
@@ -119,7 +119,7 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
   int64_t fo = 0;
   for (auto& s : plan.subs) {
     s.fac_off = fo;
-    fo += (s.fac_size + 1) & ~1LL;        // keep every record 16-byte aligned
+    fo += (s.fac_size + 3) & ~3LL;        // keep every record 16-byte aligned (FP64 and FP32 copies)
   }
   plan.fac_total = fo;
   int64_t tb = 0, rt = 0, tf = 0;
@@ -129,7 +129,7 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
     sh.r_off = rt;
     rt += (int64_t)sh.n_dof * 6;
     sh.fac_off = tf;
-    tf += (plan.subs[sh.rep_sub].fac_size + 1) & ~1LL;
+    tf += (plan.subs[sh.rep_sub].fac_size + 3) & ~3LL;
   }
   plan.template_fac_total = tf;
   plan.template_band_total = tb;

@@ -24,7 +24,7 @@ struct SubInfo {
   int n_copy;         // interface copy slots (3 per interface node)
   int fix[6];         // fixing dofs (local)
   int nb, nblk;       // factor block size and number of row blocks
-  int rec;            // doubles per off-diagonal panel record (nb * bw, rounded to even)
+  int rec;            // entries per off-diagonal panel record (nb * bw, rounded to a multiple of 4)
   int64_t fac_off;    // offset (doubles) of this subdomain's factor record in the own pool
   int64_t fac_size;   // doubles of one factor record: nblk * rec + nblk * nb * nb
   int64_t b2s_off;    // offset into Plan::sub_b2s (n_bnd of its shape entries)

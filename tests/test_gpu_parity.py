@@ -307,3 +307,45 @@ def test_cube64_full_size_properties():
                 force[c] += contrib.sum()
                 scale += np.abs(contrib).sum()
         assert np.abs(force).max() <= 1e-6 * scale
+
+
+# ---------------------------------------------------------------------------- mixed precision (FP64-refined PCGP)
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
+def test_mixed_precision_dual_pcg_reaches_fp64_accuracy(w):
+    """FP32 inner F-applies corrected by FP64 residuals reach the oracle's solution at eps = 1e-12."""
+    m, sig, kap, du = plastic_state(w, seed=51)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((20.0, 5.0, -8.0))
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    ctx.set_precision(True, 1e-3)
+    u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+    info = ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+    assert info["outer_iterations"] >= 2 and info["f32_applies"] >= info["iterations"]
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, _ = m.assemble(du, df)
+    sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+    assert rel(host(u), sol["u"]) <= 1e-9
+    assert rel(host(lam), sol["lam"]) <= 1e-9
+
+
+def test_mixed_precision_load_history_cube12():
+    w = W.CUBE12
+    ctx = T.Context(w)
+    ctx.set_precision(True, 1e-3)
+    t_y = ctx.first_yield_traction(w.traction_dir)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    df = zeros(ctx.sizes["n_dof"])
+    u = zeros(ctx.sizes["n_dof"])
+    prev = 0.0
+    for a in w.load_fractions():
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        ctx.get_state(u=u)
+        assert info["converged"] and rel(host(u), model.u) <= 1e-9
