@@ -349,3 +349,28 @@ def test_mixed_precision_load_history_cube12():
         prev = a
         ctx.get_state(u=u)
         assert info["converged"] and rel(host(u), model.u) <= 1e-9
+
+
+def test_cube64_history_matches_oracle_record():
+    """The full 20-step 64^3 history (the timed workload, FP64) against the oracle's own run of it
+    (tests/golden/cube64_oracle_record.json, written by make_cube64_oracle_record.py from oracle/ only)."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cube64_oracle_record.json")))
+    w = W.CUBE64
+    ctx = T.Context(w)
+    t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
+    assert abs(t_y - rec["t_y"]) <= 1e-9 * rec["t_y"]
+    df = zeros(ctx.sizes["n_dof"])
+    u = zeros(ctx.sizes["n_dof"])
+    prev = 0.0
+    for a, ref in zip(w.load_fractions(), rec["steps"]):
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        prev = a
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        assert info["converged"] and info["newton"] == ref["newton"], (ref["step"], info, ref)
+        assert all(abs(a_ - b_) <= 1 for a_, b_ in zip(info["pcg"], ref["pcg"])), (ref["step"], info["pcg"], ref["pcg"])
+        assert abs(info["plastic_committed"] - ref["plastic_committed"]) <= max(2, 0.005 * ref["plastic_committed"])
+        ctx.get_state(u=u)
+        un = np.linalg.norm(host(u))
+        assert abs(un - ref["u_norm"]) <= 1e-7 * ref["u_norm"]
