@@ -104,6 +104,24 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   const int R32 = std::max(1, std::min((n_el + slots32 - 1) / slots32, c->rcap32));
   build_item_list(c, plastic_count, R64, c->h_items);
   build_item_list(c, plastic_count, R32, c->h_items32);
+  // for the Schur-block inner F-apply: elastic subdomains per shape, FP32 items of the plastic ones
+  c->h_el.clear();
+  c->el_off.assign(c->plan.shapes.size(), 0);
+  c->el_cnt.assign(c->plan.shapes.size(), 0);
+  for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+    c->el_off[sh] = (int)c->h_el.size();
+    for (int p = 0; p < ns; ++p)
+      if (plastic_count[p] == 0 && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
+    c->el_cnt[sh] = (int)c->h_el.size() - c->el_off[sh];
+  }
+  std::vector<SolveItem> pl;
+  for (const SolveItem& it : c->h_items32)
+    if (it.fac >= c->own_fac_base) pl.push_back(it);
+  c->n_items_pl = (int)pl.size();
+  if (!c->h_el.empty())
+    cudaMemcpyAsync(c->d_el, c->h_el.data(), sizeof(int) * c->h_el.size(), cudaMemcpyHostToDevice, c->st);
+  if (!pl.empty())
+    cudaMemcpyAsync(c->d_items_pl, pl.data(), sizeof(SolveItem) * pl.size(), cudaMemcpyHostToDevice, c->st);
   c->n_items = (int)c->h_items.size();
   c->n_items32 = (int)c->h_items32.size();
   cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
@@ -147,16 +165,72 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
 }
 
 // F x with FP32 subdomain solves (inner iterations of the mixed-precision PCGP).
+// With the shapes' dual Schur blocks formed, subdomains on the elastic template are
+// applied as one FP32 GEMM per shape while the subdomains with plastic points run
+// their FP32 banded solves concurrently on the second stream.
 void op_F32(tfeti_ctx* c, const double* x, double* yv) {
   SolveArgs a = solve_args(c, true);
   a.lam = x;
   a.cbuf = c->cbuf;
   a.in_mode = 0;
   a.out_mode = 0;
-  launch_sub_solve(c->M, a, c->solve_smem32, c->st);
+  if (!c->schur_ready) {
+    launch_sub_solve(c->M, a, c->solve_smem32, c->st);
+    c->launches += 1;
+  } else {
+    if (c->n_items_pl > 0) {
+      cudaEventRecord(c->ev_fork, c->st);
+      cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
+      a.items = c->d_items_pl;
+      a.n_items = c->n_items_pl;
+      launch_sub_solve(c->M, a, c->solve_smem32, c->st2);
+      cudaEventRecord(c->ev_join, c->st2);
+      c->launches += 1;
+    }
+    for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+      const int cnt = c->el_cnt[sh];
+      if (!cnt) continue;
+      const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
+      launch_schur_gather(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->Xs, c->st);
+      launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->Xs,
+                                c->S32 + c->plan.shapes[sh].s_off, c->cbuf, c->st);
+      c->launches += 2;
+    }
+    if (c->n_items_pl > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+  }
   launch_contract(c->M, c->cbuf, yv, c->st);
-  c->launches += 2;
+  c->launches += 1;
   c->f32_launches += 1;
+}
+
+// Dual Schur block S = (K^+)_{boundary,boundary} of every shape's elastic template,
+// formed in FP64 by the panel solve with unit right-hand sides and stored in FP32.
+int form_schur_blocks(tfeti_ctx* c) {
+  const Plan& P = c->plan;
+  for (size_t sh = 0; sh < P.shapes.size(); ++sh) {
+    const int n_bd = 3 * P.shapes[sh].n_bnd;
+    std::vector<SolveItem> items;
+    for (int j = 0; j < n_bd; j += c->rcap) {
+      SolveItem it{};
+      it.fac = c->tmpl_fac_off[sh];
+      for (int r = 0; r < c->rcap && j + r < n_bd; ++r) it.sub[it.count++] = j + r;
+      items.push_back(it);
+    }
+    cudaMemcpyAsync(c->d_items_s, items.data(), sizeof(SolveItem) * items.size(), cudaMemcpyHostToDevice, c->st);
+    SolveArgs a = solve_args(c);
+    a.items = c->d_items_s;
+    a.n_items = (int)items.size();
+    a.in_mode = 2;
+    a.out_mode = 2;
+    a.rep_sub = P.shapes[sh].rep_sub;
+    a.S32 = c->S32;
+    a.s_off = P.shapes[sh].s_off;
+    launch_sub_solve(c->M, a, c->solve_smem, c->st);
+    c->launches += 1;
+    sync(c);
+  }
+  c->schur_ready = true;
+  return cuda_check(c, "forming dual Schur blocks");
 }
 
 void op_project(tfeti_ctx* c, const double* x, double* out) {
@@ -403,8 +477,13 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   }
   // lambda = lambda_Im + lambda_Ker ; alpha = H N (d - F lambda) ; u = K^+(f - B^T lambda) + R alpha
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
-  op_F(c, c->lam, c->tm);
-  launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->tm, c->st);
+  if (c->precision == TFETI_PRECISION_MIXED && m > 0 && r0 > 0.0) {
+    // d - F lambda = d~ - F lambda_Ker is the FP64 residual the refinement formed last
+    cudaMemcpyAsync(c->tm, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    op_F(c, c->lam, c->tm);
+    launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->tm, c->st);
+  }
   launch_G_apply(M, c->tm, nullptr, c->gx, -1.0, c->st);
   launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
   SolveArgs b = solve_args(c);
@@ -526,6 +605,7 @@ int setup_impl(tfeti_ctx* c) {
   M.shape_tnbr = upload(c, P.shape_tnbr);
   M.sub_b2s = upload(c, P.sub_b2s);
   M.slot_bnd = upload(c, P.slot_bnd);
+  M.sub_nbr = upload(c, P.sub_nbr);
   M.elem_sub = upload(c, elem_sub);
   M.helm = upload(c, helm);
   double* dN = dalloc<double>(c, 8 * 8 * 3);
@@ -576,6 +656,13 @@ int setup_impl(tfeti_ctx* c) {
   c->own_fac_base = P.template_fac_total;
   c->d_items = dalloc<SolveItem>(c, ns);
   c->d_items32 = dalloc<SolveItem>(c, ns);
+  c->d_items_pl = dalloc<SolveItem>(c, ns);
+  c->d_el = dalloc<int>(c, ns);
+  {
+    int max_bd = 0;
+    for (const ShapeInfo& sh : P.shapes) max_bd = std::max(max_bd, 3 * sh.n_bnd);
+    c->d_items_s = dalloc<SolveItem>(c, max_bd);
+  }
   c->d_list = dalloc<int>(c, ns);
   c->d_list_off = dalloc<long long>(c, ns);
   c->d_list_fac = dalloc<long long>(c, ns);
@@ -683,6 +770,9 @@ int setup_impl(tfeti_ctx* c) {
   c->launches += 4;
   cudaEventCreate(&c->fac_e0);
   cudaEventCreate(&c->fac_e1);
+  cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   for (int i = 0; i < 8192; ++i) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) break;
@@ -744,6 +834,9 @@ int tfeti_destroy(tfeti_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
   if (c->fac_e1) cudaEventDestroy(c->fac_e1);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->st2) cudaStreamDestroy(c->st2);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   delete c;
   return TFETI_OK;
@@ -871,6 +964,18 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   }
   c->precision = mode;
   c->inner_rtol = inner_rtol;
+  if (mode == TFETI_PRECISION_MIXED && !c->schur_ready) {
+    try {
+      c->S32 = dalloc<float>(c, c->plan.s_total);
+      int max_bd = 0;
+      for (const ShapeInfo& sh : c->plan.shapes) max_bd = std::max(max_bd, 3 * sh.n_bnd);
+      c->Xs = dalloc<float>(c, (size_t)c->h_subs.size() * max_bd);
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+    const int st = form_schur_blocks(c);
+    if (st != TFETI_OK) return st;
+  }
   return cuda_check(c, "tfeti_set_precision");
 }
 

@@ -42,6 +42,17 @@ struct tfeti_ctx {
   double inner_rtol = 1e-3;
   double *dtil = nullptr, *dlt = nullptr, *rin = nullptr;
   long long f32_launches = 0;
+  // dual Schur blocks of the shapes' elastic templates (mixed precision)
+  float* S32 = nullptr;
+  float* Xs = nullptr;                       // gathered interface vectors, [elastic subdomains][n_bd]
+  bool schur_ready = false;
+  int* d_el = nullptr;                       // elastic subdomains grouped by shape
+  std::vector<int> h_el, el_off, el_cnt;     // per shape: offset and count into d_el
+  tfeti::SolveItem* d_items_pl = nullptr;    // FP32 items of the subdomains with plastic points
+  int n_items_pl = 0;
+  tfeti::SolveItem* d_items_s = nullptr;     // column items for forming S
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long own_fac_base = 0;
   std::vector<long long> tmpl_fac_off;   // per shape
   tfeti::SolveItem* d_items = nullptr;   // solve work items (device), rebuilt after each assembly

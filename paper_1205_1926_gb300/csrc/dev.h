@@ -52,6 +52,7 @@ struct DevMesh {
   const int* shape_tnbr;    // [boundary node][27] neighbour boundary index or -1, per shape
   const int* sub_b2s;       // boundary index -> first copy slot or -1, per subdomain
   const int* slot_bnd;      // copy slot -> boundary index of its node
+  const int* sub_nbr;       // [interface node][28] first slot of each stencil neighbour or -1
   const int* elem_sub;     // subdomain of every element
   const double* R;         // rigid-body bases per shape, [n_dof][6] row-major
   const double* dN;        // [8 g][8 a][3] physical shape-function gradients
@@ -119,9 +120,22 @@ struct SolveArgs {
   int rec_max;                 // largest panel record of the launch (doubles, even)
   int npad;                    // vector stride in shared memory (largest n, even)
   int rcap;                    // vectors allocated per CTA (>= every item's count)
+  // in_mode 2 / out_mode 2 (dual Schur block formation of one shape): item.sub[] hold
+  // boundary-dof columns j; the geometry is subdomain rep_sub; column j of
+  // S = (K^+)_{boundary, boundary} goes to S32 + s_off + j * n_bd
+  int rep_sub;
+  float* S32;
+  long long s_off;
 };
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
 size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
+// Elastic dual Schur block applied to the elastic subdomains of one shape:
+// X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k] (0 off the interface),
+// then cbuf at the interface slots = (X S)[k][i].
+void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, float* X,
+                         cudaStream_t st);
+void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* X,
+                               const float* S, double* cbuf, cudaStream_t st);
 // FP32 copies of factor records (offsets in entries, same for both pools)
 void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_list, int n_list, long long len,
                        cudaStream_t st);

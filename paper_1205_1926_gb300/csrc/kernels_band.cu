@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   T* sm = reinterpret_cast<T*>(sm_raw);
   __shared__ int s_fail;
   const SolveItem item = a.items[blockIdx.x];
-  const SubDev& S0 = M.subs[item.sub[0]];
+  const SubDev& S0 = M.subs[a.in_mode == 2 ? a.rep_sub : item.sub[0]];
   const int n = S0.n_dof, bw = S0.bw, nb = S0.nb, nblk = S0.nblk, rec = S0.rec;
   const int R = item.count;
   const int npad = a.npad;                       // vector stride (largest n of the launch, even)
@@ -267,7 +267,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   }
 
   // ---- right-hand sides
-  for (int r = 0; r < R; ++r) {
+  const int n_bd = 3 * S0.n_bnd;
+  if (a.in_mode == 2) {   // unit vectors at boundary dofs item.sub[r]
+    for (int r = 0; r < R; ++r)
+      for (int i = tid; i < n; i += nt) vec[r * npad + i] = T(0);
+    __syncthreads();
+    if (tid < R) {
+      const int j = item.sub[tid];
+      vec[tid * npad + 3 * M.shape_bln[S0.bnd_off + j / 3] + j % 3] = T(1);
+    }
+  }
+  for (int r = 0; r < R && a.in_mode != 2; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
     T* x = vec + r * npad;
     if (a.in_mode == 0)
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
       for (int i = tid; i < n; i += nt) x[i] = a.src ? T(a.src[S.dof_off + i]) : T(0);
   }
   __syncthreads();
-  for (int r = 0; r < R; ++r) {
+  for (int r = 0; r < R && a.in_mode != 2; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
     T* x = vec + r * npad;
     if (a.in_mode == 0) {
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   }
   __syncthreads();
   if (tid < 6)
-    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = T(0);
+    for (int r = 0; r < R; ++r) vec[r * npad + S0.fix[tid]] = T(0);
   __syncthreads();
 
   // ---- x' = D^{-1} x, block-diagonal, 256 rows at a time through registers
@@ -410,10 +420,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     __syncthreads();
   }
   if (tid < 6)
-    for (int r = 0; r < R; ++r) vec[r * npad + M.subs[item.sub[r]].fix[tid]] = T(0);
+    for (int r = 0; r < R; ++r) vec[r * npad + S0.fix[tid]] = T(0);
   __syncthreads();
 
   // ---- outputs
+  if (a.out_mode == 2) {
+    for (int r = 0; r < R; ++r) {
+      float* col = a.S32 + a.s_off + (long long)item.sub[r] * n_bd;
+      for (int i = tid; i < n_bd; i += nt)
+        col[i] = (float)vec[r * npad + 3 * M.shape_bln[S0.bnd_off + i / 3] + i % 3];
+    }
+    return;
+  }
   for (int r = 0; r < R; ++r) {
     const int p = item.sub[r];
     const SubDev& S = M.subs[p];

@@ -108,20 +108,25 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* 
   for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = bt_at_slot(M, w, S.copy_off + s);
   __syncthreads();
   const double* kb = kbb + kbb_off[p];
-  const int* tn = M.shape_tnbr + S.bnd_off * 27;
-  const int* b2s = M.sub_b2s + S.b2s_off;
   for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
     const long long slot = S.copy_off + q;
     const int b = M.slot_bnd[slot], a = q % 3;
     const double* kv = kb + (long long)b * 243 + a * 3;
-    const int* nb = tn + b * 27;
+    const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
+    int nb[28];
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+      const int4 v = __ldg(nb4 + u);
+      nb[4 * u] = v.x;
+      nb[4 * u + 1] = v.y;
+      nb[4 * u + 2] = v.z;
+      nb[4 * u + 3] = v.w;
+    }
     double s = 0.0;
-#pragma unroll 9
+#pragma unroll
     for (int t = 0; t < 27; ++t) {
-      const int nu = nb[t];
-      const int sl = nu >= 0 ? b2s[nu] : -1;
-      if (sl >= 0) {
-        const int lb = (int)(sl - S.copy_off);
+      if (nb[t] >= 0) {
+        const int lb = (int)(nb[t] - S.copy_off);
         s += kv[t * 9] * xs[lb] + kv[t * 9 + 1] * xs[lb + 1] + kv[t * 9 + 2] * xs[lb + 2];
       }
     }

@@ -273,6 +273,8 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
       sh.kbb_off = kt;
       kt += (int64_t)sh.n_bnd * 243;
       boff += sh.n_bnd;
+      sh.s_off = plan.s_total;
+      plan.s_total += (9LL * sh.n_bnd * sh.n_bnd + 3) & ~3LL;
     }
     plan.kbb_template_total = kt;
     plan.slot_bnd.assign(plan.n_copy, -1);
@@ -293,6 +295,27 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
       b2 += sh.n_bnd;
     }
     plan.kbb_total = kown;
+    plan.sub_nbr.assign((size_t)(plan.n_copy / 3) * 28, -1);
+    for (int p = 0; p < ns; ++p) {
+      const auto& s = plan.subs[p];
+      int ln = 0;
+      for (int lk = 0; lk < s.nn[2]; ++lk)
+        for (int lj = 0; lj < s.nn[1]; ++lj)
+          for (int li = 0; li < s.nn[0]; ++li, ++ln) {
+            const int ii = iface_index[p][ln];
+            if (ii < 0) continue;
+            const int64_t base = (s.copy_off / 3 + ii) * 28;
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                  const int t = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                  const int a = li + dx, b = lj + dy, c = lk + dz;
+                  if (a < 0 || b < 0 || c < 0 || a >= s.nn[0] || b >= s.nn[1] || c >= s.nn[2]) continue;
+                  const int jj = iface_index[p][a + s.nn[0] * (b + s.nn[1] * c)];
+                  if (jj >= 0) plan.sub_nbr[base + t] = (int32_t)(s.copy_off + 3 * jj);
+                }
+          }
+    }
     for (int64_t sl = 0; sl < plan.n_copy; ++sl)
       if (plan.slot_bnd[sl] < 0) return bad(plan, "internal: interface node off the box boundary"), TFETI_ERR_ARG;
   }

@@ -41,6 +41,7 @@ struct ShapeInfo {
   int n_bnd;          // nodes on the box boundary
   int64_t bnd_off;    // offset into Plan::shape_bln (and 27 x into Plan::shape_tnbr)
   int64_t kbb_off;    // offset of the shape's elastic boundary blocks in the template pool
+  int64_t s_off;      // offset of the shape's elastic dual Schur block (3 n_bnd)^2 in the S pool
 };
 
 // One (global node, component) with its copies.  rows = k (Dirichlet), k-1
@@ -76,7 +77,11 @@ struct Plan {
   // Per copy slot: the boundary index of its node.  Blocks of K are stored per
   // boundary node and neighbour as 3x3 (27 x 9 doubles per boundary node).
   std::vector<int32_t> shape_bln, shape_tnbr, sub_b2s, slot_bnd;
+  // per interface node (3 slots): first slot of each of its 27 stencil neighbours
+  // that is an interface node of the same subdomain, or -1; padded to 28 entries
+  std::vector<int32_t> sub_nbr;
   int64_t kbb_template_total = 0, kbb_total = 0;
+  int64_t s_total = 0;       // floats of all shapes' dual Schur blocks
   // coarse matrix pairs (p, q) with p >= q that share at least one group,
   // and per pair the list of (group, i, j) triples
   std::vector<int32_t> pair_p, pair_q;
