@@ -204,6 +204,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------------------- replicas
+def max_over_ranks(values, device=None):
+    """Element-wise max of per-rank timings over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_value(elapsed_max, steps, world):
+    """Time per load step of the whole job: every rank solves its own replica of the workload
+    for `steps` load steps, so the job completes steps * world load steps in elapsed_max."""
+    return elapsed_max / (steps * world)
+
+
 # --------------------------------------------------------------------------------------- CUDA path
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -254,8 +272,10 @@ def run_gpu(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     timed = []
+    snaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
     for k in range(args.warmup, n_total):
         timed.append(ctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+        ctx.get_state(u=snaps[k - args.warmup])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -288,12 +308,40 @@ def run_gpu(args, rank, world, local_rank):
     elapsed_e2e = time.perf_counter() - t0
     e2e_match = bool(torch.equal(u_host.to(dev), u_final)) if not args.no_e2e else None
 
-    if world > 1:
-        t = torch.tensor([elapsed, elapsed_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed, elapsed_e2e = float(t[0]), float(t[1])
+    # ---- the other arm of the metric: mixed precision on the same load history
+    mixed = None
+    if args.precision == "fp64" and not args.no_mixed:
+        ctx.close()
+        mctx = T.Context(w, stream=stream)
+        mctx.set_precision(True, args.inner_rtol)
+        for k in range(args.warmup):
+            mctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        msnap = torch.zeros(n, dtype=torch.float64, device=dev)
+        mtimed, diffs = [], []
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(args.warmup, n_total):
+            mtimed.append(mctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+            mctx.get_state(u=msnap)
+            ref = snaps[k - args.warmup]
+            diffs.append(torch.linalg.vector_norm(msnap - ref) / torch.linalg.vector_norm(ref))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        melapsed = max_over_ranks([f0.elapsed_time(f1) / 1e3], dev)[0]
+        diffs = [float(d) for d in diffs]
+        mixed = {"value": replica_value(melapsed, args.steps, world), "unit": UNIT, "inner_rtol": args.inner_rtol,
+                 "speedup_vs_fp64": None, "rel_u_diff_vs_fp64_per_step": diffs, "max_rel_u_diff_vs_fp64": max(diffs),
+                 "newton_per_step": [s["newton"] for s in mtimed], "pcg_inner_per_step": [sum(s["pcg"]) for s in mtimed],
+                 "outer_per_step": [sum(s["outer"]) for s in mtimed],
+                 "note": "FP64-refined PCGP: FP32 dual Schur blocks (elastic) and FP32 banded solves (plastic) "
+                         "inside, FP64 residual, projector, coarse solve, return map; same 1e-8 dual test"}
+        mctx.close()
+    elapsed, elapsed_e2e = max_over_ranks([elapsed, elapsed_e2e], dev)
     units = args.steps * world
-    value = elapsed / units
+    value = replica_value(elapsed, args.steps, world)
     pk, pk_kind = peaks()
     avg_f_ms = tm["f_apply_ms_total"] / max(tm["f_apply_launches"], 1)
     flops = tm["f_apply_flops"]
@@ -335,6 +383,9 @@ def run_gpu(args, rank, world, local_rank):
                        "refactored_per_step": [s["refactored"] for s in timed],
                        "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
                        "timed_s": elapsed}}
+    if mixed is not None:
+        mixed["speedup_vs_fp64"] = value / mixed["value"]
+        line["mixed"] = mixed
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cube64_8x8x8":
         s = oracle_sample_subprocess(w.name)
         v = oracle_step_estimate(s, statistics.mean(newton_steps), statistics.mean(pcg_steps))
@@ -361,6 +412,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arm of an FP64 run")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
                     help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
     args = ap.parse_args()

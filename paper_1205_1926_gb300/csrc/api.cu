@@ -124,6 +124,7 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
     cudaMemcpyAsync(c->d_items_pl, pl.data(), sizeof(SolveItem) * pl.size(), cudaMemcpyHostToDevice, c->st);
   c->n_items = (int)c->h_items.size();
   c->n_items32 = (int)c->h_items32.size();
+  c->g_inner_stale = true;
   cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
                   c->st);
   cudaMemcpyAsync(c->d_items32, c->h_items32.data(), sizeof(SolveItem) * c->h_items32.size(),
@@ -395,6 +396,103 @@ PcgOut pcg_core(tfeti_ctx* c, double* x, double* r, double tol_abs, int maxit, b
   return o;
 }
 
+void destroy_inner_graph(tfeti_ctx* c) {
+  if (c->g_inner_exec) cudaGraphExecDestroy(c->g_inner_exec);
+  if (c->g_inner) cudaGraphDestroy(c->g_inner);
+  c->g_inner_exec = nullptr;
+  c->g_inner = nullptr;
+}
+
+// One PCGP iteration on x = dlt, r = rin with FP32 F-applies and device-side scalars;
+// the last kernel sets the WHILE condition `h` of the enclosing graph node.
+void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h) {
+  const long long m = c->M.n_mult;
+  op_project(c, c->rin, c->w);                                   // w = P r
+  op_precond(c, c->w, c->z);                                     // z = F^-1 w
+  op_project(c, c->z, c->y);                                     // y = P z
+  launch_dot2(c->w, c->w, c->y, c->w, m, c->partial, c->sc + kWW, c->sc + kYW, c->st);
+  launch_pcg_pre(c->sc, c->st);
+  launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);             // p = y + beta p
+  op_F32(c, c->pdir, c->Fp);                                     // F p
+  launch_dot(c->pdir, c->Fp, m, c->partial, c->sc + kPFP, c->st);
+  launch_pcg_mid(c->sc, c->st);
+  launch_lam_r_update_g(m, c->pdir, c->Fp, c->dlt, c->rin, c->sc, c->st);
+  launch_pcg_post(c->sc, h, c->st);
+}
+
+int build_inner_graph(tfeti_ctx* c) {
+  destroy_inner_graph(c);
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return cuda_check(c, "cudaGraphCreate");
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_check(c, "cudaGraphConditionalHandleCreate");
+  }
+  cudaGraphNodeParams params{};
+  params.type = cudaGraphNodeTypeConditional;
+  params.conditional.handle = h;
+  params.conditional.type = cudaGraphCondTypeWhile;
+  params.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &params) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_check(c, "cudaGraphAddNode(while)");
+  }
+  cudaGraph_t body = params.conditional.phGraph_out[0];
+  const long long before = c->launches;
+  // capture on the private stream (the context's stream may be the legacy default stream)
+  if (cudaStreamBeginCaptureToGraph(c->st_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+      cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_check(c, "cudaStreamBeginCaptureToGraph");
+  }
+  cudaStream_t saved = c->st;
+  c->st = c->st_cap;
+  enqueue_inner_iteration(c, (unsigned long long)h);
+  c->st = saved;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->st_cap, &captured);
+  c->g_body_kernels = (int)(c->launches - before);
+  c->launches = before;
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_check(c, "cudaStreamEndCapture");
+  }
+  if (cudaGraphInstantiate(&c->g_inner_exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    c->g_inner_exec = nullptr;
+    return cuda_check(c, "cudaGraphInstantiate");
+  }
+  c->g_inner = g;
+  c->g_inner_stale = false;
+  return TFETI_OK;
+}
+
+// Inner PCGP of the mixed-precision refinement on (dlt, rin), run as one graph launch.
+PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
+  PcgOut o;
+  if (c->g_inner_stale || !c->g_inner_exec) {
+    o.status = build_inner_graph(c);
+    if (o.status != TFETI_OK) return o;
+  }
+  launch_pcg_init(c->sc, tol_abs * tol_abs, maxit, c->st);
+  cudaGraphLaunch(c->g_inner_exec, c->st);
+  cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  const double* h = c->h_sc;
+  o.it = (int)h[kIter];
+  c->launches += 1 + (long long)c->g_body_kernels * (long long)h[kBodyRuns];
+  c->f32_launches += (long long)h[kBodyRuns];
+  o.w_norm = std::sqrt(std::max(0.0, h[kLastWW]));
+  o.converged = h[kStopAfter] != 0.0 ? 1 : 0;
+  if (h[kStatus] == 7.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+  if (h[kStatus] == 8.0) o.status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
+  const int st = cuda_check(c, "inner PCGP graph");
+  if (st != TFETI_OK) o.status = st;
+  return o;
+}
+
 int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0, double rtol,
              int maxit, tfeti_pcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -452,8 +550,9 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         if (it >= maxit) break;
         cudaMemsetAsync(c->dlt, 0, sizeof(double) * m, c->st);
         cudaMemcpyAsync(c->rin, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-        PcgOut in = pcg_core(c, c->dlt, c->rin, std::max(c->inner_rtol * wn, 0.5 * rtol * r0),
-                             std::min(maxit - it, 1000), true);
+        const double tol_in = std::max(c->inner_rtol * wn, 0.5 * rtol * r0);
+        PcgOut in = c->use_graphs ? pcg_inner_graph(c, tol_in, std::min(maxit - it, 1000))
+                                  : pcg_core(c, c->dlt, c->rin, tol_in, std::min(maxit - it, 1000), true);
         it += in.it;
         ++outer;
         if (in.status != TFETI_OK) {
@@ -702,15 +801,15 @@ int setup_impl(tfeti_ctx* c) {
   c->f_full = dalloc<double>(c, P.n_dof);
   c->tn = dalloc<double>(c, P.n_dof);
   c->tn2 = dalloc<double>(c, P.n_dof);
-  c->partial = dalloc<double>(c, kRedBlocks);
-  c->sc = dalloc<double>(c, 16);
+  c->partial = dalloc<double>(c, 2 * kRedBlocks);   // two interleaved reductions (launch_dot2)
+  c->sc = dalloc<double>(c, kNumScalars);
   c->d_err = dalloc<int>(c, 1);
-  if (cudaMallocHost(&c->h_sc, 16 * sizeof(double)) != cudaSuccess) throw std::bad_alloc();
+  if (cudaMallocHost(&c->h_sc, kNumScalars * sizeof(double)) != cudaSuccess) throw std::bad_alloc();
   cudaMemsetAsync(c->u, 0, sizeof(double) * P.n_dof, c->st);
   cudaMemsetAsync(c->sig, 0, sizeof(double) * 6 * P.n_gp, c->st);
   cudaMemsetAsync(c->kap, 0, sizeof(double) * P.n_gp, c->st);
   cudaMemsetAsync(c->elem_np, 0, sizeof(int) * P.n_elem, c->st);
-  cudaMemsetAsync(c->sc, 0, sizeof(double) * 16, c->st);
+  cudaMemsetAsync(c->sc, 0, sizeof(double) * kNumScalars, c->st);
   // coarse problem: G G^T assembled once and inverted (G depends only on B and R)
   {
     int* pp = upload(c, P.pair_p);
@@ -771,6 +870,7 @@ int setup_impl(tfeti_ctx* c) {
   cudaEventCreate(&c->fac_e0);
   cudaEventCreate(&c->fac_e1);
   cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&c->st_cap, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   for (int i = 0; i < 8192; ++i) {
@@ -834,9 +934,11 @@ int tfeti_destroy(tfeti_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
   if (c->fac_e1) cudaEventDestroy(c->fac_e1);
+  destroy_inner_graph(c);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->st_cap) cudaStreamDestroy(c->st_cap);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   delete c;
   return TFETI_OK;
@@ -964,6 +1066,7 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   }
   c->precision = mode;
   c->inner_rtol = inner_rtol;
+  c->g_inner_stale = true;
   if (mode == TFETI_PRECISION_MIXED && !c->schur_ready) {
     try {
       c->S32 = dalloc<float>(c, c->plan.s_total);

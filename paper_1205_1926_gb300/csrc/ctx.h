@@ -52,6 +52,13 @@ struct tfeti_ctx {
   int n_items_pl = 0;
   tfeti::SolveItem* d_items_s = nullptr;     // column items for forming S
   cudaStream_t st2 = nullptr;
+  cudaStream_t st_cap = nullptr;     // private stream used only to capture graphs
+  // CUDA graph of the mixed-precision inner PCGP: a WHILE node whose body is one iteration
+  cudaGraph_t g_inner = nullptr;
+  cudaGraphExec_t g_inner_exec = nullptr;
+  bool g_inner_stale = true;
+  int g_body_kernels = 0;
+  bool use_graphs = true;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long own_fac_base = 0;
   std::vector<long long> tmpl_fac_off;   // per shape

@@ -151,6 +151,23 @@ void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const l
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;
+
+// Device scalars of the graph-driven PCGP (indices into the context's scalar array)
+enum PcgScalar {
+  kYW = 0, kYWPrev = 1, kPFP = 2, kWW = 3,
+  kDone = 20, kStatus = 21, kStopAfter = 22, kFirst = 23, kTol2 = 24, kIter = 25, kMaxit = 26, kLastWW = 27,
+  kBodyRuns = 28, kNumScalars = 32
+};
+void launch_pcg_init(double* sc, double tol2, int maxit, cudaStream_t st);
+void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, long long n,
+                 double* partial, double* out1, double* out2, cudaStream_t st);
+void launch_pcg_pre(double* sc, cudaStream_t st);
+void launch_pcg_mid(double* sc, cudaStream_t st);
+void launch_pcg_post(double* sc, unsigned long long cond_handle, cudaStream_t st);
+// guarded updates: no-ops once sc[kDone] is set
+void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st);
+void launch_lam_r_update_g(long long n, const double* p, const double* Fp, double* lam, double* r, const double* sc,
+                           cudaStream_t st);
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st);
 void launch_axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st);
 void launch_p_update(long long n, const double* y, double* p, const double* sc, int first, cudaStream_t st);

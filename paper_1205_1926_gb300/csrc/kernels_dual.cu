@@ -185,6 +185,116 @@ __global__ void k_scalars_after_pfp(double* sc) {
 }
 
 // ---------------------------------------------------------------------------
+// Device-side control of the graph-driven PCGP (Algorithm 3 scalars).  The loop
+// body ends with k_pcg_post, which sets the WHILE condition of the graph: it
+// continues until the stop test of the last iteration held, the iteration limit
+// is reached, a breakdown or a non-finite value was met, or the body has run
+// 2 maxit + 4 times (a hard bound on the device loop).
+// ---------------------------------------------------------------------------
+__global__ void k_pcg_init(double* sc, double tol2, int maxit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc[kDone] = 0.0;
+    sc[kStatus] = 0.0;
+    sc[kStopAfter] = 0.0;
+    sc[kFirst] = 1.0;
+    sc[kTol2] = tol2;
+    sc[kIter] = 0.0;
+    sc[kMaxit] = (double)maxit;
+    sc[kLastWW] = 0.0;
+    sc[kBodyRuns] = 0.0;
+  }
+}
+
+__global__ void k_dot2_partial(const double* __restrict__ x1, const double* __restrict__ y1,
+                               const double* __restrict__ x2, const double* __restrict__ y2, long long n,
+                               double* partial) {
+  __shared__ double red[32];
+  double s1 = 0.0, s2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    s1 += x1[i] * y1[i];
+    s2 += x2[i] * y2[i];
+  }
+  s1 = block_reduce_sum(s1, red);
+  s2 = block_reduce_sum(s2, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s1;
+    partial[gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+__global__ void k_dot2_final(const double* partial, int nparts, double* out1, double* out2) {
+  __shared__ double red[32];
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    s1 += partial[i];
+    s2 += partial[nparts + i];
+  }
+  s1 = block_reduce_sum(s1, red);
+  s2 = block_reduce_sum(s2, red);
+  if (threadIdx.x == 0) {
+    *out1 = s1;
+    *out2 = s2;
+  }
+}
+
+__global__ void k_pcg_pre(double* sc) {
+  if (threadIdx.x || blockIdx.x || sc[kDone] != 0.0) return;
+  const double ww = sc[kWW], yw = sc[kYW];
+  sc[kLastWW] = ww;
+  if (!isfinite(ww) || !isfinite(yw)) {
+    sc[kDone] = 1.0;
+    sc[kStatus] = 8.0;
+    return;
+  }
+  if (sc[kFirst] != 0.0 && !(ww > 0.0)) {   // w^0 = 0: nothing to do
+    sc[kDone] = 1.0;
+    sc[kStopAfter] = 1.0;
+    return;
+  }
+  sc[kStopAfter] = ww <= sc[kTol2] ? 1.0 : 0.0;
+}
+
+__global__ void k_pcg_mid(double* sc) {
+  if (threadIdx.x || blockIdx.x || sc[kDone] != 0.0) return;
+  if (!(sc[kPFP] > 0.0)) {
+    sc[kDone] = 1.0;
+    sc[kStatus] = 7.0;
+  }
+}
+
+__global__ void k_pcg_post(double* sc, cudaGraphConditionalHandle h) {
+  if (threadIdx.x || blockIdx.x) return;
+  sc[kBodyRuns] += 1.0;
+  if (sc[kDone] == 0.0) {
+    sc[kYWPrev] = sc[kYW];
+    sc[kIter] += 1.0;
+    sc[kFirst] = 0.0;
+    if (sc[kStopAfter] != 0.0 || sc[kIter] >= sc[kMaxit]) sc[kDone] = 1.0;
+  }
+  const bool more = sc[kDone] == 0.0 && sc[kBodyRuns] < 2.0 * sc[kMaxit] + 4.0;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_p_update_g(long long n, const double* __restrict__ y, double* p, const double* sc) {
+  if (sc[kDone] != 0.0) return;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool first = sc[kFirst] != 0.0;
+  const double beta = first ? 0.0 : sc[kYW] / sc[kYWPrev];
+  p[i] = first ? y[i] : y[i] + beta * p[i];
+}
+
+__global__ void k_lam_r_update_g(long long n, const double* __restrict__ p, const double* __restrict__ Fp,
+                                 double* lam, double* r, const double* sc) {
+  if (sc[kDone] != 0.0) return;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gamma = sc[kYW] / sc[kPFP];
+  lam[i] += gamma * p[i];
+  r[i] -= gamma * Fp[i];
+}
+
+// ---------------------------------------------------------------------------
 // Coarse matrix G G^T = R^T B^T B R assembled per subdomain pair (p >= q):
 // block[a][b] = sum over groups with copies i in p and j in q of
 // R_p[slot_i][a] (sum_rows B[row][i] B[row][j]) R_q[slot_j][b].
@@ -392,6 +502,31 @@ void launch_lam_r_update(long long n, const double* p, const double* Fp, double*
                          cudaStream_t st) {
   k_scalars_after_pfp<<<1, 32, 0, st>>>(sc);
   if (n > 0) k_lam_r_update<<<blocks_for(n, 256), 256, 0, st>>>(n, p, Fp, lam, r, sc);
+}
+
+void launch_pcg_init(double* sc, double tol2, int maxit, cudaStream_t st) {
+  k_pcg_init<<<1, 32, 0, st>>>(sc, tol2, maxit);
+}
+
+void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, long long n,
+                 double* partial, double* out1, double* out2, cudaStream_t st) {
+  k_dot2_partial<<<kRedBlocks, 256, 0, st>>>(x1, y1, x2, y2, n, partial);
+  k_dot2_final<<<1, 256, 0, st>>>(partial, kRedBlocks, out1, out2);
+}
+
+void launch_pcg_pre(double* sc, cudaStream_t st) { k_pcg_pre<<<1, 32, 0, st>>>(sc); }
+void launch_pcg_mid(double* sc, cudaStream_t st) { k_pcg_mid<<<1, 32, 0, st>>>(sc); }
+void launch_pcg_post(double* sc, unsigned long long h, cudaStream_t st) {
+  k_pcg_post<<<1, 32, 0, st>>>(sc, (cudaGraphConditionalHandle)h);
+}
+
+void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st) {
+  if (n > 0) k_p_update_g<<<blocks_for(n, 256), 256, 0, st>>>(n, y, p, sc);
+}
+
+void launch_lam_r_update_g(long long n, const double* p, const double* Fp, double* lam, double* r, const double* sc,
+                           cudaStream_t st) {
+  if (n > 0) k_lam_r_update_g<<<blocks_for(n, 256), 256, 0, st>>>(n, p, Fp, lam, r, sc);
 }
 
 void launch_coarse_assemble(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
