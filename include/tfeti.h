@@ -166,7 +166,7 @@ typedef struct tfeti_pcg_info {
     int32_t iterations;        /* PCGP iterations j                                     */
     int32_t converged;         /* 1 if ||w|| <= rtol ||r^0||                             */
     int32_t used_lambda0;      /* 1 if a caller lambda0 was used as the start           */
-    int32_t f_applies;         /* F-applies including set-up and recovery               */
+    int32_t f_applies;         /* FP64 subdomain-solve passes incl. set-up and recovery */
     double  r0_norm;           /* ||r^0|| = ||d~||                                      */
     double  w_norm;            /* last ||w^{j-1}||                                      */
     double  seconds;           /* wall time of the call                                 */
@@ -178,7 +178,10 @@ typedef struct tfeti_pcg_info {
  * decomposed right-hand side f (device [n_dof]): lambda_Im = N^T H e,
  * d~ = d - F lambda_Im, PCGP with the lumped preconditioner and the stopping
  * test ||w^{j-1}|| <= rtol ||r^0|| after the updates, then alpha = H N (d - F lambda)
- * and u = K^+ (f - B^T lambda) + R alpha.  u_out: device [n_dof]; lambda_out:
+ * and u = K^+ (f - B^T lambda) + R alpha.  By linearity d - F lambda =
+ * B K^+ (f - B^T lambda), so d~ and the recovery each take one subdomain-solve pass
+ * v = K^+ (f - B^T lambda) (the residual B v and u = v + R alpha share it) instead of
+ * the two of d and F lambda.  u_out: device [n_dof], nullable; lambda_out:
  * device [n_mult], nullable; lambda0: device [n_mult], nullable -- if given,
  * lambda_Ker starts from P_N lambda0 instead of o.  info: host, nullable.
  * Errors: TFETI_ERR_NOT_CONVERGED (last iterate written), TFETI_ERR_BREAKDOWN,
@@ -212,8 +215,11 @@ int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double n
  * FP64.  TFETI_PRECISION_MIXED: the PCGP of Algorithm 3 runs as FP64 iterative
  * refinement of the dual problem -- the true residual r = d~ - F lambda_Ker is
  * formed with FP64 F-applies and corrected by inner PCGP solves (same projector
- * and preconditioner, FP64 vectors) whose F-applies use FP32 subdomain solves
- * with the factors rounded to FP32; each inner solve reduces its projected
+ * and preconditioner, FP64 vectors) whose F-applies are FP32: subdomains still
+ * on their shape's elastic tangent apply the shape's dual Schur block
+ * S = (K^+)_{boundary,boundary} (formed once in FP64, stored FP32) as one GEMM per
+ * shape, the others run FP32 banded solves with their factors rounded to FP32;
+ * each inner solve reduces its projected
  * residual by inner_rtol (0 < inner_rtol < 1, e.g. 1e-3).  The stopping test
  * ||P r|| <= rtol ||d~|| is applied to the FP64 residual, so both modes reach
  * the same dual residual.  The paper has no mixed-precision variant; this is an
@@ -221,6 +227,13 @@ int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double n
 #define TFETI_PRECISION_FP64  0
 #define TFETI_PRECISION_MIXED 1
 int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);
+
+/* Launch mode of the mixed-precision inner PCGP.  enable != 0 (default): each
+ * inner solve is one CUDA graph launch whose body is one iteration inside a
+ * WHILE conditional node, the scalars staying on the device.  enable == 0: the
+ * same kernels launched one by one from the host, with the same arithmetic and
+ * results (profilers that do not see into conditional graph bodies need this). */
+int tfeti_set_graphs(tfeti_ctx* ctx, int32_t enable);
 
 /* Load magnitude of the workloads: t_y = sigma_y / max_g sqrt(3/2) ||dev sigma_g||
  * for the elastic response to the unit traction `dir` (host double[3]) on the

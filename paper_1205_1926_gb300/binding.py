@@ -84,6 +84,7 @@ SIGNATURES = {
     "ssn_time_step": (C.c_int, [_P, _P, _I, _D, _D, _I, _I, C.POINTER(StepInfo)]),
     "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
+    "tfeti_set_graphs": (C.c_int, [_P, _I]),
     "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
@@ -271,6 +272,10 @@ class Context:
     def set_precision(self, mixed: bool, inner_rtol: float = 1e-3):
         """FP64 dual solve (default) or FP64-refined PCGP with FP32 inner F-applies."""
         return self._check(self.lib.tfeti_set_precision(self.h, 1 if mixed else 0, inner_rtol), "tfeti_set_precision")
+
+    def set_graphs(self, enable: bool):
+        """Inner PCGP of the mixed mode as one CUDA graph launch (default) or kernel by kernel."""
+        return self._check(self.lib.tfeti_set_graphs(self.h, 1 if enable else 0), "tfeti_set_graphs")
 
     def first_yield_traction(self, direction, rtol=1e-12) -> float:
         arr = (C.c_double * 3)(*direction)

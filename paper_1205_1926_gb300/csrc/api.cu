@@ -146,23 +146,37 @@ SolveArgs solve_args(tfeti_ctx* c, bool fp32 = false) {
 }
 
 // ---- dual operators ---------------------------------------------------------
+void collect_events(tfeti_ctx* c);
+
+// One FP64 subdomain-solve pass over all subdomains, bracketed by timing events
+// when timing is on (every counted pass is timed: a full event pool is drained first).
+void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
+  cudaEvent_t e1 = nullptr;
+  if (c->events) {
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+      sync(c);
+      collect_events(c);
+    }
+    if (c->ev_used + 2 <= c->ev_pool.size()) {
+      cudaEventRecord(c->ev_pool[c->ev_used++], c->st);
+      e1 = c->ev_pool[c->ev_used++];
+    }
+  }
+  launch_sub_solve(c->M, a, c->solve_smem, c->st);
+  if (e1) cudaEventRecord(e1, c->st);
+  c->launches += 1;
+  c->f_launches += 1;
+}
+
 void op_F(tfeti_ctx* c, const double* x, double* yv) {
   SolveArgs a = solve_args(c);
   a.lam = x;
   a.cbuf = c->cbuf;
   a.in_mode = 0;
   a.out_mode = 0;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->events && c->ev_used + 2 <= c->ev_pool.size()) {
-    e0 = c->ev_pool[c->ev_used++];
-    e1 = c->ev_pool[c->ev_used++];
-    cudaEventRecord(e0, c->st);
-  }
-  launch_sub_solve(c->M, a, c->solve_smem, c->st);
-  if (e1) cudaEventRecord(e1, c->st);
+  timed_sub_solve(c, a);
   launch_contract(c->M, c->cbuf, yv, c->st);
-  c->launches += 2;
-  c->f_launches += 1;
+  c->launches += 1;
 }
 
 // F x with FP32 subdomain solves (inner iterations of the mixed-precision PCGP).
@@ -493,37 +507,43 @@ PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
   return o;
 }
 
+// Residual solve: vsol = K^+(f - B^T lam) per subdomain and r_out = B vsol.  By
+// linearity B K^+(f - B^T lam) = d - F lam, so one subdomain-solve pass gives both
+// the dual residual of Algorithm 3 and the primal part of the recovered u.
+void residual_solve(tfeti_ctx* c, const double* f, const double* lam, double* r_out) {
+  SolveArgs a = solve_args(c);
+  a.src = f;
+  a.lam = lam;
+  a.cbuf = c->cbuf;
+  a.dst = c->vsol;
+  a.in_mode = 1;
+  a.out_mode = 3;
+  timed_sub_solve(c, a);
+  launch_contract(c->M, c->cbuf, r_out, c->st);
+  c->launches += 1;
+}
+
 int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0, double rtol,
              int maxit, tfeti_pcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   const DevMesh& M = c->M;
   const long long m = M.n_mult;
   const long long f_before = c->f_launches, f32_before = c->f32_launches;
-  // d = B K^+ f
-  SolveArgs a = solve_args(c);
-  a.src = f;
-  a.cbuf = c->cbuf;
-  a.in_mode = 1;
-  a.out_mode = 0;
-  launch_sub_solve(M, a, c->solve_smem, c->st);
-  launch_contract(M, c->cbuf, c->dvec, c->st);
   // e = -R^T f ; lambda_Im = N^T H e = -B R (H e)
   launch_G_apply(M, nullptr, f, c->ev, -1.0, c->st);
   launch_gemv(c->H, c->l, c->ev, 1.0, c->hx, c->st);
   launch_GT_update(M, nullptr, 0.0, c->hx, -1.0, c->lam_im, c->st);
-  c->launches += 5;
-  // d~ = d - F lambda_Im ; r^0 = d~
-  op_F(c, c->lam_im, c->tm);
-  launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->r, c->st);
-  c->launches += 1;
+  c->launches += 3;
+  // d~ = d - F lambda_Im = B K^+(f - B^T lambda_Im) ; r^0 = d~
+  residual_solve(c, f, c->lam_im, c->r);
   const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
-  cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);   // d~
   cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
+  bool v_current = true;   // vsol and r belong to lambda = lambda_Im + lambda_Ker
   int used_l0 = 0;
   if (lambda0) {
     op_project(c, lambda0, c->lamk);
-    op_F(c, c->lamk, c->tm);
-    launch_axpby(m, 1.0, c->r, -1.0, c->tm, c->r, c->st);
+    launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
+    residual_solve(c, f, c->lam, c->r);      // r = d~ - F lambda_Ker
     c->launches += 1;
     used_l0 = 1;
   }
@@ -532,9 +552,8 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   if (m > 0 && r0 > 0.0) {
     if (c->precision == TFETI_PRECISION_MIXED) {
       // FP64 iterative refinement of the dual problem: the true residual
-      // r = d~ - F lambda_Ker (FP64 F) is corrected by inner PCGP solves whose
-      // F-applies use FP32 subdomain solves; the stopping test is Algorithm 3's,
-      // on the FP64 residual.
+      // r = d~ - F lambda_Ker (FP64 solves) is corrected by inner PCGP solves whose
+      // F-applies are FP32; the stopping test is Algorithm 3's, on the FP64 residual.
       for (outer = 0; outer < 100;) {
         op_project(c, c->r, c->w);
         const double wn = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
@@ -557,11 +576,12 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         ++outer;
         if (in.status != TFETI_OK) {
           status = in.status;
+          v_current = false;
           break;
         }
         launch_axpby(m, 1.0, c->lamk, 1.0, c->dlt, c->lamk, c->st);
-        op_F(c, c->lamk, c->tm);
-        launch_axpby(m, 1.0, c->dtil, -1.0, c->tm, c->r, c->st);   // r = d~ - F lambda_Ker
+        launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
+        residual_solve(c, f, c->lam, c->r);    // r = d~ - F lambda_Ker
         c->launches += 2;
       }
     } else {
@@ -570,30 +590,22 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
       converged = o.converged;
       status = o.status;
       w_norm = o.w_norm;
+      v_current = false;
     }
   } else {
     converged = 1;
   }
   // lambda = lambda_Im + lambda_Ker ; alpha = H N (d - F lambda) ; u = K^+(f - B^T lambda) + R alpha
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
-  if (c->precision == TFETI_PRECISION_MIXED && m > 0 && r0 > 0.0) {
-    // d - F lambda = d~ - F lambda_Ker is the FP64 residual the refinement formed last
-    cudaMemcpyAsync(c->tm, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-  } else {
-    op_F(c, c->lam, c->tm);
-    launch_axpby(m, 1.0, c->dvec, -1.0, c->tm, c->tm, c->st);
-  }
-  launch_G_apply(M, c->tm, nullptr, c->gx, -1.0, c->st);
+  c->launches += 1;
+  if (!v_current) residual_solve(c, f, c->lam, c->r);
+  launch_G_apply(M, c->r, nullptr, c->gx, -1.0, c->st);
   launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
-  SolveArgs b = solve_args(c);
-  b.src = f;
-  b.lam = c->lam;
-  b.dst = u_out;
-  b.alpha = c->alpha;
-  b.in_mode = 1;
-  b.out_mode = 1;
-  launch_sub_solve(M, b, c->solve_smem, c->st);
-  c->launches += 5;
+  c->launches += 2;
+  if (u_out) {
+    launch_add_R_alpha(M, c->vsol, c->alpha, u_out, (int)c->plan.max_ndof, c->st);
+    c->launches += 1;
+  }
   if (lambda_out) cudaMemcpyAsync(lambda_out, c->lam, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   cudaMemsetAsync(c->sc + 6, 0, sizeof(double), c->st);
   int herr = 0;
@@ -611,7 +623,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     info->iterations = it;
     info->converged = converged;
     info->used_lambda0 = used_l0;
-    info->f_applies = (int)(c->f_launches - f_before) + 2;
+    info->f_applies = (int)(c->f_launches - f_before);
     info->f32_applies = (int)(c->f32_launches - f32_before);
     info->outer_iterations = outer;
     info->r0_norm = r0;
@@ -790,9 +802,10 @@ int setup_impl(tfeti_ctx* c) {
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
-  for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->dvec, &c->tm,
-                     &c->dtil, &c->dlt, &c->rin})
+  for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->tm, &c->dlt,
+                     &c->rin})
     *v = dalloc<double>(c, m);
+  c->vsol = dalloc<double>(c, (size_t)P.n_dof);
   c->H = dalloc<double>(c, (size_t)c->l * c->l);
   c->gx = dalloc<double>(c, c->l);
   c->hx = dalloc<double>(c, c->l);
@@ -1080,6 +1093,13 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     if (st != TFETI_OK) return st;
   }
   return cuda_check(c, "tfeti_set_precision");
+}
+
+int tfeti_set_graphs(tfeti_ctx* c, int32_t enable) {
+  if (!c) return TFETI_ERR_ARG;
+  c->use_graphs = enable != 0;
+  c->g_inner_stale = true;
+  return TFETI_OK;
 }
 
 int tfeti_first_yield_traction(tfeti_ctx* c, const double* dir, double rtol, double* t_y) {

@@ -40,7 +40,7 @@ struct tfeti_ctx {
   size_t solve_smem32 = 0;
   int precision = 0;                 // TFETI_PRECISION_*
   double inner_rtol = 1e-3;
-  double *dtil = nullptr, *dlt = nullptr, *rin = nullptr;
+  double *dlt = nullptr, *rin = nullptr;
   long long f32_launches = 0;
   // dual Schur blocks of the shapes' elastic templates (mixed precision)
   float* S32 = nullptr;
@@ -79,7 +79,8 @@ struct tfeti_ctx {
   int max_bnd = 0;
   // dual
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
-         *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *dvec = nullptr, *tm = nullptr;
+         *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *tm = nullptr;
+  double* vsol = nullptr;   // K^+(f - B^T lambda) of the last residual solve, device [n_dof]
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;

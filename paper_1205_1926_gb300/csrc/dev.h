@@ -103,7 +103,7 @@ void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const l
 
 // Subdomain K^+ solve.  in_mode 0: x = B^T lam at the interface slots (zero
 // elsewhere); 1: x = src - B^T lam (lam nullable).  out_mode 0: interface slots
-// to cbuf; 1: full local vector to dst (+ R alpha if alpha != null).
+// to cbuf; 1: full local vector to dst (+ R alpha if alpha != null); 3: both.
 struct SolveArgs {
   const double* lam;
   const double* src;
@@ -146,6 +146,9 @@ void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full,
 void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
                       cudaStream_t st);
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st);
+// out = v + R alpha per subdomain (u = K^+(f - B^T lambda) + R alpha); device [n_dof].
+void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,
+                       cudaStream_t st);
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
                    cudaStream_t st, int max_copy);
 

@@ -436,12 +436,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     const int p = item.sub[r];
     const SubDev& S = M.subs[p];
     const T* x = vec + r * npad;
-    if (a.out_mode == 0) {
+    if (a.out_mode == 0 || a.out_mode == 3) {
       for (int s = tid; s < S.n_copy; s += nt) {
         const long long slot = S.copy_off + s;
         a.cbuf[slot] = double(x[M.slot_ldof[slot]]);
       }
-    } else {
+    }
+    if (a.out_mode == 1 || a.out_mode == 3) {
       const double* Rb = M.R + S.r_off;
       for (int i = tid; i < n; i += nt) {
         double v = double(x[i]);

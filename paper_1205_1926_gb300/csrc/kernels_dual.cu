@@ -84,6 +84,20 @@ __global__ void k_GT_update(DevMesh M, const double* __restrict__ x, double ax, 
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
 }
 
+// out = v + R_p alpha_p on the dofs of subdomain p = blockIdx.y.
+__global__ void k_add_R_alpha(DevMesh M, const double* __restrict__ v, const double* __restrict__ alpha,
+                              double* out) {
+  const SubDev& S = M.subs[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n_dof) return;
+  const double* r = M.R + S.r_off + (long long)i * 6;
+  const double* al = alpha + 6 * (long long)blockIdx.y;
+  double s = v[S.dof_off + i];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s += r[c] * al[c];
+  out[S.dof_off + i] = s;
+}
+
 // y = alpha * A x, A dense n x n row-major; one warp per row.
 __global__ void k_gemv(const double* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
                        double* y) {
@@ -476,6 +490,12 @@ void launch_GT_update(const DevMesh& M, const double* x, double ax, const double
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
   k_gemv<<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+}
+
+void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,
+                       cudaStream_t st) {
+  if (M.n_sub <= 0 || max_ndof <= 0) return;
+  k_add_R_alpha<<<dim3((unsigned)((max_ndof + 255) / 256), (unsigned)M.n_sub), 256, 0, st>>>(M, v, alpha, out);
 }
 
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,

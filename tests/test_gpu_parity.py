@@ -368,7 +368,16 @@ def test_cube64_history_matches_oracle_record():
         ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
         prev = a
         info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
-        assert info["converged"] and info["newton"] == ref["newton"], (ref["step"], info, ref)
+        # The last Newton criteria sit at the floor left by the PCGP tolerance; where the oracle's
+        # criterion at the stopping iteration is within 10x of the Newton tolerance, rounding decides
+        # whether the test passes there (like the Phi = 0 tie of the return map), so one more or one
+        # fewer iteration is accepted there.
+        tol, crit = w.newton_tol, ref["criterion"]
+        one_more = 0.1 * tol < crit[-1] <= tol
+        one_fewer = len(crit) >= 2 and tol < crit[-2] <= 10 * tol
+        assert info["converged"] and (info["newton"] == ref["newton"] or
+                                      (one_more and info["newton"] == ref["newton"] + 1) or
+                                      (one_fewer and info["newton"] == ref["newton"] - 1)), (ref["step"], info, ref)
         assert all(abs(a_ - b_) <= 1 for a_, b_ in zip(info["pcg"], ref["pcg"])), (ref["step"], info["pcg"], ref["pcg"])
         assert abs(info["plastic_committed"] - ref["plastic_committed"]) <= max(2, 0.005 * ref["plastic_committed"])
         ctx.get_state(u=u)
