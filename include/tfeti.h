@@ -214,16 +214,19 @@ int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double n
 /* Arithmetic of the dual solve.  TFETI_PRECISION_FP64 (default): Algorithm 3 in
  * FP64.  TFETI_PRECISION_MIXED: the PCGP of Algorithm 3 runs as FP64 iterative
  * refinement of the dual problem -- the true residual r = d~ - F lambda_Ker is
- * formed with FP64 F-applies and corrected by inner PCGP solves (same projector
- * and preconditioner, FP64 vectors) whose F-applies are FP32: subdomains still
- * on their shape's elastic tangent apply the shape's dual Schur block
- * S = (K^+)_{boundary,boundary} (formed once in FP64, stored FP32) as one GEMM per
- * shape, the others run FP32 banded solves with their factors rounded to FP32;
- * each inner solve reduces its projected
- * residual by inner_rtol (0 < inner_rtol < 1, e.g. 1e-3).  The stopping test
+ * formed with FP64 subdomain solves and corrected by inner PCGP solves (FP64
+ * vectors and scalars) whose operators are FP32: the projector with FP32 copies
+ * of R and H, the lumped preconditioner with FP32 boundary blocks, and F with
+ * subdomains still on their shape's elastic tangent applying the shape's dual
+ * Schur block S = (K^+)_{boundary,boundary} (formed once in FP64, stored FP32) as
+ * one GEMM per shape and the others running FP32 banded solves with their factors
+ * rounded to FP32.  Each correction is projected in FP64 before it is added, so
+ * lambda_Ker stays in Ker N.  Each inner solve reduces its projected residual by
+ * inner_rtol (0 < inner_rtol < 1, e.g. 1e-3).  The stopping test
  * ||P r|| <= rtol ||d~|| is applied to the FP64 residual, so both modes reach
  * the same dual residual.  The paper has no mixed-precision variant; this is an
- * implementation choice for GPUs whose FP64 rate is far below their FP32 rate. */
+ * implementation choice for GPUs whose FP64 rate is far below their FP32 rate.
+ * Switching to MIXED allocates the FP32 copies (the first time) and forms S. */
 #define TFETI_PRECISION_FP64  0
 #define TFETI_PRECISION_MIXED 1
 int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);

@@ -255,6 +255,22 @@ void op_project(tfeti_ctx* c, const double* x, double* out) {
   c->launches += 3;
 }
 
+// FP32 projector and preconditioner of the inner iterations of the mixed mode.
+void op_project32(tfeti_ctx* c, const double* x, double* out) {
+  launch_project32(c->M, c->R32, c->H32, c->l, x, c->gx, c->hx, out, c->st);
+  c->launches += 3;
+}
+
+void op_precond32(tfeti_ctx* c, const double* x, double* out) {
+  if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
+    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
+    launch_contract(c->M, c->cbuf, out, c->st);
+    c->launches += 2;
+  } else {
+    cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
+  }
+}
+
 void op_precond(tfeti_ctx* c, const double* x, double* out) {
   if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
     launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
@@ -335,7 +351,8 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     }
   }
   if (!list.empty())
-    launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, 0, c->st);
+    launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
+                    c->kbb32, 0, c->st);
   launch_internal_force(M, c->dsig, df, c->f_full, c->st);
   c->launches += 2;
   if (f_out && f_out != c->f_full)
@@ -355,10 +372,17 @@ PcgOut pcg_core(tfeti_ctx* c, double* x, double* r, double tol_abs, int maxit, b
   const long long m = c->M.n_mult;
   PcgOut o;
   for (int j = 1; j <= maxit; ++j) {
-    op_project(c, r, c->w);                          // w = P r
-    launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
-    op_precond(c, c->w, c->z);                       // z = F^-1 w
-    op_project(c, c->z, c->y);                       // y = P z
+    if (fp32) {                                      // inner iterations of the mixed mode
+      op_project32(c, r, c->w);
+      launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
+      op_precond32(c, c->w, c->z);
+      op_project32(c, c->z, c->y);
+    } else {
+      op_project(c, r, c->w);                        // w = P r
+      launch_dot(c->w, c->w, m, c->partial, c->sc + 3, c->st);
+      op_precond(c, c->w, c->z);                     // z = F^-1 w
+      op_project(c, c->z, c->y);                     // y = P z
+    }
     launch_dot(c->y, c->w, m, c->partial, c->sc + 0, c->st);
     c->launches += 4;
     cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->st);
@@ -421,9 +445,9 @@ void destroy_inner_graph(tfeti_ctx* c) {
 // the last kernel sets the WHILE condition `h` of the enclosing graph node.
 void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h) {
   const long long m = c->M.n_mult;
-  op_project(c, c->rin, c->w);                                   // w = P r
-  op_precond(c, c->w, c->z);                                     // z = F^-1 w
-  op_project(c, c->z, c->y);                                     // y = P z
+  op_project32(c, c->rin, c->w);                                 // w = P r
+  op_precond32(c, c->w, c->z);                                   // z = F^-1 w
+  op_project32(c, c->z, c->y);                                   // y = P z
   launch_dot2(c->w, c->w, c->y, c->w, m, c->partial, c->sc + kWW, c->sc + kYW, c->st);
   launch_pcg_pre(c->sc, c->st);
   launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);             // p = y + beta p
@@ -568,7 +592,9 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         }
         if (it >= maxit) break;
         cudaMemsetAsync(c->dlt, 0, sizeof(double) * m, c->st);
-        cudaMemcpyAsync(c->rin, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+        // the inner right-hand side is P r (same correction equation: P F P delta = P r), so
+        // the FP32 projections inside work relative to ||P r||, not to ||r||
+        cudaMemcpyAsync(c->rin, c->w, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
         const double tol_in = std::max(c->inner_rtol * wn, 0.5 * rtol * r0);
         PcgOut in = c->use_graphs ? pcg_inner_graph(c, tol_in, std::min(maxit - it, 1000))
                                   : pcg_core(c, c->dlt, c->rin, tol_in, std::min(maxit - it, 1000), true);
@@ -579,7 +605,10 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
           v_current = false;
           break;
         }
-        launch_axpby(m, 1.0, c->lamk, 1.0, c->dlt, c->lamk, c->st);
+        // the correction comes from FP32 projections: project it in FP64 so that
+        // lambda_Ker stays in Ker N to FP64 accuracy
+        op_project(c, c->dlt, c->tm);
+        launch_axpby(m, 1.0, c->lamk, 1.0, c->tm, c->lamk, c->st);
         launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
         residual_solve(c, f, c->lam, c->r);    // r = d~ - F lambda_Ker
         c->launches += 2;
@@ -875,7 +904,7 @@ int setup_impl(tfeti_ctx* c) {
     std::vector<long long> kt;
     for (const ShapeInfo& sh : P.shapes) kt.push_back(sh.kbb_off);
     long long* dkt = upload(c, kt);
-    launch_kbb_fill(M, dl, dkt, (int)reps.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, 1, c->st);
+    launch_kbb_fill(M, dl, dkt, (int)reps.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, nullptr, 1, c->st);
     for (int p = 0; p < ns; ++p) c->h_kbb_off[p] = P.shapes[c->h_subs[p].shape].kbb_off;
     cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
   }
@@ -1080,6 +1109,20 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   c->precision = mode;
   c->inner_rtol = inner_rtol;
   c->g_inner_stale = true;
+  if (mode == TFETI_PRECISION_MIXED && !c->R32) {
+    // FP32 copies of R, H and the boundary blocks for the inner projector and preconditioner
+    try {
+      c->R32 = dalloc<float>(c, c->plan.r_total);
+      c->H32 = dalloc<float>(c, (size_t)c->l * c->l);
+      c->kbb32 = dalloc<float>(c, c->plan.kbb_template_total + c->plan.kbb_total);
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+    launch_to_f32(c->M.R, c->R32, c->plan.r_total, c->st);
+    launch_to_f32(c->H, c->H32, (long long)c->l * c->l, c->st);
+    launch_to_f32(c->kbb, c->kbb32, c->plan.kbb_template_total + c->plan.kbb_total, c->st);
+    c->launches += 3;
+  }
   if (mode == TFETI_PRECISION_MIXED && !c->schur_ready) {
     try {
       c->S32 = dalloc<float>(c, c->plan.s_total);

@@ -81,6 +81,8 @@ struct tfeti_ctx {
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
          *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *tm = nullptr;
   double* vsol = nullptr;   // K^+(f - B^T lambda) of the last residual solve, device [n_dof]
+  // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)
+  float *R32 = nullptr, *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;

@@ -85,9 +85,11 @@ void launch_elem_correction(const DevMesh& M, GPData gp, int* elem_np, int* sub_
 void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const int* elem_np, const double* dKe,
                       double* band, const long long* band_off_list, int elastic_only, int max_rows, int max_bw,
                       cudaStream_t st);
-// Boundary 3x3 blocks of K for the listed subdomains (elastic_only: the shape's elastic template).
+// Boundary 3x3 blocks of K for the listed subdomains (elastic_only: the shape's elastic template);
+// also rounded to FP32 into kbb32 at the same offsets when kbb32 != null.
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
-                     const int* elem_np, const double* dKe, double* kbb, int elastic_only, cudaStream_t st);
+                     const int* elem_np, const double* dKe, double* kbb, float* kbb32, int elastic_only,
+                     cudaStream_t st);
 void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st);
 void launch_apply_K(const DevMesh& M, const int* elem_np, const double* dKe, const double* x, double* y,
                     cudaStream_t st);
@@ -137,6 +139,8 @@ void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int 
 void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* X,
                                const float* S, double* cbuf, cudaStream_t st);
 // FP32 copies of factor records (offsets in entries, same for both pools)
+// dst[i] = (float) src[i], i < n.
+void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_list, int n_list, long long len,
                        cudaStream_t st);
 
@@ -151,6 +155,13 @@ void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, 
                        cudaStream_t st);
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
                    cudaStream_t st, int max_copy);
+// FP32 operators of the inner iterations of the mixed mode (FP64 vectors in and out):
+// P x with the FP32 copies of R and H, and the lumped preconditioner with the FP32
+// copy of the boundary blocks.  gx, hx: coarse work vectors [l].
+void launch_project32(const DevMesh& M, const float* R32, const float* H32, long long l, const double* x,
+                      double* gx, double* hx, double* out, cudaStream_t st);
+void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
+                     cudaStream_t st, int max_copy);
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;

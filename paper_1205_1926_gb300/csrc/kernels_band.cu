@@ -529,4 +529,15 @@ void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_lis
   k_to_f32<<<grid, 256, 0, st>>>(fac, fac32, off_list, len);
 }
 
+namespace {
+__global__ void k_to_f32_flat(const double* __restrict__ src, float* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+}  // namespace
+
+void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
+  if (n > 0) k_to_f32_flat<<<1024, 256, 0, st>>>(src, dst, n);
+}
+
 }  // namespace tfeti

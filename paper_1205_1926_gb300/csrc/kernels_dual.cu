@@ -32,39 +32,43 @@ __device__ double block_reduce_sum(double v, double* red) {
 }
 
 // gx[6p+c] = scale * (R_p^T (B^T x))_c over the interface slots of p (x_lam), or
-// scale * (R_p^T x_p)_c over all dofs of p (x_full).  One CTA per subdomain.
-__global__ void k_G_apply(DevMesh M, const double* __restrict__ x_lam, const double* __restrict__ x_full,
-                          double* gx, double scale) {
+// scale * (R_p^T x_p)_c over all dofs of p (x_full).  One CTA per subdomain.  T is the
+// type of R (M.R in FP64, its FP32 copy for the inner iterations of the mixed mode)
+// and of the products and per-thread sums.
+template <typename T>
+__global__ void k_G_apply(DevMesh M, const T* __restrict__ Rall, const double* __restrict__ x_lam,
+                          const double* __restrict__ x_full, double* gx, double scale) {
   __shared__ double red[32];
   const int p = blockIdx.x;
   const SubDev S = M.subs[p];
-  const double* R = M.R + S.r_off;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const T* R = Rall + S.r_off;
+  T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   if (x_lam) {
     for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) {
       const long long slot = S.copy_off + s;
-      const double v = bt_at_slot(M, x_lam, slot);
-      const double* r = R + (long long)M.slot_ldof[slot] * 6;
+      const T v = T(bt_at_slot(M, x_lam, slot));
+      const T* r = R + (long long)M.slot_ldof[slot] * 6;
 #pragma unroll
       for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
     }
   } else {
     for (int i = threadIdx.x; i < S.n_dof; i += blockDim.x) {
-      const double v = x_full[S.dof_off + i];
-      const double* r = R + (long long)i * 6;
+      const T v = T(x_full[S.dof_off + i]);
+      const T* r = R + (long long)i * 6;
 #pragma unroll
       for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
     }
   }
   for (int c = 0; c < 6; ++c) {
-    const double s = block_reduce_sum(acc[c], red);
+    const double s = block_reduce_sum(double(acc[c]), red);
     if (threadIdx.x == 0) gx[6 * (long long)p + c] = scale * s;
   }
 }
 
-// out[row] = ax * x[row] + bh * (B R h)[row]   (x nullable)
-__global__ void k_GT_update(DevMesh M, const double* __restrict__ x, double ax, const double* __restrict__ h,
-                            double bh, double* out) {
+// out[row] = ax * x[row] + bh * (B R h)[row]   (x nullable); T as in k_G_apply.
+template <typename T>
+__global__ void k_GT_update(DevMesh M, const T* __restrict__ Rall, const double* __restrict__ x, double ax,
+                            const double* __restrict__ h, double bh, double* out) {
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= M.n_mult) return;
   const GroupDev& g = M.groups[M.row_group[row]];
@@ -74,12 +78,12 @@ __global__ void k_GT_update(DevMesh M, const double* __restrict__ x, double ax, 
   for (int j = j0; j <= j1; ++j) {
     const long long slot = g.slot[j];
     const int q = g.sub[j];
-    const double* r = M.R + M.subs[q].r_off + (long long)M.slot_ldof[slot] * 6;
+    const T* r = Rall + M.subs[q].r_off + (long long)M.slot_ldof[slot] * 6;
     const double* hq = h + 6 * (long long)q;
-    double rh = 0.0;
+    T rh = T(0);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) rh += r[c] * hq[c];
-    s += (g.dirichlet ? 1.0 : M.helm[(rr + 1) * 8 + j]) * rh;
+    for (int c = 0; c < 6; ++c) rh += r[c] * T(hq[c]);
+    s += (g.dirichlet ? 1.0 : M.helm[(rr + 1) * 8 + j]) * double(rh);
   }
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
 }
@@ -98,34 +102,38 @@ __global__ void k_add_R_alpha(DevMesh M, const double* __restrict__ v, const dou
   out[S.dof_off + i] = s;
 }
 
-// y = alpha * A x, A dense n x n row-major; one warp per row.
-__global__ void k_gemv(const double* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
+// y = alpha * A x, A dense n x n row-major (T: FP64, or its FP32 copy); one warp per row.
+template <typename T>
+__global__ void k_gemv(const T* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
                        double* y) {
   const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double* a = A + row * n;
-  double s = 0.0;
-  for (long long j = lane; j < n; j += 32) s += a[j] * x[j];
+  const T* a = A + row * n;
+  T s = T(0);
+  for (long long j = lane; j < n; j += 32) s += a[j] * T(x[j]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = alpha * s;
+  if (lane == 0) y[row] = alpha * double(s);
 }
 
 // Lumped preconditioner, subdomain part: v = K_bb (B^T w) on the interface slots.
 // K_bb comes from the subdomain's boundary blocks (kbb + kbb_off[p]): its shape's
 // elastic template or its own blocks when it has plastic points.
-__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* __restrict__ kbb,
+// T: FP64 blocks, or their FP32 copy for the inner iterations of the mixed mode.
+template <typename T>
+__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __restrict__ kbb,
                          const long long* __restrict__ kbb_off, double* cbuf) {
-  extern __shared__ double xs[];
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  T* xs = reinterpret_cast<T*>(xs_raw);
   const int p = blockIdx.x;
   const SubDev S = M.subs[p];
-  for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = bt_at_slot(M, w, S.copy_off + s);
+  for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = T(bt_at_slot(M, w, S.copy_off + s));
   __syncthreads();
-  const double* kb = kbb + kbb_off[p];
+  const T* kb = kbb + kbb_off[p];
   for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
     const long long slot = S.copy_off + q;
     const int b = M.slot_bnd[slot], a = q % 3;
-    const double* kv = kb + (long long)b * 243 + a * 3;
+    const T* kv = kb + (long long)b * 243 + a * 3;
     const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
     int nb[28];
 #pragma unroll
@@ -136,7 +144,7 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* 
       nb[4 * u + 2] = v.z;
       nb[4 * u + 3] = v.w;
     }
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
       if (nb[t] >= 0) {
@@ -144,7 +152,7 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const double* 
         s += kv[t * 9] * xs[lb] + kv[t * 9 + 1] * xs[lb + 1] + kv[t * 9 + 2] * xs[lb + 2];
       }
     }
-    cbuf[slot] = s;
+    cbuf[slot] = double(s);
   }
 }
 
@@ -480,16 +488,23 @@ void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream
 
 void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,
                     cudaStream_t st) {
-  k_G_apply<<<M.n_sub, 256, 0, st>>>(M, x_lam, x_full, gx, scale);
+  k_G_apply<double><<<M.n_sub, 256, 0, st>>>(M, M.R, x_lam, x_full, gx, scale);
 }
 
 void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
                       cudaStream_t st) {
-  if (M.n_mult > 0) k_GT_update<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, x, ax, h, bh, out);
+  if (M.n_mult > 0) k_GT_update<double><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.R, x, ax, h, bh, out);
 }
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
-  k_gemv<<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+  k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+}
+
+void launch_project32(const DevMesh& M, const float* R32, const float* H32, long long l, const double* x,
+                      double* gx, double* hx, double* out, cudaStream_t st) {
+  k_G_apply<float><<<M.n_sub, 256, 0, st>>>(M, R32, x, nullptr, gx, 1.0);
+  k_gemv<float><<<blocks_for(l, 8), 256, 0, st>>>(H32, l, gx, 1.0, hx);
+  if (M.n_mult > 0) k_GT_update<float><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, R32, x, 1.0, hx, -1.0, out);
 }
 
 void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,
@@ -501,8 +516,15 @@ void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, 
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
                    cudaStream_t st, int max_copy) {
   const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
-  cudaFuncSetAttribute(k_lumped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_lumped<<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
+  cudaFuncSetAttribute(k_lumped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_lumped<double><<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
+}
+
+void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
+                     cudaStream_t st, int max_copy) {
+  const size_t smem = sizeof(float) * (size_t)(max_copy > 0 ? max_copy : 1);
+  cudaFuncSetAttribute(k_lumped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_lumped<float><<<M.n_sub, 256, smem, st>>>(M, w, kbb32, kbb_off, cbuf);
 }
 
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st) {

@@ -390,7 +390,7 @@ __global__ void k_band_fill(DevMesh M, const int* __restrict__ sub_list, const i
 // Lumped-preconditioner blocks of one subdomain (or its shape's elastic template):
 // K[3 ln(b) + a][3 ln(nu) + c] for every box-boundary node b and its 27 stencil neighbours nu.
 __global__ void k_kbb_fill(DevMesh M, const int* __restrict__ sub_list, const long long* __restrict__ dst_off,
-                           const int* elem_np, const double* dKe, double* kbb, int elastic_only) {
+                           const int* elem_np, const double* dKe, double* kbb, float* kbb32, int elastic_only) {
   const int p = sub_list[blockIdx.y];
   const SubDev& S = M.subs[p];
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -404,6 +404,7 @@ __global__ void k_kbb_fill(DevMesh M, const int* __restrict__ sub_list, const lo
     v = stiffness_entry(M, S, elem_np, dKe, r, c, elastic_only != 0);
   }
   kbb[dst_off[blockIdx.y] + idx] = v;
+  if (kbb32) kbb32[dst_off[blockIdx.y] + idx] = (float)v;
 }
 
 // f = df - F_k(du): internal force of eq. (F_def) gathered per dof.
@@ -534,10 +535,11 @@ void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const i
 }
 
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
-                     const int* elem_np, const double* dKe, double* kbb, int elastic_only, cudaStream_t st) {
+                     const int* elem_np, const double* dKe, double* kbb, float* kbb32, int elastic_only,
+                     cudaStream_t st) {
   if (n_list <= 0) return;
   dim3 grid(blocks_for((long long)max_bnd * 243, 256), n_list);
-  k_kbb_fill<<<grid, 256, 0, st>>>(M, sub_list, dst_off, elem_np, dKe, kbb, elastic_only);
+  k_kbb_fill<<<grid, 256, 0, st>>>(M, sub_list, dst_off, elem_np, dKe, kbb, kbb32, elastic_only);
 }
 
 void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st) {
