@@ -252,6 +252,11 @@ int tfeti_set_state(tfeti_ctx* ctx, const double* u, const double* sigma, const 
 /* ---- dual operators on the last assembled tangent (for tests and tools) --- */
 /* y = F x = B K^+ B^T x (eq. (equ:sps3)); x, y device [n_mult]. */
 int tfeti_apply_F(tfeti_ctx* ctx, const double* x, double* y);
+/* y = F x with the FP32 operators of the mixed mode's inner iterations (dual Schur
+ * blocks on the tensor cores for subdomains on their shape's elastic tangent, FP32
+ * banded solves for the others); requires TFETI_PRECISION_MIXED, else TFETI_ERR_ARG.
+ * x, y device [n_mult]. */
+int tfeti_apply_F32(tfeti_ctx* ctx, const double* x, double* y);
 /* y = P_N x = x - N^T (N N^T)^{-1} N x (Sec. 4.2); device [n_mult]. */
 int tfeti_apply_projector(tfeti_ctx* ctx, const double* x, double* y);
 /* y = B K B^T x, the lumped preconditioner (Sec. 4.2); device [n_mult]. */

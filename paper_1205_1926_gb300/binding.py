@@ -88,6 +88,7 @@ SIGNATURES = {
     "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
+    "tfeti_apply_F32": (C.c_int, [_P, _P, _P]),
     "tfeti_apply_projector": (C.c_int, [_P, _P, _P]),
     "tfeti_apply_precond": (C.c_int, [_P, _P, _P]),
     "tfeti_apply_N": (C.c_int, [_P, _P, _P]),

@@ -206,9 +206,9 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv) {
       const int cnt = c->el_cnt[sh];
       if (!cnt) continue;
       const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
-      launch_schur_gather(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->Xs, c->st);
-      launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->Xs,
-                                c->S32 + c->plan.shapes[sh].s_off, c->cbuf, c->st);
+      launch_schur_gather(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->Xhi, c->Xlo, c->st);
+      launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->Xhi, c->Xlo,
+                                c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh], c->cbuf, c->d_err, c->st);
       c->launches += 2;
     }
     if (c->n_items_pl > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
@@ -241,7 +241,9 @@ int form_schur_blocks(tfeti_ctx* c) {
     a.S32 = c->S32;
     a.s_off = P.shapes[sh].s_off;
     launch_sub_solve(c->M, a, c->solve_smem, c->st);
-    c->launches += 1;
+    launch_schur_tile_S(c->S32 + P.shapes[sh].s_off, n_bd, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
+                        c->st);
+    c->launches += 2;
     sync(c);
   }
   c->schur_ready = true;
@@ -643,9 +645,10 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   collect_events(c);
   int cst = cuda_check(c, "tfeti_dual_pcg");
   if (cst != TFETI_OK) return cst;
-  if (herr & 2) {
+  if (herr & 6) {
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    return fail(c, TFETI_ERR_CUDA, "a factor-panel copy did not complete within its time limit");
+    return fail(c, TFETI_ERR_CUDA, (herr & 2) ? "a factor-panel copy did not complete within its time limit"
+                                              : "a Schur-tile copy or MMA did not complete within its time limit");
   }
   if (status == TFETI_OK && !converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "PCGP iteration limit reached");
   if (info) {
@@ -1127,8 +1130,19 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     try {
       c->S32 = dalloc<float>(c, c->plan.s_total);
       int max_bd = 0;
-      for (const ShapeInfo& sh : c->plan.shapes) max_bd = std::max(max_bd, 3 * sh.n_bnd);
-      c->Xs = dalloc<float>(c, (size_t)c->h_subs.size() * max_bd);
+      long long s_tiles = 0;
+      c->s_tile_off.assign(c->plan.shapes.size(), 0);
+      for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+        const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
+        max_bd = std::max(max_bd, n_bd);
+        c->s_tile_off[sh] = s_tiles;
+        s_tiles += schur_s_tile_floats(n_bd);
+      }
+      c->Shi = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
+      c->Slo = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
+      const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
+      c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+      c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
@@ -1190,6 +1204,22 @@ int tfeti_apply_F(tfeti_ctx* c, const double* x, double* y) {
   sync(c);
   collect_events(c);
   return cuda_check(c, "tfeti_apply_F");
+}
+
+int tfeti_apply_F32(tfeti_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  if (c->precision != TFETI_PRECISION_MIXED) return fail(c, TFETI_ERR_ARG, "FP32 F-apply needs the mixed mode");
+  op_F32(c, x, y);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  const int cst = cuda_check(c, "tfeti_apply_F32");
+  if (cst != TFETI_OK) return cst;
+  if (herr & 6) {
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    return fail(c, TFETI_ERR_CUDA, "a bounded device wait gave up in the FP32 F-apply");
+  }
+  return TFETI_OK;
 }
 
 int tfeti_apply_projector(tfeti_ctx* c, const double* x, double* y) {

@@ -44,7 +44,10 @@ struct tfeti_ctx {
   long long f32_launches = 0;
   // dual Schur blocks of the shapes' elastic templates (mixed precision)
   float* S32 = nullptr;
-  float* Xs = nullptr;                       // gathered interface vectors, [elastic subdomains][n_bd]
+  // tensor-core operand tiles (TF32 hi/lo parts): S per shape at s_tile_off[shape],
+  // the gathered interface vectors of one shape's elastic subdomains
+  float *Shi = nullptr, *Slo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
+  std::vector<long long> s_tile_off;
   bool schur_ready = false;
   int* d_el = nullptr;                       // elastic subdomains grouped by shape
   std::vector<int> h_el, el_off, el_cnt;     // per shape: offset and count into d_el

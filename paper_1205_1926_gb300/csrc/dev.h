@@ -131,16 +131,23 @@ struct SolveArgs {
 };
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
 size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
-// Elastic dual Schur block applied to the elastic subdomains of one shape:
-// X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k] (0 off the interface),
-// then cbuf at the interface slots = (X S)[k][i].
-void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, float* X,
-                         cudaStream_t st);
-void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* X,
-                               const float* S, double* cbuf, cudaStream_t st);
-// FP32 copies of factor records (offsets in entries, same for both pools)
+// Dual Schur block applied to the elastic subdomains of one shape on the tensor
+// cores (3xTF32): X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k]
+// (0 off the interface), split into TF32 hi/lo tiles; then cbuf at the interface
+// slots = (X S)[k][i].  S tiles (hi/lo) are formed once from the FP32 block S32
+// (S32[j * n_bd + i] = S[i][j]).  err: bit 4 set if a bounded wait gives up.
+int schur_nk(int n_bd);
+long long schur_x_tile_floats(int n_list, int n_bd);   // floats of each of Xhi, Xlo
+long long schur_s_tile_floats(int n_bd);               // floats of each of Shi, Slo
+void launch_schur_tile_S(const float* S32, int n_bd, float* Shi, float* Slo, cudaStream_t st);
+void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, float* Xhi,
+                         float* Xlo, cudaStream_t st);
+void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* Xhi,
+                               const float* Xlo, const float* Shi, const float* Slo, double* cbuf, int* err,
+                               cudaStream_t st);
 // dst[i] = (float) src[i], i < n.
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
+// FP32 copies of factor records (offsets in entries, same for both pools)
 void launch_fac_to_f32(const double* fac, float* fac32, const long long* off_list, int n_list, long long len,
                        cudaStream_t st);
 

@@ -310,6 +310,34 @@ def test_cube64_full_size_properties():
 
 
 # ---------------------------------------------------------------------------- mixed precision (FP64-refined PCGP)
+@pytest.mark.parametrize("w,plastic", [(W.CUBE12, False), (W.CUBE12, True), (W.SMALL6_RAGGED, True),
+                                       (W.CUBE48, False)])
+def test_fp32_F_apply_matches_fp64(w, plastic):
+    """The inner F-apply of the mixed mode (dual Schur blocks on the tensor cores for subdomains on
+    their elastic template, FP32 banded solves for the others) against the FP64 F = B K^+ B^T, within
+    FP32 accuracy.  48^3: 216 subdomains of one shape = two 128-row tiles (ragged) x 19 64-column tiles
+    (1158 boundary dofs, ragged)."""
+    ctx = T.Context(w)
+    s = ctx.sizes
+    if plastic:
+        m, sig, kap, du = plastic_state(w, seed=61)
+        set_oracle_state(ctx, sig, kap)
+        ctx.assemble_tangent(dev(du), zeros(s["n_dof"]), zeros(s["n_dof"]))
+    else:
+        ctx.assemble_tangent(zeros(s["n_dof"]), zeros(s["n_dof"]), zeros(s["n_dof"]))
+    ctx.set_precision(True, 1e-3)
+    x = dev(W.seeded_vector(s["n_mult"], seed=62))
+    y64, y32 = zeros(s["n_mult"]), zeros(s["n_mult"])
+    ctx.apply("F", x, y64)
+    ctx.apply("F32", x, y32)
+    a, b = host(y32), host(y64)
+    assert np.isfinite(a).all() and rel(a, b) <= 1e-5, rel(a, b)
+    # twice the same input gives the same bits (fixed MMA order, no atomics)
+    y32b = zeros(s["n_mult"])
+    ctx.apply("F32", x, y32b)
+    assert torch.equal(y32, y32b)
+
+
 @pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
 def test_mixed_precision_dual_pcg_reaches_fp64_accuracy(w):
     """FP32 inner F-applies corrected by FP64 residuals reach the oracle's solution at eps = 1e-12."""
