@@ -243,6 +243,8 @@ def run_gpu(args, rank, world, local_rank):
     ctx = T.Context(w, stream=stream)
     if args.precision == "mixed":
         ctx.set_precision(True, args.inner_rtol)
+    if args.learned:
+        ctx.set_recycling(args.history)
     if args.no_graphs:
         ctx.set_graphs(False)
     n = ctx.sizes["n_dof"]
@@ -310,38 +312,48 @@ def run_gpu(args, rank, world, local_rank):
     elapsed_e2e = time.perf_counter() - t0
     e2e_match = bool(torch.equal(u_host.to(dev), u_final)) if not args.no_e2e else None
 
-    # ---- the other arm of the metric: mixed precision on the same load history
-    mixed = None
-    if args.precision == "fp64" and not args.no_mixed:
-        ctx.close()
-        mctx = T.Context(w, stream=stream)
-        mctx.set_precision(True, args.inner_rtol)
+    # ---- the other arms of the metric on the same load history: mixed precision, and mixed
+    # precision with the history start of the dual PCGP (the "learned" start)
+    def run_arm(recycling):
+        actx = T.Context(w, stream=stream)
+        actx.set_precision(True, args.inner_rtol)
+        actx.set_recycling(recycling)
         if args.no_graphs:
-            mctx.set_graphs(False)
+            actx.set_graphs(False)
         for k in range(args.warmup):
-            mctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
-        msnaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
-        mtimed = []
+            actx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        asnaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
+        atimed = []
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for k in range(args.warmup, n_total):
-            mtimed.append(mctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
-            mctx.get_state(u=msnaps[k - args.warmup])
+            atimed.append(actx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+            actx.get_state(u=asnaps[k - args.warmup])
         f1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        melapsed = max_over_ranks([f0.elapsed_time(f1) / 1e3], dev)[0]
+        aelapsed = max_over_ranks([f0.elapsed_time(f1) / 1e3], dev)[0]
+        actx.close()
         # compared after the timed region: no torch kernel runs inside it
-        diffs = (torch.linalg.vector_norm(msnaps - snaps, dim=1) / torch.linalg.vector_norm(snaps, dim=1)).tolist()
-        mixed = {"value": replica_value(melapsed, args.steps, world), "unit": UNIT, "inner_rtol": args.inner_rtol,
-                 "speedup_vs_fp64": None, "rel_u_diff_vs_fp64_per_step": diffs, "max_rel_u_diff_vs_fp64": max(diffs),
-                 "newton_per_step": [s["newton"] for s in mtimed], "pcg_inner_per_step": [sum(s["pcg"]) for s in mtimed],
-                 "outer_per_step": [sum(s["outer"]) for s in mtimed],
-                 "note": "FP64-refined PCGP: FP32 dual Schur blocks (elastic) and FP32 banded solves (plastic) "
-                         "inside, FP64 residual, projector, coarse solve, return map; same 1e-8 dual test"}
-        mctx.close()
+        diffs = (torch.linalg.vector_norm(asnaps - snaps, dim=1) / torch.linalg.vector_norm(snaps, dim=1)).tolist()
+        return {"value": replica_value(aelapsed, args.steps, world), "unit": UNIT, "inner_rtol": args.inner_rtol,
+                "history_size": recycling, "speedup_vs_fp64": None, "rel_u_diff_vs_fp64_per_step": diffs,
+                "max_rel_u_diff_vs_fp64": max(diffs), "newton_per_step": [s["newton"] for s in atimed],
+                "pcg_inner_per_step": [sum(s["pcg"]) for s in atimed],
+                "outer_per_step": [sum(s["outer"]) for s in atimed],
+                "history_starts_per_step": [sum(s["history"]) for s in atimed]}
+
+    mixed = learned = None
+    if args.precision == "fp64" and not args.no_mixed:
+        ctx.close()
+        mixed = run_arm(0)
+        mixed["note"] = ("FP64-refined PCGP: FP32 dual Schur blocks on the tensor cores (elastic) and FP32 banded "
+                         "solves (plastic), FP32 projector and preconditioner inside; FP64 residual and stopping test")
+        learned = run_arm(args.history)
+        learned["note"] = ("the mixed arm with each dual solve started from the Galerkin-optimal combination of the "
+                           "solver's last solutions (fitted online on its own lambda history), zero-start fallback")
     elapsed, elapsed_e2e = max_over_ranks([elapsed, elapsed_e2e], dev)
     units = args.steps * world
     value = replica_value(elapsed, args.steps, world)
@@ -374,6 +386,7 @@ def run_gpu(args, rank, world, local_rank):
             "config": workload_config(w, args.steps, args.warmup) | {
                 "parallelism": "replicas" if world > 1 else "1 GPU", "precision": args.precision,
                 "inner_rtol": args.inner_rtol if args.precision == "mixed" else None,
+                "history_start": args.history if args.learned else 0,
                 "inner_pcgp_launch": "kernel by kernel" if args.no_graphs else "one CUDA graph (WHILE node) per inner solve"},
             "e2e": None if args.no_e2e else {"value": elapsed_e2e / units, "unit": UNIT,
                                              "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
@@ -390,6 +403,9 @@ def run_gpu(args, rank, world, local_rank):
     if mixed is not None:
         mixed["speedup_vs_fp64"] = value / mixed["value"]
         line["mixed"] = mixed
+    if learned is not None:
+        learned["speedup_vs_fp64"] = value / learned["value"]
+        line["mixed_learned"] = learned
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cube64_8x8x8":
         s = oracle_sample_subprocess(w.name)
         v = oracle_step_estimate(s, statistics.mean(newton_steps), statistics.mean(pcg_steps))
@@ -416,7 +432,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arm of an FP64 run")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms of an FP64 run")
+    ap.add_argument("--learned", action="store_true",
+                    help="start the timed arm's dual solves from the solver's history (see --history)")
+    ap.add_argument("--history", type=int, default=8,
+                    help="stored dual solutions of the history start in the mixed+learned arm (1..8)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),

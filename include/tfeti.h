@@ -165,7 +165,7 @@ int tfeti_assemble_tangent(tfeti_ctx* ctx, const double* du, const double* df, d
 typedef struct tfeti_pcg_info {
     int32_t iterations;        /* PCGP iterations j                                     */
     int32_t converged;         /* 1 if ||w|| <= rtol ||r^0||                             */
-    int32_t used_lambda0;      /* 1 if a caller lambda0 was used as the start           */
+    int32_t used_lambda0;      /* 1: caller lambda0 used; 2: history start taken        */
     int32_t f_applies;         /* FP64 subdomain-solve passes incl. set-up and recovery */
     double  r0_norm;           /* ||r^0|| = ||d~||                                      */
     double  w_norm;            /* last ||w^{j-1}||                                      */
@@ -200,6 +200,7 @@ typedef struct tfeti_step_info {
     int64_t plastic_committed;               /* plastic points of the committed state     */
     double  seconds;
     int32_t outer[TFETI_MAX_NEWTON];         /* FP64 refinement steps per Newton iteration */
+    int32_t history[TFETI_MAX_NEWTON];       /* 1 if the dual solve started from the history */
 } tfeti_step_info;
 
 /* Algorithm 4 for one time step: du = o; Newton iterations of Algorithm 5 +
@@ -230,6 +231,20 @@ int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double n
 #define TFETI_PRECISION_FP64  0
 #define TFETI_PRECISION_MIXED 1
 int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);
+
+/* Start of the dual PCGP from the solver's history (extension; Algorithm 3 starts
+ * from lambda_Ker = o, which stays the default q = 0).  With q in 1..8 the context
+ * keeps the last q solutions lambda_j (in Ker N) of tfeti_dual_pcg and their
+ * products F lambda_j (= d~_j - r_j).  For a new right-hand side it solves the
+ * q x q Galerkin system (L^T F L) c = L^T d~ (the F-norm-optimal start in
+ * span{lambda_j}; vectors found dependent are dropped) and, if the residual this
+ * predicts with the stored products is below half of ||P d~||, starts from
+ * lambda_Ker = P sum_j c_j lambda_j; if the true projected residual is not below
+ * ||P d~|| it falls back to lambda_Ker = o.  The stopping test stays
+ * ||w|| <= rtol ||d~||, so the converged solution is the same within the
+ * tolerance.  Stored products of earlier tangents are used as they are (the
+ * fallback covers a stale prediction).  Resets the history. */
+int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
 
 /* Launch mode of the mixed-precision inner PCGP.  enable != 0 (default): each
  * inner solve is one CUDA graph launch whose body is one iteration inside a

@@ -45,14 +45,14 @@ class StepInfo(C.Structure):
     _fields_ = [("newton", C.c_int32), ("converged", C.c_int32), ("pcg", C.c_int32 * MAX_NEWTON),
                 ("plastic", C.c_int64 * MAX_NEWTON), ("criterion", C.c_double * MAX_NEWTON),
                 ("refactored", C.c_int32 * MAX_NEWTON), ("plastic_committed", C.c_int64), ("seconds", C.c_double),
-                ("outer", C.c_int32 * MAX_NEWTON)]
+                ("outer", C.c_int32 * MAX_NEWTON), ("history", C.c_int32 * MAX_NEWTON)]
 
     def as_dict(self) -> dict:
         n = self.newton
         return {"newton": n, "converged": bool(self.converged), "pcg": list(self.pcg[:n]),
                 "plastic": list(self.plastic[:n]), "criterion": list(self.criterion[:n]),
                 "refactored": list(self.refactored[:n]), "plastic_committed": self.plastic_committed,
-                "seconds": self.seconds, "outer": list(self.outer[:n])}
+                "seconds": self.seconds, "outer": list(self.outer[:n]), "history": list(self.history[:n])}
 
 
 class Timing(C.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = {
     "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
+    "tfeti_set_recycling": (C.c_int, [_P, _I]),
     "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
@@ -273,6 +274,10 @@ class Context:
     def set_precision(self, mixed: bool, inner_rtol: float = 1e-3):
         """FP64 dual solve (default) or FP64-refined PCGP with FP32 inner F-applies."""
         return self._check(self.lib.tfeti_set_precision(self.h, 1 if mixed else 0, inner_rtol), "tfeti_set_precision")
+
+    def set_recycling(self, q: int):
+        """Start each dual solve from the best combination of the last q solutions (0: off)."""
+        return self._check(self.lib.tfeti_set_recycling(self.h, int(q)), "tfeti_set_recycling")
 
     def set_graphs(self, enable: bool):
         """Inner PCGP of the mixed mode as one CUDA graph launch (default) or kernel by kernel."""

@@ -259,7 +259,7 @@ void op_project(tfeti_ctx* c, const double* x, double* out) {
 
 // FP32 projector and preconditioner of the inner iterations of the mixed mode.
 void op_project32(tfeti_ctx* c, const double* x, double* out) {
-  launch_project32(c->M, c->R32, c->H32, c->l, x, c->gx, c->hx, out, c->st);
+  launch_project32(c->M, c->H32, c->l, x, c->gx, c->hx, out, c->st);
   c->launches += 3;
 }
 
@@ -549,6 +549,105 @@ void residual_solve(tfeti_ctx* c, const double* f, const double* lam, double* r_
   c->launches += 1;
 }
 
+// Solve the Gram system (L^T F L) c = L^T d~ of the history start on the host:
+// Cholesky of the symmetrised matrix over the stored vectors in order, skipping any
+// whose pivot shows it (numerically) dependent on those kept; skipped ones get c = 0.
+std::vector<double> history_coefficients(const double* g, int n) {
+  std::vector<double> A(n * n), b(n), Lc(n * n, 0.0), c(n, 0.0), y(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[i * n + j] = 0.5 * (g[i * kRecMax + j] + g[j * kRecMax + i]);
+    b[i] = g[kRecMax * kRecMax + i];
+  }
+  std::vector<int> kept;
+  for (int j = 0; j < n; ++j) {
+    if (!(A[j * n + j] > 0.0)) continue;
+    double piv = A[j * n + j];
+    for (int t = 0; t < (int)kept.size(); ++t) {
+      const int kk = kept[t];
+      double v = A[j * n + kk];
+      for (int u = 0; u < t; ++u) v -= Lc[j * n + kept[u]] * Lc[kk * n + kept[u]];
+      v /= Lc[kk * n + kk];
+      Lc[j * n + kk] = v;
+      piv -= v * v;
+    }
+    if (piv > 1e-10 * A[j * n + j]) {
+      Lc[j * n + j] = std::sqrt(piv);
+      kept.push_back(j);
+    } else {
+      for (int t = 0; t < (int)kept.size(); ++t) Lc[j * n + kept[t]] = 0.0;
+    }
+  }
+  for (int t = 0; t < (int)kept.size(); ++t) {
+    const int j = kept[t];
+    double v = b[j];
+    for (int u = 0; u < t; ++u) v -= Lc[j * n + kept[u]] * y[kept[u]];
+    y[j] = v / Lc[j * n + j];
+  }
+  for (int t = (int)kept.size() - 1; t >= 0; --t) {
+    const int j = kept[t];
+    double v = y[j];
+    for (int u = t + 1; u < (int)kept.size(); ++u) v -= Lc[kept[u] * n + j] * c[kept[u]];
+    c[j] = v / Lc[j * n + j];
+  }
+  return c;
+}
+
+// History start (extension of Algorithm 3): on entry r = d~ and lambda_Ker = o.
+// Returns 0 if not applied (state unchanged), 1 if lambda_Ker = P(sum c_j lambda_j)
+// was taken (r = d~ - F lambda_Ker by a residual solve), 2 if it was tried and
+// rejected because ||P r|| did not fall below ||P d~|| (state reset to d~, the
+// residual-solve vector no longer matches).
+int history_start(tfeti_ctx* c, const double* f, double tol_abs) {
+  const long long m = c->M.n_mult;
+  const int n = c->rec_n;
+  op_project(c, c->r, c->w);
+  const double w0 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
+  if (w0 <= tol_abs) return 0;   // the zero start already meets the stopping test
+  launch_rec_gram(c->rec_L, c->rec_FL, c->r, n, m, c->rec_partial, c->rec_out, c->st);
+  double g[kRecMax * kRecMax + kRecMax];
+  cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  c->launches += 2;
+  std::vector<double> coef = history_coefficients(g, n);
+  bool any = false;
+  for (double v : coef) any = any || (v != 0.0 && std::isfinite(v));
+  if (!any || !(w0 > 0.0)) return 0;
+  cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st);
+  // predicted residual with the stored products: d~ - sum c_j F lambda_j
+  launch_rec_combine(c->rec_FL, c->rec_c, n, m, c->r, -1.0, c->tm, c->st);
+  op_project(c, c->tm, c->z);
+  c->launches += 1;
+  const double pred = std::sqrt(std::max(0.0, dot_host(c, c->z, c->z, m)));
+  if (!(pred < c->rec_accept * w0)) return 0;
+  ++c->rec_tried;
+  launch_rec_combine(c->rec_L, c->rec_c, n, m, nullptr, 1.0, c->y, c->st);
+  op_project(c, c->y, c->lamk);
+  launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
+  c->launches += 2;
+  residual_solve(c, f, c->lam, c->r);   // r = d~ - F lambda_Ker
+  op_project(c, c->r, c->w);
+  const double w1 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
+  if (!(w1 < w0)) {
+    cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
+    cudaMemcpyAsync(c->r, c->dtil, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+    return 2;
+  }
+  ++c->rec_used;
+  return 1;
+}
+
+// Store the solution of the finished solve: lambda_Ker and F lambda_Ker = d~ - r.
+void history_push(tfeti_ctx* c) {
+  const long long m = c->M.n_mult;
+  double* Lj = c->rec_L + (long long)c->rec_head * m;
+  double* FLj = c->rec_FL + (long long)c->rec_head * m;
+  cudaMemcpyAsync(Lj, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  launch_axpby(m, 1.0, c->dtil, -1.0, c->r, FLj, c->st);
+  c->launches += 1;
+  c->rec_head = (c->rec_head + 1) % c->rec_q;
+  c->rec_n = std::min(c->rec_n + 1, c->rec_q);
+}
+
 int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, const double* lambda0, double rtol,
              int maxit, tfeti_pcg_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -566,12 +665,18 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
   bool v_current = true;   // vsol and r belong to lambda = lambda_Im + lambda_Ker
   int used_l0 = 0;
+  const bool history = c->rec_q > 0 && m > 0;
+  if (history) cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   if (lambda0) {
     op_project(c, lambda0, c->lamk);
     launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
     residual_solve(c, f, c->lam, c->r);      // r = d~ - F lambda_Ker
     c->launches += 1;
     used_l0 = 1;
+  } else if (history && c->rec_n > 0 && r0 > 0.0) {
+    const int h = history_start(c, f, rtol * r0);
+    if (h == 1) used_l0 = 2;
+    if (h == 2) v_current = false;
   }
   int it = 0, converged = 0, status = TFETI_OK, outer = 0;
   double w_norm = 0.0;
@@ -613,6 +718,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         launch_axpby(m, 1.0, c->lamk, 1.0, c->tm, c->lamk, c->st);
         launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
         residual_solve(c, f, c->lam, c->r);    // r = d~ - F lambda_Ker
+        v_current = true;
         c->launches += 2;
       }
     } else {
@@ -630,6 +736,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
   c->launches += 1;
   if (!v_current) residual_solve(c, f, c->lam, c->r);
+  if (history && r0 > 0.0 && status == TFETI_OK) history_push(c);   // r is the true residual here
   launch_G_apply(M, c->r, nullptr, c->gx, -1.0, c->st);
   launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
   c->launches += 2;
@@ -775,6 +882,64 @@ int setup_impl(tfeti_ctx* c) {
   launch_tables(P.h, lam, mu, dN, Kel, Q, c->st);
   for (const ShapeInfo& sh : P.shapes) launch_rigid_for_shape(c->h_subs[sh.rep_sub], P.h, R + sh.r_off, c->st);
   c->launches += 1 + (long long)P.shapes.size();
+  {
+    // explicit G = R^T B^T: entries (row, slot, B coefficient) in subdomain order, and
+    // the permutation into row order (a counting sort; subdomain order within a row)
+    std::vector<long long> gp_ptr(ns + 1, 0);
+    std::vector<int> gp_row, gp_slot;
+    std::vector<double> gp_coef;
+    for (int p = 0; p < ns; ++p) {
+      gp_ptr[p] = (long long)gp_row.size();
+      const SubInfo& sb = P.subs[p];
+      for (long long sl = sb.copy_off; sl < sb.copy_off + sb.n_copy; ++sl) {
+        const Group& g = P.groups[P.slot_group[sl]];
+        const int j = P.slot_j[sl];
+        if (g.nrows == 0) continue;
+        if (g.dirichlet) {
+          gp_row.push_back((int)(g.row0 + j));
+          gp_slot.push_back((int)sl);
+          gp_coef.push_back(1.0);
+        } else {
+          for (int r = std::max(j, 1); r < g.k; ++r) {
+            gp_row.push_back((int)(g.row0 + r - 1));
+            gp_slot.push_back((int)sl);
+            gp_coef.push_back(helmert_coef(r, j));
+          }
+        }
+      }
+    }
+    const long long ne = (long long)gp_row.size();
+    gp_ptr[ns] = ne;
+    std::vector<long long> gt_ptr(P.n_mult + 1, 0);
+    for (long long e = 0; e < ne; ++e) ++gt_ptr[gp_row[e] + 1];
+    for (long long r = 0; r < P.n_mult; ++r) gt_ptr[r + 1] += gt_ptr[r];
+    std::vector<long long> fill(gt_ptr.begin(), gt_ptr.end() - 1);
+    std::vector<int> gt_e(ne), gt_p(ne);
+    for (long long e = 0; e < ne; ++e) {
+      const long long et = fill[gp_row[e]]++;
+      gt_e[et] = (int)e;
+      gt_p[et] = P.slot_sub[gp_slot[e]];
+    }
+    M.n_gpairs = ne;
+    M.gp_ptr = upload(c, gp_ptr);
+    M.gp_row = upload(c, gp_row);
+    M.gt_ptr = upload(c, gt_ptr);
+    M.gt_p = upload(c, gt_p);
+    double* Gv = dalloc<double>(c, (size_t)std::max(1LL, 6 * ne));
+    double* GTv = dalloc<double>(c, (size_t)std::max(1LL, 6 * ne));
+    float* Gv32 = dalloc<float>(c, (size_t)std::max(1LL, 6 * ne));
+    float* GTv32 = dalloc<float>(c, (size_t)std::max(1LL, 6 * ne));
+    M.Gv = Gv;
+    M.GTv = GTv;
+    M.Gv32 = Gv32;
+    M.GTv32 = GTv32;
+    int* d_slot = upload(c, gp_slot);
+    double* d_coef = upload(c, gp_coef);
+    int* d_gte = upload(c, gt_e);
+    launch_fill_G(M, d_slot, d_coef, d_gte, Gv, Gv32, GTv, GTv32, c->st);
+    c->launches += 1;
+    sync(c);
+  }
   // state and iterate buffers
   c->u = dalloc<double>(c, P.n_dof);
   c->sig = dalloc<double>(c, 6 * P.n_gp);
@@ -1057,6 +1222,7 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
     loc.newton = i;
     loc.pcg[i - 1] = pi.iterations;
     loc.outer[i - 1] = pi.outer_iterations;
+    loc.history[i - 1] = pi.used_lambda0 == 2 ? 1 : 0;
     loc.plastic[i - 1] = npl;
     loc.criterion[i - 1] = crit;
     loc.refactored[i - 1] = c->last_refactored.empty() ? 0 : c->last_refactored.back();
@@ -1112,19 +1278,18 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   c->precision = mode;
   c->inner_rtol = inner_rtol;
   c->g_inner_stale = true;
-  if (mode == TFETI_PRECISION_MIXED && !c->R32) {
-    // FP32 copies of R, H and the boundary blocks for the inner projector and preconditioner
+  if (mode == TFETI_PRECISION_MIXED && !c->H32) {
+    // FP32 copies of H and the boundary blocks for the inner projector and preconditioner
+    // (the FP32 values of G are formed at set-up)
     try {
-      c->R32 = dalloc<float>(c, c->plan.r_total);
       c->H32 = dalloc<float>(c, (size_t)c->l * c->l);
       c->kbb32 = dalloc<float>(c, c->plan.kbb_template_total + c->plan.kbb_total);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
-    launch_to_f32(c->M.R, c->R32, c->plan.r_total, c->st);
     launch_to_f32(c->H, c->H32, (long long)c->l * c->l, c->st);
     launch_to_f32(c->kbb, c->kbb32, c->plan.kbb_template_total + c->plan.kbb_total, c->st);
-    c->launches += 3;
+    c->launches += 2;
   }
   if (mode == TFETI_PRECISION_MIXED && !c->schur_ready) {
     try {
@@ -1157,6 +1322,30 @@ int tfeti_set_graphs(tfeti_ctx* c, int32_t enable) {
   c->use_graphs = enable != 0;
   c->g_inner_stale = true;
   return TFETI_OK;
+}
+
+int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
+  if (!c || q < 0 || q > kRecMax) return fail(c, TFETI_ERR_ARG, "history size must be in 0..8");
+  const long long m = c->M.n_mult;
+  if (q > 0 && q > c->rec_q) {
+    try {
+      c->rec_L = dalloc<double>(c, (size_t)q * (size_t)std::max(1LL, m));
+      c->rec_FL = dalloc<double>(c, (size_t)q * (size_t)std::max(1LL, m));
+      if (!c->rec_partial) {
+        c->rec_partial = dalloc<double>(c, (size_t)kRedBlocks * (kRecMax * kRecMax + kRecMax));
+        c->rec_out = dalloc<double>(c, kRecMax * kRecMax + kRecMax);
+        c->rec_c = dalloc<double>(c, kRecMax);
+        c->dtil = dalloc<double>(c, (size_t)std::max(1LL, m));
+      }
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+  }
+  c->rec_q = q;
+  c->rec_n = 0;
+  c->rec_head = 0;
+  c->rec_tried = c->rec_used = 0;
+  return cuda_check(c, "tfeti_set_recycling");
 }
 
 int tfeti_first_yield_traction(tfeti_ctx* c, const double* dir, double rtol, double* t_y) {

@@ -84,8 +84,15 @@ struct tfeti_ctx {
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
          *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *tm = nullptr;
   double* vsol = nullptr;   // K^+(f - B^T lambda) of the last residual solve, device [n_dof]
+  // history start (tfeti_set_recycling): ring of the last rec_q solutions lambda_Ker and
+  // their products F lambda_Ker, [rec_q][n_mult] each
+  int rec_q = 0, rec_n = 0, rec_head = 0;
+  double *rec_L = nullptr, *rec_FL = nullptr, *rec_partial = nullptr, *rec_out = nullptr, *rec_c = nullptr;
+  double* dtil = nullptr;        // d~ of the current solve (kept when the history start is on)
+  double rec_accept = 0.5;       // try the start if the predicted ||P r|| < rec_accept ||P d~||
+  long long rec_tried = 0, rec_used = 0;
   // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)
-  float *R32 = nullptr, *H32 = nullptr, *kbb32 = nullptr;
+  float *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;

@@ -59,6 +59,20 @@ struct DevMesh {
   const double* Kel;       // [24][24] elastic brick stiffness
   const double* Q;         // [8 g][24][24] w detJ B_g^T E_eps B_g
   const double* helm;      // [8 r][8 j] Helmert coefficients (row r = 1..7, copy j)
+  // G = R^T B^T explicitly (it depends only on B and R): one entry per (multiplier
+  // row, copy slot) with B[row][slot] != 0, value B[row][slot] * R[slot dof][0..5].
+  // Subdomain order: entries gp_ptr[p]..gp_ptr[p+1] of subdomain p, their rows gp_row,
+  // values Gv / Gv32 [entry][6].  Row order: entries gt_ptr[row]..gt_ptr[row+1],
+  // subdomain gt_p, values GTv / GTv32 [entry][6].
+  const long long* gp_ptr;
+  const int* gp_row;
+  const double* Gv;
+  const float* Gv32;
+  const long long* gt_ptr;
+  const int* gt_p;
+  const double* GTv;
+  const float* GTv32;
+  long long n_gpairs;
   double wdet;
   double lam, mu, sigma_y, H;
   long long n_dof, n_gp, n_mult, n_copy, n_elem;
@@ -165,13 +179,26 @@ void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const l
 // FP32 operators of the inner iterations of the mixed mode (FP64 vectors in and out):
 // P x with the FP32 copies of R and H, and the lumped preconditioner with the FP32
 // copy of the boundary blocks.  gx, hx: coarse work vectors [l].
-void launch_project32(const DevMesh& M, const float* R32, const float* H32, long long l, const double* x,
-                      double* gx, double* hx, double* out, cudaStream_t st);
+void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
+                      double* out, cudaStream_t st);
+// Values of the explicit G from R and the (row, slot, coefficient) entries (set-up).
+void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, const int* gt_e, double* Gv,
+                   float* Gv32, double* GTv, float* GTv32, cudaStream_t st);
 void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
                      cudaStream_t st, int max_copy);
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;
+
+// History start of the dual PCGP: at most kRecMax stored solutions.  Gram system
+// out[i * kRecMax + j] = L_i . FL_j, out[kRecMax^2 + i] = L_i . d (L, FL: q vectors
+// of length m, stride m); partial: kRedBlocks * (kRecMax^2 + kRecMax) doubles.
+constexpr int kRecMax = 8;
+void launch_rec_gram(const double* L, const double* FL, const double* d, int q, long long m, double* partial,
+                     double* out, cudaStream_t st);
+// out = (base ? base : 0) + sign * sum_j c_j X_j, c device [q].
+void launch_rec_combine(const double* X, const double* c, int q, long long m, const double* base, double sign,
+                        double* out, cudaStream_t st);
 
 // Device scalars of the graph-driven PCGP (indices into the context's scalar array)
 enum PcgScalar {

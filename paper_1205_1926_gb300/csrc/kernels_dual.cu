@@ -31,33 +31,41 @@ __device__ double block_reduce_sum(double v, double* red) {
   return s;   // valid in thread 0
 }
 
-// gx[6p+c] = scale * (R_p^T (B^T x))_c over the interface slots of p (x_lam), or
-// scale * (R_p^T x_p)_c over all dofs of p (x_full).  One CTA per subdomain.  T is the
-// type of R (M.R in FP64, its FP32 copy for the inner iterations of the mixed mode)
-// and of the products and per-thread sums.
-template <typename T>
-__global__ void k_G_apply(DevMesh M, const T* __restrict__ Rall, const double* __restrict__ x_lam,
-                          const double* __restrict__ x_full, double* gx, double scale) {
+// gx[6p+c] = scale * (R_p^T x_p)_c over all dofs of subdomain p (set-up: e = -R^T f).
+// One CTA per subdomain.
+__global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* gx, double scale) {
   __shared__ double red[32];
   const int p = blockIdx.x;
   const SubDev S = M.subs[p];
-  const T* R = Rall + S.r_off;
+  const double* R = M.R + S.r_off;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < S.n_dof; i += blockDim.x) {
+    const double v = x_full[S.dof_off + i];
+    const double* r = R + (long long)i * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double s = block_reduce_sum(acc[c], red);
+    if (threadIdx.x == 0) gx[6 * (long long)p + c] = scale * s;
+  }
+}
+
+// gx[6p+c] = scale * (G x)[6p+c] = scale * sum over the entries of subdomain p of
+// G[entry][c] x[row].  One CTA per subdomain.  T: FP64 values, or their FP32 copy
+// (products and per-thread sums in T) for the inner iterations of the mixed mode.
+template <typename T>
+__global__ void k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x, double* gx,
+                        double scale) {
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  const long long e0 = M.gp_ptr[p], e1 = M.gp_ptr[p + 1];
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  if (x_lam) {
-    for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) {
-      const long long slot = S.copy_off + s;
-      const T v = T(bt_at_slot(M, x_lam, slot));
-      const T* r = R + (long long)M.slot_ldof[slot] * 6;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const T v = T(x[M.gp_row[e]]);
+    const T* g = Gv + e * 6;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
-    }
-  } else {
-    for (int i = threadIdx.x; i < S.n_dof; i += blockDim.x) {
-      const T v = T(x_full[S.dof_off + i]);
-      const T* r = R + (long long)i * 6;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += r[c] * v;
-    }
+    for (int c = 0; c < 6; ++c) acc[c] += g[c] * v;
   }
   for (int c = 0; c < 6; ++c) {
     const double s = block_reduce_sum(double(acc[c]), red);
@@ -65,27 +73,42 @@ __global__ void k_G_apply(DevMesh M, const T* __restrict__ Rall, const double* _
   }
 }
 
-// out[row] = ax * x[row] + bh * (B R h)[row]   (x nullable); T as in k_G_apply.
+// out[row] = ax * x[row] + bh * (G^T h)[row]   (x nullable); T as in k_G_csr.
 template <typename T>
-__global__ void k_GT_update(DevMesh M, const T* __restrict__ Rall, const double* __restrict__ x, double ax,
-                            const double* __restrict__ h, double bh, double* out) {
+__global__ void k_GT_csr(DevMesh M, const T* __restrict__ GTv, const double* __restrict__ x, double ax,
+                         const double* __restrict__ h, double bh, double* out) {
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= M.n_mult) return;
-  const GroupDev& g = M.groups[M.row_group[row]];
-  const int rr = M.row_r[row];
   double s = 0.0;
-  const int j0 = g.dirichlet ? rr : 0, j1 = g.dirichlet ? rr : rr + 1;
-  for (int j = j0; j <= j1; ++j) {
-    const long long slot = g.slot[j];
-    const int q = g.sub[j];
-    const T* r = Rall + M.subs[q].r_off + (long long)M.slot_ldof[slot] * 6;
-    const double* hq = h + 6 * (long long)q;
-    T rh = T(0);
+  for (long long e = M.gt_ptr[row]; e < M.gt_ptr[row + 1]; ++e) {
+    const double* hq = h + 6 * (long long)M.gt_p[e];
+    const T* g = GTv + e * 6;
+    T t = T(0);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) rh += r[c] * T(hq[c]);
-    s += (g.dirichlet ? 1.0 : M.helm[(rr + 1) * 8 + j]) * double(rh);
+    for (int c = 0; c < 6; ++c) t += g[c] * T(hq[c]);
+    s += double(t);
   }
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
+}
+
+// Entry values of G: e' runs over the row-ordered entries, e = gt_e[e'] is the same
+// entry in subdomain order (a permutation), v = coef * R_p[slot dof][c].
+__global__ void k_fill_G(DevMesh M, const int* __restrict__ gp_slot, const double* __restrict__ gp_coef,
+                         const int* __restrict__ gt_e, double* Gv, float* Gv32, double* GTv, float* GTv32) {
+  const long long et = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (et >= M.n_gpairs) return;
+  const long long e = gt_e[et];
+  const long long slot = gp_slot[e];
+  const SubDev& S = M.subs[M.slot_sub[slot]];
+  const double* r = M.R + S.r_off + (long long)M.slot_ldof[slot] * 6;
+  const double cf = gp_coef[e];
+  for (int c = 0; c < 6; ++c) {
+    const double v = cf * r[c];
+    Gv[e * 6 + c] = v;
+    Gv32[e * 6 + c] = (float)v;
+    GTv[et * 6 + c] = v;
+    GTv32[et * 6 + c] = (float)v;
+  }
 }
 
 // out = v + R_p alpha_p on the dofs of subdomain p = blockIdx.y.
@@ -111,6 +134,7 @@ __global__ void k_gemv(const T* __restrict__ A, long long n, const double* __res
   if (row >= n) return;
   const T* a = A + row * n;
   T s = T(0);
+#pragma unroll 4
   for (long long j = lane; j < n; j += 32) s += a[j] * T(x[j]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) y[row] = alpha * double(s);
@@ -488,23 +512,30 @@ void launch_contract(const DevMesh& M, const double* cbuf, double* y, cudaStream
 
 void launch_G_apply(const DevMesh& M, const double* x_lam, const double* x_full, double* gx, double scale,
                     cudaStream_t st) {
-  k_G_apply<double><<<M.n_sub, 256, 0, st>>>(M, M.R, x_lam, x_full, gx, scale);
+  if (x_lam) k_G_csr<double><<<M.n_sub, 256, 0, st>>>(M, M.Gv, x_lam, gx, scale);
+  else k_G_full<<<M.n_sub, 256, 0, st>>>(M, x_full, gx, scale);
 }
 
 void launch_GT_update(const DevMesh& M, const double* x, double ax, const double* h, double bh, double* out,
                       cudaStream_t st) {
-  if (M.n_mult > 0) k_GT_update<double><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.R, x, ax, h, bh, out);
+  if (M.n_mult > 0) k_GT_csr<double><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv, x, ax, h, bh, out);
+}
+
+void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, const int* gt_e, double* Gv,
+                   float* Gv32, double* GTv, float* GTv32, cudaStream_t st) {
+  if (M.n_gpairs > 0)
+    k_fill_G<<<blocks_for(M.n_gpairs, 256), 256, 0, st>>>(M, gp_slot, gp_coef, gt_e, Gv, Gv32, GTv, GTv32);
 }
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
   k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
 }
 
-void launch_project32(const DevMesh& M, const float* R32, const float* H32, long long l, const double* x,
-                      double* gx, double* hx, double* out, cudaStream_t st) {
-  k_G_apply<float><<<M.n_sub, 256, 0, st>>>(M, R32, x, nullptr, gx, 1.0);
+void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
+                      double* out, cudaStream_t st) {
+  k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
   k_gemv<float><<<blocks_for(l, 8), 256, 0, st>>>(H32, l, gx, 1.0, hx);
-  if (M.n_mult > 0) k_GT_update<float><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, R32, x, 1.0, hx, -1.0, out);
+  if (M.n_mult > 0) k_GT_csr<float><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv32, x, 1.0, hx, -1.0, out);
 }
 
 void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,

@@ -379,6 +379,68 @@ def test_mixed_precision_load_history_cube12():
         assert info["converged"] and rel(host(u), model.u) <= 1e-9
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_history_start_load_history_cube12(mixed):
+    """The history start (last 8 dual solutions, Galerkin-fitted) reaches the oracle's displacements at
+    every load step, takes the start in some solves, and needs fewer PCGP iterations than the zero start."""
+    w = W.CUBE12
+    runs = {}
+    for q in (0, 8):
+        ctx = T.Context(w)
+        if mixed:
+            ctx.set_precision(True, 1e-3)
+        ctx.set_recycling(q)
+        t_y = ctx.first_yield_traction(w.traction_dir)
+        df = zeros(ctx.sizes["n_dof"])
+        u = zeros(ctx.sizes["n_dof"])
+        prev, us, its, hist = 0.0, [], 0, 0
+        for a in w.load_fractions():
+            ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+            prev = a
+            info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+            assert info["converged"]
+            its += sum(info["pcg"])
+            hist += sum(info["history"])
+            ctx.get_state(u=u)
+            us.append(host(u).copy())
+        runs[q] = (us, its, hist)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    prev = 0.0
+    for k, a in enumerate(w.load_fractions()):
+        model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        assert rel(runs[8][0][k], model.u) <= 1e-9, k
+    assert runs[0][2] == 0 and runs[8][2] > 0
+    assert runs[8][1] < runs[0][1], (runs[8][1], runs[0][1])
+
+
+def test_history_start_repeated_rhs():
+    """The same dual problem solved twice: the second solve starts from the first solution and stops at
+    once; both reach the oracle's u and lambda."""
+    w = W.SMALL6_RAGGED
+    m, sig, kap, du = plastic_state(w, seed=71)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((20.0, 5.0, -8.0))
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    ctx.set_recycling(4)
+    u1, l1, u2, l2 = zeros(s["n_dof"]), zeros(s["n_mult"]), zeros(s["n_dof"]), zeros(s["n_mult"])
+    i1 = ctx.dual_pcg(f, u1, l1, rtol=1e-12, maxit=5000)
+    i2 = ctx.dual_pcg(f, u2, l2, rtol=1e-12, maxit=5000)
+    assert i1["used_lambda0"] == 0 and i2["used_lambda0"] == 2
+    assert i2["iterations"] <= 1 < i1["iterations"]
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, _ = m.assemble(du, df)
+    sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+    for u, lam in ((u1, l1), (u2, l2)):
+        assert rel(host(u), sol["u"]) <= 1e-9
+        assert rel(host(lam), sol["lam"]) <= 1e-9
+
+
 def test_cube64_history_matches_oracle_record():
     """The full 20-step 64^3 history (the timed workload, FP64) against the oracle's own run of it
     (tests/golden/cube64_oracle_record.json, written by make_cube64_oracle_record.py from oracle/ only)."""
