@@ -64,6 +64,13 @@ def norm_sigma(tau: np.ndarray) -> np.ndarray:
     return np.sqrt(np.einsum("ni,ij,nj->n", tau, P_MATRIX, tau))
 
 
+# Exact ties of the elastic-predictor test: a point returned to the yield surface at
+# step k satisfies Phi(sigma_k, kappa_k) = 0 in exact arithmetic, which eq.
+# (elast_pred) and the tangent of Sec. 3.1 treat as elastic (Phi <= 0).  Rounding
+# leaves it at +-1 ulp, so |Phi| <= TIE (sigma_y + H kappa_k) counts as Phi = 0.
+TIE = 1e-12
+
+
 class Material:
     """Linear isotropic hardening von Mises material (Sec. 2.3, 2.4)."""
 
@@ -85,6 +92,11 @@ class Material:
         dev = tau @ self.E_sig.T
         return SQRT_3_2 * norm_sigma(dev) - (self.sigma_y + self.H * kappa)
 
+    def is_plastic(self, phi: np.ndarray, kappa: np.ndarray) -> np.ndarray:
+        """Plastic branch of eq. (elast_pred): Phi > 0, with exact ties (|Phi| within TIE of the
+        yield stress, the rounding of a return-mapped state) read as Phi = 0, i.e. elastic."""
+        return phi > TIE * (self.sigma_y + self.H * kappa)
+
     def n_hat(self, tau: np.ndarray) -> np.ndarray:
         """n-hat(tau) = E_sig tau / ||E_sig tau||_sigma (eq. (hat_n))."""
         dev = tau @ self.E_sig.T
@@ -103,7 +115,7 @@ class Material:
         """
         tau = self.trial(sigma_k, eta)
         phi = self.yield_function(tau, kappa_k)
-        plastic = phi > 0.0
+        plastic = self.is_plastic(phi, kappa_k)
         phi_plus = np.where(plastic, phi, 0.0)
         c = 3.0 * self.mu / (3.0 * self.mu + self.H)
         ds = eta @ self.C.T
@@ -123,7 +135,7 @@ class Material:
         tau = self.trial(sigma_k, eta)
         phi = self.yield_function(tau, kappa_k)
         D = np.broadcast_to(self.C, (tau.shape[0], 6, 6)).copy()
-        plastic = phi > 0.0
+        plastic = self.is_plastic(phi, kappa_k)
         if np.any(plastic):
             tp = tau[plastic]
             nbar = self.n_hat(tp)

@@ -12,6 +12,7 @@ namespace {
 
 constexpr double kSqrt32 = 1.2247448713915890491;   // sqrt(3/2), correctly rounded
 constexpr double kSqrt23 = 0.81649658092772603273;  // sqrt(2/3), correctly rounded
+constexpr double kTie = 1e-12;                       // exact-tie band of the elastic predictor test
 
 // element local node of offset (ox, oy, oz) -> index ox + 2 oy + 4 oz
 __constant__ int c_off2local[8] = {0, 1, 3, 2, 4, 5, 7, 6};
@@ -190,6 +191,9 @@ __global__ void k_traction(DevMesh M, int face, int nel0, int nel1, int nel2, do
 // eta = B_g u_e; tau = sigma_k + C eta; Phi = sqrt(3/2)||dev tau|| - (sigma_y + H kappa_k).
 // Phi <= 0: dsigma = C eta, dkappa = 0, D = C.
 // Phi > 0 : dsigma = C eta - c sqrt(2/3) Phi n, dkappa = Phi/(3mu+H),
+// A point returned to the yield surface has Phi = 0 in exact arithmetic (elastic by
+// the rule above) but +-1 ulp after rounding: |Phi| <= kTie (sigma_y + H kappa_k)
+// is read as that tie, i.e. elastic.
 //           D = C - 2mu c (1 - rho) E_eps - 2mu c rho n n^T, rho = sqrt(2/3)(sigma_y+H kappa)/||dev tau||,
 //           c = 3mu/(3mu+H)  (the Sec. 3.1 form of eq. (stress_op_deriv_plast)).
 // ---------------------------------------------------------------------------
@@ -240,7 +244,7 @@ __global__ void k_return_map(DevMesh M, const double* __restrict__ du, const dou
   const double phi = kSqrt32 * nrm - yield;
   double ds[6];
   double a = 0.0, b = 0.0, nb[6] = {0, 0, 0, 0, 0, 0};
-  const bool pl = phi > 0.0;
+  const bool pl = phi > kTie * yield;
   if (pl) {
     const double c = 3.0 * mu / (3.0 * mu + M.H);
     const double inv = 1.0 / nrm;

@@ -224,6 +224,27 @@ def test_ssn_load_history_cube12_parity():
     assert np.abs(host(sig).reshape(6, n_gp).T - model.sigma).max() <= 1e-7 * np.abs(model.sigma).max()
 
 
+def test_ssn_cyclic_history_cube12_parity():
+    """The cyclic schedule (load to 1.5 t_y, unload, reverse, unload) on 12^3: unloading from plastic
+    states and reversed flow; displacements per step and the final kappa against the oracle."""
+    w = W.CUBE12_CYCLIC
+    ctx, infos, us, t_y = gpu_history(w, w.n_steps)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    prev = 0.0
+    for k, a in enumerate(w.load_fractions()):
+        info = model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        assert infos[k]["converged"] and info["converged"]
+        assert rel(us[k], model.u) <= 1e-9, (k, rel(us[k], model.u))
+        assert abs(infos[k]["newton"] - info["newton"]) <= 1
+    kap = zeros(ctx.sizes["n_gp"])
+    ctx.get_state(kappa=kap)
+    assert (model.kappa > 0).sum() > 0
+    assert np.abs(host(kap) - model.kappa).max() <= 1e-7 * model.kappa.max()
+
+
 def test_checkpoint_resume_bitwise():
     w = W.SMALL6_RAGGED.with_(newton_tol=1e-9, pcg_rtol=1e-11)
     ctx_a, _, us_a, t_y = gpu_history(w, 4)

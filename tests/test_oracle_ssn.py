@@ -41,6 +41,36 @@ def test_uniaxial_stress_closed_form(n_steps):
         np.testing.assert_allclose(m.kappa, max(s - sy, 0.0) / H, rtol=1e-9, atol=1e-15)
 
 
+def test_uniaxial_cyclic_closed_form():
+    """Load, unload, reverse (the cyclic schedule's phases) on the uniaxial bar.  With isotropic hardening
+    the yield radius after loading is sigma_y + H kappa, so unloading stays elastic until the stress
+    reaches minus that radius; beyond it the reverse flow raises kappa by the excess over H and lowers the
+    plastic strain by the same amount: e11 = s/E + ep, e22 = -nu s/E - ep/2."""
+    m = ElastoplasticModel(UNIAXIAL)
+    E, nu, sy, H = (W.MATERIAL[k] for k in ("young", "poisson", "sigma_y", "hardening"))
+    f1 = m.traction_load((1.0, 0.0, 0.0))
+    ep = kappa = prev = 0.0
+    for level in (0.9, 1.8, 0.6, -0.6, -1.5, -2.0, -1.0, 0.0):
+        s = level * sy
+        info = m.time_step((s - prev) * f1, newton_tol=1e-12, pcg_rtol=1e-14)
+        prev = s
+        assert info["converged"]
+        radius = sy + H * kappa
+        if abs(s) > radius:
+            dk = (abs(s) - radius) / H
+            kappa += dk
+            ep += np.sign(s) * dk
+        e11 = s / E + ep
+        e22 = -nu * s / E - ep / 2
+        scale = abs(e11) + abs(ep) + 1e-30
+        for sub in m.dec.subs:
+            ul = m.u[m.dec.dof_off[sub.p]:m.dec.dof_off[sub.p + 1]].reshape(-1, 3)
+            np.testing.assert_allclose(ul[:, 0], e11 * sub.coords[:, 0], rtol=1e-9, atol=1e-10 * scale)
+            np.testing.assert_allclose(ul[:, 1], e22 * sub.coords[:, 1], rtol=1e-9, atol=1e-10 * scale)
+        np.testing.assert_allclose(m.sigma[:, 0], s, rtol=1e-9, atol=1e-9 * sy)
+        np.testing.assert_allclose(m.kappa, kappa, rtol=1e-9, atol=1e-15)
+
+
 def test_elastic_step_two_newton_iterations_and_criterion_one():
     w = W.SMALL6_RAGGED
     m = ElastoplasticModel(w)

@@ -68,6 +68,7 @@ class Workload:
     pcg_rtol: float = 1e-12
     newton_maxit: int = 30
     pcg_maxit: int = 2000
+    cyclic: bool = False             # load, unload, reverse, unload in four equal phases
 
     @property
     def n_sub(self) -> int:
@@ -78,9 +79,21 @@ class Workload:
         return tuple(int(self.dirichlet.get(f, 0)) for f in FACES)
 
     def load_fractions(self, n_steps: int | None = None) -> list:
-        """Linear ramp: step k (1-based) carries load_factor * k / n_steps."""
+        """Load level after step k (1-based), as a multiple of the first-yield load.
+
+        Linear ramp: load_factor * k / n_steps.  Cyclic: with t = 4 k / n_steps the
+        level is load_factor * (t, 2 - t, 2 - t, t - 4) on the phases t in
+        (0,1], (1,2], (2,3], (3,4]: 0 -> +F -> 0 -> -F -> 0, piecewise linear.
+        """
         n = self.n_steps if n_steps is None else n_steps
-        return [self.load_factor * k / self.n_steps for k in range(1, n + 1)]
+        if not self.cyclic:
+            return [self.load_factor * k / self.n_steps for k in range(1, n + 1)]
+        out = []
+        for k in range(1, n + 1):
+            t = 4.0 * k / self.n_steps
+            level = t if t <= 1.0 else (2.0 - t if t <= 3.0 else t - 4.0)
+            out.append(self.load_factor * level)
+        return out
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -104,8 +117,10 @@ CUBE64 = cube("cube64_8x8x8", 64, 8, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
 CUBE48 = cube("cube48_6x6x6", 48, 6, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
 # 96^3 hex8, 12^3 subdomains of 8^3.
 CUBE96 = cube("cube96_12x12x12", 96, 12, n_steps=20, newton_tol=1e-6, pcg_rtol=1e-8)
-# 128^3 hex8, 16^3 subdomains of 8^3, cyclic load (40 steps).
-CUBE128 = cube("cube128_16x16x16", 128, 16, n_steps=40, newton_tol=1e-6, pcg_rtol=1e-8)
+# 128^3 hex8, 16^3 subdomains of 8^3, cyclic load (40 steps: load, unload, reverse, unload).
+CUBE128 = cube("cube128_16x16x16", 128, 16, n_steps=40, newton_tol=1e-6, pcg_rtol=1e-8, cyclic=True)
+# 12^3 with the cyclic schedule (parity case of the cyclic load).
+CUBE12_CYCLIC = cube("cube12_cyclic", 12, 2, n_steps=8, newton_tol=1e-10, pcg_rtol=1e-12, cyclic=True)
 
 # Small cases for pins and parity tests.
 TINY_1x1x2 = Workload(name="tiny2_1x1x2", nel=(2, 2, 2), cuts=((0, 2), (0, 2), (0, 1, 2)), n_steps=4)
@@ -113,7 +128,8 @@ SMALL4 = cube("small4_2x2x2", 4, 2, n_steps=4)
 SMALL6_RAGGED = Workload(name="small_ragged", nel=(5, 4, 6), cuts=((0, 2, 5), (0, 4), (0, 3, 4, 6)),
                          length=(1.0, 0.8, 1.2), n_steps=4)
 
-WORKLOADS = {w.name: w for w in (CUBE12, CUBE48, CUBE64, CUBE96, CUBE128, TINY_1x1x2, SMALL4, SMALL6_RAGGED)}
+WORKLOADS = {w.name: w for w in (CUBE12, CUBE48, CUBE64, CUBE96, CUBE128, CUBE12_CYCLIC, TINY_1x1x2, SMALL4,
+                                  SMALL6_RAGGED)}
 
 
 def irregular_cube80(seed: int = 0, n: int = 80) -> Workload:
