@@ -10,7 +10,10 @@ and the steps of Algorithm 3 in the paper's order: lambda_Im = N^T H e,
 d~ = d - F lambda_Im, PCGP on lambda_Ker with r^0 = d~, then
 alpha = H N (d - F lambda) and u = K^dagger (f - B^T lambda) + R alpha.
 
-Preconditioner: lumped, F^-1 ~ B K B^T (Sec. 4.2).  The stopping test sits
+Preconditioners (Sec. 4.2): lumped, F^-1 ~ B K B^T; Dirichlet, F^-1 ~ Bbar Sbar Bbar^T
+with Sbar_p the Schur complement of K_p onto the nodes that carry Dirichlet or
+gluing conditions (all three components of such a node), eliminating the other
+("interior") nodes, and Bbar the columns of B at those nodes.  The stopping test sits
 after the updates and reads ||w^{j-1}|| <= eps ||r^0|| (Algorithm 3).  If
 ||w^0|| = 0 the loop ends with lambda_Ker = 0 and zero iterations.
 """
@@ -19,6 +22,36 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+
+
+def constrained_node_dofs(dec, B: sp.spmatrix, p: int) -> np.ndarray:
+    """Local dofs of subdomain p's nodes that carry a row of B (Dirichlet or gluing), all three
+    components of each such node, in local order."""
+    lo, hi = dec.dof_off[p], dec.dof_off[p + 1]
+    has_col = np.diff(B.tocsc()[:, lo:hi].indptr) > 0
+    node = has_col.reshape(-1, 3).any(axis=1)
+    return np.nonzero(np.repeat(node, 3))[0]
+
+
+def dirichlet_schur_blocks(dec, B: sp.spmatrix, K_blocks) -> list:
+    """Per subdomain (global dof indices of the constrained nodes, Sbar_p), with
+    Sbar_p = K_bb - K_bi K_ii^{-1} K_ib (dense Cholesky of the interior block)."""
+    out = []
+    for p, Kp in enumerate(K_blocks):
+        Kp = sp.csr_matrix(Kp)
+        n = Kp.shape[0]
+        b = constrained_node_dofs(dec, B, p)
+        i = np.setdiff1d(np.arange(n), b)
+        Kbb = Kp[b][:, b].toarray()
+        if i.size:
+            Kib = Kp[i][:, b].toarray()
+            Kii = Kp[i][:, i].toarray()
+            X = sla.cho_solve(sla.cho_factor(Kii, lower=True), Kib)
+            S = Kbb - Kib.T @ X
+        else:
+            S = Kbb
+        out.append((dec.dof_off[p] + b, 0.5 * (S + S.T)))
+    return out
 
 
 class TFETISolver:
@@ -34,6 +67,8 @@ class TFETISolver:
         self.NNt_chol = sla.cho_factor(NNt, lower=True)            # H = (N N^T)^{-1} via Cholesky
         self.precond = precond
         self.f_applies = 0
+        if precond == "dirichlet":
+            self.dirichlet_blocks = dirichlet_schur_blocks(dec, self.B, K_blocks)
 
     # -- operators ---------------------------------------------------------------
     def apply_kdag(self, x: np.ndarray) -> np.ndarray:
@@ -58,6 +93,12 @@ class TFETISolver:
     def apply_precond(self, w: np.ndarray) -> np.ndarray:
         if self.precond == "lumped":
             return self.B @ (self.K @ (self.B.T @ w))
+        if self.precond == "dirichlet":
+            v = self.B.T @ w
+            z = np.zeros_like(v)
+            for idx, S in self.dirichlet_blocks:
+                z[idx] = S @ v[idx]
+            return self.B @ z
         if self.precond == "none":
             return w.copy()
         raise ValueError(self.precond)
