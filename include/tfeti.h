@@ -75,6 +75,13 @@ extern "C" {
 /* ---- problem description (host struct, copied by tfeti_setup) ------------ */
 #define TFETI_PRECOND_NONE   0
 #define TFETI_PRECOND_LUMPED 1      /* F^-1 ~ B K B^T (Sec. 4.2) */
+/* F^-1 ~ Bbar Sbar Bbar^T (Sec. 4.2): Sbar_p the Schur complement of K_p onto the
+ * nodes that carry Dirichlet or gluing rows (all components of such a node), the
+ * other nodes eliminated; Bbar the columns of B there.  Applied without forming
+ * Sbar: Sbar x_b = (K_p [x_b; -K_ii^-1 (K_p [x_b; 0])_i])_b with a banded Cholesky
+ * of K_ii (shared by elastic subdomains of one shape and constrained-dof pattern,
+ * refactorised for subdomains with plastic points). */
+#define TFETI_PRECOND_DIRICHLET 2
 
 typedef struct tfeti_problem {
     int32_t nel[3];            /* elements per axis, each >= 1                         */
@@ -274,7 +281,8 @@ int tfeti_apply_F(tfeti_ctx* ctx, const double* x, double* y);
 int tfeti_apply_F32(tfeti_ctx* ctx, const double* x, double* y);
 /* y = P_N x = x - N^T (N N^T)^{-1} N x (Sec. 4.2); device [n_mult]. */
 int tfeti_apply_projector(tfeti_ctx* ctx, const double* x, double* y);
-/* y = B K B^T x, the lumped preconditioner (Sec. 4.2); device [n_mult]. */
+/* y = the problem's preconditioner applied to x (lumped B K B^T or Dirichlet
+ * Bbar Sbar Bbar^T, Sec. 4.2); device [n_mult]. */
 int tfeti_apply_precond(tfeti_ctx* ctx, const double* x, double* y);
 /* y = N x = -R^T B^T x; x device [n_mult], y device [n_coarse]. */
 int tfeti_apply_N(tfeti_ctx* ctx, const double* x, double* y);

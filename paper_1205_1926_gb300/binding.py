@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 TFETI_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "non-positive pivot",
           5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value"}
-PRECOND_NONE, PRECOND_LUMPED = 0, 1
+PRECOND_NONE, PRECOND_LUMPED, PRECOND_DIRICHLET = 0, 1, 2
 MAX_NEWTON = 64
 FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/tfeti.h"
@@ -93,6 +94,34 @@ void build_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R,
     }
 }
 
+// Items of the Dirichlet-preconditioner solves: elastic subdomains grouped R to a CTA
+// per template class, subdomains with plastic points on their own factors.
+void build_dir_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R, std::vector<SolveItem>& items) {
+  const int ns = (int)c->h_subs.size();
+  items.clear();
+  for (size_t k = 0; k < c->dtmpl_off.size(); ++k) {
+    SolveItem it{};
+    it.fac = c->dtmpl_off[k];
+    for (int p = 0; p < ns; ++p) {
+      if (plastic_count[p] > 0 || c->dclass[p] != (int)k) continue;
+      it.sub[it.count++] = p;
+      if (it.count == R) {
+        items.push_back(it);
+        it.count = 0;
+      }
+    }
+    if (it.count) items.push_back(it);
+  }
+  for (int p = 0; p < ns; ++p)
+    if (plastic_count[p] > 0) {
+      SolveItem it{};
+      it.fac = c->dfac_own_base + c->plan.subs[p].fac_off;
+      it.count = 1;
+      it.sub[0] = p;
+      items.push_back(it);
+    }
+}
+
 void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   const int ns = (int)c->h_subs.size();
   int n_pl = 0;
@@ -125,6 +154,16 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   c->n_items = (int)c->h_items.size();
   c->n_items32 = (int)c->h_items32.size();
   c->g_inner_stale = true;
+  if (c->dirichlet) {
+    build_dir_item_list(c, plastic_count, R64, c->h_items_d);
+    build_dir_item_list(c, plastic_count, R32, c->h_items_d32);
+    c->n_items_d = (int)c->h_items_d.size();
+    c->n_items_d32 = (int)c->h_items_d32.size();
+    cudaMemcpyAsync(c->d_items_d, c->h_items_d.data(), sizeof(SolveItem) * c->h_items_d.size(),
+                    cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_items_d32, c->h_items_d32.data(), sizeof(SolveItem) * c->h_items_d32.size(),
+                    cudaMemcpyHostToDevice, c->st);
+  }
   cudaMemcpyAsync(c->d_items, c->h_items.data(), sizeof(SolveItem) * c->h_items.size(), cudaMemcpyHostToDevice,
                   c->st);
   cudaMemcpyAsync(c->d_items32, c->h_items32.data(), sizeof(SolveItem) * c->h_items32.size(),
@@ -257,6 +296,32 @@ void op_project(tfeti_ctx* c, const double* x, double* out) {
   c->launches += 3;
 }
 
+// Dirichlet preconditioner (Sec. 4.2): z = Bbar Sbar Bbar^T w with
+// Sbar x_b = (K [x_b; -K_ii^-1 (K [x_b; 0])_i])_b, the K_ii solves on the masked
+// factors (FP32 copies in the inner iterations of the mixed mode), K applied in FP64.
+void op_precond_dirichlet(tfeti_ctx* c, const double* w, double* out, bool fp32) {
+  const DevMesh& M = c->M;
+  cudaMemsetAsync(c->dx_a, 0, sizeof(double) * M.n_dof, c->st);
+  launch_slots_to_full(M, w, c->dx_a, c->st);                        // [x_b; 0]
+  launch_apply_K(M, c->elem_np, c->dKe, c->dx_a, c->dx_b, c->st);    // v = K [x_b; 0]
+  SolveArgs a = solve_args(c, fp32);
+  a.fac = c->dfac;
+  a.fac32 = c->dfac32;
+  a.items = fp32 ? c->d_items_d32 : c->d_items_d;
+  a.n_items = fp32 ? c->n_items_d32 : c->n_items_d;
+  a.src = c->dx_b;
+  a.bmask = c->d_bmask;
+  a.no_fix = 1;
+  a.dst = c->dx_c;
+  a.in_mode = 4;
+  a.out_mode = 1;
+  launch_sub_solve(M, a, fp32 ? c->solve_smem32 : c->solve_smem, c->st);   // y = K_ii^-1 v_i, 0 on b
+  launch_apply_K(M, c->elem_np, c->dKe, c->dx_c, c->dx_a, c->st);    // t = K [0; y]
+  launch_slots_diff(M, c->dx_b, c->dx_a, c->cbuf, c->st);            // (v - t)_b
+  launch_contract(M, c->cbuf, out, c->st);
+  c->launches += 6;
+}
+
 // FP32 projector and preconditioner of the inner iterations of the mixed mode.
 void op_project32(tfeti_ctx* c, const double* x, double* out) {
   launch_project32(c->M, c->H32, c->l, x, c->gx, c->hx, out, c->st);
@@ -264,7 +329,9 @@ void op_project32(tfeti_ctx* c, const double* x, double* out) {
 }
 
 void op_precond32(tfeti_ctx* c, const double* x, double* out) {
-  if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
+  if (c->dirichlet) {
+    op_precond_dirichlet(c, x, out, true);
+  } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
     launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
     c->launches += 2;
@@ -274,7 +341,9 @@ void op_precond32(tfeti_ctx* c, const double* x, double* out) {
 }
 
 void op_precond(tfeti_ctx* c, const double* x, double* out) {
-  if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
+  if (c->dirichlet) {
+    op_precond_dirichlet(c, x, out, false);
+  } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
     launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
     c->launches += 2;
@@ -350,6 +419,31 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
       for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
       launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)list.size(), len, c->st);
       c->launches += 1;
+    }
+    if (c->dirichlet) {
+      // K_ii factors of the plastic subdomains, on the same band workspaces
+      std::vector<long long> dfacs;
+      for (int p : list) dfacs.push_back(c->dfac_own_base + c->plan.subs[p].fac_off);
+      cudaMemcpyAsync(c->d_list_fac, dfacs.data(), sizeof(long long) * dfacs.size(), cudaMemcpyHostToDevice, c->st);
+      launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band, c->d_list_off, 0, max_rows,
+                       c->plan.max_bw, c->st, c->d_bmask);
+      cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+      launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_list_fac, c->dfac, c->d_err,
+                       c->plan.max_bw, c->n_sm, c->st);
+      c->launches += 2;
+      c->factor_launches += 1;
+      if (c->precision == TFETI_PRECISION_MIXED) {
+        long long len = 0;
+        for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
+        launch_fac_to_f32(c->dfac, c->dfac32, c->d_list_fac, (int)list.size(), len, c->st);
+        c->launches += 1;
+      }
+      int derr = 0;
+      cudaMemcpyAsync(&derr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+      sync(c);
+      if (derr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a Dirichlet-preconditioner factorisation");
+      // the K^+ factor list for kbb fill and later use
+      cudaMemcpyAsync(c->d_list_fac, facs.data(), sizeof(long long) * facs.size(), cudaMemcpyHostToDevice, c->st);
     }
   }
   if (!list.empty())
@@ -1042,6 +1136,62 @@ int setup_impl(tfeti_ctx* c) {
     cudaFree(work);
     if (herr) return fail(c, TFETI_ERR_SINGULAR, "coarse matrix G G^T is not positive definite");
   }
+  // Dirichlet preconditioner: constrained-dof mask, template classes, factor pools
+  if (P.prob.precond == TFETI_PRECOND_DIRICHLET) {
+    c->dirichlet = true;
+    std::vector<uint8_t> mask(P.n_dof, 0);
+    for (long long sl = 0; sl < P.n_copy; ++sl) mask[P.subs[P.slot_sub[sl]].dof_off + P.slot_ldof[sl]] = 1;
+    c->d_bmask = upload(c, mask);
+    std::map<std::pair<int, std::vector<int>>, int> classes;
+    c->dclass.assign(ns, 0);
+    long long tmpl = 0;
+    for (int p = 0; p < ns; ++p) {
+      const SubInfo& sb = P.subs[p];
+      std::vector<int> key(P.slot_ldof.begin() + sb.copy_off, P.slot_ldof.begin() + sb.copy_off + sb.n_copy);
+      auto it = classes.find({sb.shape, key});
+      if (it == classes.end()) {
+        it = classes.emplace(std::make_pair(sb.shape, std::move(key)), (int)c->dclass_rep.size()).first;
+        c->dclass_rep.push_back(p);
+        c->dtmpl_off.push_back(tmpl);
+        tmpl += sb.fac_size;
+      }
+      c->dclass[p] = it->second;
+    }
+    long long max_fac = 0;
+    for (const SubInfo& sb : P.subs) max_fac = std::max<long long>(max_fac, sb.fac_size);
+    c->dfac_own_base = tmpl;
+    c->dfac = dalloc<double>(c, tmpl + P.fac_total + max_fac);
+    c->dfac32 = dalloc<float>(c, tmpl + P.fac_total + max_fac);
+    c->d_items_d = dalloc<SolveItem>(c, ns);
+    c->d_items_d32 = dalloc<SolveItem>(c, ns);
+    c->dx_a = dalloc<double>(c, P.n_dof);
+    c->dx_b = dalloc<double>(c, P.n_dof);
+    c->dx_c = dalloc<double>(c, P.n_dof);
+    // template factors on the representatives' own band workspaces (unused at set-up)
+    std::vector<long long> boffs, foffs;
+    int max_rows = 0;
+    for (size_t k = 0; k < c->dclass_rep.size(); ++k) {
+      const int rp = c->dclass_rep[k];
+      boffs.push_back(c->own_base + P.subs[rp].band_off);
+      foffs.push_back(c->dtmpl_off[k]);
+      max_rows = std::max(max_rows, P.subs[rp].n_dof);
+    }
+    int* dl = upload(c, c->dclass_rep);
+    long long* dbo = upload(c, boffs);
+    long long* dfo = upload(c, foffs);
+    launch_band_fill(M, dl, (int)boffs.size(), c->elem_np, c->dKe, c->band, dbo, 1, max_rows, P.max_bw, c->st,
+                     c->d_bmask);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    launch_band_chol(M, dl, (int)boffs.size(), dbo, c->band, dfo, c->dfac, c->d_err, P.max_bw, c->n_sm, c->st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a Dirichlet-preconditioner factorisation");
+    long long len = 0;
+    for (int rp : c->dclass_rep) len = std::max<long long>(len, P.subs[rp].fac_size);
+    launch_fac_to_f32(c->dfac, c->dfac32, dfo, (int)foffs.size(), len, c->st);
+    c->launches += 3;
+  }
   // shared elastic factor per subdomain shape
   {
     std::vector<int> reps;
@@ -1273,6 +1423,17 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
       cudaMemcpyAsync(c->d_list_fac, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
       launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)offs.size(), len, c->st);
       sync(c);
+    }
+    if (c->dirichlet) {
+      std::vector<long long> doffs;
+      for (const SolveItem& it : c->h_items_d)
+        if (it.fac >= c->dfac_own_base) doffs.push_back(it.fac);
+      if (!doffs.empty()) {
+        cudaMemcpyAsync(c->d_list_fac, doffs.data(), sizeof(long long) * doffs.size(), cudaMemcpyHostToDevice,
+                        c->st);
+        launch_fac_to_f32(c->dfac, c->dfac32, c->d_list_fac, (int)doffs.size(), len, c->st);
+        sync(c);
+      }
     }
   }
   c->precision = mode;

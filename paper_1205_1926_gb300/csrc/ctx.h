@@ -84,6 +84,20 @@ struct tfeti_ctx {
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
          *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *tm = nullptr;
   double* vsol = nullptr;   // K^+(f - B^T lambda) of the last residual solve, device [n_dof]
+  // Dirichlet preconditioner (Sec. 4.2): factors of K_p with the constrained-node dofs
+  // replaced by identity rows and columns (K_ii), one template per (shape, pattern of
+  // constrained dofs) class for elastic subdomains, own ones for plastic subdomains
+  bool dirichlet = false;
+  uint8_t* d_bmask = nullptr;               // 1 at the local dofs of constrained nodes, [n_dof]
+  std::vector<int> dclass, dclass_rep;      // class of each subdomain; a representative of each class
+  std::vector<long long> dtmpl_off;         // per class: offset of its factor in dfac
+  long long dfac_own_base = 0;
+  double* dfac = nullptr;
+  float* dfac32 = nullptr;
+  std::vector<tfeti::SolveItem> h_items_d, h_items_d32;
+  tfeti::SolveItem *d_items_d = nullptr, *d_items_d32 = nullptr;
+  int n_items_d = 0, n_items_d32 = 0;
+  double *dx_a = nullptr, *dx_b = nullptr, *dx_c = nullptr;   // [n_dof] work vectors
   // history start (tfeti_set_recycling): ring of the last rec_q solutions lambda_Ker and
   // their products F lambda_Ker, [rec_q][n_mult] each
   int rec_q = 0, rec_n = 0, rec_head = 0;

@@ -98,7 +98,8 @@ void launch_return_map(const DevMesh& M, const double* du, const double* sig_k, 
 void launch_elem_correction(const DevMesh& M, GPData gp, int* elem_np, int* sub_np, double* dKe, cudaStream_t st);
 void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const int* elem_np, const double* dKe,
                       double* band, const long long* band_off_list, int elastic_only, int max_rows, int max_bw,
-                      cudaStream_t st);
+                      cudaStream_t st,
+                      const uint8_t* bmask = nullptr);
 // Boundary 3x3 blocks of K for the listed subdomains (elastic_only: the shape's elastic template);
 // also rounded to FP32 into kbb32 at the same offsets when kbb32 != null.
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
@@ -118,7 +119,7 @@ void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const l
                       int n_sm, cudaStream_t st);
 
 // Subdomain K^+ solve.  in_mode 0: x = B^T lam at the interface slots (zero
-// elsewhere); 1: x = src - B^T lam (lam nullable).  out_mode 0: interface slots
+// elsewhere); 1: x = src - B^T lam (lam nullable); 4: see bmask.  out_mode 0: interface slots
 // to cbuf; 1: full local vector to dst (+ R alpha if alpha != null); 3: both.
 struct SolveArgs {
   const double* lam;
@@ -142,6 +143,10 @@ struct SolveArgs {
   int rep_sub;
   float* S32;
   long long s_off;
+  // in_mode 4 (Dirichlet preconditioner): x = src with the dofs marked in bmask zeroed;
+  // no_fix: the factor has no fixing dofs (they are not zeroed before and after)
+  const uint8_t* bmask;
+  int no_fix;
 };
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
 size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
@@ -184,6 +189,10 @@ void launch_project32(const DevMesh& M, const float* H32, long long l, const dou
 // Values of the explicit G from R and the (row, slot, coefficient) entries (set-up).
 void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, const int* gt_e, double* Gv,
                    float* Gv32, double* GTv, float* GTv32, cudaStream_t st);
+// Dirichlet preconditioner pieces: xfull = B^T w on the copy-slot dofs, 0 elsewhere
+// (xfull zeroed by the caller); cbuf[slot] = v[dof] - t[dof] on the copy slots.
+void launch_slots_to_full(const DevMesh& M, const double* w, double* xfull, cudaStream_t st);
+void launch_slots_diff(const DevMesh& M, const double* v, const double* t, double* cbuf, cudaStream_t st);
 void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
                      cudaStream_t st, int max_copy);
 

@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     T* x = vec + r * npad;
     if (a.in_mode == 0)
       for (int i = tid; i < n; i += nt) x[i] = T(0);
+    else if (a.in_mode == 4)
+      for (int i = tid; i < n; i += nt) x[i] = a.bmask[S.dof_off + i] ? T(0) : T(a.src[S.dof_off + i]);
     else
       for (int i = tid; i < n; i += nt) x[i] = a.src ? T(a.src[S.dof_off + i]) : T(0);
   }
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
     }
   }
   __syncthreads();
-  if (tid < 6)
+  if (tid < 6 && !a.no_fix)
     for (int r = 0; r < R; ++r) vec[r * npad + S0.fix[tid]] = T(0);
   __syncthreads();
 
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
         if (r < R) vec[r * npad + i] = v[r];
     __syncthreads();
   }
-  if (tid < 6)
+  if (tid < 6 && !a.no_fix)
     for (int r = 0; r < R; ++r) vec[r * npad + S0.fix[tid]] = T(0);
   __syncthreads();
 

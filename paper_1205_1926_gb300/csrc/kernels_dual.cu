@@ -180,6 +180,21 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __res
   }
 }
 
+// Dirichlet preconditioner: B^T w onto the copy-slot dofs of the full local vectors.
+__global__ void k_slots_to_full(DevMesh M, const double* __restrict__ w, double* xfull) {
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= M.n_copy) return;
+  const SubDev& S = M.subs[M.slot_sub[sl]];
+  xfull[S.dof_off + M.slot_ldof[sl]] = bt_at_slot(M, w, sl);
+}
+
+__global__ void k_slots_diff(DevMesh M, const double* __restrict__ v, const double* __restrict__ t, double* cbuf) {
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= M.n_copy) return;
+  const long long d = M.subs[M.slot_sub[sl]].dof_off + M.slot_ldof[sl];
+  cbuf[sl] = v[d] - t[d];
+}
+
 // Deterministic dot product: fixed grid, fixed per-block order, fixed final order.
 __global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, long long n,
                               double* partial) {
@@ -549,6 +564,14 @@ void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const l
   const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
   cudaFuncSetAttribute(k_lumped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_lumped<double><<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
+}
+
+void launch_slots_to_full(const DevMesh& M, const double* w, double* xfull, cudaStream_t st) {
+  if (M.n_copy > 0) k_slots_to_full<<<blocks_for(M.n_copy, 256), 256, 0, st>>>(M, w, xfull);
+}
+
+void launch_slots_diff(const DevMesh& M, const double* v, const double* t, double* cbuf, cudaStream_t st) {
+  if (M.n_copy > 0) k_slots_diff<<<blocks_for(M.n_copy, 256), 256, 0, st>>>(M, v, t, cbuf);
 }
 
 void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,

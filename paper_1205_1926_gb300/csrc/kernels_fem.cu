@@ -370,8 +370,12 @@ __device__ double stiffness_entry(const DevMesh& M, const SubDev& S, const int* 
 
 // Band storage of subdomain K_p with the fixing dofs replaced by identity rows:
 // band[r*(bw+1) + k] = K[r][r - bw + k] (lower band, row-major).
+// With bmask == null the six fixing dofs of Remark 1 get identity rows and columns
+// (K_rr of the generalised inverse); with bmask the dofs marked in it do (K_ii of the
+// Dirichlet preconditioner: the constrained nodes eliminated, Sec. 4.2).
 __global__ void k_band_fill(DevMesh M, const int* __restrict__ sub_list, const int* elem_np, const double* dKe,
-                            double* band, const long long* __restrict__ band_off_list, int elastic_only) {
+                            double* band, const long long* __restrict__ band_off_list, int elastic_only,
+                            const uint8_t* __restrict__ bmask) {
   const int item = blockIdx.y;
   const int p = sub_list[item];
   const SubDev& S = M.subs[p];
@@ -383,8 +387,12 @@ __global__ void k_band_fill(DevMesh M, const int* __restrict__ sub_list, const i
   double v = 0.0;
   if (c >= 0) {
     bool fixed = false;
+    if (bmask) {
+      fixed = bmask[S.dof_off + r] | bmask[S.dof_off + c];
+    } else {
 #pragma unroll
-    for (int t = 0; t < 6; ++t) fixed |= (S.fix[t] == r) | (S.fix[t] == c);
+      for (int t = 0; t < 6; ++t) fixed |= (S.fix[t] == r) | (S.fix[t] == c);
+    }
     if (fixed) v = (r == c) ? 1.0 : 0.0;
     else v = stiffness_entry(M, S, elem_np, dKe, r, c, elastic_only != 0);
   }
@@ -532,10 +540,10 @@ void launch_elem_correction(const DevMesh& M, GPData gp, int* elem_np, int* sub_
 
 void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const int* elem_np, const double* dKe,
                       double* band, const long long* band_off_list, int elastic_only, int max_rows, int max_bw,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint8_t* bmask) {
   if (n_list <= 0) return;
   dim3 grid(blocks_for((long long)max_rows * (max_bw + 1), 256), n_list);
-  k_band_fill<<<grid, 256, 0, st>>>(M, sub_list, elem_np, dKe, band, band_off_list, elastic_only);
+  k_band_fill<<<grid, 256, 0, st>>>(M, sub_list, elem_np, dKe, band, band_off_list, elastic_only, bmask);
 }
 
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,

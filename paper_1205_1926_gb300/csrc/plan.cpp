@@ -50,7 +50,8 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
   for (int f = 0; f < 6; ++f)
     if (prob->dirichlet[f] < 0 || prob->dirichlet[f] > 7) return bad(plan, "bad dirichlet mask"), TFETI_ERR_ARG;
   if (prob->traction_face < 0 || prob->traction_face > 5) return bad(plan, "bad traction face"), TFETI_ERR_ARG;
-  if (prob->precond != TFETI_PRECOND_NONE && prob->precond != TFETI_PRECOND_LUMPED)
+  if (prob->precond != TFETI_PRECOND_NONE && prob->precond != TFETI_PRECOND_LUMPED &&
+      prob->precond != TFETI_PRECOND_DIRICHLET)
     return bad(plan, "bad preconditioner"), TFETI_ERR_ARG;
 
   const int nx = prob->nel[0], ny = prob->nel[1], nz = prob->nel[2];

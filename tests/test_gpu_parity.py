@@ -15,6 +15,7 @@ import pytest
 import workloads as W
 from oracle.decomp import FixingNodeInverse
 from oracle.ssn import ElastoplasticModel, run_load_history
+from oracle.tfeti import TFETISolver
 from oracle.fem import element_strain_matrices, gauss_weight_detj, NODE_OFFSETS
 from oracle.material import Material
 
@@ -328,6 +329,65 @@ def test_cube64_full_size_properties():
                 force[c] += contrib.sum()
                 scale += np.abs(contrib).sum()
         assert np.abs(force).max() <= 1e-6 * scale
+
+
+# ---------------------------------------------------------------------------- Dirichlet preconditioner (Sec. 4.2)
+@pytest.mark.parametrize("w,plastic", [(W.SMALL6_RAGGED, True), (W.CUBE12, True), (W.CUBE12, False),
+                                       (ONE_ELEMENT_BOXES, True)])
+def test_dirichlet_precond_parity(w, plastic):
+    """Bbar Sbar Bbar^T through the masked K_ii factors (templates for elastic subdomains, own factors for
+    plastic ones) against the oracle's dense Schur complements."""
+    m, sig, kap, du = plastic_state(w, seed=81)
+    if not plastic:
+        du = np.zeros_like(du)
+        sig, kap = np.zeros_like(sig), np.zeros_like(kap)
+    ctx = T.Context(w, precond=T.PRECOND_DIRICHLET)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    ctx.assemble_tangent(dev(du), dev(np.zeros(s["n_dof"])))
+    m.sigma, m.kappa = sig, kap
+    Kb, _, _ = m.assemble(du, np.zeros(m.dec.n_dof))
+    solver = TFETISolver(m.dec, Kb, None, R=m.R, precond="dirichlet")
+    lam = W.seeded_vector(s["n_mult"], seed=82)
+    out = zeros(s["n_mult"])
+    ctx.apply("precond", dev(lam), out)
+    assert rel(host(out), solver.apply_precond(lam)) <= 1e-10
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_dirichlet_dual_pcg_and_history_cube12(mixed):
+    """Algorithm 3 with the Dirichlet preconditioner: the 12^3 load history against the oracle run with
+    the same preconditioner (displacements per step, Newton counts), fewer PCGP iterations than lumped."""
+    w = W.CUBE12
+    ctx = T.Context(w, precond=T.PRECOND_DIRICHLET)
+    if mixed:
+        ctx.set_precision(True, 1e-3)
+    t_y = ctx.first_yield_traction(w.traction_dir)
+    model = ElastoplasticModel(w, precond="dirichlet")
+    t_or = model.first_yield_traction()
+    assert abs(t_y - t_or) <= 1e-10 * t_or
+    f1 = model.traction_load(w.traction_dir)
+    df, u = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_dof"])
+    prev, its_d = 0.0, 0
+    for a in w.load_fractions():
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        oinfo = model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        ctx.get_state(u=u)
+        assert info["converged"] and rel(host(u), model.u) <= 1e-9
+        assert abs(info["newton"] - oinfo["newton"]) <= 1
+        if not mixed:
+            assert all(abs(a_ - b_) <= 1 for a_, b_ in zip(info["pcg"], oinfo["pcg"]))
+        its_d += sum(oinfo["pcg"])
+    lump = ElastoplasticModel(w)
+    t_l = lump.first_yield_traction()
+    f1 = lump.traction_load(w.traction_dir)
+    prev, its_l = 0.0, 0
+    for a in w.load_fractions():
+        its_l += sum(lump.time_step((a - prev) * t_l * f1, w.newton_tol, w.pcg_rtol)["pcg"])
+        prev = a
+    assert its_d < its_l
 
 
 # ---------------------------------------------------------------------------- mixed precision (FP64-refined PCGP)
