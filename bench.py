@@ -45,11 +45,12 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def workload_config(w, steps, warmup):
+def workload_config(w, steps, warmup, precond="lumped"):
+    sched = "cyclic (load, unload, reverse, unload) to +-" if w.cyclic else "ramp to "
     return {"workload": f"{w.name}: {w.nel[0]}x{w.nel[1]}x{w.nel[2]} hex8 bricks, "
                         f"{len(w.cuts[0]) - 1}x{len(w.cuts[1]) - 1}x{len(w.cuts[2]) - 1} subdomains, "
-                        f"{w.n_steps}-step ramp to {w.load_factor} x first-yield x-traction on z=1",
-            "newton_tol": w.newton_tol, "pcg_rtol": w.pcg_rtol, "preconditioner": "lumped",
+                        f"{w.n_steps}-step {sched}{w.load_factor} x first-yield x-traction on z=1",
+            "newton_tol": w.newton_tol, "pcg_rtol": w.pcg_rtol, "preconditioner": precond,
             "kdag": "fixing-node banded Cholesky (shared elastic factor per box shape)",
             "load_steps_timed": f"{warmup + 1}..{warmup + steps}",
             "l2": "inputs larger than L2 (subdomain factors 2.5 GB), no flush"}
@@ -240,7 +241,8 @@ def run_gpu(args, rank, world, local_rank):
     w = W.WORKLOADS[args.workload]
     n_total = args.warmup + args.steps
     stream = torch.cuda.Stream(device=dev)
-    ctx = T.Context(w, stream=stream)
+    pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
+    ctx = T.Context(w, stream=stream, precond=pre)
     if args.precision == "mixed":
         ctx.set_precision(True, args.inner_rtol)
     if args.learned:
@@ -315,7 +317,7 @@ def run_gpu(args, rank, world, local_rank):
     # ---- the other arms of the metric on the same load history: mixed precision, and mixed
     # precision with the history start of the dual PCGP (the "learned" start)
     def run_arm(recycling):
-        actx = T.Context(w, stream=stream)
+        actx = T.Context(w, stream=stream, precond=pre)
         actx.set_precision(True, args.inner_rtol)
         actx.set_recycling(recycling)
         if args.no_graphs:
@@ -383,7 +385,7 @@ def run_gpu(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": workload_config(w, args.steps, args.warmup) | {
+            "config": workload_config(w, args.steps, args.warmup, args.precond) | {
                 "parallelism": "replicas" if world > 1 else "1 GPU", "precision": args.precision,
                 "inner_rtol": args.inner_rtol if args.precision == "mixed" else None,
                 "history_start": args.history if args.learned else 0,
@@ -433,6 +435,8 @@ def main():
                     help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms of an FP64 run")
+    ap.add_argument("--precond", default="lumped", choices=["lumped", "dirichlet"],
+                    help="PCGP preconditioner of Sec. 4.2 (every arm)")
     ap.add_argument("--learned", action="store_true",
                     help="start the timed arm's dual solves from the solver's history (see --history)")
     ap.add_argument("--history", type=int, default=8,
