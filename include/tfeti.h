@@ -172,7 +172,7 @@ int tfeti_assemble_tangent(tfeti_ctx* ctx, const double* du, const double* df, d
 typedef struct tfeti_pcg_info {
     int32_t iterations;        /* PCGP iterations j                                     */
     int32_t converged;         /* 1 if ||w|| <= rtol ||r^0||                             */
-    int32_t used_lambda0;      /* 1: caller lambda0 used; 2: history start taken        */
+    int32_t used_lambda0;      /* 1: caller lambda0; 2: history start; 3: with the MLP  */
     int32_t f_applies;         /* FP64 subdomain-solve passes incl. set-up and recovery */
     double  r0_norm;           /* ||r^0|| = ||d~||                                      */
     double  w_norm;            /* last ||w^{j-1}||                                      */
@@ -207,7 +207,7 @@ typedef struct tfeti_step_info {
     int64_t plastic_committed;               /* plastic points of the committed state     */
     double  seconds;
     int32_t outer[TFETI_MAX_NEWTON];         /* FP64 refinement steps per Newton iteration */
-    int32_t history[TFETI_MAX_NEWTON];       /* 1 if the dual solve started from the history */
+    int32_t history[TFETI_MAX_NEWTON];       /* 1: history start, 2: with the MLP vector  */
 } tfeti_step_info;
 
 /* Algorithm 4 for one time step: du = o; Newton iterations of Algorithm 5 +
@@ -252,6 +252,30 @@ int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);
  * tolerance.  Stored products of earlier tangents are used as they are (the
  * fallback covers a stale prediction).  Resets the history. */
 int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
+
+/* Learned start (extension; needs tfeti_set_recycling with q in 1..7): for the first
+ * Newton solve of every load step a per-interface MLP predicts lambda_Ker row by row
+ * from the row's values of the first-solve lambda_Ker of the previous two load steps
+ * (la, lb), the current d~, the load-increment ratio rho = df.df_prev / |df_prev|^2
+ * and the plastic fractions of the row's subdomains now and at the previous step:
+ * features x = (la/s, (la - lb)/s, d~/s_d, rho, pf_now, pf_prev, 0, 0), s = RMS(la),
+ * s_d = RMS(d~); prediction s (x_0 + net(x)), net = 8 -> 64 -> 64 -> 1 with ReLU,
+ * FP16 weights, FP32 accumulation.  The projected prediction joins the stored
+ * solutions as one more vector of the Galerkin start (so the zero start stays the
+ * fallback).  After the solve the network takes `epochs` Adam steps (learning rate
+ * lr, FP32 master weights) on 64 x 128 rows of this solve against its lambda_Ker.
+ * Weights start from a fixed seed with a zero last layer.  enable = 0 turns it off. */
+#define TFETI_MLP_PARAMS 4801
+int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr);
+/* For tests and tools: the FP32 master weights (host float[TFETI_MLP_PARAMS]: W1 [64][8],
+ * b1 [64], W2 [64][64], b2 [64], w3 [64], b3), the prediction y (device [n_mult]) for
+ * given device inputs la, lb, d [n_mult], pf_now, pf_prev [n_sub] and host scal[4] =
+ * (1/s, 1/s_d, rho, s), and `steps` Adam steps towards the device target [n_mult]. */
+int tfeti_mlp_weights(tfeti_ctx* ctx, float* out);
+int tfeti_mlp_predict(tfeti_ctx* ctx, const double* la, const double* lb, const double* d, const float* pf_now,
+                      const float* pf_prev, const float* scal, double* y);
+int tfeti_mlp_train(tfeti_ctx* ctx, const double* la, const double* lb, const double* d, const float* pf_now,
+                    const float* pf_prev, const float* scal, const double* target, int32_t steps);
 
 /* Launch mode of the mixed-precision inner PCGP.  enable != 0 (default): each
  * inner solve is one CUDA graph launch whose body is one iteration inside a

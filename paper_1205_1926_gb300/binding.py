@@ -19,6 +19,7 @@ TFETI_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "non-positive pivot",
           5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value"}
 PRECOND_NONE, PRECOND_LUMPED, PRECOND_DIRICHLET = 0, 1, 2
+MLP_PARAMS = 4801
 MAX_NEWTON = 64
 FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
 
@@ -86,6 +87,10 @@ SIGNATURES = {
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
     "tfeti_set_recycling": (C.c_int, [_P, _I]),
+    "tfeti_set_learned": (C.c_int, [_P, _I, _I, _D]),
+    "tfeti_mlp_weights": (C.c_int, [_P, _P]),
+    "tfeti_mlp_predict": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "tfeti_mlp_train": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "tfeti_get_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_state": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_apply_F": (C.c_int, [_P, _P, _P]),
@@ -278,6 +283,26 @@ class Context:
     def set_recycling(self, q: int):
         """Start each dual solve from the best combination of the last q solutions (0: off)."""
         return self._check(self.lib.tfeti_set_recycling(self.h, int(q)), "tfeti_set_recycling")
+
+    def set_learned(self, enable: bool, epochs: int = 16, lr: float = 1e-3):
+        """Per-interface MLP prediction in the history start of every load step's first Newton solve."""
+        return self._check(self.lib.tfeti_set_learned(self.h, 1 if enable else 0, int(epochs), float(lr)),
+                           "tfeti_set_learned")
+
+    def mlp_weights(self):
+        out = (C.c_float * MLP_PARAMS)()
+        self._check(self.lib.tfeti_mlp_weights(self.h, C.cast(out, _P)), "tfeti_mlp_weights")
+        return list(out)
+
+    def mlp_predict(self, la, lb, d, pf_now, pf_prev, scal, y):
+        sc = (C.c_float * 4)(*scal)
+        return self._check(self.lib.tfeti_mlp_predict(self.h, _ptr(la), _ptr(lb), _ptr(d), _ptr(pf_now), _ptr(pf_prev),
+                                                      C.cast(sc, _P), _ptr(y)), "tfeti_mlp_predict")
+
+    def mlp_train(self, la, lb, d, pf_now, pf_prev, scal, target, steps):
+        sc = (C.c_float * 4)(*scal)
+        return self._check(self.lib.tfeti_mlp_train(self.h, _ptr(la), _ptr(lb), _ptr(d), _ptr(pf_now), _ptr(pf_prev),
+                                                    C.cast(sc, _P), _ptr(target), int(steps)), "tfeti_mlp_train")
 
     def set_graphs(self, enable: bool):
         """Inner PCGP of the mixed mode as one CUDA graph launch (default) or kernel by kernel."""

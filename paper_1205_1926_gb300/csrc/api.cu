@@ -686,35 +686,72 @@ std::vector<double> history_coefficients(const double* g, int n) {
   return c;
 }
 
+bool mlp_ready(const tfeti_ctx* c) { return c->mlp_on && c->newton_first && c->mlp_seen >= 1; }
+
+// Scalars of the MLP features: 1/s, 1/s_d, rho, s with s the RMS of the previous
+// step's first-solve lambda_Ker and s_d the RMS of d~ (||d~|| = r0).  False if s = 0.
+bool mlp_scalars(tfeti_ctx* c, double r0) {
+  const long long m = c->M.n_mult;
+  const double s = std::sqrt(std::max(0.0, dot_host(c, c->mlp_la, c->mlp_la, m)) / (double)m);
+  const double sd = r0 / std::sqrt((double)m);
+  c->mlp_scal_valid = s > 0.0 && sd > 0.0;
+  if (!c->mlp_scal_valid) return false;
+  c->h_scal[0] = (float)(1.0 / s);
+  c->h_scal[1] = (float)(1.0 / sd);
+  c->h_scal[2] = (float)c->mlp_rho;
+  c->h_scal[3] = (float)s;
+  cudaMemcpyAsync(c->mlp_scal, c->h_scal, sizeof(c->h_scal), cudaMemcpyHostToDevice, c->st);
+  sync(c);
+  return true;
+}
+
 // History start (extension of Algorithm 3): on entry r = d~ and lambda_Ker = o.
-// Returns 0 if not applied (state unchanged), 1 if lambda_Ker = P(sum c_j lambda_j)
-// was taken (r = d~ - F lambda_Ker by a residual solve), 2 if it was tried and
+// The basis is the stored solutions and, for the first Newton solve of a load step
+// with the learned start on, the projected MLP prediction (its F-product by one
+// F-apply, FP32 in the mixed mode).  Returns 0 if not applied (state unchanged), 1
+// if lambda_Ker = P(sum c_j lambda_j) was taken (r = d~ - F lambda_Ker by a residual
+// solve), 3 if so with a nonzero coefficient on the MLP vector, 2 if it was tried and
 // rejected because ||P r|| did not fall below ||P d~|| (state reset to d~, the
 // residual-solve vector no longer matches).
-int history_start(tfeti_ctx* c, const double* f, double tol_abs) {
+int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   const long long m = c->M.n_mult;
   const int n = c->rec_n;
   op_project(c, c->r, c->w);
   const double w0 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
   if (w0 <= tol_abs) return 0;   // the zero start already meets the stopping test
-  launch_rec_gram(c->rec_L, c->rec_FL, c->r, n, m, c->rec_partial, c->rec_out, c->st);
+  int nb = n;
+  bool with_mlp = false;
+  if (mlp_ready(c) && mlp_scalars(c, r0)) {
+    // slot n is free: the ring keeps rec_q solutions in rec_q + 1 slots
+    double* Ln = c->rec_L + (long long)n * m;
+    double* FLn = c->rec_FL + (long long)n * m;
+    launch_mlp_infer(c->M, c->mlp_w16, c->mlp_la, c->mlp_lb, c->r, c->pf_now, c->pf_prev, c->mlp_scal, c->y, c->st);
+    op_project(c, c->y, Ln);
+    if (c->precision == TFETI_PRECISION_MIXED) op_F32(c, Ln, FLn);
+    else op_F(c, Ln, FLn);
+    c->launches += 1;
+    nb = n + 1;
+    with_mlp = true;
+  }
+  if (nb == 0) return 0;
+  launch_rec_gram(c->rec_L, c->rec_FL, c->r, nb, m, c->rec_partial, c->rec_out, c->st);
   double g[kRecMax * kRecMax + kRecMax];
   cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
   sync(c);
   c->launches += 2;
-  std::vector<double> coef = history_coefficients(g, n);
+  std::vector<double> coef = history_coefficients(g, nb);
   bool any = false;
   for (double v : coef) any = any || (v != 0.0 && std::isfinite(v));
   if (!any || !(w0 > 0.0)) return 0;
-  cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->st);
   // predicted residual with the stored products: d~ - sum c_j F lambda_j
-  launch_rec_combine(c->rec_FL, c->rec_c, n, m, c->r, -1.0, c->tm, c->st);
+  launch_rec_combine(c->rec_FL, c->rec_c, nb, m, c->r, -1.0, c->tm, c->st);
   op_project(c, c->tm, c->z);
   c->launches += 1;
   const double pred = std::sqrt(std::max(0.0, dot_host(c, c->z, c->z, m)));
   if (!(pred < c->rec_accept * w0)) return 0;
   ++c->rec_tried;
-  launch_rec_combine(c->rec_L, c->rec_c, n, m, nullptr, 1.0, c->y, c->st);
+  launch_rec_combine(c->rec_L, c->rec_c, nb, m, nullptr, 1.0, c->y, c->st);
   op_project(c, c->y, c->lamk);
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
   c->launches += 2;
@@ -727,7 +764,33 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs) {
     return 2;
   }
   ++c->rec_used;
+  if (with_mlp && coef[n] != 0.0) {
+    ++c->mlp_used;
+    return 3;
+  }
   return 1;
+}
+
+// Online training of the MLP after the first Newton solve of a load step: target
+// lambda_Ker of this solve, features from the two previous steps' solutions, this
+// solve's d~, the plastic fractions and rho; then the histories move on by one step.
+void mlp_train(tfeti_ctx* c, double r0) {
+  const long long m = c->M.n_mult;
+  if (c->mlp_seen >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0))) {
+    for (int e = 0; e < c->mlp_epochs; ++e) {
+      ++c->mlp_t;
+      const long long start = (104729LL * c->mlp_t + 7919LL * e) % m;
+      launch_mlp_train_step(c->M, c->mlp_w, c->mlp_la, c->mlp_lb, c->dtil, c->pf_now, c->pf_prev, c->mlp_scal,
+                            c->lamk, start, 7919, c->mlp_blocks, c->mlp_partial, c->mlp_w, c->mlp_m1, c->mlp_m2,
+                            c->mlp_w16, c->mlp_lr, c->mlp_t, c->st);
+      c->launches += 2;
+    }
+  }
+  cudaMemcpyAsync(c->mlp_lb, c->mlp_la, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->mlp_la, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->pf_prev, c->pf_now, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st);
+  c->mlp_scal_valid = false;
+  ++c->mlp_seen;
 }
 
 // Store the solution of the finished solve: lambda_Ker and F lambda_Ker = d~ - r.
@@ -767,9 +830,10 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     residual_solve(c, f, c->lam, c->r);      // r = d~ - F lambda_Ker
     c->launches += 1;
     used_l0 = 1;
-  } else if (history && c->rec_n > 0 && r0 > 0.0) {
-    const int h = history_start(c, f, rtol * r0);
+  } else if (history && (c->rec_n > 0 || mlp_ready(c)) && r0 > 0.0) {
+    const int h = history_start(c, f, rtol * r0, r0);
     if (h == 1) used_l0 = 2;
+    if (h == 3) used_l0 = 3;
     if (h == 2) v_current = false;
   }
   int it = 0, converged = 0, status = TFETI_OK, outer = 0;
@@ -830,7 +894,10 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
   c->launches += 1;
   if (!v_current) residual_solve(c, f, c->lam, c->r);
-  if (history && r0 > 0.0 && status == TFETI_OK) history_push(c);   // r is the true residual here
+  if (history && r0 > 0.0 && status == TFETI_OK) {   // r is the true residual here
+    if (c->mlp_on && c->newton_first) mlp_train(c, r0);
+    history_push(c);
+  }
   launch_G_apply(M, c->r, nullptr, c->gx, -1.0, c->st);
   launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
   c->launches += 2;
@@ -1350,15 +1417,23 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
   cudaMemcpyAsync(c->df, df, sizeof(double) * n, df_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                   c->st);
   cudaMemsetAsync(c->du, 0, sizeof(double) * n, c->st);
+  if (c->mlp_on) {
+    // load-increment ratio of the MLP features: (df . df_prev) / ||df_prev||^2
+    double den = c->have_dfprev ? dot_host(c, c->mlp_dfprev, c->mlp_dfprev, n) : 0.0;
+    c->mlp_rho = den > 0.0 ? dot_host(c, c->df, c->mlp_dfprev, n) / den : 1.0;
+  }
   int status = TFETI_OK;
   double nrm_old = 0.0;
   for (int i = 1; i <= newton_maxit; ++i) {
     status = assemble(c, c->du, c->df, nullptr);
     if (status != TFETI_OK) break;
+    if (c->mlp_on && i == 1) launch_plastic_fraction(M, c->sub_np, c->pf_now, c->st);
+    c->newton_first = i == 1;
     std::vector<int> np(M.n_sub);
     cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
     tfeti_pcg_info pi{};
     status = dual_pcg(c, c->f_full, c->tn, nullptr, nullptr, pcg_rtol, pcg_maxit, &pi);
+    c->newton_first = false;
     if (status != TFETI_OK) break;
     const double nd = std::sqrt(dot_host(c, c->tn, c->tn, n));
     launch_axpby(n, 1.0, c->du, 1.0, c->tn, c->du, c->st);
@@ -1372,7 +1447,7 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
     loc.newton = i;
     loc.pcg[i - 1] = pi.iterations;
     loc.outer[i - 1] = pi.outer_iterations;
-    loc.history[i - 1] = pi.used_lambda0 == 2 ? 1 : 0;
+    loc.history[i - 1] = pi.used_lambda0 == 2 ? 1 : (pi.used_lambda0 == 3 ? 2 : 0);
     loc.plastic[i - 1] = npl;
     loc.criterion[i - 1] = crit;
     loc.refactored[i - 1] = c->last_refactored.empty() ? 0 : c->last_refactored.back();
@@ -1384,6 +1459,10 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
       loc.converged = 1;
       break;
     }
+  }
+  if (c->mlp_on) {
+    cudaMemcpyAsync(c->mlp_dfprev, c->df, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
+    c->have_dfprev = true;
   }
   if (status == TFETI_OK && !loc.converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "Newton iteration limit");
   if (status == TFETI_OK) {
@@ -1487,11 +1566,14 @@ int tfeti_set_graphs(tfeti_ctx* c, int32_t enable) {
 
 int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   if (!c || q < 0 || q > kRecMax) return fail(c, TFETI_ERR_ARG, "history size must be in 0..8");
+  if (c->mlp_on && (q < 1 || q > kRecMax - 1))
+    return fail(c, TFETI_ERR_ARG, "with the learned start the history size must be in 1..7");
   const long long m = c->M.n_mult;
   if (q > 0 && q > c->rec_q) {
     try {
-      c->rec_L = dalloc<double>(c, (size_t)q * (size_t)std::max(1LL, m));
-      c->rec_FL = dalloc<double>(c, (size_t)q * (size_t)std::max(1LL, m));
+      // one spare slot for the MLP vector of the learned start
+      c->rec_L = dalloc<double>(c, (size_t)(q + 1) * (size_t)std::max(1LL, m));
+      c->rec_FL = dalloc<double>(c, (size_t)(q + 1) * (size_t)std::max(1LL, m));
       if (!c->rec_partial) {
         c->rec_partial = dalloc<double>(c, (size_t)kRedBlocks * (kRecMax * kRecMax + kRecMax));
         c->rec_out = dalloc<double>(c, kRecMax * kRecMax + kRecMax);
@@ -1507,6 +1589,101 @@ int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   c->rec_head = 0;
   c->rec_tried = c->rec_used = 0;
   return cuda_check(c, "tfeti_set_recycling");
+}
+
+int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
+  if (!c || epochs < 0 || epochs > 1000 || !(lr > 0.0 && lr < 1.0)) return fail(c, TFETI_ERR_ARG, "bad argument");
+  if (enable && (c->rec_q < 1 || c->rec_q > kRecMax - 1))
+    return fail(c, TFETI_ERR_ARG, "the learned start needs a history of 1..7 (tfeti_set_recycling)");
+  const long long m = c->M.n_mult;
+  if (enable && !c->mlp_w) {
+    try {
+      c->mlp_w = dalloc<float>(c, kMlpParams);
+      c->mlp_m1 = dalloc<float>(c, kMlpParams);
+      c->mlp_m2 = dalloc<float>(c, kMlpParams);
+      c->mlp_partial = dalloc<float>(c, (size_t)c->mlp_blocks * kMlpParams);
+      c->mlp_scal = dalloc<float>(c, 4);
+      c->mlp_w16 = dalloc<uint16_t>(c, kMlpParams);
+      c->mlp_la = dalloc<double>(c, (size_t)std::max(1LL, m));
+      c->mlp_lb = dalloc<double>(c, (size_t)std::max(1LL, m));
+      c->mlp_dfprev = dalloc<double>(c, (size_t)std::max(1LL, c->M.n_dof));
+      c->pf_now = dalloc<float>(c, c->M.n_sub);
+      c->pf_prev = dalloc<float>(c, c->M.n_sub);
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+  }
+  if (enable) {
+    // seeded initialisation: uniform(-a, a), a = sqrt(6 / (fan_in + fan_out)) for the two
+    // hidden layers, zero biases and a zero last layer (the untrained predictor is the
+    // previous step's value)
+    std::vector<float> w(kMlpParams, 0.0f);
+    unsigned long long st = 0x9E3779B97F4A7C15ULL;
+    auto uni = [&st]() {
+      st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+      return (double)(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    const double a1 = std::sqrt(6.0 / (kMlpIn + kMlpHid)), a2 = std::sqrt(6.0 / (2 * kMlpHid));
+    for (int i = 0; i < kMlpHid * kMlpIn; ++i) w[i] = (float)(a1 * uni());
+    const int w2 = kMlpHid * kMlpIn + kMlpHid;
+    for (int i = 0; i < kMlpHid * kMlpHid; ++i) w[w2 + i] = (float)(a2 * uni());
+    cudaMemcpyAsync(c->mlp_w, w.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(c->mlp_m1, 0, sizeof(float) * kMlpParams, c->st);
+    cudaMemsetAsync(c->mlp_m2, 0, sizeof(float) * kMlpParams, c->st);
+    cudaMemsetAsync(c->mlp_la, 0, sizeof(double) * m, c->st);
+    cudaMemsetAsync(c->mlp_lb, 0, sizeof(double) * m, c->st);
+    cudaMemsetAsync(c->pf_now, 0, sizeof(float) * c->M.n_sub, c->st);
+    cudaMemsetAsync(c->pf_prev, 0, sizeof(float) * c->M.n_sub, c->st);
+    launch_mlp_cast(c->mlp_w, c->mlp_w16, c->st);
+    sync(c);
+  }
+  c->mlp_on = enable != 0;
+  c->mlp_epochs = epochs;
+  c->mlp_lr = (float)lr;
+  c->mlp_t = c->mlp_seen = 0;
+  c->mlp_used = 0;
+  c->have_dfprev = false;
+  return cuda_check(c, "tfeti_set_learned");
+}
+
+int tfeti_mlp_predict(tfeti_ctx* c, const double* la, const double* lb, const double* d, const float* pf_now,
+                      const float* pf_prev, const float* scal, double* y) {
+  if (!c || !la || !lb || !d || !pf_now || !pf_prev || !scal || !y) return fail(c, TFETI_ERR_ARG, "null argument");
+  if (!c->mlp_w) return fail(c, TFETI_ERR_ARG, "the learned start is not set up");
+  cudaMemcpyAsync(c->mlp_scal, scal, 4 * sizeof(float), cudaMemcpyHostToDevice, c->st);
+  launch_mlp_infer(c->M, c->mlp_w16, la, lb, d, pf_now, pf_prev, c->mlp_scal, y, c->st);
+  c->launches += 1;
+  sync(c);
+  c->mlp_scal_valid = false;
+  return cuda_check(c, "tfeti_mlp_predict");
+}
+
+int tfeti_mlp_train(tfeti_ctx* c, const double* la, const double* lb, const double* d, const float* pf_now,
+                    const float* pf_prev, const float* scal, const double* target, int32_t steps) {
+  if (!c || !la || !lb || !d || !pf_now || !pf_prev || !scal || !target || steps < 0)
+    return fail(c, TFETI_ERR_ARG, "bad argument");
+  if (!c->mlp_w) return fail(c, TFETI_ERR_ARG, "the learned start is not set up");
+  const long long m = c->M.n_mult;
+  cudaMemcpyAsync(c->mlp_scal, scal, 4 * sizeof(float), cudaMemcpyHostToDevice, c->st);
+  for (int e = 0; e < steps && m > 0; ++e) {
+    ++c->mlp_t;
+    const long long start = (104729LL * c->mlp_t + 7919LL * e) % m;
+    launch_mlp_train_step(c->M, c->mlp_w, la, lb, d, pf_now, pf_prev, c->mlp_scal, target, start, 7919,
+                          c->mlp_blocks, c->mlp_partial, c->mlp_w, c->mlp_m1, c->mlp_m2, c->mlp_w16, c->mlp_lr,
+                          c->mlp_t, c->st);
+    c->launches += 2;
+  }
+  sync(c);
+  c->mlp_scal_valid = false;
+  return cuda_check(c, "tfeti_mlp_train");
+}
+
+int tfeti_mlp_weights(tfeti_ctx* c, float* out) {
+  if (!c || !out) return fail(c, TFETI_ERR_ARG, "null argument");
+  if (!c->mlp_w) return fail(c, TFETI_ERR_ARG, "the learned start is not set up");
+  cudaMemcpyAsync(out, c->mlp_w, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  return cuda_check(c, "tfeti_mlp_weights");
 }
 
 int tfeti_first_yield_traction(tfeti_ctx* c, const double* dir, double rtol, double* t_y) {

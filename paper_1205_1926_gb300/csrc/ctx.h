@@ -105,6 +105,20 @@ struct tfeti_ctx {
   double* dtil = nullptr;        // d~ of the current solve (kept when the history start is on)
   double rec_accept = 0.5;       // try the start if the predicted ||P r|| < rec_accept ||P d~||
   long long rec_tried = 0, rec_used = 0;
+  // per-interface MLP of the learned start (tfeti_set_learned): FP32 master weights and
+  // Adam moments, FP16 copy for inference, the first-Newton-solve solutions of the last
+  // two load steps, per-subdomain plastic fractions, the previous load increment
+  bool mlp_on = false, newton_first = false, have_dfprev = false;
+  int mlp_epochs = 16, mlp_t = 0, mlp_seen = 0, mlp_blocks = 64;
+  float mlp_lr = 1e-3f;
+  float *mlp_w = nullptr, *mlp_m1 = nullptr, *mlp_m2 = nullptr, *mlp_partial = nullptr, *mlp_scal = nullptr;
+  void* mlp_w16 = nullptr;
+  double *mlp_la = nullptr, *mlp_lb = nullptr, *mlp_dfprev = nullptr;
+  float *pf_now = nullptr, *pf_prev = nullptr;
+  double mlp_rho = 1.0;
+  float h_scal[4] = {0.f, 0.f, 0.f, 0.f};
+  bool mlp_scal_valid = false;
+  long long mlp_used = 0;
   // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)
   float *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;

@@ -203,6 +203,22 @@ constexpr int kRedBlocks = 304;
 // out[i * kRecMax + j] = L_i . FL_j, out[kRecMax^2 + i] = L_i . d (L, FL: q vectors
 // of length m, stride m); partial: kRedBlocks * (kRecMax^2 + kRecMax) doubles.
 constexpr int kRecMax = 8;
+
+// Per-interface MLP of the learned start (kernels_mlp.cu).  scal (device, 4 floats):
+// 1/s, 1/s_d, rho, s with s = RMS of the previous step's lambda, s_d = RMS of d~.
+constexpr int kMlpIn = 8, kMlpHid = 64, kMlpBatch = 128;
+constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;
+size_t mlp_grad_smem();
+void launch_mlp_infer(const DevMesh& M, const void* w16, const double* la, const double* lb, const double* d,
+                      const float* pf_now, const float* pf_prev, const float* scal, double* y, cudaStream_t st);
+// One Adam step on nblocks x kMlpBatch rows (start + i * stride mod n_mult); partial:
+// nblocks x kMlpParams floats.
+void launch_mlp_train_step(const DevMesh& M, const float* wm, const double* la, const double* lb, const double* d,
+                           const float* pf_now, const float* pf_prev, const float* scal, const double* target,
+                           long long start, long long stride, int nblocks, float* partial, float* wm_out, float* m1,
+                           float* m2, void* w16, float lr, int t, cudaStream_t st);
+void launch_plastic_fraction(const DevMesh& M, const int* sub_np, float* pf, cudaStream_t st);
+void launch_mlp_cast(const float* wm, void* w16, cudaStream_t st);
 void launch_rec_gram(const double* L, const double* FL, const double* d, int q, long long m, double* partial,
                      double* out, cudaStream_t st);
 // out = (base ? base : 0) + sign * sum_j c_j X_j, c device [q].

@@ -522,6 +522,82 @@ def test_history_start_repeated_rhs():
         assert rel(host(lam), sol["lam"]) <= 1e-9
 
 
+def _mlp_forward_numpy(wts, la, lb, d, scal):
+    """Plain FP64 forward of the per-interface MLP (FP16-rounded weights) with zero plastic fractions."""
+    w = np.asarray(wts, dtype=np.float32).astype(np.float16).astype(np.float64)
+    nin, nh = 8, 64
+    W1 = w[:nh * nin].reshape(nh, nin)
+    b1 = w[nh * nin:nh * nin + nh]
+    o = nh * nin + nh
+    W2 = w[o:o + nh * nh].reshape(nh, nh)
+    b2 = w[o + nh * nh:o + nh * nh + nh]
+    w3 = w[o + nh * nh + nh:o + nh * nh + 2 * nh]
+    b3 = w[-1]
+    x = np.zeros((la.size, nin))
+    x[:, 0] = la * scal[0]
+    x[:, 1] = (la - lb) * scal[0]
+    x[:, 2] = d * scal[1]
+    x[:, 3] = scal[2]
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    return (x[:, 0] + h2 @ w3 + b3) * scal[3]
+
+
+def test_mlp_training_and_inference_kernels():
+    """Hand-written MLP kernels: Adam training on a target the residual network can represent (linear
+    extrapolation of the history plus a multiple of d~) lowers the error more than tenfold, and the
+    inference kernel matches a plain FP64 forward of the same FP16 weights."""
+    w = W.CUBE12
+    ctx = T.Context(w)
+    ctx.set_recycling(4)
+    ctx.set_learned(True, epochs=0, lr=3e-3)
+    m, ns = ctx.sizes["n_mult"], ctx.sizes["n_sub"]
+    la = W.seeded_vector(m, seed=91)
+    lb = 0.8 * la + 0.1 * W.seeded_vector(m, seed=92)
+    d = W.seeded_vector(m, seed=93)
+    target = la + 0.5 * (la - lb) + 0.05 * d
+    s = np.sqrt(np.mean(la ** 2))
+    sd = np.sqrt(np.mean(d ** 2))
+    scal = (1.0 / s, 1.0 / sd, 1.0, s)
+    pf = zeros(ns, torch.float32)
+    dla, dlb, dd, dt, y = dev(la), dev(lb), dev(d), dev(target), zeros(m)
+    ctx.mlp_predict(dla, dlb, dd, pf, pf, scal, y)
+    err0 = rel(host(y), target)
+    ctx.mlp_train(dla, dlb, dd, pf, pf, scal, dt, 400)
+    ctx.mlp_predict(dla, dlb, dd, pf, pf, scal, y)
+    err1 = rel(host(y), target)
+    assert err1 < 0.1 * err0, (err0, err1)
+    ref = _mlp_forward_numpy(ctx.mlp_weights(), la, lb, d, np.asarray(scal, dtype=np.float32).astype(np.float64))
+    assert rel(host(y), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_learned_start_load_history_cube12(mixed):
+    """History start with the MLP vector on the 12^3 history: the oracle's displacements at every step, and
+    the MLP vector enters the start in some first Newton solves."""
+    w = W.CUBE12
+    ctx = T.Context(w)
+    if mixed:
+        ctx.set_precision(True, 1e-3)
+    ctx.set_recycling(7)
+    ctx.set_learned(True)
+    t_y = ctx.first_yield_traction(w.traction_dir)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    df, u = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_dof"])
+    prev, with_mlp = 0.0, 0
+    for a in w.load_fractions():
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        ctx.get_state(u=u)
+        assert info["converged"] and rel(host(u), model.u) <= 1e-9
+        with_mlp += sum(1 for h in info["history"] if h == 2)
+    assert with_mlp > 0
+
+
 def test_cube64_history_matches_oracle_record():
     """The full 20-step 64^3 history (the timed workload, FP64) against the oracle's own run of it
     (tests/golden/cube64_oracle_record.json, written by make_cube64_oracle_record.py from oracle/ only)."""
