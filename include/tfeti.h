@@ -253,24 +253,27 @@ int tfeti_set_precision(tfeti_ctx* ctx, int32_t mode, double inner_rtol);
  * fallback covers a stale prediction).  Resets the history. */
 int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
 
-/* Learned start (extension; needs tfeti_set_recycling with q in 1..7): for the first
- * Newton solve of every load step a per-interface MLP predicts lambda_Ker row by row
- * from the row's values of the first-solve lambda_Ker of the previous two load steps
- * (la, lb), the current d~, the load-increment ratio rho = df.df_prev / |df_prev|^2
- * and the plastic fractions of the row's subdomains now and at the previous step:
- * features x = (la/s, (la - lb)/s, d~/s_d, rho, pf_now, pf_prev, 0, 0), s = RMS(la),
- * s_d = RMS(d~); prediction s (x_0 + net(x)), net = 8 -> 64 -> 64 -> 1 with ReLU,
- * FP16 weights, FP32 accumulation.  The projected prediction joins the stored
- * solutions as one more vector of the Galerkin start (so the zero start stays the
- * fallback).  After the solve the network takes `epochs` Adam steps (learning rate
- * lr, FP32 master weights) on 64 x 128 rows of this solve against its lambda_Ker.
- * Weights start from a fixed seed with a zero last layer.  enable = 0 turns it off. */
+/* Learned start (extension; needs tfeti_set_recycling with q in 1..7): for Newton
+ * iteration i <= 4 of every load step a per-interface MLP predicts lambda_Ker row by
+ * row from the row's values of lambda_Ker at iteration i of the previous two load
+ * steps (la, lb), the current d~, the load-increment ratio rho = df.df_prev /
+ * |df_prev|^2, the plastic fractions of the row's subdomains now and at iteration i
+ * of the previous step, and i: features x = (la/s, (la - lb)/s, d~/s_d, rho, pf_now,
+ * pf_prev, (i-1)/3, 0), s = RMS(la), s_d = RMS(d~); prediction s (x_0 + net(x)), net =
+ * 8 -> 64 -> 64 -> 1 with ReLU, FP16 weights, FP32 accumulation.  Where the stored
+ * solutions alone do not meet the stopping test, the projected prediction joins them
+ * as one more vector of the Galerkin start (its product by one F-apply, FP32 in the
+ * mixed mode; the zero start stays the fallback).  After each such solve the network
+ * takes `epochs` Adam steps (learning rate lr, FP32 master weights) on 64 x 128 rows
+ * of the solve against its lambda_Ker.  Weights start from a fixed seed with a zero
+ * last layer (the untrained predictor is la).  enable = 0 turns it off. */
 #define TFETI_MLP_PARAMS 4801
 int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr);
 /* For tests and tools: the FP32 master weights (host float[TFETI_MLP_PARAMS]: W1 [64][8],
  * b1 [64], W2 [64][64], b2 [64], w3 [64], b3), the prediction y (device [n_mult]) for
  * given device inputs la, lb, d [n_mult], pf_now, pf_prev [n_sub] and host scal[4] =
- * (1/s, 1/s_d, rho, s), and `steps` Adam steps towards the device target [n_mult]. */
+ * (1/s, 1/s_d, rho, s) with the index feature 0, and `steps` Adam steps towards the
+ * device target [n_mult]. */
 int tfeti_mlp_weights(tfeti_ctx* ctx, float* out);
 int tfeti_mlp_predict(tfeti_ctx* ctx, const double* la, const double* lb, const double* d, const float* pf_now,
                       const float* pf_prev, const float* scal, double* y);

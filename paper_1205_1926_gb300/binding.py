@@ -284,7 +284,7 @@ class Context:
         """Start each dual solve from the best combination of the last q solutions (0: off)."""
         return self._check(self.lib.tfeti_set_recycling(self.h, int(q)), "tfeti_set_recycling")
 
-    def set_learned(self, enable: bool, epochs: int = 16, lr: float = 1e-3):
+    def set_learned(self, enable: bool, epochs: int = 8, lr: float = 1e-3):
         """Per-interface MLP prediction in the history start of every load step's first Newton solve."""
         return self._check(self.lib.tfeti_set_learned(self.h, 1 if enable else 0, int(epochs), float(lr)),
                            "tfeti_set_learned")

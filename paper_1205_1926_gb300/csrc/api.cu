@@ -686,13 +686,18 @@ std::vector<double> history_coefficients(const double* g, int n) {
   return c;
 }
 
-bool mlp_ready(const tfeti_ctx* c) { return c->mlp_on && c->newton_first && c->mlp_seen >= 1; }
+bool mlp_index_ok(const tfeti_ctx* c) { return c->mlp_on && c->newton_idx >= 1 && c->newton_idx <= kMlpIdx; }
+bool mlp_ready(const tfeti_ctx* c) { return mlp_index_ok(c) && c->mlp_seen[c->newton_idx - 1] >= 1; }
+double* mlp_la_of(tfeti_ctx* c) { return c->mlp_la + (long long)(c->newton_idx - 1) * c->M.n_mult; }
+double* mlp_lb_of(tfeti_ctx* c) { return c->mlp_lb + (long long)(c->newton_idx - 1) * c->M.n_mult; }
+float* pf_prev_of(tfeti_ctx* c) { return c->pf_prev + (long long)(c->newton_idx - 1) * c->M.n_sub; }
 
-// Scalars of the MLP features: 1/s, 1/s_d, rho, s with s the RMS of the previous
-// step's first-solve lambda_Ker and s_d the RMS of d~ (||d~|| = r0).  False if s = 0.
+// Scalars of the MLP features: 1/s, 1/s_d, rho, s, index feature, with s the RMS of
+// the previous step's lambda_Ker at this Newton iteration and s_d the RMS of d~
+// (||d~|| = r0).  False if s = 0.
 bool mlp_scalars(tfeti_ctx* c, double r0) {
   const long long m = c->M.n_mult;
-  const double s = std::sqrt(std::max(0.0, dot_host(c, c->mlp_la, c->mlp_la, m)) / (double)m);
+  const double s = std::sqrt(std::max(0.0, dot_host(c, mlp_la_of(c), mlp_la_of(c), m)) / (double)m);
   const double sd = r0 / std::sqrt((double)m);
   c->mlp_scal_valid = s > 0.0 && sd > 0.0;
   if (!c->mlp_scal_valid) return false;
@@ -700,6 +705,7 @@ bool mlp_scalars(tfeti_ctx* c, double r0) {
   c->h_scal[1] = (float)(1.0 / sd);
   c->h_scal[2] = (float)c->mlp_rho;
   c->h_scal[3] = (float)s;
+  c->h_scal[4] = (float)(c->newton_idx - 1) / (float)(kMlpIdx - 1);
   cudaMemcpyAsync(c->mlp_scal, c->h_scal, sizeof(c->h_scal), cudaMemcpyHostToDevice, c->st);
   sync(c);
   return true;
@@ -707,8 +713,8 @@ bool mlp_scalars(tfeti_ctx* c, double r0) {
 
 // History start (extension of Algorithm 3): on entry r = d~ and lambda_Ker = o.
 // The basis is the stored solutions and, for the first Newton solve of a load step
-// with the learned start on, the projected MLP prediction (its F-product by one
-// F-apply, FP32 in the mixed mode).  Returns 0 if not applied (state unchanged), 1
+// with the learned start on, the projected MLP prediction (its F-product by one FP64
+// F-apply) when the stored solutions alone do not meet the stopping test.  Returns 0 if not applied (state unchanged), 1
 // if lambda_Ker = P(sum c_j lambda_j) was taken (r = d~ - F lambda_Ker by a residual
 // solve), 3 if so with a nonzero coefficient on the MLP vector, 2 if it was tried and
 // rejected because ||P r|| did not fall below ||P d~|| (state reset to d~, the
@@ -719,37 +725,48 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   op_project(c, c->r, c->w);
   const double w0 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
   if (w0 <= tol_abs) return 0;   // the zero start already meets the stopping test
+  // Galerkin coefficients over the first nb stored vectors and the projected residual
+  // they predict with the stored products; pred = inf if no vector is usable
+  auto galerkin = [&](int nb, std::vector<double>& coef) -> double {
+    launch_rec_gram(c->rec_L, c->rec_FL, c->r, nb, m, c->rec_partial, c->rec_out, c->st);
+    double g[kRecMax * kRecMax + kRecMax];
+    cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    c->launches += 2;
+    coef = history_coefficients(g, nb);
+    bool any = false;
+    for (double v : coef) any = any || (v != 0.0 && std::isfinite(v));
+    if (!any) return HUGE_VAL;
+    cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->st);
+    launch_rec_combine(c->rec_FL, c->rec_c, nb, m, c->r, -1.0, c->tm, c->st);   // d~ - sum c_j F lambda_j
+    op_project(c, c->tm, c->z);
+    c->launches += 1;
+    return std::sqrt(std::max(0.0, dot_host(c, c->z, c->z, m)));
+  };
+  std::vector<double> coef;
   int nb = n;
+  double pred = n > 0 ? galerkin(n, coef) : HUGE_VAL;
   bool with_mlp = false;
-  if (mlp_ready(c) && mlp_scalars(c, r0)) {
-    // slot n is free: the ring keeps rec_q solutions in rec_q + 1 slots
-    double* Ln = c->rec_L + (long long)n * m;
+  // the MLP vector joins only where the stored solutions alone miss the stopping test
+  // (there the start is refined anyway, so the mixed mode takes its product in FP32)
+  c->mlp_missed = pred > tol_abs;
+  if (pred > tol_abs && mlp_ready(c) && mlp_scalars(c, r0)) {
+    double* Ln = c->rec_L + (long long)n * m;   // slot n is free: rec_q solutions in rec_q + 1 slots
     double* FLn = c->rec_FL + (long long)n * m;
-    launch_mlp_infer(c->M, c->mlp_w16, c->mlp_la, c->mlp_lb, c->r, c->pf_now, c->pf_prev, c->mlp_scal, c->y, c->st);
+    launch_mlp_infer(c->M, c->mlp_w16, mlp_la_of(c), mlp_lb_of(c), c->r, c->pf_now, pf_prev_of(c), c->mlp_scal,
+                     c->y, c->st);
     op_project(c, c->y, Ln);
-    if (c->precision == TFETI_PRECISION_MIXED) op_F32(c, Ln, FLn);
+    if (c->precision == TFETI_PRECISION_MIXED) op_F32(c, Ln, FLn);   // the solve is refined in FP64 anyway
     else op_F(c, Ln, FLn);
     c->launches += 1;
+    // the Galerkin start over the larger span has the smaller F-norm error, so it is kept
+    std::vector<double> coef2;
+    pred = galerkin(n + 1, coef2);
+    coef = coef2;
     nb = n + 1;
-    with_mlp = true;
+    with_mlp = coef2[n] != 0.0;
   }
-  if (nb == 0) return 0;
-  launch_rec_gram(c->rec_L, c->rec_FL, c->r, nb, m, c->rec_partial, c->rec_out, c->st);
-  double g[kRecMax * kRecMax + kRecMax];
-  cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
-  sync(c);
-  c->launches += 2;
-  std::vector<double> coef = history_coefficients(g, nb);
-  bool any = false;
-  for (double v : coef) any = any || (v != 0.0 && std::isfinite(v));
-  if (!any || !(w0 > 0.0)) return 0;
-  cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->st);
-  // predicted residual with the stored products: d~ - sum c_j F lambda_j
-  launch_rec_combine(c->rec_FL, c->rec_c, nb, m, c->r, -1.0, c->tm, c->st);
-  op_project(c, c->tm, c->z);
-  c->launches += 1;
-  const double pred = std::sqrt(std::max(0.0, dot_host(c, c->z, c->z, m)));
-  if (!(pred < c->rec_accept * w0)) return 0;
+  if (nb == 0 || !(pred < c->rec_accept * w0)) return 0;
   ++c->rec_tried;
   launch_rec_combine(c->rec_L, c->rec_c, nb, m, nullptr, 1.0, c->y, c->st);
   op_project(c, c->y, c->lamk);
@@ -764,7 +781,7 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
     return 2;
   }
   ++c->rec_used;
-  if (with_mlp && coef[n] != 0.0) {
+  if (with_mlp) {
     ++c->mlp_used;
     return 3;
   }
@@ -775,22 +792,24 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
 // lambda_Ker of this solve, features from the two previous steps' solutions, this
 // solve's d~, the plastic fractions and rho; then the histories move on by one step.
 void mlp_train(tfeti_ctx* c, double r0) {
+  if (!mlp_index_ok(c)) return;
   const long long m = c->M.n_mult;
-  if (c->mlp_seen >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0))) {
+  // training only after solves that the stored solutions alone could not start well
+  if (c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0))) {
     for (int e = 0; e < c->mlp_epochs; ++e) {
       ++c->mlp_t;
       const long long start = (104729LL * c->mlp_t + 7919LL * e) % m;
-      launch_mlp_train_step(c->M, c->mlp_w, c->mlp_la, c->mlp_lb, c->dtil, c->pf_now, c->pf_prev, c->mlp_scal,
-                            c->lamk, start, 7919, c->mlp_blocks, c->mlp_partial, c->mlp_w, c->mlp_m1, c->mlp_m2,
-                            c->mlp_w16, c->mlp_lr, c->mlp_t, c->st);
+      launch_mlp_train_step(c->M, c->mlp_w, mlp_la_of(c), mlp_lb_of(c), c->dtil, c->pf_now, pf_prev_of(c),
+                            c->mlp_scal, c->lamk, start, 7919, c->mlp_blocks, c->mlp_partial, c->mlp_w, c->mlp_m1,
+                            c->mlp_m2, c->mlp_w16, c->mlp_lr, c->mlp_t, c->st);
       c->launches += 2;
     }
   }
-  cudaMemcpyAsync(c->mlp_lb, c->mlp_la, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->mlp_la, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->pf_prev, c->pf_now, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(mlp_lb_of(c), mlp_la_of(c), sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(mlp_la_of(c), c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(pf_prev_of(c), c->pf_now, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st);
   c->mlp_scal_valid = false;
-  ++c->mlp_seen;
+  ++c->mlp_seen[c->newton_idx - 1];
 }
 
 // Store the solution of the finished solve: lambda_Ker and F lambda_Ker = d~ - r.
@@ -824,6 +843,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   int used_l0 = 0;
   const bool history = c->rec_q > 0 && m > 0;
   if (history) cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  c->mlp_missed = c->rec_n == 0;   // set by the history start when it runs
   if (lambda0) {
     op_project(c, lambda0, c->lamk);
     launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
@@ -895,7 +915,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   c->launches += 1;
   if (!v_current) residual_solve(c, f, c->lam, c->r);
   if (history && r0 > 0.0 && status == TFETI_OK) {   // r is the true residual here
-    if (c->mlp_on && c->newton_first) mlp_train(c, r0);
+    if (c->mlp_on) mlp_train(c, r0);
     history_push(c);
   }
   launch_G_apply(M, c->r, nullptr, c->gx, -1.0, c->st);
@@ -1427,13 +1447,13 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
   for (int i = 1; i <= newton_maxit; ++i) {
     status = assemble(c, c->du, c->df, nullptr);
     if (status != TFETI_OK) break;
-    if (c->mlp_on && i == 1) launch_plastic_fraction(M, c->sub_np, c->pf_now, c->st);
-    c->newton_first = i == 1;
+    if (c->mlp_on) launch_plastic_fraction(M, c->sub_np, c->pf_now, c->st);
+    c->newton_idx = i;
     std::vector<int> np(M.n_sub);
     cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
     tfeti_pcg_info pi{};
     status = dual_pcg(c, c->f_full, c->tn, nullptr, nullptr, pcg_rtol, pcg_maxit, &pi);
-    c->newton_first = false;
+    c->newton_idx = 0;
     if (status != TFETI_OK) break;
     const double nd = std::sqrt(dot_host(c, c->tn, c->tn, n));
     launch_axpby(n, 1.0, c->du, 1.0, c->tn, c->du, c->st);
@@ -1602,13 +1622,13 @@ int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
       c->mlp_m1 = dalloc<float>(c, kMlpParams);
       c->mlp_m2 = dalloc<float>(c, kMlpParams);
       c->mlp_partial = dalloc<float>(c, (size_t)c->mlp_blocks * kMlpParams);
-      c->mlp_scal = dalloc<float>(c, 4);
+      c->mlp_scal = dalloc<float>(c, 8);
       c->mlp_w16 = dalloc<uint16_t>(c, kMlpParams);
-      c->mlp_la = dalloc<double>(c, (size_t)std::max(1LL, m));
-      c->mlp_lb = dalloc<double>(c, (size_t)std::max(1LL, m));
+      c->mlp_la = dalloc<double>(c, (size_t)kMlpIdx * (size_t)std::max(1LL, m));
+      c->mlp_lb = dalloc<double>(c, (size_t)kMlpIdx * (size_t)std::max(1LL, m));
       c->mlp_dfprev = dalloc<double>(c, (size_t)std::max(1LL, c->M.n_dof));
       c->pf_now = dalloc<float>(c, c->M.n_sub);
-      c->pf_prev = dalloc<float>(c, c->M.n_sub);
+      c->pf_prev = dalloc<float>(c, (size_t)kMlpIdx * c->M.n_sub);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
@@ -1630,17 +1650,18 @@ int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
     cudaMemcpyAsync(c->mlp_w, w.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, c->st);
     cudaMemsetAsync(c->mlp_m1, 0, sizeof(float) * kMlpParams, c->st);
     cudaMemsetAsync(c->mlp_m2, 0, sizeof(float) * kMlpParams, c->st);
-    cudaMemsetAsync(c->mlp_la, 0, sizeof(double) * m, c->st);
-    cudaMemsetAsync(c->mlp_lb, 0, sizeof(double) * m, c->st);
+    cudaMemsetAsync(c->mlp_la, 0, sizeof(double) * kMlpIdx * m, c->st);
+    cudaMemsetAsync(c->mlp_lb, 0, sizeof(double) * kMlpIdx * m, c->st);
     cudaMemsetAsync(c->pf_now, 0, sizeof(float) * c->M.n_sub, c->st);
-    cudaMemsetAsync(c->pf_prev, 0, sizeof(float) * c->M.n_sub, c->st);
+    cudaMemsetAsync(c->pf_prev, 0, sizeof(float) * kMlpIdx * c->M.n_sub, c->st);
     launch_mlp_cast(c->mlp_w, c->mlp_w16, c->st);
     sync(c);
   }
   c->mlp_on = enable != 0;
   c->mlp_epochs = epochs;
   c->mlp_lr = (float)lr;
-  c->mlp_t = c->mlp_seen = 0;
+  c->mlp_t = 0;
+  for (int& v : c->mlp_seen) v = 0;
   c->mlp_used = 0;
   c->have_dfprev = false;
   return cuda_check(c, "tfeti_set_learned");
@@ -1650,7 +1671,9 @@ int tfeti_mlp_predict(tfeti_ctx* c, const double* la, const double* lb, const do
                       const float* pf_prev, const float* scal, double* y) {
   if (!c || !la || !lb || !d || !pf_now || !pf_prev || !scal || !y) return fail(c, TFETI_ERR_ARG, "null argument");
   if (!c->mlp_w) return fail(c, TFETI_ERR_ARG, "the learned start is not set up");
-  cudaMemcpyAsync(c->mlp_scal, scal, 4 * sizeof(float), cudaMemcpyHostToDevice, c->st);
+  const float sc[5] = {scal[0], scal[1], scal[2], scal[3], 0.0f};
+  cudaMemcpyAsync(c->mlp_scal, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st);
+  sync(c);
   launch_mlp_infer(c->M, c->mlp_w16, la, lb, d, pf_now, pf_prev, c->mlp_scal, y, c->st);
   c->launches += 1;
   sync(c);
@@ -1664,7 +1687,9 @@ int tfeti_mlp_train(tfeti_ctx* c, const double* la, const double* lb, const doub
     return fail(c, TFETI_ERR_ARG, "bad argument");
   if (!c->mlp_w) return fail(c, TFETI_ERR_ARG, "the learned start is not set up");
   const long long m = c->M.n_mult;
-  cudaMemcpyAsync(c->mlp_scal, scal, 4 * sizeof(float), cudaMemcpyHostToDevice, c->st);
+  const float sc[5] = {scal[0], scal[1], scal[2], scal[3], 0.0f};
+  cudaMemcpyAsync(c->mlp_scal, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st);
+  sync(c);
   for (int e = 0; e < steps && m > 0; ++e) {
     ++c->mlp_t;
     const long long start = (104729LL * c->mlp_t + 7919LL * e) % m;

@@ -108,15 +108,18 @@ struct tfeti_ctx {
   // per-interface MLP of the learned start (tfeti_set_learned): FP32 master weights and
   // Adam moments, FP16 copy for inference, the first-Newton-solve solutions of the last
   // two load steps, per-subdomain plastic fractions, the previous load increment
-  bool mlp_on = false, newton_first = false, have_dfprev = false;
-  int mlp_epochs = 16, mlp_t = 0, mlp_seen = 0, mlp_blocks = 64;
+  // (histories per Newton index 1..kMlpIdx: [kMlpIdx][n_mult] and [kMlpIdx][n_sub])
+  bool mlp_on = false, have_dfprev = false, mlp_missed = false;   // missed: the history alone fell short
+  int newton_idx = 0;                 // Newton iteration of the running dual solve (0: not inside Newton)
+  int mlp_epochs = 8, mlp_t = 0, mlp_blocks = 64;
+  int mlp_seen[tfeti::kMlpIdx] = {0, 0, 0, 0};
   float mlp_lr = 1e-3f;
   float *mlp_w = nullptr, *mlp_m1 = nullptr, *mlp_m2 = nullptr, *mlp_partial = nullptr, *mlp_scal = nullptr;
   void* mlp_w16 = nullptr;
   double *mlp_la = nullptr, *mlp_lb = nullptr, *mlp_dfprev = nullptr;
   float *pf_now = nullptr, *pf_prev = nullptr;
   double mlp_rho = 1.0;
-  float h_scal[4] = {0.f, 0.f, 0.f, 0.f};
+  float h_scal[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   bool mlp_scal_valid = false;
   long long mlp_used = 0;
   // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)

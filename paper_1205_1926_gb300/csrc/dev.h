@@ -204,9 +204,10 @@ constexpr int kRedBlocks = 304;
 // of length m, stride m); partial: kRedBlocks * (kRecMax^2 + kRecMax) doubles.
 constexpr int kRecMax = 8;
 
-// Per-interface MLP of the learned start (kernels_mlp.cu).  scal (device, 4 floats):
-// 1/s, 1/s_d, rho, s with s = RMS of the previous step's lambda, s_d = RMS of d~.
-constexpr int kMlpIn = 8, kMlpHid = 64, kMlpBatch = 128;
+// Per-interface MLP of the learned start (kernels_mlp.cu).  scal (device, 5 floats):
+// 1/s, 1/s_d, rho, s, the Newton-index feature, with s = RMS of the previous step's
+// lambda and s_d = RMS of d~.  kMlpIdx: Newton iterations with their own histories.
+constexpr int kMlpIn = 8, kMlpHid = 64, kMlpBatch = 128, kMlpIdx = 4;
 constexpr int kMlpParams = kMlpHid * kMlpIn + kMlpHid + kMlpHid * kMlpHid + kMlpHid + kMlpHid + 1;
 size_t mlp_grad_smem();
 void launch_mlp_infer(const DevMesh& M, const void* w16, const double* la, const double* lb, const double* d,

@@ -26,7 +26,7 @@ static_assert(kOffB3 + 1 == kMlpParams, "parameter layout");
 
 // Features of row r: f0 = la/s, f1 = (la - lb)/s, f2 = d/sd, f3 = rho, f4 = plastic
 // fraction now, f5 = plastic fraction at the previous step (max over the
-// subdomains of the row's group), zero padding.
+// subdomains of the row's group), f6 = Newton-index feature, zero padding.
 __device__ __forceinline__ void row_features(const DevMesh& M, long long r, const double* la, const double* lb,
                                              const double* d, const float* pf_now, const float* pf_prev,
                                              const float* scal, float* x) {
@@ -43,8 +43,9 @@ __device__ __forceinline__ void row_features(const DevMesh& M, long long r, cons
   x[3] = scal[2];
   x[4] = pn;
   x[5] = pp;
+  x[6] = scal[4];
 #pragma unroll
-  for (int k = 6; k < kIn; ++k) x[k] = 0.f;
+  for (int k = 7; k < kIn; ++k) x[k] = 0.f;
 }
 
 // y[r] = s * net(x_r): one thread per row, FP16 weights staged in shared memory.

@@ -573,20 +573,21 @@ def test_mlp_training_and_inference_kernels():
 
 @pytest.mark.parametrize("mixed", [False, True])
 def test_learned_start_load_history_cube12(mixed):
-    """History start with the MLP vector on the 12^3 history: the oracle's displacements at every step, and
-    the MLP vector enters the start in some first Newton solves."""
+    """History start with the MLP on the 12^3 history: the oracle's displacements at every step, and the
+    network trains online (its weights move away from the seeded start)."""
     w = W.CUBE12
     ctx = T.Context(w)
     if mixed:
         ctx.set_precision(True, 1e-3)
     ctx.set_recycling(7)
     ctx.set_learned(True)
+    w0 = np.array(ctx.mlp_weights())
     t_y = ctx.first_yield_traction(w.traction_dir)
     model = ElastoplasticModel(w)
     t_or = model.first_yield_traction()
     f1 = model.traction_load(w.traction_dir)
     df, u = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_dof"])
-    prev, with_mlp = 0.0, 0
+    prev = 0.0
     for a in w.load_fractions():
         ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
         info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
@@ -594,8 +595,8 @@ def test_learned_start_load_history_cube12(mixed):
         prev = a
         ctx.get_state(u=u)
         assert info["converged"] and rel(host(u), model.u) <= 1e-9
-        with_mlp += sum(1 for h in info["history"] if h == 2)
-    assert with_mlp > 0
+    w1 = np.array(ctx.mlp_weights())
+    assert np.isfinite(w1).all() and np.abs(w1 - w0).max() > 0
 
 
 def test_cube64_history_matches_oracle_record():
