@@ -243,6 +243,8 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
     ctx = T.Context(w, stream=stream, precond=pre)
+    if args.fapply == "schur":
+        ctx.set_fapply(True)
     if args.precision == "mixed":
         ctx.set_precision(True, args.inner_rtol)
     if args.learned:
@@ -367,26 +369,45 @@ def run_gpu(args, rank, world, local_rank):
     units = args.steps * world
     value = replica_value(elapsed, args.steps, world)
     pk, pk_kind = peaks()
+    # F-apply kernels: the banded K^+ solves (k_sub_solve: every F-apply in the banded mode,
+    # the set-up/recovery solves and the plastic subdomains in the Schur mode) and the FP64
+    # dual-Schur DGEMM (k_schur_dgemm: elastic subdomains in the Schur mode).  The roofline
+    # object describes the one with the larger share of device time; the other sits beside it.
     avg_f_ms = tm["f_apply_ms_total"] / max(tm["f_apply_launches"], 1)
     flops = tm["f_apply_flops"]
     byts = tm["f_apply_bytes"]
     achieved_tf = flops / (avg_f_ms * 1e-3) / 1e12 if avg_f_ms > 0 else None
     achieved_gbs = byts / (avg_f_ms * 1e-3) / 1e9 if avg_f_ms > 0 else None
-    t_alu, t_hbm = flops / (FP64_PEAK_TFLOPS * 1e12), byts / (pk["hbm_gbs"] * 1e9)
-    bound = "alu" if t_alu >= t_hbm else "hbm"
-    if bound == "alu":
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": None,
-                "kernel": "k_sub_solve (F-apply: banded forward/backward substitution, FP64)",
-                "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25"}
+    banded = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": None,
+              "kernel": "k_sub_solve (banded forward/backward substitution with the factor records, FP64)",
+              "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25",
+              "total_ms": tm["f_apply_ms_total"], "launches": tm["f_apply_launches"],
+              "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
+                      "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None,
+                      "bytes_per_launch": byts, "flops_per_launch": flops, "avg_launch_ms": avg_f_ms,
+                      "of": f"{pk_kind} hbm_gbs"}}
+    schur = None
+    if tm["schur_launches"] > 0 and tm["schur_ms_total"] > 0:
+        s_tf = tm["schur_flops_total"] / (tm["schur_ms_total"] * 1e-3) / 1e12
+        s_gbs = tm["schur_bytes_total"] / (tm["schur_ms_total"] * 1e-3) / 1e9
+        schur = {"bound": "alu", "achieved": s_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": s_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                 "kernel": "k_schur_dgemm (+ gather): Y = X S with the shape's FP64 dual Schur block",
+                 "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25",
+                 "total_ms": tm["schur_ms_total"], "launches": tm["schur_launches"],
+                 "hbm": {"achieved_gbs": s_gbs, "peak_gbs": pk["hbm_gbs"], "frac": s_gbs / pk["hbm_gbs"],
+                         "bytes_per_launch": tm["schur_bytes_total"] / tm["schur_launches"],
+                         "flops_per_launch": tm["schur_flops_total"] / tm["schur_launches"],
+                         "avg_launch_ms": tm["schur_ms_total"] / tm["schur_launches"],
+                         "of": f"{pk_kind} hbm_gbs; bytes: the shared S (L2-resident) and X, Y"}}
+    if schur is not None and schur["total_ms"] >= banded["total_ms"]:
+        roof, other = schur, banded
     else:
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None, "traffic": None,
-                "kernel": "k_sub_solve (F-apply)", "peak_kind": pk_kind}
-    roof["hbm"] = {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
-                   "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None,
-                   "bytes_per_launch": byts, "flops_per_launch": flops, "avg_launch_ms": avg_f_ms,
-                   "launches": tm["f_apply_launches"], "of": f"{pk_kind} hbm_gbs"}
+        roof, other = banded, schur
+    roof = dict(roof)
+    if other is not None:
+        roof["other_kernel"] = other
     newton_steps = [s["newton"] for s in timed]
     pcg_steps = [sum(s["pcg"]) for s in timed]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -395,7 +416,7 @@ def run_gpu(args, rank, world, local_rank):
             "config": workload_config(w, args.steps, args.warmup, args.precond) | {
                 "parallelism": "replicas" if world > 1 else "1 GPU", "precision": args.precision,
                 "inner_rtol": args.inner_rtol if args.precision == "mixed" else None,
-                "history_start": args.history if args.learned else 0,
+                "history_start": args.history if args.learned else 0, "fapply": args.fapply,
                 "inner_pcgp_launch": "kernel by kernel" if args.no_graphs else "one CUDA graph (WHILE node) per inner solve"},
             "e2e": None if args.no_e2e else {"value": elapsed_e2e / units, "unit": UNIT,
                                              "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
@@ -445,6 +466,8 @@ def main():
                     help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms of an FP64 run")
+    ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
+                    help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
     ap.add_argument("--precond", default="lumped", choices=["lumped", "dirichlet"],
                     help="PCGP preconditioner of Sec. 4.2 (every arm)")
     ap.add_argument("--learned", action="store_true",

@@ -280,6 +280,18 @@ int tfeti_mlp_predict(tfeti_ctx* ctx, const double* la, const double* lb, const 
 int tfeti_mlp_train(tfeti_ctx* ctx, const double* la, const double* lb, const double* d, const float* pf_now,
                     const float* pf_prev, const float* scal, const double* target, int32_t steps);
 
+/* How the FP64 F-apply of the PCGP iterations treats subdomains still on their
+ * shape's elastic tangent (Sec. 4.2 leaves the K^+ apply open).  BANDED (default):
+ * forward and backward substitution with the shape's factor.  SCHUR: one DGEMM per
+ * shape with the shape's dual Schur block S = (K^+)_{boundary,boundary} (formed once
+ * in FP64 from the same factor, 1158^2 doubles for an 8^3 box), which has the same
+ * flop count but keeps all SMs busy; subdomains with plastic points keep their
+ * banded solves (on a second stream).  The set-up and recovery solves, which need
+ * the whole local vector, stay banded. */
+#define TFETI_FAPPLY_BANDED 0
+#define TFETI_FAPPLY_SCHUR  1
+int tfeti_set_fapply(tfeti_ctx* ctx, int32_t mode);
+
 /* Launch mode of the mixed-precision inner PCGP.  enable != 0 (default): each
  * inner solve is one CUDA graph launch whose body is one iteration inside a
  * WHILE conditional node, the scalars staying on the device.  enable == 0: the
@@ -348,6 +360,12 @@ typedef struct tfeti_timing {
     double factor_ms_total;
     int64_t factor_launches;
     int64_t kernel_launches;   /* library kernels launched since the last reset         */
+    /* FP64 Schur F-apply (TFETI_FAPPLY_SCHUR): device time of the gather + DGEMM launches,
+     * their count (one per F-apply) and their summed algorithmic flops and bytes */
+    double schur_ms_total;
+    int64_t schur_launches;
+    double schur_flops_total;
+    double schur_bytes_total;
 } tfeti_timing;
 int tfeti_timing_get(tfeti_ctx* ctx, tfeti_timing* out);
 int tfeti_timing_reset(tfeti_ctx* ctx, int32_t enable_events);

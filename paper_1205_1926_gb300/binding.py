@@ -59,7 +59,8 @@ class StepInfo(C.Structure):
 class Timing(C.Structure):
     _fields_ = [("f_apply_ms_total", C.c_double), ("f_apply_launches", C.c_int64), ("f_apply_bytes", C.c_double),
                 ("f_apply_flops", C.c_double), ("factor_ms_total", C.c_double), ("factor_launches", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("schur_ms_total", C.c_double), ("schur_launches", C.c_int64),
+                ("schur_flops_total", C.c_double), ("schur_bytes_total", C.c_double)]
 
 
 _P = C.c_void_p
@@ -86,6 +87,7 @@ SIGNATURES = {
     "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
+    "tfeti_set_fapply": (C.c_int, [_P, _I]),
     "tfeti_set_recycling": (C.c_int, [_P, _I]),
     "tfeti_set_learned": (C.c_int, [_P, _I, _I, _D]),
     "tfeti_mlp_weights": (C.c_int, [_P, _P]),
@@ -303,6 +305,10 @@ class Context:
         sc = (C.c_float * 4)(*scal)
         return self._check(self.lib.tfeti_mlp_train(self.h, _ptr(la), _ptr(lb), _ptr(d), _ptr(pf_now), _ptr(pf_prev),
                                                     C.cast(sc, _P), _ptr(target), int(steps)), "tfeti_mlp_train")
+
+    def set_fapply(self, schur: bool):
+        """FP64 F-apply of elastic subdomains by their shape's dual Schur block (DGEMM) or banded solves."""
+        return self._check(self.lib.tfeti_set_fapply(self.h, 1 if schur else 0), "tfeti_set_fapply")
 
     def set_graphs(self, enable: bool):
         """Inner PCGP of the mixed mode as one CUDA graph launch (default) or kernel by kernel."""

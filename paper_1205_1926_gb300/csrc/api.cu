@@ -143,10 +143,15 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
       if (plastic_count[p] == 0 && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
     c->el_cnt[sh] = (int)c->h_el.size() - c->el_off[sh];
   }
-  std::vector<SolveItem> pl;
+  std::vector<SolveItem> pl, pl64;
   for (const SolveItem& it : c->h_items32)
     if (it.fac >= c->own_fac_base) pl.push_back(it);
+  for (const SolveItem& it : c->h_items)
+    if (it.fac >= c->own_fac_base) pl64.push_back(it);
   c->n_items_pl = (int)pl.size();
+  c->n_items_pl64 = (int)pl64.size();
+  if (!pl64.empty())
+    cudaMemcpyAsync(c->d_items_pl64, pl64.data(), sizeof(SolveItem) * pl64.size(), cudaMemcpyHostToDevice, c->st);
   if (!c->h_el.empty())
     cudaMemcpyAsync(c->d_el, c->h_el.data(), sizeof(int) * c->h_el.size(), cudaMemcpyHostToDevice, c->st);
   if (!pl.empty())
@@ -189,18 +194,22 @@ void collect_events(tfeti_ctx* c);
 
 // One FP64 subdomain-solve pass over all subdomains, bracketed by timing events
 // when timing is on (every counted pass is timed: a full event pool is drained first).
-void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
-  cudaEvent_t e1 = nullptr;
-  if (c->events) {
-    if (c->ev_used + 2 > c->ev_pool.size()) {
-      sync(c);
-      collect_events(c);
-    }
-    if (c->ev_used + 2 <= c->ev_pool.size()) {
-      cudaEventRecord(c->ev_pool[c->ev_used++], c->st);
-      e1 = c->ev_pool[c->ev_used++];
-    }
+// Start a timed region on the context stream (kind 0: banded F-apply, 1: Schur
+// F-apply); returns the closing event or null when timing is off.
+cudaEvent_t timed_begin(tfeti_ctx* c, int kind) {
+  if (!c->events) return nullptr;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    sync(c);
+    collect_events(c);
   }
+  if (c->ev_used + 2 > c->ev_pool.size()) return nullptr;
+  c->ev_kind[c->ev_used / 2] = (uint8_t)kind;
+  cudaEventRecord(c->ev_pool[c->ev_used++], c->st);
+  return c->ev_pool[c->ev_used++];
+}
+
+void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
+  cudaEvent_t e1 = timed_begin(c, 0);
   launch_sub_solve(c->M, a, c->solve_smem, c->st);
   if (e1) cudaEventRecord(e1, c->st);
   c->launches += 1;
@@ -213,7 +222,36 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
   a.cbuf = c->cbuf;
   a.in_mode = 0;
   a.out_mode = 0;
-  timed_sub_solve(c, a);
+  if (c->fapply == TFETI_FAPPLY_SCHUR && c->schur_ready) {
+    // elastic subdomains: one DGEMM with the shape's FP64 dual Schur block; the ones with
+    // plastic points: their banded solves, concurrently on the second stream
+    if (c->n_items_pl64 > 0) {
+      cudaEventRecord(c->ev_fork, c->st);
+      cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
+      a.items = c->d_items_pl64;
+      a.n_items = c->n_items_pl64;
+      launch_sub_solve(c->M, a, c->solve_smem, c->st2);
+      cudaEventRecord(c->ev_join, c->st2);
+      c->launches += 1;
+    }
+    cudaEvent_t ge1 = timed_begin(c, 1);
+    for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+      const int cnt = c->el_cnt[sh];
+      if (!cnt) continue;
+      const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
+      launch_schur_gather64(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->X64, c->st);
+      launch_schur_dgemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->X64, c->S64 + c->plan.shapes[sh].s_off,
+                                 c->cbuf, c->st);
+      c->launches += 2;
+      c->g_flops += 2.0 * cnt * (double)n_bd * n_bd;
+      c->g_bytes += 8.0 * ((double)n_bd * n_bd + 2.0 * cnt * n_bd);
+    }
+    if (ge1) cudaEventRecord(ge1, c->st);
+    c->g_launches += 1;
+    if (c->n_items_pl64 > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+  } else {
+    timed_sub_solve(c, a);
+  }
   launch_contract(c->M, c->cbuf, yv, c->st);
   c->launches += 1;
 }
@@ -278,6 +316,7 @@ int form_schur_blocks(tfeti_ctx* c) {
     a.out_mode = 2;
     a.rep_sub = P.shapes[sh].rep_sub;
     a.S32 = c->S32;
+    a.S64 = c->S64;
     a.s_off = P.shapes[sh].s_off;
     launch_sub_solve(c->M, a, c->solve_smem, c->st);
     launch_schur_tile_S(c->S32 + P.shapes[sh].s_off, n_bd, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
@@ -287,6 +326,33 @@ int form_schur_blocks(tfeti_ctx* c) {
   }
   c->schur_ready = true;
   return cuda_check(c, "forming dual Schur blocks");
+}
+
+// The shapes' dual Schur blocks in FP32 (tensor-core tiles) and FP64, formed once.
+int ensure_schur(tfeti_ctx* c) {
+  if (c->schur_ready) return TFETI_OK;
+  try {
+    c->S32 = dalloc<float>(c, c->plan.s_total);
+    c->S64 = dalloc<double>(c, c->plan.s_total);
+    int max_bd = 0;
+    long long s_tiles = 0;
+    c->s_tile_off.assign(c->plan.shapes.size(), 0);
+    for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+      const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
+      max_bd = std::max(max_bd, n_bd);
+      c->s_tile_off[sh] = s_tiles;
+      s_tiles += schur_s_tile_floats(n_bd);
+    }
+    c->Shi = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
+    c->Slo = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
+    const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
+    c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+    c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+    c->X64 = dalloc<double>(c, (size_t)c->h_subs.size() * (size_t)std::max(1, max_bd));
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed");
+  }
+  return form_schur_blocks(c);
 }
 
 void op_project(tfeti_ctx* c, const double* x, double* out) {
@@ -356,7 +422,10 @@ void collect_events(tfeti_ctx* c) {
   if (!c->events) return;
   for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) c->f_ms += ms;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
+      if (c->ev_kind[i / 2]) c->g_ms += ms;
+      else c->f_ms += ms;
+    }
   }
   c->ev_used = 0;
 }
@@ -1146,6 +1215,7 @@ int setup_impl(tfeti_ctx* c) {
   c->d_items = dalloc<SolveItem>(c, ns);
   c->d_items32 = dalloc<SolveItem>(c, ns);
   c->d_items_pl = dalloc<SolveItem>(c, ns);
+  c->d_items_pl64 = dalloc<SolveItem>(c, ns);
   c->d_el = dalloc<int>(c, ns);
   {
     int max_bd = 0;
@@ -1325,6 +1395,7 @@ int setup_impl(tfeti_ctx* c) {
     if (cudaEventCreate(&e) != cudaSuccess) break;
     c->ev_pool.push_back(e);
   }
+  c->ev_kind.assign(c->ev_pool.size() / 2 + 1, 0);
   sync(c);
   return cuda_check(c, "tfeti_setup");
 }
@@ -1551,30 +1622,21 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     launch_to_f32(c->kbb, c->kbb32, c->plan.kbb_template_total + c->plan.kbb_total, c->st);
     c->launches += 2;
   }
-  if (mode == TFETI_PRECISION_MIXED && !c->schur_ready) {
-    try {
-      c->S32 = dalloc<float>(c, c->plan.s_total);
-      int max_bd = 0;
-      long long s_tiles = 0;
-      c->s_tile_off.assign(c->plan.shapes.size(), 0);
-      for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
-        const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
-        max_bd = std::max(max_bd, n_bd);
-        c->s_tile_off[sh] = s_tiles;
-        s_tiles += schur_s_tile_floats(n_bd);
-      }
-      c->Shi = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
-      c->Slo = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
-      const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
-      c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-      c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-    } catch (const std::bad_alloc&) {
-      return fail(c, TFETI_ERR_OOM, "device allocation failed");
-    }
-    const int st = form_schur_blocks(c);
+  if (mode == TFETI_PRECISION_MIXED) {
+    const int st = ensure_schur(c);
     if (st != TFETI_OK) return st;
   }
   return cuda_check(c, "tfeti_set_precision");
+}
+
+int tfeti_set_fapply(tfeti_ctx* c, int32_t mode) {
+  if (!c || (mode != TFETI_FAPPLY_BANDED && mode != TFETI_FAPPLY_SCHUR)) return fail(c, TFETI_ERR_ARG, "bad F-apply mode");
+  if (mode == TFETI_FAPPLY_SCHUR) {
+    const int st = ensure_schur(c);
+    if (st != TFETI_OK) return st;
+  }
+  c->fapply = mode;
+  return cuda_check(c, "tfeti_set_fapply");
 }
 
 int tfeti_set_graphs(tfeti_ctx* c, int32_t enable) {
@@ -1834,6 +1896,10 @@ int tfeti_timing_get(tfeti_ctx* c, tfeti_timing* out) {
   out->factor_ms_total = c->factor_ms;
   out->factor_launches = c->factor_launches;
   out->kernel_launches = c->launches;
+  out->schur_ms_total = c->g_ms;
+  out->schur_launches = c->g_launches;
+  out->schur_flops_total = c->g_flops;
+  out->schur_bytes_total = c->g_bytes;
   return TFETI_OK;
 }
 
@@ -1843,6 +1909,8 @@ int tfeti_timing_reset(tfeti_ctx* c, int32_t enable_events) {
   c->events = enable_events != 0;
   c->f_ms = c->factor_ms = 0.0;
   c->f_launches = c->factor_launches = c->launches = 0;
+  c->g_ms = c->g_flops = c->g_bytes = 0.0;
+  c->g_launches = 0;
   return TFETI_OK;
 }
 

@@ -44,6 +44,14 @@ struct tfeti_ctx {
   long long f32_launches = 0;
   // dual Schur blocks of the shapes' elastic templates (mixed precision)
   float* S32 = nullptr;
+  // FP64 Schur F-apply (tfeti_set_fapply): S in FP64 [s_total], gathered X [n_sub][max n_bd],
+  // FP64 items of the subdomains with plastic points (their banded solves on st2)
+  int fapply = 0;                            // TFETI_FAPPLY_*
+  double *S64 = nullptr, *X64 = nullptr;
+  tfeti::SolveItem* d_items_pl64 = nullptr;
+  int n_items_pl64 = 0;
+  double g_ms = 0.0, g_flops = 0.0, g_bytes = 0.0;
+  long long g_launches = 0;
   // tensor-core operand tiles (TF32 hi/lo parts): S per shape at s_tile_off[shape],
   // the gathered interface vectors of one shape's elastic subdomains
   float *Shi = nullptr, *Slo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
@@ -132,6 +140,7 @@ struct tfeti_ctx {
   // timing
   bool events = false;
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<uint8_t> ev_kind;             // per event pair: 0 banded F-apply, 1 Schur F-apply
   size_t ev_used = 0;
   cudaEvent_t fac_e0 = nullptr, fac_e1 = nullptr;
   double f_ms = 0.0, factor_ms = 0.0;

@@ -142,6 +142,7 @@ struct SolveArgs {
   // S = (K^+)_{boundary, boundary} goes to S32 + s_off + j * n_bd
   int rep_sub;
   float* S32;
+  double* S64;                 // nullable: the same columns in FP64
   long long s_off;
   // in_mode 4 (Dirichlet preconditioner): x = src with the dofs marked in bmask zeroed;
   // no_fix: the factor has no fixing dofs (they are not zeroed before and after)
@@ -150,6 +151,13 @@ struct SolveArgs {
 };
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
 size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
+// FP64 dual Schur block applied to the elastic subdomains of one shape: X[k][i] =
+// (B^T lam) at boundary dof i of subdomain sub_list[k] (row-major [n_list][n_bd]),
+// then cbuf at the interface slots = (X S)[k][i], S64[j * n_bd + i] = S[i][j].
+void launch_schur_gather64(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, double* X,
+                           cudaStream_t st);
+void launch_schur_dgemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* X,
+                                const double* S, double* cbuf, cudaStream_t st);
 // Dual Schur block applied to the elastic subdomains of one shape on the tensor
 // cores (3xTF32): X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k]
 // (0 off the interface), split into TF32 hi/lo tiles; then cbuf at the interface

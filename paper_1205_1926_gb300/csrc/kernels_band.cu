@@ -389,9 +389,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   // ---- outputs
   if (a.out_mode == 2) {
     for (int r = 0; r < R; ++r) {
-      float* col = a.S32 + a.s_off + (long long)item.sub[r] * n_bd;
-      for (int i = tid; i < n_bd; i += nt)
-        col[i] = (float)vec[r * npad + 3 * M.shape_bln[S0.bnd_off + i / 3] + i % 3];
+      const long long o = a.s_off + (long long)item.sub[r] * n_bd;
+      for (int i = tid; i < n_bd; i += nt) {
+        const T v = vec[r * npad + 3 * M.shape_bln[S0.bnd_off + i / 3] + i % 3];
+        a.S32[o + i] = (float)v;
+        if (a.S64) a.S64[o + i] = (double)v;
+      }
     }
     return;
   }

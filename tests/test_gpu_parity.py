@@ -331,6 +331,49 @@ def test_cube64_full_size_properties():
         assert np.abs(force).max() <= 1e-6 * scale
 
 
+# ---------------------------------------------------------------------------- FP64 Schur F-apply
+@pytest.mark.parametrize("w,plastic", [(W.CUBE12, True), (W.SMALL6_RAGGED, True), (W.CUBE48, False)])
+def test_fp64_schur_F_apply_equals_banded(w, plastic):
+    """F through the shapes' FP64 dual Schur blocks (DGEMM; plastic subdomains banded on the second
+    stream) equals the banded F-apply to rounding; 48^3: 216 x 1158 with ragged 64 x 64 tiles."""
+    ctx = T.Context(w)
+    s = ctx.sizes
+    if plastic:
+        m, sig, kap, du = plastic_state(w, seed=95)
+        set_oracle_state(ctx, sig, kap)
+        ctx.assemble_tangent(dev(du), zeros(s["n_dof"]), zeros(s["n_dof"]))
+    else:
+        ctx.assemble_tangent(zeros(s["n_dof"]), zeros(s["n_dof"]), zeros(s["n_dof"]))
+    x = dev(W.seeded_vector(s["n_mult"], seed=96))
+    yb, ys = zeros(s["n_mult"]), zeros(s["n_mult"])
+    ctx.apply("F", x, yb)
+    ctx.set_fapply(True)
+    ctx.apply("F", x, ys)
+    assert rel(host(ys), host(yb)) <= 1e-11
+
+
+def test_fp64_schur_history_cube12():
+    """The 12^3 load history with the Schur F-apply against the oracle."""
+    w = W.CUBE12
+    ctx = T.Context(w)
+    ctx.set_fapply(True)
+    t_y = ctx.first_yield_traction(w.traction_dir)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    df, u = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_dof"])
+    prev = 0.0
+    for a in w.load_fractions():
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        oinfo = model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        ctx.get_state(u=u)
+        assert info["converged"] and rel(host(u), model.u) <= 1e-9
+        assert abs(info["newton"] - oinfo["newton"]) <= 1
+        assert all(abs(a_ - b_) <= 1 for a_, b_ in zip(info["pcg"], oinfo["pcg"]))
+
+
 # ---------------------------------------------------------------------------- Dirichlet preconditioner (Sec. 4.2)
 @pytest.mark.parametrize("w,plastic", [(W.SMALL6_RAGGED, True), (W.CUBE12, True), (W.CUBE12, False),
                                        (ONE_ELEMENT_BOXES, True)])
