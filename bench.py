@@ -20,6 +20,7 @@ itself runs on one GPU).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -35,6 +36,27 @@ import workloads as W  # noqa: E402
 METRIC = "time per load step @1e-8 dual res: FP64 vs mixed+learned; F-apply % HBM peak"
 UNIT = "s/load_step"
 FP64_PEAK_TFLOPS = 1.207      # measured DFMA throughput of this GB300 pool
+
+
+# DRAM traffic per launch of the banded F-apply kernel at the 64^3 benchmark size, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_cube64_bench.md gives the command).
+# Valid only while the kernel source is the one measured.
+MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.33e6,
+                                    "src": "paper_1205_1926_gb300/csrc/kernels_band.cu",
+                                    "sha256": "12466ff4652892216b70fd16c68946e2e4f9ac51f6d0dbd59b6c2f50890d8b75"}}
+
+
+def measured_traffic(kernel, workload):
+    rec = MEASURED_TRAFFIC.get(kernel)
+    if rec is None or rec["workload"] != workload:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["src"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != rec["sha256"]:
+                return None
+    except OSError:
+        return None
+    return rec["bytes"]
 
 
 def peaks():
@@ -379,7 +401,8 @@ def run_gpu(args, rank, world, local_rank):
     achieved_tf = flops / (avg_f_ms * 1e-3) / 1e12 if avg_f_ms > 0 else None
     achieved_gbs = byts / (avg_f_ms * 1e-3) / 1e9 if avg_f_ms > 0 else None
     banded = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": None,
+              "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None,
+              "traffic": measured_traffic("k_sub_solve", w.name),
               "kernel": "k_sub_solve (banded forward/backward substitution with the factor records, FP64)",
               "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25",
               "total_ms": tm["f_apply_ms_total"], "launches": tm["f_apply_launches"],
