@@ -364,10 +364,13 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         aelapsed = max_over_ranks([f0.elapsed_time(f1) / 1e3], dev)[0]
+        actx_tuning = actx.tuning()
         actx.close()
         # compared after the timed region: no torch kernel runs inside it
         diffs = (torch.linalg.vector_norm(asnaps - snaps, dim=1) / torch.linalg.vector_norm(snaps, dim=1)).tolist()
+        tun = actx_tuning
         return {"value": replica_value(aelapsed, args.steps, world), "unit": UNIT, "inner_rtol": args.inner_rtol,
+                "inner_fapply_tuning": tun,
                 "history_size": recycling, "mlp": learned, "speedup_vs_fp64": None,
                 "rel_u_diff_vs_fp64_per_step": diffs,
                 "max_rel_u_diff_vs_fp64": max(diffs), "newton_per_step": [s["newton"] for s in atimed],

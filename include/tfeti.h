@@ -292,6 +292,15 @@ int tfeti_mlp_train(tfeti_ctx* ctx, const double* la, const double* lb, const do
 #define TFETI_FAPPLY_SCHUR  1
 int tfeti_set_fapply(tfeti_ctx* ctx, int32_t mode);
 
+/* Autotuner of the mixed mode's inner F-apply (run when the mixed mode is switched on):
+ * shapes with at least kSchurMinCount = 4 subdomains form their dual Schur block; a
+ * shape applies it (one tensor-core GEMM over its elastic subdomains) only if it has at
+ * least T subdomains, the others take FP32 banded solves.  T is chosen among 4, 16, 64
+ * and "never" by timing the FP32 F-apply once per distinct choice.  Outputs (host,
+ * nullable): the chosen T (1 << 30 = never, 0 = not tuned yet), the number of shapes
+ * applying their block, and the four measured times in ms (-1 if not measured). */
+int tfeti_get_tuning(tfeti_ctx* ctx, int32_t* schur_threshold, int32_t* n_schur_shapes, float* tune_ms);
+
 /* Launch mode of the mixed-precision inner PCGP.  enable != 0 (default): each
  * inner solve is one CUDA graph launch whose body is one iteration inside a
  * WHILE conditional node, the scalars staying on the device.  enable == 0: the

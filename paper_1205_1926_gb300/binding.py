@@ -88,6 +88,7 @@ SIGNATURES = {
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
     "tfeti_set_fapply": (C.c_int, [_P, _I]),
+    "tfeti_get_tuning": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_recycling": (C.c_int, [_P, _I]),
     "tfeti_set_learned": (C.c_int, [_P, _I, _I, _D]),
     "tfeti_mlp_weights": (C.c_int, [_P, _P]),
@@ -309,6 +310,12 @@ class Context:
     def set_fapply(self, schur: bool):
         """FP64 F-apply of elastic subdomains by their shape's dual Schur block (DGEMM) or banded solves."""
         return self._check(self.lib.tfeti_set_fapply(self.h, 1 if schur else 0), "tfeti_set_fapply")
+
+    def tuning(self) -> dict:
+        t, n = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 4)()
+        self.lib.tfeti_get_tuning(self.h, C.byref(t), C.byref(n), C.cast(ms, _P))
+        return {"schur_threshold": t.value, "n_schur_shapes": n.value, "tune_ms": list(ms)}
 
     def set_graphs(self, enable: bool):
         """Inner PCGP of the mixed mode as one CUDA graph launch (default) or kernel by kernel."""

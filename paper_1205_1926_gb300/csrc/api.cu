@@ -65,6 +65,18 @@ double dot_host(tfeti_ctx* c, const double* x, const double* y, long long n) {
   return v;
 }
 
+// Largest work first: CTAs start roughly in index order, so with uneven subdomains the
+// long solves begin early and the short ones fill in behind them (a stable order, so
+// the items, and therefore the results, do not depend on anything but the inputs).
+void sort_items_by_cost(const tfeti_ctx* c, std::vector<SolveItem>& items) {
+  auto cost = [c](const SolveItem& it) {
+    const SubDev& S = c->h_subs[it.sub[0]];
+    return (double)it.count * S.n_dof * (S.bw + 1);
+  };
+  std::stable_sort(items.begin(), items.end(),
+                   [&cost](const SolveItem& a, const SolveItem& b) { return cost(a) > cost(b); });
+}
+
 // Solve work items: elastic subdomains of one shape share the shape's template
 // factor and are grouped R to a CTA so that the items fit one wave of SMs;
 // subdomains with plastic points carry their own factor, one per CTA.
@@ -92,6 +104,7 @@ void build_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R,
       it.sub[0] = p;
       items.push_back(it);
     }
+  sort_items_by_cost(c, items);
 }
 
 // Items of the Dirichlet-preconditioner solves: elastic subdomains grouped R to a CTA
@@ -137,17 +150,23 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   c->h_el.clear();
   c->el_off.assign(c->plan.shapes.size(), 0);
   c->el_cnt.assign(c->plan.shapes.size(), 0);
+  c->h_np = plastic_count;
+  const bool have_use = c->schur_use.size() == c->plan.shapes.size();
+  auto uses_schur = [&](int sh) { return have_use && c->schur_use[sh]; };
   for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
     c->el_off[sh] = (int)c->h_el.size();
-    for (int p = 0; p < ns; ++p)
-      if (plastic_count[p] == 0 && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
+    if (uses_schur((int)sh))
+      for (int p = 0; p < ns; ++p)
+        if (plastic_count[p] == 0 && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
     c->el_cnt[sh] = (int)c->h_el.size() - c->el_off[sh];
   }
+  // banded items beside the Schur GEMMs: subdomains with plastic points and the elastic
+  // subdomains of shapes without a Schur block in use
   std::vector<SolveItem> pl, pl64;
   for (const SolveItem& it : c->h_items32)
-    if (it.fac >= c->own_fac_base) pl.push_back(it);
+    if (it.fac >= c->own_fac_base || !uses_schur(c->h_subs[it.sub[0]].shape)) pl.push_back(it);
   for (const SolveItem& it : c->h_items)
-    if (it.fac >= c->own_fac_base) pl64.push_back(it);
+    if (it.fac >= c->own_fac_base || !uses_schur(c->h_subs[it.sub[0]].shape)) pl64.push_back(it);
   c->n_items_pl = (int)pl.size();
   c->n_items_pl64 = (int)pl64.size();
   if (!pl64.empty())
@@ -240,7 +259,7 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
       if (!cnt) continue;
       const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
       launch_schur_gather64(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->X64, c->st);
-      launch_schur_dgemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->X64, c->S64 + c->plan.shapes[sh].s_off,
+      launch_schur_dgemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->X64, c->S64 + c->s_off_c[sh],
                                  c->cbuf, c->st);
       c->launches += 2;
       c->g_flops += 2.0 * cnt * (double)n_bd * n_bd;
@@ -300,6 +319,7 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv) {
 int form_schur_blocks(tfeti_ctx* c) {
   const Plan& P = c->plan;
   for (size_t sh = 0; sh < P.shapes.size(); ++sh) {
+    if (!c->schur_formed[sh]) continue;
     const int n_bd = 3 * P.shapes[sh].n_bnd;
     std::vector<SolveItem> items;
     for (int j = 0; j < n_bd; j += c->rcap) {
@@ -317,9 +337,9 @@ int form_schur_blocks(tfeti_ctx* c) {
     a.rep_sub = P.shapes[sh].rep_sub;
     a.S32 = c->S32;
     a.S64 = c->S64;
-    a.s_off = P.shapes[sh].s_off;
+    a.s_off = c->s_off_c[sh];
     launch_sub_solve(c->M, a, c->solve_smem, c->st);
-    launch_schur_tile_S(c->S32 + P.shapes[sh].s_off, n_bd, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
+    launch_schur_tile_S(c->S32 + c->s_off_c[sh], n_bd, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
                         c->st);
     c->launches += 2;
     sync(c);
@@ -331,18 +351,27 @@ int form_schur_blocks(tfeti_ctx* c) {
 // The shapes' dual Schur blocks in FP32 (tensor-core tiles) and FP64, formed once.
 int ensure_schur(tfeti_ctx* c) {
   if (c->schur_ready) return TFETI_OK;
+  const size_t nsh = c->plan.shapes.size();
+  std::vector<int> count(nsh, 0);
+  for (const SubDev& sd : c->h_subs) ++count[sd.shape];
+  c->schur_formed.assign(nsh, 0);
+  c->s_off_c.assign(nsh, 0);
   try {
-    c->S32 = dalloc<float>(c, c->plan.s_total);
-    c->S64 = dalloc<double>(c, c->plan.s_total);
     int max_bd = 0;
-    long long s_tiles = 0;
-    c->s_tile_off.assign(c->plan.shapes.size(), 0);
-    for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+    long long s_tiles = 0, s_tot = 0;
+    c->s_tile_off.assign(nsh, 0);
+    for (size_t sh = 0; sh < nsh; ++sh) {
+      if (count[sh] < kSchurMinCount) continue;
+      c->schur_formed[sh] = 1;
       const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
       max_bd = std::max(max_bd, n_bd);
+      c->s_off_c[sh] = s_tot;
+      s_tot += (long long)n_bd * n_bd;
       c->s_tile_off[sh] = s_tiles;
       s_tiles += schur_s_tile_floats(n_bd);
     }
+    c->S32 = dalloc<float>(c, (size_t)std::max(1LL, s_tot));
+    c->S64 = dalloc<double>(c, (size_t)std::max(1LL, s_tot));
     c->Shi = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
     c->Slo = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
     const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
@@ -352,7 +381,59 @@ int ensure_schur(tfeti_ctx* c) {
   } catch (const std::bad_alloc&) {
     return fail(c, TFETI_ERR_OOM, "device allocation failed");
   }
+  c->schur_use = c->schur_formed;
   return form_schur_blocks(c);
+}
+
+void op_F32(tfeti_ctx* c, const double* x, double* yv);
+
+// Autotuner of the inner F-apply: a shape uses its dual Schur block (one tensor-core
+// GEMM over its elastic subdomains) only if it has at least T subdomains, the others
+// run FP32 banded solves.  T is picked among a few candidates by timing the FP32
+// F-apply once per distinct choice (after one warm-up application each).
+int tune_schur_threshold(tfeti_ctx* c) {
+  const size_t nsh = c->plan.shapes.size();
+  std::vector<int> count(nsh, 0);
+  for (const SubDev& sd : c->h_subs) ++count[sd.shape];
+  const std::vector<int> np = c->h_np.size() == c->h_subs.size() ? c->h_np : std::vector<int>(c->h_subs.size(), 0);
+  const int cands[] = {kSchurMinCount, 16, 64, 1 << 30};
+  const long long m = c->M.n_mult;
+  cudaMemsetAsync(c->tm, 0, sizeof(double) * m, c->st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  c->schur_tune_ms.clear();
+  float best = 0.f;
+  int best_t = cands[3];
+  std::vector<char> last;
+  for (int t : cands) {
+    std::vector<char> use(nsh, 0);
+    for (size_t sh = 0; sh < nsh; ++sh) use[sh] = c->schur_formed[sh] && count[sh] >= t;
+    if (use == last) {
+      c->schur_tune_ms.push_back(c->schur_tune_ms.back());
+      continue;
+    }
+    last = use;
+    c->schur_use = use;
+    build_items(c, np);
+    op_F32(c, c->tm, c->Fp);
+    cudaEventRecord(e0, c->st);
+    for (int r = 0; r < 3; ++r) op_F32(c, c->tm, c->Fp);
+    cudaEventRecord(e1, c->st);
+    sync(c);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    c->schur_tune_ms.push_back(ms);
+    if (best_t == cands[3] && c->schur_tune_ms.size() == 1) best = ms, best_t = t;
+    else if (ms < best) best = ms, best_t = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->schur_threshold = best_t;
+  for (size_t sh = 0; sh < nsh; ++sh) c->schur_use[sh] = c->schur_formed[sh] && count[sh] >= best_t;
+  build_items(c, np);
+  return cuda_check(c, "tuning the inner F-apply");
 }
 
 void op_project(tfeti_ctx* c, const double* x, double* out) {
@@ -1623,8 +1704,13 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     c->launches += 2;
   }
   if (mode == TFETI_PRECISION_MIXED) {
-    const int st = ensure_schur(c);
+    const bool fresh = !c->schur_ready;
+    int st = ensure_schur(c);
     if (st != TFETI_OK) return st;
+    if (fresh || c->schur_threshold == 0) {
+      st = tune_schur_threshold(c);
+      if (st != TFETI_OK) return st;
+    }
   }
   return cuda_check(c, "tfeti_set_precision");
 }
@@ -1637,6 +1723,17 @@ int tfeti_set_fapply(tfeti_ctx* c, int32_t mode) {
   }
   c->fapply = mode;
   return cuda_check(c, "tfeti_set_fapply");
+}
+
+int tfeti_get_tuning(tfeti_ctx* c, int32_t* schur_threshold, int32_t* n_schur_shapes, float* tune_ms) {
+  if (!c) return TFETI_ERR_ARG;
+  int n = 0;
+  for (char u : c->schur_use) n += u != 0;
+  if (schur_threshold) *schur_threshold = c->schur_threshold;
+  if (n_schur_shapes) *n_schur_shapes = n;
+  if (tune_ms)
+    for (int i = 0; i < 4; ++i) tune_ms[i] = i < (int)c->schur_tune_ms.size() ? c->schur_tune_ms[i] : -1.f;
+  return TFETI_OK;
 }
 
 int tfeti_set_graphs(tfeti_ctx* c, int32_t enable) {

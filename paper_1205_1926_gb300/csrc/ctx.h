@@ -47,6 +47,14 @@ struct tfeti_ctx {
   // FP64 Schur F-apply (tfeti_set_fapply): S in FP64 [s_total], gathered X [n_sub][max n_bd],
   // FP64 items of the subdomains with plastic points (their banded solves on st2)
   int fapply = 0;                            // TFETI_FAPPLY_*
+  // per shape: S formed (shapes with at least kSchurMinCount subdomains), compact offsets
+  // of S and its tiles, and whether the inner F-apply uses it (count >= schur_threshold,
+  // the threshold picked by timing the FP32 F-apply for a few candidates)
+  std::vector<char> schur_formed, schur_use;
+  std::vector<long long> s_off_c;
+  int schur_threshold = 0;
+  std::vector<float> schur_tune_ms;          // measured FP32 F-apply per candidate threshold
+  std::vector<int> h_np;                     // plastic points per subdomain at the last assembly
   double *S64 = nullptr, *X64 = nullptr;
   tfeti::SolveItem* d_items_pl64 = nullptr;
   int n_items_pl64 = 0;

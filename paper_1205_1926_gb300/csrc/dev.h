@@ -21,6 +21,7 @@ struct SubDev {
 };
 
 constexpr int kMaxRHS = 4;     // right-hand sides one solve CTA carries
+constexpr int kSchurMinCount = 4;   // shapes with fewer subdomains never form their dual Schur block
 
 // One CTA of the subdomain solve: up to kMaxRHS subdomains of one shape that
 // share the factor record at `fac` (the elastic template) or a single

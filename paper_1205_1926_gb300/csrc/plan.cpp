@@ -105,18 +105,22 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
         int fx[6] = {3 * a, 3 * a + 1, 3 * a + 2, 3 * b + 1, 3 * b + 2, 3 * c + 2};
         std::sort(fx, fx + 6);
         for (int t = 0; t < 6; ++t) s.fix[t] = fx[t];
-        // factor blocks: 32 rows unless two panels of 32 x bw and one vector exceed 200 KB of shared memory
-        s.nb = std::min(32, s.bw + 1);
-        if ((2LL * s.nb * s.bw + s.n_dof) * 8 > 200 * 1024) s.nb = std::min(16, s.bw + 1);
-        s.nblk = (s.n_dof + s.nb - 1) / s.nb;
-        s.rec = ((s.nb * s.bw) + 3) & ~3;                  // 16-byte records in FP64 and FP32
-        s.fac_size = (int64_t)s.nblk * s.rec + (int64_t)s.nblk * s.nb * s.nb;
         plan.max_bw = std::max(plan.max_bw, s.bw);
         plan.max_ndof = std::max(plan.max_ndof, s.n_dof);
         plan.subs.push_back(s);
       }
   plan.n_dof = dof_off;
   plan.band_total = band_off;
+  // factor blocks: 32 rows unless two panels of 32 x bw and one local vector exceed 200 KB
+  // of shared memory; the solve launch sizes its shared memory by the largest record and
+  // the largest local vector of all subdomains, so the test uses the largest n
+  for (auto& s : plan.subs) {
+    s.nb = std::min(32, s.bw + 1);
+    if ((2LL * s.nb * s.bw + plan.max_ndof) * 8 > 200 * 1024) s.nb = std::min(16, s.bw + 1);
+    s.nblk = (s.n_dof + s.nb - 1) / s.nb;
+    s.rec = ((s.nb * s.bw) + 3) & ~3;                  // 16-byte records in FP64 and FP32
+    s.fac_size = (int64_t)s.nblk * s.rec + (int64_t)s.nblk * s.nb * s.nb;
+  }
   int64_t fo = 0;
   for (auto& s : plan.subs) {
     s.fac_off = fo;

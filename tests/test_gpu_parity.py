@@ -331,6 +331,37 @@ def test_cube64_full_size_properties():
         assert np.abs(force).max() <= 1e-6 * scale
 
 
+# ---------------------------------------------------------------------------- uneven boxes, tuned inner F-apply
+# 21 x 16 x 16 bricks: 64 boxes of 4^3 and 16 of 5 x 4 x 4 (two shapes with Schur blocks, counts 64 and 16)
+UNEVEN_BOXES = W.Workload(name="uneven_boxes", nel=(21, 16, 16),
+                          cuts=((0, 4, 8, 12, 16, 21), (0, 4, 8, 12, 16), (0, 4, 8, 12, 16)), n_steps=4)
+
+
+@pytest.mark.parametrize("w", [UNEVEN_BOXES, W.CUBE24_IRREGULAR])
+def test_tuned_mixed_dual_pcg_on_uneven_boxes(w):
+    """The mixed mode's autotuned inner F-apply (Schur GEMMs for the shapes above the tuned count, FP32
+    banded solves for the rest, largest solves first) reaches the oracle's solution at eps = 1e-12."""
+    m, sig, kap, du = plastic_state(w, seed=97)
+    du = 0.2 * du
+    ctx = T.Context(w)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((20.0, 5.0, -8.0))
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    ctx.set_precision(True, 1e-3)
+    tun = ctx.tuning()
+    assert tun["schur_threshold"] in (4, 16, 64, 1 << 30)
+    assert min(t for t in tun["tune_ms"] if t >= 0) > 0
+    u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+    ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, _ = m.assemble(du, df)
+    sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+    assert rel(host(u), sol["u"]) <= 1e-9
+    assert rel(host(lam), sol["lam"]) <= 1e-9
+
+
 # ---------------------------------------------------------------------------- FP64 Schur F-apply
 @pytest.mark.parametrize("w,plastic", [(W.CUBE12, True), (W.SMALL6_RAGGED, True), (W.CUBE48, False)])
 def test_fp64_schur_F_apply_equals_banded(w, plastic):

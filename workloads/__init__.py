@@ -139,6 +139,13 @@ def irregular_cube80(seed: int = 0, n: int = 80) -> Workload:
     return Workload(name=f"cube80_irregular_s{seed}", nel=(n, n, n), cuts=cuts, n_steps=20)
 
 
+def irregular_cube(n: int, seed: int, n_steps: int = 20, **kw) -> Workload:
+    """n^3 cube with a seeded tensor-product partition into boxes of 4..12 elements per edge."""
+    rng = random.Random(seed)
+    cuts = tuple(irregular_cuts(n, rng) for _ in range(3))
+    return Workload(name=f"cube{n}_irregular_s{seed}", nel=(n, n, n), cuts=cuts, n_steps=n_steps, **kw)
+
+
 def irregular_cases(seed: int = 0, n_cases: int = 16) -> list:
     """Seeded material/load cases: sigma_y ~ U[300,600], H ~ U[1e3,2e4], traction angle ~ U[0, 2pi)."""
     import math
@@ -171,3 +178,11 @@ def seeded_gauss_point_inputs(n: int, seed: int, scale_strain: float = 1e-3, sca
     kap = rng.uniform(0.0, 1e-3, size=n)
     eta = rng.standard_normal((n, 6)) * scale_strain
     return sig, kap, eta
+
+
+# Batching geometry (config 4): 80^3 in a seeded irregular partition (seed 0: 9 x 10 x 9 = 810 boxes of
+# 252 distinct shapes), timed like the 64^3 case; and a 24^3 irregular parity case.
+CUBE80_IRREGULAR = irregular_cube(80, 0, newton_tol=1e-6, pcg_rtol=1e-8)
+CUBE24_IRREGULAR = irregular_cube(24, 3, n_steps=4)
+WORKLOADS[CUBE80_IRREGULAR.name] = CUBE80_IRREGULAR
+WORKLOADS[CUBE24_IRREGULAR.name] = CUBE24_IRREGULAR
