@@ -13,8 +13,8 @@
 // the MMA reads (no swizzle, K-major "core matrices" of 8 rows x 16 bytes), so
 // one pipeline stage is four contiguous 1-D bulk copies:
 //   A (X) tile: 128 rows (subdomains) x 32 columns (dofs), core matrix (kg, mg)
-//               at byte (kg * 16 + mg) * 128;  B (S) tile: 64 rows x 32 columns,
-//               core matrix (kg, ng) at byte (kg * 8 + ng) * 128;
+//               at byte (kg * 16 + mg) * 128;  B (S) tile: kTN = 32 rows x 32 columns,
+//               core matrix (kg, ng) at byte (kg * 4 + ng) * 128;
 // row r of a core matrix holds 4 consecutive K elements (16 bytes).
 #include "async_common.cuh"
 #include "dev.h"
@@ -24,10 +24,10 @@ namespace tfeti {
 
 namespace {
 
-constexpr int kTM = 128, kTN = 64, kTK = 32, kStages = 4;
+constexpr int kTM = 128, kTN = 32, kTK = 32, kStages = 4;
 constexpr uint32_t kABytes = kTM * kTK * 4, kBBytes = kTN * kTK * 4;
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr uint32_t kTmemCols = 64;   // FP32 accumulator columns (= kTN)
+constexpr uint32_t kTmemCols = kTN;  // FP32 accumulator columns (a power of two >= 32)
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// C = X S for one 128 x 64 output tile (blockIdx.y: subdomain tile, blockIdx.x:
+// C = X S for one 128 x kTN output tile (blockIdx.y: subdomain tile, blockIdx.x:
 // boundary-dof tile), written to the copy slots of the interface dofs.  128
 // threads: thread 0 streams the stages, thread 32 issues the MMAs, all four warps
 // read the accumulator (warp w owns TMEM lanes 32w..32w+31 = output rows).
