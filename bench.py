@@ -246,6 +246,28 @@ def replica_value(elapsed_max, steps, world):
 
 
 # --------------------------------------------------------------------------------------- CUDA path
+ARMS = ("fp64", "mixed", "mixed_history", "mixed_learned")
+ARM_NOTES = {
+    "fp64": "Algorithm 3 in FP64 (banded K^+ applies), the paper's method",
+    "mixed": "FP64-refined PCGP: FP32 dual Schur blocks on the tensor cores (elastic) and FP32 banded solves "
+             "(plastic), FP32 projector and preconditioner inside; FP64 residual and stopping test",
+    "mixed_history": "the mixed arm with each dual solve started from the Galerkin-optimal combination of the "
+                     "solver's last 8 solutions, zero-start fallback",
+    "mixed_learned": "the mixed arm with the learned start: the last 7 solutions plus the per-interface MLP "
+                     "prediction (trained online on the solver's own lambda histories) as Galerkin vectors",
+}
+
+
+def resolve_arm(args):
+    if args.arm:
+        return args.arm
+    if args.precision == "fp64":
+        return "fp64"
+    if args.precision == "mixed":
+        return "mixed_learned" if args.learned else "mixed"
+    return "mixed_learned"
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -264,19 +286,35 @@ def run_gpu(args, rank, world, local_rank):
     n_total = args.warmup + args.steps
     stream = torch.cuda.Stream(device=dev)
     pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
-    ctx = T.Context(w, stream=stream, precond=pre)
-    if args.fapply == "schur":
-        ctx.set_fapply(True)
-    if args.precision == "mixed":
-        ctx.set_precision(True, args.inner_rtol)
-    if args.learned:
-        ctx.set_recycling(min(args.history, 7))
-        ctx.set_learned(True)
-    if args.no_graphs:
-        ctx.set_graphs(False)
+    main_arm = resolve_arm(args)
+
+    def make_ctx(arm):
+        c = T.Context(w, stream=stream, precond=pre)
+        if args.fapply == "schur":
+            c.set_fapply(True)
+        if arm != "fp64":
+            c.set_precision(True, args.inner_rtol)
+        if arm == "mixed_history":
+            c.set_recycling(args.history)
+        if arm == "mixed_learned":
+            c.set_recycling(min(args.history, 7))
+            c.set_learned(True)
+        if args.no_graphs:
+            c.set_graphs(False)
+        return c
+
+    def reset_start(c, arm):
+        # the history and the network start over (the first-yield solve must not seed them)
+        if arm == "mixed_history":
+            c.set_recycling(args.history)
+        if arm == "mixed_learned":
+            c.set_recycling(min(args.history, 7))
+            c.set_learned(True)
+
+    ctx = make_ctx(main_arm)
     n = ctx.sizes["n_dof"]
-    n_gp = ctx.sizes["n_gp"]
     t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
+    reset_start(ctx, main_arm)
     fr = w.load_fractions(n_total)
     dfs, prev = [], 0.0
     with torch.cuda.stream(stream):
@@ -286,118 +324,88 @@ def run_gpu(args, rank, world, local_rank):
             dfs.append(d)
             prev = a
     stream.synchronize()
-    infos = []
-    for k in range(args.warmup):
-        infos.append(ctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
-    # checkpoint for the end-to-end pass
-    ck = [torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(6 * n_gp, dtype=torch.float64, device=dev),
-          torch.zeros(n_gp, dtype=torch.float64, device=dev)]
-    ctx.get_state(*ck)
 
-    # ---- timed pass: inputs resident in HBM
-    sampler = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ctx.timing_reset(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    timed = []
-    snaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
-    for k in range(args.warmup, n_total):
-        timed.append(ctx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
-        ctx.get_state(u=snaps[k - args.warmup])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    tm = ctx.timing()
-    u_dev = torch.zeros(n, dtype=torch.float64, device=dev)
-    ctx.get_state(u=u_dev)
-    u_final = u_dev.clone()
-
-    # ---- end-to-end pass: same steps through the C ABI with host (pinned) buffers
-    if args.no_e2e:
-        n_total_e2e = args.warmup
-    else:
-        n_total_e2e = n_total
-    ctx.set_state(*ck)
-    dfs_h = [d.cpu().pin_memory() for d in dfs]
-    u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.warmup, n_total_e2e):
-        ctx.time_step(dfs_h[k].data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit, df_on_host=True)
-        ctx.get_state(u=u_dev)
-        with torch.cuda.stream(stream):
-            u_host.copy_(u_dev, non_blocking=True)
-        stream.synchronize()
-    torch.cuda.synchronize()
-    barrier()
-    elapsed_e2e = time.perf_counter() - t0
-    e2e_match = bool(torch.equal(u_host.to(dev), u_final)) if not args.no_e2e else None
-
-    # ---- the other arms of the metric on the same load history: mixed precision, and mixed
-    # precision with the history start of the dual PCGP (the "learned" start)
-    def run_arm(recycling, learned=False):
-        actx = T.Context(w, stream=stream, precond=pre)
-        actx.set_precision(True, args.inner_rtol)
-        actx.set_recycling(recycling)
-        if learned:
-            actx.set_learned(True)
-        if args.no_graphs:
-            actx.set_graphs(False)
+    def timed_run(c, headline=False):
+        """Warm-up steps, then the K timed steps (inputs resident in HBM, CUDA events on the context
+        stream, max over ranks); u after every step is kept for the comparisons made afterwards."""
         for k in range(args.warmup):
-            actx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
-        asnaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
-        atimed = []
+            c.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        snaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
+        infos = []
+        sampler = ClockSampler(local_rank) if headline else None
         barrier()
         torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
+        if sampler:
+            sampler.start()
+        c.timing_reset(headline)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for k in range(args.warmup, n_total):
-            atimed.append(actx.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
-            actx.get_state(u=asnaps[k - args.warmup])
-        f1.record(stream)
+            infos.append(c.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+            c.get_state(u=snaps[k - args.warmup])
+        e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        aelapsed = max_over_ranks([f0.elapsed_time(f1) / 1e3], dev)[0]
-        actx_tuning = actx.tuning()
-        actx.close()
-        # compared after the timed region: no torch kernel runs inside it
-        diffs = (torch.linalg.vector_norm(asnaps - snaps, dim=1) / torch.linalg.vector_norm(snaps, dim=1)).tolist()
-        tun = actx_tuning
-        return {"value": replica_value(aelapsed, args.steps, world), "unit": UNIT, "inner_rtol": args.inner_rtol,
-                "inner_fapply_tuning": tun,
-                "history_size": recycling, "mlp": learned, "speedup_vs_fp64": None,
-                "rel_u_diff_vs_fp64_per_step": diffs,
-                "max_rel_u_diff_vs_fp64": max(diffs), "newton_per_step": [s["newton"] for s in atimed],
-                "pcg_inner_per_step": [sum(s["pcg"]) for s in atimed],
-                "outer_per_step": [sum(s["outer"]) for s in atimed],
-                "history_starts_per_step": [sum(s["history"]) for s in atimed]}
+        clocks = sampler.stop() if sampler else None
+        elapsed = max_over_ranks([e0.elapsed_time(e1) / 1e3], dev)[0]
+        return {"elapsed": elapsed, "infos": infos, "snaps": snaps, "tm": c.timing(), "clocks": clocks,
+                "tuning": c.tuning() if hasattr(c, "tuning") else None}
 
-    mixed = learned = history = None
-    if args.precision == "fp64" and not args.no_mixed:
-        ctx.close()
-        mixed = run_arm(0)
-        mixed["note"] = ("FP64-refined PCGP: FP32 dual Schur blocks on the tensor cores (elastic) and FP32 banded "
-                         "solves (plastic), FP32 projector and preconditioner inside; FP64 residual and stopping test")
-        history = run_arm(args.history)
-        history["note"] = ("the mixed arm with each dual solve started from the Galerkin-optimal combination of the "
-                           "solver's last solutions, zero-start fallback")
-        learned = run_arm(min(args.history, 7), learned=True)
-        learned["note"] = ("the history start plus the per-interface MLP prediction (trained online on the solver's "
-                           "own lambda histories) as one more Galerkin vector in each load step's first solve")
-    elapsed, elapsed_e2e = max_over_ranks([elapsed, elapsed_e2e], dev)
+    main = timed_run(ctx, headline=True)
+    ctx.close()
+
+    # ---- end-to-end pass of the headline arm through the C ABI with host (pinned) buffers, on a fresh
+    # context (the learned start's history and network must start over with the states)
+    e2e = None
+    if not args.no_e2e:
+        ce = make_ctx(main_arm)
+        for k in range(args.warmup):
+            ce.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        dfs_h = [d.cpu().pin_memory() for d in dfs]
+        u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
+        u_dev = torch.zeros(n, dtype=torch.float64, device=dev)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, n_total):
+            ce.time_step(dfs_h[k].data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit, df_on_host=True)
+            ce.get_state(u=u_dev)
+            with torch.cuda.stream(stream):
+                u_host.copy_(u_dev, non_blocking=True)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        elapsed_e2e = max_over_ranks([time.perf_counter() - t0], dev)[0]
+        ce.close()
+        e2e = {"value": replica_value(elapsed_e2e, args.steps, world), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+               "matches_device_pass": bool(torch.equal(u_host.to(dev), main["snaps"][-1]))}
+
+    # ---- the other arms of the metric on the same load history
+    runs = {main_arm: main}
+    if not args.no_mixed:
+        for arm in ARMS:
+            if arm == main_arm:
+                continue
+            c = make_ctx(arm)
+            runs[arm] = timed_run(c)
+            c.close()
+    ref = runs.get("fp64")
+
+    def rel_u_diffs(r):
+        if ref is None or r is ref:
+            return None
+        # compared after the timed regions: no torch kernel runs inside them
+        return (torch.linalg.vector_norm(r["snaps"] - ref["snaps"], dim=1) /
+                torch.linalg.vector_norm(ref["snaps"], dim=1)).tolist()
+
+    value = replica_value(main["elapsed"], args.steps, world)
     units = args.steps * world
-    value = replica_value(elapsed, args.steps, world)
     pk, pk_kind = peaks()
-    # F-apply kernels: the banded K^+ solves (k_sub_solve: every F-apply in the banded mode,
-    # the set-up/recovery solves and the plastic subdomains in the Schur mode) and the FP64
-    # dual-Schur DGEMM (k_schur_dgemm: elastic subdomains in the Schur mode).  The roofline
-    # object describes the one with the larger share of device time; the other sits beside it.
+    tm = main["tm"]
+    # F-apply kernels: the banded K^+ solves (k_sub_solve: every F-apply of the FP64 arm, the residual
+    # solves of the mixed arms) and, with --fapply schur, the FP64 dual-Schur DGEMM.  The roofline object
+    # describes the one with the larger share of the headline arm's device time; the other sits beside it.
     avg_f_ms = tm["f_apply_ms_total"] / max(tm["f_apply_launches"], 1)
     flops = tm["f_apply_flops"]
     byts = tm["f_apply_bytes"]
@@ -428,53 +436,63 @@ def run_gpu(args, rank, world, local_rank):
                          "avg_launch_ms": tm["schur_ms_total"] / tm["schur_launches"],
                          "of": f"{pk_kind} hbm_gbs; bytes: the shared S (L2-resident) and X, Y"}}
     if schur is not None and schur["total_ms"] >= banded["total_ms"]:
-        roof, other = schur, banded
+        roof, other = dict(schur), banded
     else:
-        roof, other = banded, schur
-    roof = dict(roof)
+        roof, other = dict(banded), schur
     if other is not None:
         roof["other_kernel"] = other
-    newton_steps = [s["newton"] for s in timed]
-    pcg_steps = [sum(s["pcg"]) for s in timed]
+
+    def per_step(r):
+        return {"newton_per_step": [s["newton"] for s in r["infos"]],
+                "pcg_per_step": [sum(s["pcg"]) for s in r["infos"]],
+                "outer_per_step": [sum(s["outer"]) for s in r["infos"]],
+                "history_starts_per_step": [sum(1 for h in s["history"] if h) for s in r["infos"]]}
+
+    arms = {}
+    for arm, r in runs.items():
+        if arm == main_arm:
+            continue
+        v = replica_value(r["elapsed"], args.steps, world)
+        d = rel_u_diffs(r)
+        arms[arm] = {"value": v, "unit": UNIT, "headline_speedup": v / value, "note": ARM_NOTES[arm],
+                     "max_rel_u_diff_vs_fp64": max(d) if d else None, "rel_u_diff_vs_fp64_per_step": d,
+                     "inner_fapply_tuning": r["tuning"] if arm != "fp64" else None} | per_step(r)
+    main_d = rel_u_diffs(main)
+    fp64_run = runs.get("fp64")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if main_arm == "fp64" else "f64+f32", "data": "synthetic",
             "config": workload_config(w, args.steps, args.warmup, args.precond) | {
-                "parallelism": "replicas" if world > 1 else "1 GPU", "precision": args.precision,
-                "inner_rtol": args.inner_rtol if args.precision == "mixed" else None,
-                "history_start": args.history if args.learned else 0, "fapply": args.fapply,
+                "parallelism": "replicas" if world > 1 else "1 GPU", "arm": main_arm,
+                "arm_note": ARM_NOTES[main_arm],
+                "inner_rtol": args.inner_rtol if main_arm != "fp64" else None, "fapply": args.fapply,
                 "inner_pcgp_launch": "kernel by kernel" if args.no_graphs else "one CUDA graph (WHILE node) per inner solve"},
-            "e2e": None if args.no_e2e else {"value": elapsed_e2e / units, "unit": UNIT,
-                                             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
-                                             "matches_device_pass": e2e_match},
+            "e2e": e2e,
             "gpu_launches": int(tm["kernel_launches"]),
             "roofline": roof,
-            "clocks": clocks,
-            "solver": {"t_y": t_y, "newton_per_step": newton_steps, "pcg_per_step": pcg_steps,
-                       "outer_per_step": [sum(s["outer"]) for s in timed],
-                       "plastic_gp_final": timed[-1]["plastic_committed"],
-                       "refactored_per_step": [s["refactored"] for s in timed],
+            "clocks": main["clocks"],
+            "max_rel_u_diff_vs_fp64": max(main_d) if main_d else None,
+            "solver": {"t_y": t_y, "plastic_gp_final": main["infos"][-1]["plastic_committed"],
+                       "refactored_per_step": [s["refactored"] for s in main["infos"]],
                        "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
-                       "timed_s": elapsed}}
-    if mixed is not None:
-        mixed["speedup_vs_fp64"] = value / mixed["value"]
-        line["mixed"] = mixed
-    if history is not None:
-        history["speedup_vs_fp64"] = value / history["value"]
-        line["mixed_history"] = history
-    if learned is not None:
-        learned["speedup_vs_fp64"] = value / learned["value"]
-        line["mixed_learned"] = learned
+                       "inner_fapply_tuning": main["tuning"] if main_arm != "fp64" else None,
+                       "rel_u_diff_vs_fp64_per_step": main_d, "timed_s": main["elapsed"]} | per_step(main),
+            "arms": arms}
+    if fp64_run is not None:
+        line["fp64_value"] = replica_value(fp64_run["elapsed"], args.steps, world)
+        line["speedup_vs_fp64"] = line["fp64_value"] / value
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cube64_8x8x8":
+        counts = fp64_run if fp64_run is not None else main
         s = oracle_sample_subprocess(w.name)
-        v = oracle_step_estimate(s, statistics.mean(newton_steps), statistics.mean(pcg_steps))
+        v = oracle_step_estimate(s, statistics.mean(x["newton"] for x in counts["infos"]),
+                                 statistics.mean(sum(x["pcg"]) for x in counts["infos"]))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
-                                "sample": s["sample"] + "; scaled with this run's Newton/PCGP counts per step",
+                                "sample": s["sample"] + "; scaled with the FP64 arm's Newton/PCGP counts per step "
+                                                        "(the oracle runs Algorithm 3 as printed)",
                                 "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s",
                                                                    "f_apply_s")}}
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -488,16 +506,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", metavar="WORKLOAD", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiler runs)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="fp64: Algorithm 3 in FP64; mixed: FP64-refined PCGP with FP32 subdomain solves")
+    ap.add_argument("--arm", default=None, choices=list(ARMS),
+                    help="the headline (timed, end-to-end) arm; default mixed_learned, the metric's method")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="shorthand: fp64 = --arm fp64, mixed = --arm mixed (or mixed_learned with --learned)")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision arms of an FP64 run")
+    ap.add_argument("--no-mixed", action="store_true", help="time the headline arm only (no other arms)")
     ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
     ap.add_argument("--precond", default="lumped", choices=["lumped", "dirichlet"],
                     help="PCGP preconditioner of Sec. 4.2 (every arm)")
     ap.add_argument("--learned", action="store_true",
-                    help="start the timed arm's dual solves from the solver's history (see --history)")
+                    help="with --precision mixed: the learned start (mixed_learned arm)")
     ap.add_argument("--history", type=int, default=8,
                     help="stored dual solutions of the history start in the mixed+learned arm (1..8)")
     ap.add_argument("--no-graphs", action="store_true",
