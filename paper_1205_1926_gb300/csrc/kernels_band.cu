@@ -52,9 +52,15 @@ __device__ __forceinline__ unsigned cluster_size() {
 }
 
 // Cholesky of the jb x jb block D (lower, in shared memory) and its inverse X, all threads.
+// The pivot's square root and reciprocal come from y = 1/sqrt(d) by Newton-Raphson,
+// y <- y (3 - d y^2) / 2, two steps from an FP32 rsqrtf guess (2^-23 -> below FP64
+// rounding): on this part every FP64 instruction of a lone thread occupies the
+// sub-partition's FP64 pipe for a whole warp's worth of cycles, so the library
+// square root and division sequences dominated the column step.  A pivot that is
+// not positive sets bit 1 of err and is replaced by 1.
 __device__ void diag_factor_invert(double* D, double* X, int jb, int* err) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ double s_inv;
+  __shared__ double s_rdiag[kMaxNB];
   for (int c = 0; c < jb; ++c) {
     if (tid == 0) {
       double d = D[c * kNB1 + c];
@@ -62,26 +68,32 @@ __device__ void diag_factor_invert(double* D, double* X, int jb, int* err) {
         atomicOr(err, 1);
         d = 1.0;
       }
-      d = sqrt(d);
-      D[c * kNB1 + c] = d;
-      s_inv = 1.0 / d;
+      double y = (double)rsqrtf((float)d);
+      y = y * (1.5 - 0.5 * d * y * y);
+      y = y * (1.5 - 0.5 * d * y * y);
+      D[c * kNB1 + c] = d * y;
+      s_rdiag[c] = y;
     }
     __syncthreads();
-    const double inv = s_inv;
+    const double inv = s_rdiag[c];
     for (int r = c + 1 + tid; r < jb; r += nt) D[r * kNB1 + c] *= inv;
     __syncthreads();
-    const int m = jb - c - 1;                 // trailing size
-    for (int e = tid; e < m * m; e += nt) {
-      const int r = c + 1 + e / m, q = c + 1 + e % m;
-      if (q <= r) D[r * kNB1 + q] -= D[r * kNB1 + c] * D[q * kNB1 + c];
+    // trailing lower triangle, enumerated densely so that every lane of a warp has an entry
+    const int m = jb - c - 1;
+    for (int e = tid; e < m * (m + 1) / 2; e += nt) {
+      int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (t * (t + 1) / 2 > e) --t;
+      while ((t + 1) * (t + 2) / 2 <= e) ++t;
+      const int r = c + 1 + t, q = c + 1 + (e - t * (t + 1) / 2);
+      D[r * kNB1 + q] -= D[r * kNB1 + c] * D[q * kNB1 + c];
     }
     __syncthreads();
   }
-  // X = L^{-1}: X = I, then for c: X[c][:] /= L[c][c]; X[r][:] -= L[r][c] X[c][:] for r > c
+  // X = L^{-1}: X = I, then for c: X[c][:] *= 1/L[c][c]; X[r][:] -= L[r][c] X[c][:] for r > c
   for (int e = tid; e < jb * jb; e += nt) X[(e / jb) * kNB1 + e % jb] = (e / jb == e % jb) ? 1.0 : 0.0;
   __syncthreads();
   for (int c = 0; c < jb; ++c) {
-    const double inv = 1.0 / D[c * kNB1 + c];
+    const double inv = s_rdiag[c];
     for (int q = tid; q <= c; q += nt) X[c * kNB1 + q] *= inv;
     __syncthreads();
     const int m = jb - c - 1;
