@@ -497,6 +497,134 @@ def run_gpu(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_cases(args, rank, world, local_rank):
+    """Several load cases of one mesh at once (--cases N): N case contexts sharing one base's read-only
+    set-up, each on its own stream; every load step of all cases is one ssn_time_step_cases call (one host
+    thread per case, the GPU overlapping the cases' kernels).  The same cases are then reset and stepped
+    one after another on the same contexts (warm pools and tuning: favours the sequential run), and both
+    are timed with CUDA events spanning all case streams."""
+    import torch
+    import paper_1205_1926_gb300 as T
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = W.WORKLOADS[args.workload]
+    cases = W.direction_cases(args.cases) if args.case_set == "directions" else W.irregular_cases(0, args.cases)
+    arm = resolve_arm(args)
+    n_total = args.warmup + args.steps
+    pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
+    main_stream = torch.cuda.Stream(device=dev)
+    base = T.Context(w, stream=main_stream, precond=pre)
+    streams = [torch.cuda.Stream(device=dev) for _ in cases]
+    ctxs = [T.Context.case_of(base, c["sigma_y"], c["hardening"], stream=st) for c, st in zip(cases, streams)]
+
+    def start(c):
+        if arm != "fp64":
+            c.set_precision(True, args.inner_rtol)
+        if arm == "mixed_history":
+            c.set_recycling(args.history)
+        if arm == "mixed_learned":
+            c.set_recycling(min(args.history, 7))
+            c.set_learned(True)
+
+    for c in ctxs:
+        start(c)
+    n = base.sizes["n_dof"]
+    t_ys = [c.first_yield_traction(cs["traction_dir"], rtol=1e-10) for c, cs in zip(ctxs, cases)]
+    for c in ctxs:
+        start(c)      # the history and the network start over (the first-yield solve must not seed them)
+    dfs = []
+    for c, cs, t_y in zip(ctxs, cases, t_ys):
+        row, prev = [], 0.0
+        for a in w.load_fractions(n_total):
+            d = torch.zeros(n, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            c.traction_load(tuple((a - prev) * t_y * x for x in cs["traction_dir"]), d)
+            row.append(d)
+            prev = a
+        dfs.append(row)
+    zero_u = torch.zeros(n, dtype=torch.float64, device=dev)
+    zero_s = torch.zeros(6 * base.sizes["n_gp"], dtype=torch.float64, device=dev)
+    zero_k = torch.zeros(base.sizes["n_gp"], dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def reset():
+        for c in ctxs:
+            c.set_state(u=zero_u, sigma=zero_s, kappa=zero_k)
+            start(c)
+        torch.cuda.synchronize()
+
+    def timed(concurrent, sampler=None):
+        for k in range(args.warmup):
+            if concurrent:
+                T.time_step_cases(ctxs, [d[k] for d in dfs], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+            else:
+                for c, d in zip(ctxs, dfs):
+                    c.time_step(d[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        torch.cuda.synchronize()
+        for c in ctxs:
+            c.timing_reset(False)
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main_stream)
+        for st in streams:
+            st.wait_event(e0)
+        infos = [[] for _ in cases]
+        for k in range(args.warmup, n_total):
+            if concurrent:
+                out = T.time_step_cases(ctxs, [d[k] for d in dfs], w.newton_tol, w.pcg_rtol, w.newton_maxit,
+                                        w.pcg_maxit)
+            else:
+                out = [c.time_step(d[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+                       for c, d in zip(ctxs, dfs)]
+            for j, o in enumerate(out):
+                infos[j].append(o)
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            main_stream.wait_event(ev)
+        e1.record(main_stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        u = torch.zeros((len(cases), n), dtype=torch.float64, device=dev)
+        launches = sum(c.timing()["kernel_launches"] for c in ctxs)
+        for j, c in enumerate(ctxs):
+            c.get_state(u=u[j])
+        return e0.elapsed_time(e1) / 1e3, infos, u, clocks, launches
+
+    el_c, inf_c, u_c, clocks, launches = timed(True, ClockSampler(local_rank))
+    reset()
+    el_s, inf_s, u_s, _, _ = timed(False)
+    diff = (torch.linalg.vector_norm(u_c - u_s, dim=1) / torch.linalg.vector_norm(u_s, dim=1)).max().item()
+    units = args.steps * len(cases)
+    line = {"metric": f"time per load step per case @1e-8 dual res ({len(cases)} concurrent cases)",
+            "value": el_c / units, "unit": "s/(load_step case)", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_c / args.steps * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if arm == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": workload_config(w, args.steps, args.warmup, args.precond) | {
+                "arm": arm, "arm_note": ARM_NOTES[arm], "cases": len(cases), "case_set": args.case_set,
+                "parallelism": "1 GPU, one stream and host thread per case",
+                "shared": "mesh tables, G, H, shape templates, dual Schur blocks (one copy for all cases)"},
+            "e2e": None, "gpu_launches": int(launches),
+            "roofline": None, "clocks": clocks,
+            "sequential_value": el_s / units, "concurrency_speedup": el_s / el_c,
+            "max_rel_u_diff_concurrent_vs_sequential": diff,
+            "cases": [{"sigma_y": cs["sigma_y"], "hardening": cs["hardening"], "traction_dir": cs["traction_dir"],
+                       "t_y": t_y, "newton_per_step": [s["newton"] for s in inf],
+                       "pcg_per_step": [sum(s["pcg"]) for s in inf],
+                       "plastic_gp_final": inf[-1]["plastic_committed"]}
+                      for cs, t_y, inf in zip(cases, t_ys, inf_c)],
+            "device_bytes": {"base": base.sizes["device_bytes"],
+                             "per_case_at_setup": [c.sizes["device_bytes"] for c in ctxs]}}
+    if rank == 0:
+        print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    base.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -524,6 +652,11 @@ def main():
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
                     help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
+    ap.add_argument("--cases", type=int, default=0,
+                    help="N > 0: N load cases on one mesh stepped concurrently (case contexts), one JSON line")
+    ap.add_argument("--case-set", default="directions", choices=["directions", "seeded"],
+                    help="directions: theta_k = 2 pi k / N, the Sec. 5 material; seeded: sigma_y, H and the "
+                         "direction drawn per case")
     args = ap.parse_args()
     if args.oracle_sample:
         print(json.dumps(oracle_sample(W.WORKLOADS[args.oracle_sample])))
@@ -533,6 +666,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.cases > 0:
+        run_cases(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
 

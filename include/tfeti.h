@@ -140,6 +140,21 @@ typedef struct tfeti_ctx tfeti_ctx;
  * Errors: TFETI_ERR_ARG, TFETI_ERR_OOM, TFETI_ERR_CUDA, TFETI_ERR_SINGULAR,
  * TFETI_ERR_NUMERIC. */
 int tfeti_setup(const tfeti_problem* prob, void* cuda_stream, tfeti_ctx** out);
+
+/* Case context: another load case on the mesh, decomposition and elastic material
+ * (E, nu) of `base`, with its own yield stress sigma_y and hardening modulus H_m
+ * (Sec. 2's material parameters; both > 0).  Everything that depends only on the
+ * mesh, B, R and the elastic stiffness is shared with base, read-only, not copied:
+ * index maps, R, G, the coarse inverse H (and its FP32 copy), the shape templates'
+ * elastic factors and boundary blocks, the Dirichlet templates and the dual Schur
+ * blocks.  The case owns its state (zero at creation), the factors of its plastic
+ * subdomains and its work vectors, and has its own settings (precision, history,
+ * learned start, timing).  base must be a context made by tfeti_setup, must outlive
+ * the case, and must not be modified by another thread while a case context is being
+ * set up or switched to mixed precision.  cuda_stream: the case's stream (nullable: the
+ * context creates and owns a non-blocking stream).
+ * Errors: TFETI_ERR_ARG, TFETI_ERR_OOM, TFETI_ERR_CUDA. */
+int tfeti_setup_case(tfeti_ctx* base, double sigma_y, double hardening, void* cuda_stream, tfeti_ctx** out);
 int tfeti_destroy(tfeti_ctx* ctx);
 int tfeti_sizes_get(const tfeti_ctx* ctx, tfeti_sizes* out);
 const char* tfeti_last_error(const tfeti_ctx* ctx);
@@ -218,6 +233,19 @@ typedef struct tfeti_step_info {
  * Errors: TFETI_ERR_NOT_CONVERGED, and those of the calls above. */
 int ssn_time_step(tfeti_ctx* ctx, const double* df, int32_t df_on_host, double newton_tol,
                   double pcg_rtol, int32_t newton_maxit, int32_t pcg_maxit, tfeti_step_info* info);
+
+/* One time step (Algorithm 4) of n_cases independent cases at once: case k runs
+ * ssn_time_step(ctxs[k], df[k], ...) on a host thread of its own and on its context's
+ * stream, so the GPU overlaps the cases' kernels (the cases' Newton and PCGP iteration
+ * counts differ; each stops on its own test).  ctxs: n_cases distinct contexts, each
+ * with its own stream (e.g. the case contexts of one base, with or without the base);
+ * df[k]: case k's load increment (host if df_on_host, else device [n_dof]); info:
+ * host [n_cases], nullable.  Returns when every case's step has ended: TFETI_OK, or
+ * the first non-OK status in case order (each failed case keeps its state at step k
+ * and its message in tfeti_last_error(ctxs[k])). */
+int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* const* df, int32_t df_on_host,
+                        double newton_tol, double pcg_rtol, int32_t newton_maxit, int32_t pcg_maxit,
+                        tfeti_step_info* info);
 
 /* Arithmetic of the dual solve.  TFETI_PRECISION_FP64 (default): Algorithm 3 in
  * FP64.  TFETI_PRECISION_MIXED: the PCGP of Algorithm 3 runs as FP64 iterative

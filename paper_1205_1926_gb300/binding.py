@@ -75,6 +75,7 @@ SIGNATURES = {
     "tfeti_plan_export_subdomains": (C.c_int, [_P, _P]),
     "tfeti_plan_export_fixing": (C.c_int, [_P, _P]),
     "tfeti_setup": (C.c_int, [C.POINTER(Problem), _P, C.POINTER(_P)]),
+    "tfeti_setup_case": (C.c_int, [_P, _D, _D, _P, C.POINTER(_P)]),
     "tfeti_destroy": (C.c_int, [_P]),
     "tfeti_sizes_get": (C.c_int, [_P, C.POINTER(Sizes)]),
     "tfeti_last_error": (C.c_char_p, [_P]),
@@ -84,6 +85,7 @@ SIGNATURES = {
     "tfeti_assemble_tangent": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_dual_pcg": (C.c_int, [_P, _P, _P, _P, _P, _D, _I, C.POINTER(PcgInfo)]),
     "ssn_time_step": (C.c_int, [_P, _P, _I, _D, _D, _I, _I, C.POINTER(StepInfo)]),
+    "ssn_time_step_cases": (C.c_int, [_P, _I, _P, _I, _D, _D, _I, _I, _P]),
     "tfeti_first_yield_traction": (C.c_int, [_P, _P, _D, C.POINTER(_D)]),
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
@@ -239,6 +241,27 @@ class Context:
         self.lib.tfeti_sizes_get(self.h, C.byref(s))
         self.sizes = {k: getattr(s, k) for k, _ in Sizes._fields_}
 
+    @classmethod
+    def case_of(cls, base: "Context", sigma_y: float, hardening: float, stream=None) -> "Context":
+        """A case context (``tfeti_setup_case``) sharing base's read-only set-up; it keeps
+        a reference to base so that base outlives it."""
+        obj = cls.__new__(cls)
+        obj.lib = base.lib
+        obj.problem = Problem.from_buffer_copy(base.problem)
+        obj.problem.sigma_y = sigma_y
+        obj.problem.hardening = hardening
+        obj._base = base
+        h = _P()
+        st = obj.lib.tfeti_setup_case(base.h, sigma_y, hardening, _ptr_stream(stream), C.byref(h))
+        if st != TFETI_OK:
+            obj.h = None
+            raise TfetiError(st, f"tfeti_setup_case: {base.lib.tfeti_last_error(base.h).decode()}")
+        obj.h = h
+        s = Sizes()
+        obj.lib.tfeti_sizes_get(obj.h, C.byref(s))
+        obj.sizes = {k: getattr(s, k) for k, _ in Sizes._fields_}
+        return obj
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.tfeti_destroy(self.h)
@@ -350,6 +373,23 @@ class Context:
 
     def timing_reset(self, events: bool):
         self.lib.tfeti_timing_reset(self.h, 1 if events else 0)
+
+
+def time_step_cases(ctxs, dfs, newton_tol, pcg_rtol, newton_maxit=30, pcg_maxit=5000, df_on_host=False,
+                    check=True):
+    """``ssn_time_step_cases``: one time step of every context in ``ctxs`` (distinct, each
+    on its own stream), case k with load increment ``dfs[k]``; returns one info dict per case."""
+    n = len(ctxs)
+    lib = load()
+    hs = (_P * n)(*[c.h for c in ctxs])
+    ps = (_P * n)(*[_ptr(d) for d in dfs])
+    infos = (StepInfo * n)()
+    st = lib.ssn_time_step_cases(C.cast(hs, _P), n, C.cast(ps, _P), 1 if df_on_host else 0, newton_tol, pcg_rtol,
+                                 newton_maxit, pcg_maxit, C.cast(infos, _P))
+    if check and st != TFETI_OK:
+        msgs = "; ".join(f"case {k}: {lib.tfeti_last_error(c.h).decode()}" for k, c in enumerate(ctxs))
+        raise TfetiError(st, f"ssn_time_step_cases: {msgs}")
+    return [infos[k].as_dict() | {"status": st} for k in range(n)]
 
 
 def _ptr_stream(stream):

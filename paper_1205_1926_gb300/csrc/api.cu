@@ -8,8 +8,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <map>
 #include <vector>
 
@@ -56,6 +59,84 @@ T* upload(tfeti_ctx* c, const std::vector<T>& v) {
 
 void sync(tfeti_ctx* c) { cudaStreamSynchronize(c->st); }
 
+template <class T>
+void dfree(tfeti_ctx* c, T*& p, size_t n) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), static_cast<void*>(p));
+  if (it != c->allocs.end()) {
+    c->allocs.erase(it);
+    c->bytes -= std::max<size_t>(n, 1) * sizeof(T);
+  }
+  cudaFree(p);
+  p = nullptr;
+}
+
+// Grow an own-record pool from old_n to new_n values, keeping the first old_n.
+template <class T>
+void grow_pool(tfeti_ctx* c, T*& p, long long old_n, long long new_n) {
+  T* q = dalloc<T>(c, (size_t)new_n);
+  if (p && old_n > 0) cudaMemcpyAsync(q, p, sizeof(T) * old_n, cudaMemcpyDeviceToDevice, c->st);
+  sync(c);
+  dfree(c, p, (size_t)old_n);
+  p = q;
+}
+
+// Give every subdomain with plastic points (np[p] > 0) an own-record slot and take the
+// slots of the others back; the pools grow (to at least twice their size, at most one
+// slot per subdomain) when the free slots do not suffice.  Slots are handed out lowest
+// first in subdomain order.  Throws std::bad_alloc when the device is full.
+void update_slots(tfeti_ctx* c, const std::vector<int>& np) {
+  const int ns = (int)np.size();
+  for (int p = 0; p < ns; ++p)
+    if (np[p] == 0 && c->slot_of[p] >= 0) {
+      c->free_slots.push_back(c->slot_of[p]);
+      c->slot_of[p] = -1;
+    }
+  int need = 0;
+  for (int p = 0; p < ns; ++p) need += np[p] > 0 && c->slot_of[p] < 0;
+  if (need > (int)c->free_slots.size()) {
+    const int want = c->slot_cap + need - (int)c->free_slots.size();
+    const int cap = std::min(ns, std::max(want, std::max(8, 2 * c->slot_cap)));
+    // slack of one record after the last slot: whole-record bulk copies may read past it
+    const long long old_n = c->slot_cap ? (long long)(c->slot_cap + 1) * c->slot_size : 0;
+    const long long new_n = (long long)(cap + 1) * c->slot_size;
+    grow_pool(c, c->fac_own, old_n, new_n);
+    grow_pool(c, c->fac32_own, old_n, new_n);
+    if (c->dirichlet) {
+      grow_pool(c, c->dfac_own, old_n, new_n);
+      grow_pool(c, c->dfac32_own, old_n, new_n);
+    }
+    for (int k = c->slot_cap; k < cap; ++k) c->free_slots.push_back(k);
+    c->slot_cap = cap;
+  }
+  std::sort(c->free_slots.begin(), c->free_slots.end(), std::greater<int>());
+  for (int p = 0; p < ns; ++p)
+    if (np[p] > 0 && c->slot_of[p] < 0) {
+      c->slot_of[p] = c->free_slots.back();
+      c->free_slots.pop_back();
+    }
+}
+
+long long own_off(const tfeti_ctx* c, int p) { return (long long)c->slot_of[p] * c->slot_size; }
+
+// Band workspaces for factorising the subdomains of `list`: offsets (16-byte aligned)
+// into band_ws, which grows (without keeping its contents) when it is too small.
+std::vector<long long> band_workspace(tfeti_ctx* c, const std::vector<int>& list) {
+  std::vector<long long> offs;
+  long long tot = 0;
+  for (int p : list) {
+    offs.push_back(tot);
+    tot += ((long long)c->h_subs[p].n_dof * (c->h_subs[p].bw + 1) + 3) & ~3LL;
+  }
+  if (tot > c->band_ws_cap) {
+    sync(c);
+    dfree(c, c->band_ws, (size_t)c->band_ws_cap);
+    c->band_ws_cap = std::max(tot, c->band_ws_cap + c->band_ws_cap / 2);
+    c->band_ws = dalloc<double>(c, (size_t)c->band_ws_cap);
+  }
+  return offs;
+}
+
 double dot_host(tfeti_ctx* c, const double* x, const double* y, long long n) {
   launch_dot(x, y, n, c->partial, c->sc + 8, c->st);
   c->launches += 2;
@@ -99,7 +180,7 @@ void build_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R,
   for (int p = 0; p < ns; ++p)
     if (plastic_count[p] > 0) {
       SolveItem it{};
-      it.fac = c->own_fac_base + c->plan.subs[p].fac_off;
+      it.fac = kOwnFac | own_off(c, p);
       it.count = 1;
       it.sub[0] = p;
       items.push_back(it);
@@ -128,7 +209,7 @@ void build_dir_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, in
   for (int p = 0; p < ns; ++p)
     if (plastic_count[p] > 0) {
       SolveItem it{};
-      it.fac = c->dfac_own_base + c->plan.subs[p].fac_off;
+      it.fac = kOwnFac | own_off(c, p);
       it.count = 1;
       it.sub[0] = p;
       items.push_back(it);
@@ -164,9 +245,9 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   // subdomains of shapes without a Schur block in use
   std::vector<SolveItem> pl, pl64;
   for (const SolveItem& it : c->h_items32)
-    if (it.fac >= c->own_fac_base || !uses_schur(c->h_subs[it.sub[0]].shape)) pl.push_back(it);
+    if ((it.fac & kOwnFac) || !uses_schur(c->h_subs[it.sub[0]].shape)) pl.push_back(it);
   for (const SolveItem& it : c->h_items)
-    if (it.fac >= c->own_fac_base || !uses_schur(c->h_subs[it.sub[0]].shape)) pl64.push_back(it);
+    if ((it.fac & kOwnFac) || !uses_schur(c->h_subs[it.sub[0]].shape)) pl64.push_back(it);
   c->n_items_pl = (int)pl.size();
   c->n_items_pl64 = (int)pl64.size();
   if (!pl64.empty())
@@ -198,6 +279,8 @@ SolveArgs solve_args(tfeti_ctx* c, bool fp32 = false) {
   SolveArgs a{};
   a.fac = c->fac;
   a.fac32 = c->fac32;
+  a.fac_own = c->fac_own;
+  a.fac32_own = c->fac32_own;
   a.fp32 = fp32 ? 1 : 0;
   a.items = fp32 ? c->d_items32 : c->d_items;
   a.n_items = fp32 ? c->n_items32 : c->n_items;
@@ -351,6 +434,33 @@ int form_schur_blocks(tfeti_ctx* c) {
 // The shapes' dual Schur blocks in FP32 (tensor-core tiles) and FP64, formed once.
 int ensure_schur(tfeti_ctx* c) {
   if (c->schur_ready) return TFETI_OK;
+  if (c->base) {
+    // the Schur blocks depend only on the shapes' elastic templates: share the base's
+    int st = ensure_schur(c->base);
+    if (st != TFETI_OK) return fail(c, st, c->base->err);
+    tfeti_ctx* b = c->base;
+    c->schur_formed = b->schur_formed;
+    c->s_off_c = b->s_off_c;
+    c->s_tile_off = b->s_tile_off;
+    c->S32 = b->S32;
+    c->S64 = b->S64;
+    c->Shi = b->Shi;
+    c->Slo = b->Slo;
+    int max_bd = 0;
+    for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh)
+      if (c->schur_formed[sh]) max_bd = std::max(max_bd, 3 * c->plan.shapes[sh].n_bnd);
+    try {
+      const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
+      c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+      c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+      c->X64 = dalloc<double>(c, (size_t)c->h_subs.size() * (size_t)std::max(1, max_bd));
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+    c->schur_use = c->schur_formed;
+    c->schur_ready = true;
+    return TFETI_OK;
+  }
   const size_t nsh = c->plan.shapes.size();
   std::vector<int> count(nsh, 0);
   for (const SubDev& sd : c->h_subs) ++count[sd.shape];
@@ -454,6 +564,8 @@ void op_precond_dirichlet(tfeti_ctx* c, const double* w, double* out, bool fp32)
   SolveArgs a = solve_args(c, fp32);
   a.fac = c->dfac;
   a.fac32 = c->dfac32;
+  a.fac_own = c->dfac_own;
+  a.fac32_own = c->dfac32_own;
   a.items = fp32 ? c->d_items_d32 : c->d_items_d;
   a.n_items = fp32 ? c->n_items_d32 : c->n_items_d;
   a.src = c->dx_b;
@@ -523,12 +635,18 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
   sync(c);
   std::vector<int> list;
   std::vector<long long> offs, facs, kbbs;
+  try {
+    update_slots(c, np);
+    for (int p = 0; p < M.n_sub; ++p)
+      if (np[p] > 0) list.push_back(p);
+    offs = band_workspace(c, list);
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed (own factor records)");
+  }
   for (int p = 0; p < M.n_sub; ++p) {
     const SubDev& S = c->h_subs[p];
     if (np[p] > 0) {
-      list.push_back(p);
-      offs.push_back(c->own_base + S.band_off);
-      facs.push_back(c->own_fac_base + c->plan.subs[p].fac_off);
+      facs.push_back(own_off(c, p));
       kbbs.push_back(c->own_kbb_base + c->plan.subs[p].kbb_off);
       c->h_kbb_off[p] = kbbs.back();
     } else {
@@ -545,13 +663,13 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     cudaMemcpyAsync(c->d_list_kbb, kbbs.data(), sizeof(long long) * kbbs.size(), cudaMemcpyHostToDevice, c->st);
     int max_rows = 0;
     for (int p : list) max_rows = std::max(max_rows, c->h_subs[p].n_dof);
-    launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band, c->d_list_off, 0, max_rows,
+    launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band_ws, c->d_list_off, 0, max_rows,
                      c->plan.max_bw, c->st);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
     cudaEvent_t e0 = c->events ? c->fac_e0 : nullptr, e1 = c->events ? c->fac_e1 : nullptr;
     if (e0) cudaEventRecord(e0, c->st);
-    launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_list_fac, c->fac, c->d_err,
-                     c->plan.max_bw, c->n_sm, c->st);
+    launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band_ws, c->d_list_fac, c->fac_own,
+                     c->d_err, c->plan.max_bw, c->n_sm, c->st);
     if (e1) cudaEventRecord(e1, c->st);
     c->launches += 2;
     c->factor_launches += 1;
@@ -567,33 +685,28 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     if (c->precision == TFETI_PRECISION_MIXED) {
       long long len = 0;
       for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
-      launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)list.size(), len, c->st);
+      launch_fac_to_f32(c->fac_own, c->fac32_own, c->d_list_fac, (int)list.size(), len, c->st);
       c->launches += 1;
     }
     if (c->dirichlet) {
-      // K_ii factors of the plastic subdomains, on the same band workspaces
-      std::vector<long long> dfacs;
-      for (int p : list) dfacs.push_back(c->dfac_own_base + c->plan.subs[p].fac_off);
-      cudaMemcpyAsync(c->d_list_fac, dfacs.data(), sizeof(long long) * dfacs.size(), cudaMemcpyHostToDevice, c->st);
-      launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band, c->d_list_off, 0, max_rows,
+      // K_ii factors of the plastic subdomains (same slots), on the same band workspaces
+      launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band_ws, c->d_list_off, 0, max_rows,
                        c->plan.max_bw, c->st, c->d_bmask);
       cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-      launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band, c->d_list_fac, c->dfac, c->d_err,
-                       c->plan.max_bw, c->n_sm, c->st);
+      launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band_ws, c->d_list_fac, c->dfac_own,
+                       c->d_err, c->plan.max_bw, c->n_sm, c->st);
       c->launches += 2;
       c->factor_launches += 1;
       if (c->precision == TFETI_PRECISION_MIXED) {
         long long len = 0;
         for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
-        launch_fac_to_f32(c->dfac, c->dfac32, c->d_list_fac, (int)list.size(), len, c->st);
+        launch_fac_to_f32(c->dfac_own, c->dfac32_own, c->d_list_fac, (int)list.size(), len, c->st);
         c->launches += 1;
       }
       int derr = 0;
       cudaMemcpyAsync(&derr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
       sync(c);
       if (derr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a Dirichlet-preconditioner factorisation");
-      // the K^+ factor list for kbb fill and later use
-      cudaMemcpyAsync(c->d_list_fac, facs.data(), sizeof(long long) * facs.size(), cudaMemcpyHostToDevice, c->st);
     }
   }
   if (!list.empty())
@@ -1117,7 +1230,11 @@ void fill_sizes(const tfeti_ctx* c, tfeti_sizes* out) {
   out->device_bytes = (int64_t)c->bytes;
 }
 
-int setup_impl(tfeti_ctx* c) {
+// Set-up of a context.  With `base` (a case context, tfeti_setup_case) the read-only
+// device set-up is taken from base instead of being built: subdomain descriptors, index
+// maps, R, G, the coarse inverse H, the shape templates' factors and boundary blocks and
+// the Dirichlet templates; everything the case writes is its own.
+int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   Plan& P = c->plan;
   const int ns = (int)P.subs.size();
   c->l = 6LL * ns;
@@ -1151,6 +1268,14 @@ int setup_impl(tfeti_ctx* c) {
     c->h_subs[p] = d;
     c->max_copy = std::max(c->max_copy, s.n_copy);
   }
+  DevMesh& M = c->M;
+  const tfeti_problem& pr = P.prob;
+  if (base) {
+    c->d_subs = base->d_subs;
+    M = base->M;
+    M.sigma_y = pr.sigma_y;
+    M.H = pr.hardening;
+  } else {
   c->d_subs = upload(c, c->h_subs);
   std::vector<GroupDev> gd(P.groups.size());
   for (size_t g = 0; g < P.groups.size(); ++g) {
@@ -1172,7 +1297,6 @@ int setup_impl(tfeti_ctx* c) {
   std::vector<double> helm(64, 0.0);
   for (int r = 1; r < 8; ++r)
     for (int j = 0; j <= r; ++j) helm[r * 8 + j] = helmert_coef(r, j);
-  DevMesh& M = c->M;
   M.subs = c->d_subs;
   M.n_sub = ns;
   M.groups = upload(c, gd);
@@ -1197,7 +1321,6 @@ int setup_impl(tfeti_ctx* c) {
   M.Kel = Kel;
   M.Q = Q;
   M.R = R;
-  const tfeti_problem& pr = P.prob;
   const double lam = pr.young * pr.poisson / ((1.0 + pr.poisson) * (1.0 - 2.0 * pr.poisson));
   const double mu = pr.young / (2.0 * (1.0 + pr.poisson));
   M.lam = lam;
@@ -1271,6 +1394,7 @@ int setup_impl(tfeti_ctx* c) {
     c->launches += 1;
     sync(c);
   }
+  }   // shared tables
   // state and iterate buffers
   c->u = dalloc<double>(c, P.n_dof);
   c->sig = dalloc<double>(c, 6 * P.n_gp);
@@ -1286,13 +1410,19 @@ int setup_impl(tfeti_ctx* c) {
   c->elem_np = dalloc<int>(c, P.n_elem);
   c->sub_np = dalloc<int>(c, ns);
   c->dKe = dalloc<double>(c, (size_t)P.n_elem * kTri24);
-  c->band = dalloc<double>(c, P.template_band_total + P.band_total);
-  c->own_base = P.template_band_total;
   long long max_fac = 0;
   for (const SubInfo& s : P.subs) max_fac = std::max<long long>(max_fac, s.fac_size);
-  c->fac = dalloc<double>(c, P.template_fac_total + P.fac_total + max_fac);   // slack for whole-record copies
-  c->fac32 = dalloc<float>(c, P.template_fac_total + P.fac_total + max_fac);
-  c->own_fac_base = P.template_fac_total;
+  c->slot_size = (max_fac + 3) & ~3LL;
+  c->slot_of.assign(ns, -1);
+  if (base) {
+    c->band = base->band;
+    c->fac = base->fac;
+    c->fac32 = base->fac32;
+  } else {
+    c->band = dalloc<double>(c, P.template_band_total);
+    c->fac = dalloc<double>(c, P.template_fac_total + max_fac);   // slack for whole-record copies
+    c->fac32 = dalloc<float>(c, P.template_fac_total + max_fac);
+  }
   c->d_items = dalloc<SolveItem>(c, ns);
   c->d_items32 = dalloc<SolveItem>(c, ns);
   c->d_items_pl = dalloc<SolveItem>(c, ns);
@@ -1325,6 +1455,8 @@ int setup_impl(tfeti_ctx* c) {
   }
   c->kbb = dalloc<double>(c, P.kbb_template_total + P.kbb_total);
   c->own_kbb_base = P.kbb_template_total;
+  if (base)
+    cudaMemcpyAsync(c->kbb, base->kbb, sizeof(double) * P.kbb_template_total, cudaMemcpyDeviceToDevice, c->st);
   c->d_kbb_off = dalloc<long long>(c, ns);
   c->h_kbb_off.assign(ns, 0);
   c->d_list_kbb = dalloc<long long>(c, ns);
@@ -1335,7 +1467,7 @@ int setup_impl(tfeti_ctx* c) {
                      &c->rin})
     *v = dalloc<double>(c, m);
   c->vsol = dalloc<double>(c, (size_t)P.n_dof);
-  c->H = dalloc<double>(c, (size_t)c->l * c->l);
+  if (!base) c->H = dalloc<double>(c, (size_t)c->l * c->l);
   c->gx = dalloc<double>(c, c->l);
   c->hx = dalloc<double>(c, c->l);
   c->ev = dalloc<double>(c, c->l);
@@ -1353,7 +1485,9 @@ int setup_impl(tfeti_ctx* c) {
   cudaMemsetAsync(c->elem_np, 0, sizeof(int) * P.n_elem, c->st);
   cudaMemsetAsync(c->sc, 0, sizeof(double) * kNumScalars, c->st);
   // coarse problem: G G^T assembled once and inverted (G depends only on B and R)
-  {
+  if (base) {
+    c->H = base->H;
+  } else {
     int* pp = upload(c, P.pair_p);
     int* pq = upload(c, P.pair_q);
     long long* ps = upload(c, std::vector<long long>(P.pair_start.begin(), P.pair_start.end()));
@@ -1375,7 +1509,20 @@ int setup_impl(tfeti_ctx* c) {
     if (herr) return fail(c, TFETI_ERR_SINGULAR, "coarse matrix G G^T is not positive definite");
   }
   // Dirichlet preconditioner: constrained-dof mask, template classes, factor pools
-  if (P.prob.precond == TFETI_PRECOND_DIRICHLET) {
+  if (P.prob.precond == TFETI_PRECOND_DIRICHLET && base) {
+    c->dirichlet = true;
+    c->d_bmask = base->d_bmask;
+    c->dclass = base->dclass;
+    c->dclass_rep = base->dclass_rep;
+    c->dtmpl_off = base->dtmpl_off;
+    c->dfac = base->dfac;
+    c->dfac32 = base->dfac32;
+    c->d_items_d = dalloc<SolveItem>(c, ns);
+    c->d_items_d32 = dalloc<SolveItem>(c, ns);
+    c->dx_a = dalloc<double>(c, P.n_dof);
+    c->dx_b = dalloc<double>(c, P.n_dof);
+    c->dx_c = dalloc<double>(c, P.n_dof);
+  } else if (P.prob.precond == TFETI_PRECOND_DIRICHLET) {
     c->dirichlet = true;
     std::vector<uint8_t> mask(P.n_dof, 0);
     for (long long sl = 0; sl < P.n_copy; ++sl) mask[P.subs[P.slot_sub[sl]].dof_off + P.slot_ldof[sl]] = 1;
@@ -1391,36 +1538,34 @@ int setup_impl(tfeti_ctx* c) {
         it = classes.emplace(std::make_pair(sb.shape, std::move(key)), (int)c->dclass_rep.size()).first;
         c->dclass_rep.push_back(p);
         c->dtmpl_off.push_back(tmpl);
-        tmpl += sb.fac_size;
+        tmpl += (sb.fac_size + 3) & ~3LL;     // 16-byte aligned records (bulk copies)
       }
       c->dclass[p] = it->second;
     }
     long long max_fac = 0;
     for (const SubInfo& sb : P.subs) max_fac = std::max<long long>(max_fac, sb.fac_size);
-    c->dfac_own_base = tmpl;
-    c->dfac = dalloc<double>(c, tmpl + P.fac_total + max_fac);
-    c->dfac32 = dalloc<float>(c, tmpl + P.fac_total + max_fac);
+    c->dfac = dalloc<double>(c, tmpl + max_fac);
+    c->dfac32 = dalloc<float>(c, tmpl + max_fac);
     c->d_items_d = dalloc<SolveItem>(c, ns);
     c->d_items_d32 = dalloc<SolveItem>(c, ns);
     c->dx_a = dalloc<double>(c, P.n_dof);
     c->dx_b = dalloc<double>(c, P.n_dof);
     c->dx_c = dalloc<double>(c, P.n_dof);
     // template factors on the representatives' own band workspaces (unused at set-up)
-    std::vector<long long> boffs, foffs;
+    std::vector<long long> boffs = band_workspace(c, c->dclass_rep), foffs;
     int max_rows = 0;
     for (size_t k = 0; k < c->dclass_rep.size(); ++k) {
       const int rp = c->dclass_rep[k];
-      boffs.push_back(c->own_base + P.subs[rp].band_off);
       foffs.push_back(c->dtmpl_off[k]);
       max_rows = std::max(max_rows, P.subs[rp].n_dof);
     }
     int* dl = upload(c, c->dclass_rep);
     long long* dbo = upload(c, boffs);
     long long* dfo = upload(c, foffs);
-    launch_band_fill(M, dl, (int)boffs.size(), c->elem_np, c->dKe, c->band, dbo, 1, max_rows, P.max_bw, c->st,
+    launch_band_fill(M, dl, (int)boffs.size(), c->elem_np, c->dKe, c->band_ws, dbo, 1, max_rows, P.max_bw, c->st,
                      c->d_bmask);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    launch_band_chol(M, dl, (int)boffs.size(), dbo, c->band, dfo, c->dfac, c->d_err, P.max_bw, c->n_sm, c->st);
+    launch_band_chol(M, dl, (int)boffs.size(), dbo, c->band_ws, dfo, c->dfac, c->d_err, P.max_bw, c->n_sm, c->st);
     int herr = 0;
     cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     sync(c);
@@ -1443,6 +1588,7 @@ int setup_impl(tfeti_ctx* c) {
       c->tmpl_fac_off.push_back(P.shapes[s].fac_off);
       max_rows = std::max(max_rows, P.shapes[s].n_dof);
     }
+    if (!base) {
     int* dl = upload(c, reps);
     long long* dof = upload(c, offs);
     long long* dfac = upload(c, facs);
@@ -1461,6 +1607,9 @@ int setup_impl(tfeti_ctx* c) {
     for (const ShapeInfo& sh : P.shapes) kt.push_back(sh.kbb_off);
     long long* dkt = upload(c, kt);
     launch_kbb_fill(M, dl, dkt, (int)reps.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb, nullptr, 1, c->st);
+    } else {
+      build_items(c, std::vector<int>(ns, 0));
+    }
     for (int p = 0; p < ns; ++p) c->h_kbb_off[p] = P.shapes[c->h_subs[p].shape].kbb_off;
     cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
   }
@@ -1525,6 +1674,76 @@ int tfeti_setup(const tfeti_problem* prob, void* cuda_stream, tfeti_ctx** out) {
   return TFETI_OK;
 }
 
+int tfeti_setup_case(tfeti_ctx* base, double sigma_y, double hardening, void* cuda_stream, tfeti_ctx** out) {
+  if (!out) return TFETI_ERR_ARG;
+  *out = nullptr;
+  if (!base || base->base) return TFETI_ERR_ARG;
+  if (!(sigma_y > 0.0) || !(hardening > 0.0)) return fail(base, TFETI_ERR_ARG, "case: sigma_y and H must be > 0");
+  tfeti_ctx* c = new (std::nothrow) tfeti_ctx();
+  if (!c) return TFETI_ERR_OOM;
+  c->base = base;
+  if (cuda_stream) {
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+  } else if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) == cudaSuccess) {
+    c->owns_stream = true;
+  } else {
+    delete c;
+    cudaGetLastError();
+    return TFETI_ERR_CUDA;
+  }
+  int st = TFETI_OK;
+  try {
+    c->plan = base->plan;
+    c->plan.prob.sigma_y = sigma_y;
+    c->plan.prob.hardening = hardening;
+    for (int a = 0; a < 3; ++a) c->plan.prob.cuts[a] = nullptr;   // already applied in the plan
+    sync(base);
+    st = setup_impl(c, base);
+  } catch (const std::bad_alloc&) {
+    st = fail(c, TFETI_ERR_OOM, "device allocation failed");
+  }
+  if (st != TFETI_OK) {
+    tfeti_destroy(c);
+    return st;
+  }
+  *out = c;
+  return TFETI_OK;
+}
+
+int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* const* df, int32_t df_on_host,
+                        double newton_tol, double pcg_rtol, int32_t newton_maxit, int32_t pcg_maxit,
+                        tfeti_step_info* info) {
+  if (!ctxs || !df || n_cases < 1) return TFETI_ERR_ARG;
+  for (int k = 0; k < n_cases; ++k) {
+    if (!ctxs[k] || !df[k]) return TFETI_ERR_ARG;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(ctxs[k], TFETI_ERR_ARG, "ssn_time_step_cases: a context appears twice");
+  }
+  std::vector<int> status(n_cases, TFETI_OK);
+  auto run = [&](int k) {
+    try {
+      status[k] = ssn_time_step(ctxs[k], df[k], df_on_host, newton_tol, pcg_rtol, newton_maxit, pcg_maxit,
+                                info ? info + k : nullptr);
+    } catch (const std::bad_alloc&) {
+      status[k] = fail(ctxs[k], TFETI_ERR_OOM, "host allocation failed");
+    } catch (...) {
+      status[k] = fail(ctxs[k], TFETI_ERR_ARG, "unexpected exception");
+    }
+  };
+  std::vector<std::thread> threads;
+  try {
+    for (int k = 1; k < n_cases; ++k) threads.emplace_back(run, k);
+  } catch (const std::system_error&) {
+    for (std::thread& t : threads) t.join();
+    return fail(ctxs[0], TFETI_ERR_ARG, "ssn_time_step_cases: could not start a host thread");
+  }
+  run(0);
+  for (std::thread& t : threads) t.join();
+  for (int k = 0; k < n_cases; ++k)
+    if (status[k] != TFETI_OK) return status[k];
+  return TFETI_OK;
+}
+
 int tfeti_destroy(tfeti_ctx* c) {
   if (!c) return TFETI_OK;
   if (c->st) cudaStreamSynchronize(c->st);
@@ -1539,6 +1758,7 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st_cap) cudaStreamDestroy(c->st_cap);
   if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->owns_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
   return TFETI_OK;
 }
@@ -1666,23 +1886,23 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     std::vector<long long> offs;
     long long len = 0;
     for (const SolveItem& it : c->h_items)
-      if (it.fac >= c->own_fac_base) {
-        offs.push_back(it.fac);
+      if (it.fac & kOwnFac) {
+        offs.push_back(it.fac & ~kOwnFac);
         len = std::max<long long>(len, c->plan.subs[it.sub[0]].fac_size);
       }
     if (!offs.empty()) {
       cudaMemcpyAsync(c->d_list_fac, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
-      launch_fac_to_f32(c->fac, c->fac32, c->d_list_fac, (int)offs.size(), len, c->st);
+      launch_fac_to_f32(c->fac_own, c->fac32_own, c->d_list_fac, (int)offs.size(), len, c->st);
       sync(c);
     }
     if (c->dirichlet) {
       std::vector<long long> doffs;
       for (const SolveItem& it : c->h_items_d)
-        if (it.fac >= c->dfac_own_base) doffs.push_back(it.fac);
+        if (it.fac & kOwnFac) doffs.push_back(it.fac & ~kOwnFac);
       if (!doffs.empty()) {
         cudaMemcpyAsync(c->d_list_fac, doffs.data(), sizeof(long long) * doffs.size(), cudaMemcpyHostToDevice,
                         c->st);
-        launch_fac_to_f32(c->dfac, c->dfac32, c->d_list_fac, (int)doffs.size(), len, c->st);
+        launch_fac_to_f32(c->dfac_own, c->dfac32_own, c->d_list_fac, (int)doffs.size(), len, c->st);
         sync(c);
       }
     }
@@ -1693,13 +1913,19 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   if (mode == TFETI_PRECISION_MIXED && !c->H32) {
     // FP32 copies of H and the boundary blocks for the inner projector and preconditioner
     // (the FP32 values of G are formed at set-up)
+    // (a case context shares the base's FP32 H, formed here if the base has none)
+    tfeti_ctx* hown = c->base ? c->base : c;
     try {
-      c->H32 = dalloc<float>(c, (size_t)c->l * c->l);
+      if (!hown->H32) {
+        hown->H32 = dalloc<float>(hown, (size_t)c->l * c->l);
+        launch_to_f32(c->H, hown->H32, (long long)c->l * c->l, c->st);
+        sync(c);
+      }
+      c->H32 = hown->H32;
       c->kbb32 = dalloc<float>(c, c->plan.kbb_template_total + c->plan.kbb_total);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
-    launch_to_f32(c->H, c->H32, (long long)c->l * c->l, c->st);
     launch_to_f32(c->kbb, c->kbb32, c->plan.kbb_template_total + c->plan.kbb_total, c->st);
     c->launches += 2;
   }

@@ -13,6 +13,9 @@ struct tfeti_ctx {
   // all members are owned by the context and released by tfeti_destroy
   tfeti::Plan plan;
   cudaStream_t st = nullptr;
+  bool owns_stream = false;          // st was created by the context (case contexts without a stream)
+  // case context (tfeti_setup_case): the context whose read-only set-up this one shares
+  tfeti_ctx* base = nullptr;
   std::string err;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -28,11 +31,23 @@ struct tfeti_ctx {
   uint8_t* plastic = nullptr;
   int *elem_np = nullptr, *sub_np = nullptr;
   double* dKe = nullptr;
-  double* band = nullptr;            // template pool followed by the per-subdomain pool
-  long long own_base = 0;            // offset of the per-subdomain pool
+  double* band = nullptr;            // band matrices of the shape templates
   std::vector<long long> tmpl_off;   // per shape
-  double* fac = nullptr;             // factor records: template pool followed by the per-subdomain pool
+  double* fac = nullptr;             // factor records of the shape templates
   float* fac32 = nullptr;            // the same records rounded to FP32 (mixed-precision inner solves)
+  // factor records of the subdomains with plastic points: one slot each (slot_size
+  // values, the largest record), taken when a subdomain first has plastic points and
+  // given back when it is elastic again; the pools grow on demand and keep their
+  // records.  The Dirichlet K_ii factors use the same slot numbers in their own pools.
+  double* fac_own = nullptr;
+  float* fac32_own = nullptr;
+  double* dfac_own = nullptr;
+  float* dfac32_own = nullptr;
+  long long slot_size = 0;
+  int slot_cap = 0;
+  std::vector<int> slot_of, free_slots;
+  double* band_ws = nullptr;         // band workspace of the refactorisations (grows on demand)
+  long long band_ws_cap = 0;
   std::vector<tfeti::SolveItem> h_items32;
   tfeti::SolveItem* d_items32 = nullptr;
   int n_items32 = 0;
@@ -79,7 +94,6 @@ struct tfeti_ctx {
   int g_body_kernels = 0;
   bool use_graphs = true;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  long long own_fac_base = 0;
   std::vector<long long> tmpl_fac_off;   // per shape
   tfeti::SolveItem* d_items = nullptr;   // solve work items (device), rebuilt after each assembly
   std::vector<tfeti::SolveItem> h_items;
@@ -107,7 +121,6 @@ struct tfeti_ctx {
   uint8_t* d_bmask = nullptr;               // 1 at the local dofs of constrained nodes, [n_dof]
   std::vector<int> dclass, dclass_rep;      // class of each subdomain; a representative of each class
   std::vector<long long> dtmpl_off;         // per class: offset of its factor in dfac
-  long long dfac_own_base = 0;
   double* dfac = nullptr;
   float* dfac32 = nullptr;
   std::vector<tfeti::SolveItem> h_items_d, h_items_d32;

@@ -26,6 +26,9 @@ constexpr int kSchurMinCount = 4;   // shapes with fewer subdomains never form t
 // One CTA of the subdomain solve: up to kMaxRHS subdomains of one shape that
 // share the factor record at `fac` (the elastic template) or a single
 // subdomain with its own factor.
+// A work item's factor record: an offset into the shape-template pool, or, with the
+// kOwnFac bit set, into the pool of records of subdomains with plastic points.
+constexpr long long kOwnFac = 1LL << 62;
 struct SolveItem {
   long long fac;
   int count;
@@ -130,6 +133,8 @@ struct SolveArgs {
   const double* alpha;
   const double* fac;           // factor pool (FP64)
   const float* fac32;          // the same records rounded to FP32 (used when fp32 != 0)
+  const double* fac_own;       // records of subdomains with plastic points (items with kOwnFac)
+  const float* fac32_own;
   int fp32;                    // 1: FP32 arithmetic (inner solves of the mixed-precision PCGP)
   const SolveItem* items;
   int n_items;
@@ -150,6 +155,8 @@ struct SolveArgs {
   const uint8_t* bmask;
   int no_fix;
 };
+int smem_optin_max();
+int dyn_smem_limit(const void* fn);
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st);
 size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes);
 // FP64 dual Schur block applied to the elastic subdomains of one shape: X[k][i] =

@@ -219,7 +219,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   T* pan[2] = {sm, sm + a.rec_max};
   T* vec = sm + 2 * a.rec_max;                   // [rcap][npad]
   uint64_t* bar = reinterpret_cast<uint64_t*>(vec + ((a.rcap * npad + 1) & ~1));
-  const T* fac = (sizeof(T) == 8 ? reinterpret_cast<const T*>(a.fac) : reinterpret_cast<const T*>(a.fac32)) + item.fac;
+  const bool own = (item.fac & kOwnFac) != 0;
+  const T* fac = (sizeof(T) == 8 ? reinterpret_cast<const T*>(own ? a.fac_own : a.fac)
+                                 : reinterpret_cast<const T*>(own ? a.fac32_own : a.fac32)) +
+                 (item.fac & ~kOwnFac);
   const T* dinv = fac + (long long)nblk * rec;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nsteps = 2 * nblk;
@@ -436,12 +439,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
 
 }  // namespace
 
+// The device's opt-in shared-memory limit per block.  Kernels whose dynamic shared memory
+// depends on the problem get the largest allowed size as their attribute (not the launch's
+// own size), so that launches of different contexts from several host threads cannot
+// undercut each other.
+int smem_optin_max() {
+  static const int v = [] {
+    int dev = 0, m = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return m;
+  }();
+  return v;
+}
+
+// Largest dynamic shared memory a kernel may be given: the opt-in limit less its static
+// shared memory (the two together must not exceed the limit).
+int dyn_smem_limit(const void* fn) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 48 * 1024;
+  }
+  return smem_optin_max() - (int)fa.sharedSizeBytes;
+}
+
 void launch_band_chol(const DevMesh& M, const int* sub_list, int n_list, const long long* band_off_list,
                       double* band, const long long* fac_off_list, double* fac, int* err, int max_bw,
                       int n_sm, cudaStream_t st) {
   if (n_list <= 0) return;
   const size_t smem = sizeof(double) * (2 * kMaxNB * kNB1 + (size_t)max_bw * kNB1);
-  cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const int lim = dyn_smem_limit((const void*)k_band_chol);
+  cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   const bool big = cudaFuncSetAttribute(k_band_chol, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
                    cudaSuccess;
   cudaGetLastError();
@@ -483,10 +512,12 @@ size_t sub_solve_smem(int rec_max, int npad, int rcap, int elem_bytes) {
 void launch_sub_solve(const DevMesh& M, const SolveArgs& a, size_t smem_bytes, cudaStream_t st) {
   if (a.n_items <= 0) return;
   if (a.fp32) {
-    cudaFuncSetAttribute(k_sub_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    static const int lim = dyn_smem_limit((const void*)k_sub_solve<float>);
+    cudaFuncSetAttribute(k_sub_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     k_sub_solve<float><<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
   } else {
-    cudaFuncSetAttribute(k_sub_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    static const int lim = dyn_smem_limit((const void*)k_sub_solve<double>);
+    cudaFuncSetAttribute(k_sub_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     k_sub_solve<double><<<a.n_items, kThreads, smem_bytes, st>>>(M, a);
   }
 }

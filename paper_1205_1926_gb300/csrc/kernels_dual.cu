@@ -562,7 +562,8 @@ void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, 
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
                    cudaStream_t st, int max_copy) {
   const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
-  cudaFuncSetAttribute(k_lumped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const int lim = dyn_smem_limit((const void*)k_lumped<double>);
+  cudaFuncSetAttribute(k_lumped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   k_lumped<double><<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
 }
 
@@ -577,7 +578,8 @@ void launch_slots_diff(const DevMesh& M, const double* v, const double* t, doubl
 void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
                      cudaStream_t st, int max_copy) {
   const size_t smem = sizeof(float) * (size_t)(max_copy > 0 ? max_copy : 1);
-  cudaFuncSetAttribute(k_lumped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const int lim = dyn_smem_limit((const void*)k_lumped<float>);
+  cudaFuncSetAttribute(k_lumped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   k_lumped<float><<<M.n_sub, 256, smem, st>>>(M, w, kbb32, kbb_off, cbuf);
 }
 

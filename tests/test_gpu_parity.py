@@ -705,3 +705,90 @@ def test_cube64_history_matches_oracle_record():
         ctx.get_state(u=u)
         un = np.linalg.norm(host(u))
         assert abs(un - ref["u_norm"]) <= 1e-7 * ref["u_norm"]
+
+
+# ---- case contexts: several load cases on one mesh, stepped concurrently ---------------------------
+
+def case_run(w, cases, n_steps, mixed=False, history=0):
+    """Cases on case contexts of one base, each step of all cases by one concurrent call;
+    returns the contexts and u per case per step."""
+    base = T.Context(w)
+    ctxs = [T.Context.case_of(base, c["sigma_y"], c["hardening"]) for c in cases]
+    for cx in ctxs:
+        if mixed:
+            cx.set_precision(True, 1e-3)
+        if history:
+            cx.set_recycling(history)
+    t_ys = [cx.first_yield_traction(c["traction_dir"]) for cx, c in zip(ctxs, cases)]
+    n = base.sizes["n_dof"]
+    dfs = [zeros(n) for _ in cases]
+    u = zeros(n)
+    torch.cuda.synchronize()
+    us, infos = [[] for _ in cases], []
+    prev = 0.0
+    for a in w.load_fractions(n_steps):
+        for cx, c, t_y, df in zip(ctxs, cases, t_ys, dfs):
+            cx.traction_load(tuple((a - prev) * t_y * d for d in c["traction_dir"]), df)
+        prev = a
+        infos.append(T.time_step_cases(ctxs, dfs, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+        for k, cx in enumerate(ctxs):
+            cx.get_state(u=u)
+            us[k].append(host(u).copy())
+    return base, ctxs, us, infos, t_ys
+
+
+def test_case_contexts_match_separate_contexts_bitwise():
+    """Four cases (seeded yield stress, hardening and traction direction) on case contexts sharing one
+    base's set-up, stepped concurrently, give bit for bit the displacements of four separate contexts
+    run one after another; the shared set-up is read-only (the base's own state is untouched)."""
+    w = W.CUBE12
+    cases = W.irregular_cases(0, 4)
+    base, ctxs, us, infos, t_ys = case_run(w, cases, w.n_steps)
+    for k, c in enumerate(cases):
+        assert all(step[k]["converged"] for step in infos)
+        wk = W.case_workload(w, c)
+        _, infos_k, us_k, t_k = gpu_history(wk, w.n_steps)
+        assert t_k == t_ys[k]
+        for j in range(w.n_steps):
+            assert np.array_equal(us[k][j], us_k[j]), (k, j, rel(us[k][j], us_k[j]))
+            assert infos[j][k]["newton"] == infos_k[j]["newton"]
+            assert infos[j][k]["pcg"] == infos_k[j]["pcg"]
+    assert max(step[k]["plastic_committed"] for step in infos for k in range(4)) > 0
+    u0 = zeros(base.sizes["n_dof"])
+    base.get_state(u=u0)
+    assert not host(u0).any()
+
+
+def test_case_contexts_against_oracle():
+    """One case of a concurrent group of four (the -y traction direction of the four-direction
+    set) against the oracle run of the same material and load, step by step."""
+    w = W.CUBE12.with_(n_steps=8)
+    cases = W.direction_cases(4)
+    _, _, us, infos, t_ys = case_run(w, cases, w.n_steps)
+    k = 3
+    wk = W.case_workload(w, cases[k])
+    model = ElastoplasticModel(wk)
+    t_or = model.first_yield_traction()
+    assert abs(t_ys[k] - t_or) <= 1e-10 * t_or
+    f1 = model.traction_load(wk.traction_dir)
+    prev = 0.0
+    for j, a in enumerate(wk.load_fractions()):
+        info = model.time_step((a - prev) * t_or * f1, wk.newton_tol, wk.pcg_rtol, wk.newton_maxit, wk.pcg_maxit)
+        prev = a
+        assert info["converged"] and infos[j][k]["converged"]
+        assert rel(us[k][j], model.u) <= 1e-9, (j, rel(us[k][j], model.u))
+    assert (model.kappa > 0).sum() > 0
+
+
+@pytest.mark.parametrize("history", [0, 4])
+def test_case_contexts_mixed_precision(history):
+    """Cases in the mixed mode (shared FP32 H and dual Schur blocks of the base), with and without
+    the history start, against the FP64 separate-context displacements."""
+    w = W.CUBE12
+    cases = W.irregular_cases(1, 3)
+    _, ctxs, us, infos, _ = case_run(w, cases, w.n_steps, mixed=True, history=history)
+    for k, c in enumerate(cases):
+        _, _, us_k, _ = gpu_history(W.case_workload(w, c), w.n_steps)
+        for j in range(w.n_steps):
+            assert infos[j][k]["converged"]
+            assert rel(us[k][j], us_k[j]) <= 1e-8, (k, j, rel(us[k][j], us_k[j]))

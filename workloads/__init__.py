@@ -159,6 +159,27 @@ def irregular_cases(seed: int = 0, n_cases: int = 16) -> list:
     return cases
 
 
+def direction_cases(n_cases: int = 4) -> list:
+    """Load cases of one material whose x-y traction directions split the circle evenly:
+    theta_k = 2 pi k / n_cases (four cases: the x, y, -x and -y directions)."""
+    import math
+    cases = []
+    for k in range(n_cases):
+        th = 2.0 * math.pi * k / n_cases
+        cases.append({"sigma_y": MATERIAL["sigma_y"], "hardening": MATERIAL["hardening"],
+                      "traction_dir": (math.cos(th), math.sin(th), 0.0)})
+    return cases
+
+
+def case_workload(w: Workload, case: dict) -> Workload:
+    """The workload ``w`` with one case's yield stress, hardening and traction direction."""
+    mat = dict(w.material)
+    mat["sigma_y"] = case["sigma_y"]
+    mat["hardening"] = case["hardening"]
+    return w.with_(material=mat, traction_dir=tuple(case["traction_dir"]),
+                   name=f"{w.name}_sy{case['sigma_y']:.1f}_h{case['hardening']:.0f}")
+
+
 def seeded_vector(n: int, seed: int, dtype="float64"):
     """Deterministic standard-normal vector (numpy) for operator parity tests."""
     import numpy as np
