@@ -583,7 +583,7 @@ void op_precond_dirichlet(tfeti_ctx* c, const double* w, double* out, bool fp32)
 
 // FP32 projector and preconditioner of the inner iterations of the mixed mode.
 void op_project32(tfeti_ctx* c, const double* x, double* out) {
-  launch_project32(c->M, c->H32, c->l, x, c->gx, c->hx, out, c->st);
+  launch_project32(c->M, c->H32, c->l, x, c->gx, c->hx, c->hx8, out, c->st);
   c->launches += 3;
 }
 
@@ -1381,8 +1381,8 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
     M.gt_p = upload(c, gt_p);
     double* Gv = dalloc<double>(c, (size_t)std::max(1LL, 6 * ne));
     double* GTv = dalloc<double>(c, (size_t)std::max(1LL, 6 * ne));
-    float* Gv32 = dalloc<float>(c, (size_t)std::max(1LL, 6 * ne));
-    float* GTv32 = dalloc<float>(c, (size_t)std::max(1LL, 6 * ne));
+    float* Gv32 = dalloc<float>(c, (size_t)std::max(1LL, 8 * ne));
+    float* GTv32 = dalloc<float>(c, (size_t)std::max(1LL, 8 * ne));
     M.Gv = Gv;
     M.GTv = GTv;
     M.Gv32 = Gv32;
@@ -1470,6 +1470,8 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   if (!base) c->H = dalloc<double>(c, (size_t)c->l * c->l);
   c->gx = dalloc<double>(c, c->l);
   c->hx = dalloc<double>(c, c->l);
+  c->hx8 = dalloc<float>(c, 8 * (size_t)ns);
+  cudaMemsetAsync(c->hx8, 0, sizeof(float) * 8 * (size_t)ns, c->st);
   c->ev = dalloc<double>(c, c->l);
   c->alpha = dalloc<double>(c, c->l);
   c->f_full = dalloc<double>(c, P.n_dof);
@@ -1917,8 +1919,8 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     tfeti_ctx* hown = c->base ? c->base : c;
     try {
       if (!hown->H32) {
-        hown->H32 = dalloc<float>(hown, (size_t)c->l * c->l);
-        launch_to_f32(c->H, hown->H32, (long long)c->l * c->l, c->st);
+        hown->H32 = dalloc<float>(hown, (size_t)c->l * (size_t)h32_ld(c->l));
+        launch_h_to_f32(c->H, c->l, hown->H32, c->st);
         sync(c);
       }
       c->H32 = hown->H32;

@@ -154,6 +154,7 @@ struct tfeti_ctx {
   // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)
   float *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
+  float* hx8 = nullptr;              // FP32 H g padded to 8 per subdomain (FP32 projector)
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;
   int* d_err = nullptr;

@@ -105,7 +105,8 @@ void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const i
                       cudaStream_t st,
                       const uint8_t* bmask = nullptr);
 // Boundary 3x3 blocks of K for the listed subdomains (elastic_only: the shape's elastic template);
-// also rounded to FP32 into kbb32 at the same offsets when kbb32 != null.
+// also rounded to FP32 into kbb32 at the same offsets when kbb32 != null.  Per subdomain the
+// 27 x 9 values of its n_bnd boundary nodes are stored [t][cc][3 b + a]: K[3 node_b + a][3 nbr_t + cc].
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
                      const int* elem_np, const double* dKe, double* kbb, float* kbb32, int elastic_only,
                      cudaStream_t st);
@@ -200,8 +201,13 @@ void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const l
 // FP32 operators of the inner iterations of the mixed mode (FP64 vectors in and out):
 // P x with the FP32 copies of R and H, and the lumped preconditioner with the FP32
 // copy of the boundary blocks.  gx, hx: coarse work vectors [l].
+// hx8: FP32 copy of H g padded to 8 values per subdomain (entries 6, 7 zero), [n_sub][8].
+// H32: FP32 copy of H, rows padded to h32_ld(l) floats (launch_h_to_f32).  G values in
+// FP32 (M.Gv32, M.GTv32) are stored 8 per entry (6 and two zeros).
 void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                      double* out, cudaStream_t st);
+                      float* hx8, double* out, cudaStream_t st);
+inline long long h32_ld(long long l) { return (l + 3) & ~3LL; }
+void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st);
 // Values of the explicit G from R and the (row, slot, coefficient) entries (set-up).
 void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, const int* gt_e, double* Gv,
                    float* Gv32, double* GTv, float* GTv32, cudaStream_t st);

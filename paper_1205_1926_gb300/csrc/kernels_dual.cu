@@ -31,6 +31,28 @@ __device__ double block_reduce_sum(double v, double* red) {
   return s;   // valid in thread 0
 }
 
+// Six block sums at once, in the order of block_reduce_sum (shuffle tree within each
+// warp, then a shuffle tree over the warps' partials), with one barrier; red holds
+// 6 x 32 doubles.  The sums are valid in thread 0.
+__device__ void block_reduce_sum6(double v[6], double* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  if (l == 0)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) red[c * 32 + w] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = threadIdx.x < nw ? red[c * 32 + threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[c] = s;
+    }
+  }
+}
+
 // gx[6p+c] = scale * (R_p^T x_p)_c over all dofs of subdomain p (set-up: e = -R^T f).
 // One CTA per subdomain.
 __global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* gx, double scale) {
@@ -54,23 +76,42 @@ __global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* g
 // gx[6p+c] = scale * (G x)[6p+c] = scale * sum over the entries of subdomain p of
 // G[entry][c] x[row].  One CTA per subdomain.  T: FP64 values, or their FP32 copy
 // (products and per-thread sums in T) for the inner iterations of the mixed mode.
+// FP64 values: 6 per entry; FP32 values: 8 per entry (6 and two zeros), read as two float4.
+template <typename T>
+__device__ __forceinline__ void g_entry(const T* __restrict__ Gv, long long e, T g[6]);
+template <>
+__device__ __forceinline__ void g_entry<double>(const double* __restrict__ Gv, long long e, double g[6]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) g[c] = Gv[e * 6 + c];
+}
+template <>
+__device__ __forceinline__ void g_entry<float>(const float* __restrict__ Gv, long long e, float g[6]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(Gv) + 2 * e);
+  const float4 b = __ldg(reinterpret_cast<const float4*>(Gv) + 2 * e + 1);
+  g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w; g[4] = b.x; g[5] = b.y;
+}
+
 template <typename T>
 __global__ void k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x, double* gx,
                         double scale) {
-  __shared__ double red[32];
+  __shared__ double red[6 * 32];
   const int p = blockIdx.x;
   const long long e0 = M.gp_ptr[p], e1 = M.gp_ptr[p + 1];
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const T v = T(x[M.gp_row[e]]);
-    const T* g = Gv + e * 6;
+    T g[6];
+    g_entry<T>(Gv, e, g);
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[c] += g[c] * v;
   }
-  for (int c = 0; c < 6; ++c) {
-    const double s = block_reduce_sum(double(acc[c]), red);
-    if (threadIdx.x == 0) gx[6 * (long long)p + c] = scale * s;
-  }
+  double s[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = double(acc[c]);
+  block_reduce_sum6(s, red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gx[6 * (long long)p + c] = scale * s[c];
 }
 
 // out[row] = ax * x[row] + bh * (G^T h)[row]   (x nullable); T as in k_G_csr.
@@ -91,6 +132,62 @@ __global__ void k_GT_csr(DevMesh M, const T* __restrict__ GTv, const double* __r
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
 }
 
+// FP32: out[row] = x[row] - (G^T h)[row] with the padded FP32 values and h8, the FP32
+// copy of h padded to 8 per subdomain (two float4 per entry and subdomain).
+__global__ void k_GT_csr32(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x,
+                           const float* __restrict__ h8, double* out) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row >= M.n_mult) return;
+  const long long e0 = M.gt_ptr[row], e1 = M.gt_ptr[row + 1];
+  const float4* g4 = reinterpret_cast<const float4*>(GTv8);
+  const float4* h4 = reinterpret_cast<const float4*>(h8);
+  double s = 0.0;
+  for (long long e = e0; e < e1; ++e) {
+    const int q = __ldg(M.gt_p + e);
+    const float4 a = __ldg(g4 + 2 * e), b = __ldg(g4 + 2 * e + 1);
+    const float4 u = __ldg(h4 + 2 * q), v = __ldg(h4 + 2 * q + 1);
+    const float t = a.x * u.x + a.y * u.y + a.z * u.z + a.w * u.w + b.x * v.x + b.y * v.y;
+    s += double(t);
+  }
+  out[row] = x[row] - s;
+}
+
+// y = H x with the FP32 copy of H (n x n, rows padded with zeros to ld, a multiple of 4),
+// x rounded to FP32 in shared memory; two rows per warp, float4 loads; writes y (FP64)
+// and its padded FP32 copy h8.
+__global__ void k_gemv32(const float* __restrict__ A, long long n, long long ld, const double* __restrict__ x,
+                         double* y, float* h8) {
+  extern __shared__ __align__(16) float xs[];
+  for (long long j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = j < n ? float(x[j]) : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long r0 = (blockIdx.x * (long long)(blockDim.x >> 5) + warp) * 2;
+  const long long n4 = ld >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(xs);
+  float s[2] = {0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long row = r0 + k;
+    if (row >= n) break;
+    const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
+    float acc = 0.f;
+#pragma unroll 4
+    for (long long j = lane; j < n4; j += 32) {
+      const float4 a = __ldg(a4 + j), v = x4[j];
+      acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    s[k] = acc;
+  }
+  if (lane == 0)
+    for (int k = 0; k < 2; ++k) {
+      const long long row = r0 + k;
+      if (row >= n) break;
+      y[row] = double(s[k]);
+      h8[(row / 6) * 8 + row % 6] = s[k];
+    }
+}
+
 // Entry values of G: e' runs over the row-ordered entries, e = gt_e[e'] is the same
 // entry in subdomain order (a permutation), v = coef * R_p[slot dof][c].
 __global__ void k_fill_G(DevMesh M, const int* __restrict__ gp_slot, const double* __restrict__ gp_coef,
@@ -102,12 +199,14 @@ __global__ void k_fill_G(DevMesh M, const int* __restrict__ gp_slot, const doubl
   const SubDev& S = M.subs[M.slot_sub[slot]];
   const double* r = M.R + S.r_off + (long long)M.slot_ldof[slot] * 6;
   const double cf = gp_coef[e];
-  for (int c = 0; c < 6; ++c) {
-    const double v = cf * r[c];
-    Gv[e * 6 + c] = v;
-    Gv32[e * 6 + c] = (float)v;
-    GTv[et * 6 + c] = v;
-    GTv32[et * 6 + c] = (float)v;
+  for (int c = 0; c < 8; ++c) {
+    const double v = c < 6 ? cf * r[c] : 0.0;
+    if (c < 6) {
+      Gv[e * 6 + c] = v;
+      GTv[et * 6 + c] = v;
+    }
+    Gv32[e * 8 + c] = (float)v;
+    GTv32[et * 8 + c] = (float)v;
   }
 }
 
@@ -153,11 +252,13 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __res
   const SubDev S = M.subs[p];
   for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = T(bt_at_slot(M, w, S.copy_off + s));
   __syncthreads();
+  // blocks stored [t][cc][3 b + a] (neighbour t, column cc, row 3 b + a of boundary node b)
   const T* kb = kbb + kbb_off[p];
+  const long long nr = 3LL * S.n_bnd;
   for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
     const long long slot = S.copy_off + q;
     const int b = M.slot_bnd[slot], a = q % 3;
-    const T* kv = kb + (long long)b * 243 + a * 3;
+    const T* kv = kb + 3LL * b + a;
     const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
     int nb[28];
 #pragma unroll
@@ -173,7 +274,7 @@ __global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __res
     for (int t = 0; t < 27; ++t) {
       if (nb[t] >= 0) {
         const int lb = (int)(nb[t] - S.copy_off);
-        s += kv[t * 9] * xs[lb] + kv[t * 9 + 1] * xs[lb + 1] + kv[t * 9 + 2] * xs[lb + 2];
+        s += kv[(3 * t) * nr] * xs[lb] + kv[(3 * t + 1) * nr] * xs[lb + 1] + kv[(3 * t + 2) * nr] * xs[lb + 2];
       }
     }
     cbuf[slot] = double(s);
@@ -546,11 +647,27 @@ void launch_gemv(const double* A, long long n, const double* x, double alpha, do
   k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
 }
 
+// FP32 copy of the dense H with rows padded to h32_ld(l) (zeros beyond column l).
+__global__ void k_h_to_f32(const double* __restrict__ H, long long l, long long ld, float* H32) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= l * ld) return;
+  const long long r = i / ld, c = i % ld;
+  H32[i] = c < l ? float(H[r * l + c]) : 0.f;
+}
+
+void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st) {
+  const long long ld = h32_ld(l);
+  if (l > 0) k_h_to_f32<<<blocks_for(l * ld, 256), 256, 0, st>>>(H, l, ld, H32);
+}
+
 void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                      double* out, cudaStream_t st) {
+                      float* hx8, double* out, cudaStream_t st) {
   k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
-  k_gemv<float><<<blocks_for(l, 8), 256, 0, st>>>(H32, l, gx, 1.0, hx);
-  if (M.n_mult > 0) k_GT_csr<float><<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv32, x, 1.0, hx, -1.0, out);
+  static const int lim = dyn_smem_limit((const void*)k_gemv32);
+  cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  const long long ld = h32_ld(l);
+  k_gemv32<<<blocks_for(l, 16), 256, sizeof(float) * (size_t)ld, st>>>(H32, l, ld, gx, hx, hx8);
+  if (M.n_mult > 0) k_GT_csr32<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv32, x, hx8, out);
 }
 
 void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,

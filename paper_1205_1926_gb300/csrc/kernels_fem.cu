@@ -407,7 +407,11 @@ __global__ void k_kbb_fill(DevMesh M, const int* __restrict__ sub_list, const lo
   const SubDev& S = M.subs[p];
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)S.n_bnd * 243) return;
-  const int b = (int)(idx / 243), rem = (int)(idx % 243), t = rem / 9, a = (rem % 9) / 3, cc = rem % 3;
+  // layout [t][cc][3 b + a]: for a fixed neighbour t and column cc the rows of all boundary
+  // nodes are contiguous, so the lumped kernel's threads (consecutive rows) read coalesced
+  const long long nr = 3LL * S.n_bnd;
+  const int tc = (int)(idx / nr), ra = (int)(idx % nr);
+  const int t = tc / 3, cc = tc % 3, b = ra / 3, a = ra % 3;
   const int nu = M.shape_tnbr[(S.bnd_off + b) * 27 + t];
   double v = 0.0;
   if (nu >= 0) {

@@ -81,3 +81,19 @@ def test_device_calls_fail_cleanly_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(T.TfetiError):
         T.Context(W.TINY_1x1x2)
+
+
+def test_case_entry_points_reject_bad_arguments():
+    """The case calls check their arguments on the host before touching the device."""
+    import ctypes as C
+    lib = T.load()
+    out = C.c_void_p()
+    assert lib.tfeti_setup_case(None, 450.0, 1e4, None, C.byref(out)) == 1
+    assert lib.tfeti_setup_case(None, 450.0, 1e4, None, None) == 1
+    assert lib.ssn_time_step_cases(None, 1, None, 0, 1e-6, 1e-8, 30, 100, None) == 1
+    hs = (C.c_void_p * 1)(None)
+    ps = (C.c_void_p * 1)(None)
+    assert lib.ssn_time_step_cases(C.cast(hs, C.c_void_p), 0, C.cast(ps, C.c_void_p), 0, 1e-6, 1e-8, 30, 100,
+                                   None) == 1
+    assert lib.ssn_time_step_cases(C.cast(hs, C.c_void_p), 1, C.cast(ps, C.c_void_p), 0, 1e-6, 1e-8, 30, 100,
+                                   None) == 1
