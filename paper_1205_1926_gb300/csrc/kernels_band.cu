@@ -61,6 +61,11 @@ __device__ __forceinline__ unsigned cluster_size() {
 __device__ void diag_factor_invert(double* D, double* X, int jb, int* err) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double s_rdiag[kMaxNB];
+  // X = I; column c of the factor and row c of X = L^{-1} advance together: after the
+  // pivot, column c of L and row c of X are scaled by 1/L[c][c]; then the trailing lower
+  // triangle of D and the rows r > c of X (X[r][:] -= L[r][c] X[c][:]) are updated in the
+  // same phase, three barriers per column
+  for (int e = tid; e < jb * jb; e += nt) X[(e / jb) * kNB1 + e % jb] = (e / jb == e % jb) ? 1.0 : 0.0;
   for (int c = 0; c < jb; ++c) {
     if (tid == 0) {
       double d = D[c * kNB1 + c];
@@ -76,30 +81,26 @@ __device__ void diag_factor_invert(double* D, double* X, int jb, int* err) {
     }
     __syncthreads();
     const double inv = s_rdiag[c];
-    for (int r = c + 1 + tid; r < jb; r += nt) D[r * kNB1 + c] *= inv;
-    __syncthreads();
-    // trailing lower triangle, enumerated densely so that every lane of a warp has an entry
     const int m = jb - c - 1;
-    for (int e = tid; e < m * (m + 1) / 2; e += nt) {
-      int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while (t * (t + 1) / 2 > e) --t;
-      while ((t + 1) * (t + 2) / 2 <= e) ++t;
-      const int r = c + 1 + t, q = c + 1 + (e - t * (t + 1) / 2);
-      D[r * kNB1 + q] -= D[r * kNB1 + c] * D[q * kNB1 + c];
+    for (int e = tid; e < jb; e += nt) {
+      if (e < m) D[(c + 1 + e) * kNB1 + c] *= inv;
+      else X[c * kNB1 + (e - m)] *= inv;
     }
     __syncthreads();
-  }
-  // X = L^{-1}: X = I, then for c: X[c][:] *= 1/L[c][c]; X[r][:] -= L[r][c] X[c][:] for r > c
-  for (int e = tid; e < jb * jb; e += nt) X[(e / jb) * kNB1 + e % jb] = (e / jb == e % jb) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int c = 0; c < jb; ++c) {
-    const double inv = s_rdiag[c];
-    for (int q = tid; q <= c; q += nt) X[c * kNB1 + q] *= inv;
-    __syncthreads();
-    const int m = jb - c - 1;
-    for (int e = tid; e < m * (c + 1); e += nt) {
-      const int r = c + 1 + e / (c + 1), q = e % (c + 1);
-      X[r * kNB1 + q] -= D[r * kNB1 + c] * X[c * kNB1 + q];
+    // trailing lower triangle, enumerated densely so that every lane of a warp has an entry,
+    // followed by the m x (c + 1) update of X
+    const int ntri = m * (m + 1) / 2;
+    for (int e = tid; e < ntri + m * (c + 1); e += nt) {
+      if (e < ntri) {
+        int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (t * (t + 1) / 2 > e) --t;
+        while ((t + 1) * (t + 2) / 2 <= e) ++t;
+        const int r = c + 1 + t, q = c + 1 + (e - t * (t + 1) / 2);
+        D[r * kNB1 + q] -= D[r * kNB1 + c] * D[q * kNB1 + c];
+      } else {
+        const int f = e - ntri, r = c + 1 + f / (c + 1), q = f % (c + 1);
+        X[r * kNB1 + q] -= D[r * kNB1 + c] * X[c * kNB1 + q];
+      }
     }
     __syncthreads();
   }
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j0 = 0, b = 0; j0 < n; j0 += NB, ++b) {
     const int jb = min(NB, n - j0);
+    #pragma unroll 4
     for (int idx = tid; idx < jb * jb; idx += nt) {
       const int r = idx / jb, c = idx % jb;
       Dm[r * kNB1 + c] = (c <= r) ? A[(long long)(j0 + r) * W + c - r + bw] : 0.0;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
       // panel TRSM, rows split over the cluster: L[i][j0+c] = sum_{s<=c} A[i][j0+s] Di[c][s]
       const int rchunk = (P + C - 1) / C;
       const int t0 = q * rchunk, t1 = min(P, t0 + rchunk);
+      #pragma unroll 4
       for (int idx = tid; idx < (t1 - t0) * jb; idx += nt) {
         const int t = t0 + idx / jb, c = idx % jb;
         const int i = i0 + t, k = j0 + c - i + bw;
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_band_chol(DevMesh M, const int* __
     }
     cluster_sync_all();
     if (P > 0) {
+      #pragma unroll 4
       for (int idx = tid; idx < P * jb; idx += nt) {
         const int t = idx / jb, c = idx % jb;
         const int i = i0 + t, k = j0 + c - i + bw;
