@@ -183,6 +183,31 @@ def oracle_sample_subprocess(workload_name):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def oracle_sample_all_cores(workload_name, n_proc=None):
+    """The same sample run as n_proc concurrent single-thread oracle processes (one per host core):
+    their mean per-process result is the oracle's speed per core with every core busy (shared memory
+    bandwidth and caches included).  Dividing a step's time by n_proc estimates the oracle with its
+    subdomain-local work split over all cores, the parallelism of Sec. 4.3 (the coarse problem and the
+    reductions would not split that well, so this is a lower bound on its time)."""
+    n_proc = n_proc or os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in THREAD_ENV:
+        env[k] = "1"
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name],
+                              env=env, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+             for _ in range(n_proc)]
+    outs = []
+    for pr in procs:
+        out, _ = pr.communicate()
+        if pr.returncode == 0:
+            outs.append(json.loads(out.strip().splitlines()[-1]))
+    if not outs:
+        return None
+    keys = ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s")
+    mean = {k: statistics.mean(o[k] for o in outs) for k in keys}
+    return mean | {"cores": len(outs)}
+
+
 def oracle_step_estimate(s, newton_per_step, pcg_per_step):
     """Seconds per load step: per Newton iteration assembly + factorisation + 3 set-up/recovery
     F-applies, plus the PCGP iterations, with the given iteration counts."""
@@ -213,6 +238,7 @@ def run_reference(args, rank, world):
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration-count record missing"}))
         return
     v = oracle_step_estimate(s, newton, pcg)
+    sa = oracle_sample_all_cores(w.name) if args.oracle_all_cores else None
     elapsed = time.perf_counter() - t_start
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -224,6 +250,11 @@ def run_reference(args, rank, world):
                              "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s")},
                              "wall_s": elapsed},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if sa is not None:
+        va = oracle_step_estimate(sa, newton, pcg)
+        line["cpu_baseline"]["all_cores"] = {"value": va / sa["cores"], "unit": UNIT, "cores": sa["cores"],
+                                             "per_core_step_s": va,
+                                             "kind": "oracle, one single-thread process per core"}
     print(json.dumps(line))
 
 
@@ -491,6 +522,16 @@ def run_gpu(args, rank, world, local_rank):
                                                         "(the oracle runs Algorithm 3 as printed)",
                                 "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s",
                                                                    "f_apply_s")}}
+        if args.oracle_all_cores:
+            sa = oracle_sample_all_cores(w.name)
+            if sa is not None:
+                va = oracle_step_estimate(sa, statistics.mean(x["newton"] for x in counts["infos"]),
+                                          statistics.mean(sum(x["pcg"]) for x in counts["infos"]))
+                line["cpu_baseline"]["all_cores"] = {
+                    "value": va / sa["cores"], "unit": UNIT, "cores": sa["cores"], "per_core_step_s": va,
+                    "kind": "oracle, one single-thread process per core",
+                    "note": "the same sample run concurrently on every core; per-core step time / cores = the "
+                            "oracle with its subdomain work split over all cores (lower bound)"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -652,6 +693,8 @@ def main():
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
                     help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
+    ap.add_argument("--oracle-all-cores", action="store_true",
+                    help="also time the oracle sample on every host core at once (cpu_baseline.all_cores)")
     ap.add_argument("--cases", type=int, default=0,
                     help="N > 0: N load cases on one mesh stepped concurrently (case contexts), one JSON line")
     ap.add_argument("--case-set", default="directions", choices=["directions", "seeded"],

@@ -71,6 +71,7 @@ extern "C" {
 #define TFETI_ERR_NOT_CONVERGED  6  /* iteration limit reached (last iterate written)  */
 #define TFETI_ERR_BREAKDOWN      7  /* p^T F p <= 0 in PCGP                           */
 #define TFETI_ERR_NONFINITE      8  /* NaN or Inf met in a residual or scalar         */
+#define TFETI_ERR_TIMEOUT        9  /* a bounded device wait (bulk copy, MMA) gave up */
 
 /* ---- problem description (host struct, copied by tfeti_setup) ------------ */
 #define TFETI_PRECOND_NONE   0
@@ -207,7 +208,8 @@ typedef struct tfeti_pcg_info {
  * device [n_mult], nullable; lambda0: device [n_mult], nullable -- if given,
  * lambda_Ker starts from P_N lambda0 instead of o.  info: host, nullable.
  * Errors: TFETI_ERR_NOT_CONVERGED (last iterate written), TFETI_ERR_BREAKDOWN,
- * TFETI_ERR_NONFINITE. */
+ * TFETI_ERR_NONFINITE, TFETI_ERR_TIMEOUT (a bounded wait of the F-apply kernels on a
+ * bulk copy or MMA gave up; the context stays usable). */
 int tfeti_dual_pcg(tfeti_ctx* ctx, const double* f, double* u_out, double* lambda_out,
                    const double* lambda0, double rtol, int32_t maxit, tfeti_pcg_info* info);
 

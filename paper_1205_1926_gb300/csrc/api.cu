@@ -591,9 +591,9 @@ void op_precond32(tfeti_ctx* c, const double* x, double* out) {
   if (c->dirichlet) {
     op_precond_dirichlet(c, x, out, true);
   } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
+    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbt, c->cbuf, c->st);
     launch_contract(c->M, c->cbuf, out, c->st);
-    c->launches += 2;
+    c->launches += 3;
   } else {
     cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
   }
@@ -603,9 +603,9 @@ void op_precond(tfeti_ctx* c, const double* x, double* out) {
   if (c->dirichlet) {
     op_precond_dirichlet(c, x, out, false);
   } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
+    launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbt, c->cbuf, c->st);
     launch_contract(c->M, c->cbuf, out, c->st);
-    c->launches += 2;
+    c->launches += 3;
   } else {
     cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
   }
@@ -1198,7 +1198,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   if (cst != TFETI_OK) return cst;
   if (herr & 6) {
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    return fail(c, TFETI_ERR_CUDA, (herr & 2) ? "a factor-panel copy did not complete within its time limit"
+    return fail(c, TFETI_ERR_TIMEOUT, (herr & 2) ? "a factor-panel copy did not complete within its time limit"
                                               : "a Schur-tile copy or MMA did not complete within its time limit");
   }
   if (status == TFETI_OK && !converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "PCGP iteration limit reached");
@@ -1462,6 +1462,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->d_list_kbb = dalloc<long long>(c, ns);
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
+  c->cbt = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
   for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->tm, &c->dlt,
                      &c->rin})
@@ -1648,6 +1649,7 @@ const char* tfeti_status_str(int s) {
     case TFETI_ERR_NOT_CONVERGED: return "not converged";
     case TFETI_ERR_BREAKDOWN: return "PCGP breakdown";
     case TFETI_ERR_NONFINITE: return "non-finite value";
+    case TFETI_ERR_TIMEOUT: return "bounded device wait gave up";
     default: return "unknown status";
   }
 }
@@ -2156,7 +2158,7 @@ int tfeti_apply_F32(tfeti_ctx* c, const double* x, double* y) {
   if (cst != TFETI_OK) return cst;
   if (herr & 6) {
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    return fail(c, TFETI_ERR_CUDA, "a bounded device wait gave up in the FP32 F-apply");
+    return fail(c, TFETI_ERR_TIMEOUT, "a bounded device wait gave up in the FP32 F-apply");
   }
   return TFETI_OK;
 }
