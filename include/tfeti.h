@@ -409,6 +409,13 @@ typedef struct tfeti_timing {
 int tfeti_timing_get(tfeti_ctx* ctx, tfeti_timing* out);
 int tfeti_timing_reset(tfeti_ctx* ctx, int32_t enable_events);
 
+/* Failure detection of the bounded device waits (no context needed): one CTA waits on
+ * an mbarrier phase that nothing completes, with the bounded wait of the F-apply
+ * kernels limited to limit_cycles SM cycles (1 .. 2^31); the wait gives up, the kernel
+ * returns normally and *gave_up (host) is set to 1 (0 would mean the wait completed).
+ * Nothing faults or hangs; the device stays usable.  cuda_stream: nullable. */
+int tfeti_check_bounded_wait(void* cuda_stream, int64_t limit_cycles, int32_t* gave_up);
+
 #ifdef __cplusplus
 }
 #endif

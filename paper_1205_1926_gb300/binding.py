@@ -108,6 +108,7 @@ SIGNATURES = {
     "tfeti_apply_projector_noalloc": (C.c_int, [_P, _P, _P]),
     "tfeti_timing_get": (C.c_int, [_P, C.POINTER(Timing)]),
     "tfeti_timing_reset": (C.c_int, [_P, _I]),
+    "tfeti_check_bounded_wait": (C.c_int, [_P, C.c_int64, C.POINTER(_I)]),
 }
 
 _lib = None

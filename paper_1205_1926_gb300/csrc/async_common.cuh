@@ -44,12 +44,12 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`, giving up after about 2^31 SM cycles (~1 s).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of `bar`, giving up after `limit` SM cycles (default 2^31, ~1 s).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 1LL << 31) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity))
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 

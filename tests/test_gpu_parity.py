@@ -792,3 +792,18 @@ def test_case_contexts_mixed_precision(history):
         for j in range(w.n_steps):
             assert infos[j][k]["converged"]
             assert rel(us[k][j], us_k[j]) <= 1e-8, (k, j, rel(us[k][j], us_k[j]))
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """Failure detection on the GPU without a fault: one CTA waits, with the F-apply kernels'
+    bounded mbarrier wait limited to 2^21 cycles (about 1 ms), on a phase that nothing completes;
+    the wait gives up, the call reports it, and the device then solves a load step as before."""
+    import ctypes as C
+    lib = T.load()
+    flag = C.c_int32(-1)
+    assert lib.tfeti_check_bounded_wait(None, 1 << 21, C.byref(flag)) == 0
+    assert flag.value == 1
+    assert lib.tfeti_check_bounded_wait(None, 0, C.byref(flag)) == 1
+    w = W.SMALL6_RAGGED
+    ctx, infos, us, _ = gpu_history(w, 2)
+    assert all(i["converged"] for i in infos) and np.isfinite(us[-1]).all()
