@@ -591,9 +591,9 @@ void op_precond32(tfeti_ctx* c, const double* x, double* out) {
   if (c->dirichlet) {
     op_precond_dirichlet(c, x, out, true);
   } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbt, c->cbuf, c->st);
+    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
-    c->launches += 3;
+    c->launches += 2;
   } else {
     cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
   }
@@ -603,9 +603,9 @@ void op_precond(tfeti_ctx* c, const double* x, double* out) {
   if (c->dirichlet) {
     op_precond_dirichlet(c, x, out, false);
   } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbt, c->cbuf, c->st);
+    launch_lumped(c->M, x, c->kbb, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
-    c->launches += 3;
+    c->launches += 2;
   } else {
     cudaMemcpyAsync(out, x, sizeof(double) * c->M.n_mult, cudaMemcpyDeviceToDevice, c->st);
   }
@@ -1462,7 +1462,6 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->d_list_kbb = dalloc<long long>(c, ns);
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
-  c->cbt = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
   for (double** v : {&c->lam, &c->lam_im, &c->lamk, &c->r, &c->w, &c->z, &c->y, &c->pdir, &c->Fp, &c->tm, &c->dlt,
                      &c->rin})

@@ -114,7 +114,6 @@ struct tfeti_ctx {
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,
          *z = nullptr, *y = nullptr, *pdir = nullptr, *Fp = nullptr, *tm = nullptr;
   double* vsol = nullptr;   // K^+(f - B^T lambda) of the last residual solve, device [n_dof]
-  double* cbt = nullptr;    // B^T w at the copy slots (lumped preconditioner), device [n_copy]
   // Dirichlet preconditioner (Sec. 4.2): factors of K_p with the constrained-node dofs
   // replaced by identity rows and columns (K_ii), one template per (shape, pattern of
   // constrained dofs) class for elastic subdomains, own ones for plastic subdomains

@@ -196,8 +196,8 @@ void launch_gemv(const double* A, long long n, const double* x, double alpha, do
 // out = v + R alpha per subdomain (u = K^+(f - B^T lambda) + R alpha); device [n_dof].
 void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, double* out, int max_ndof,
                        cudaStream_t st);
-void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbt,
-                   double* cbuf, cudaStream_t st);
+void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
+                   cudaStream_t st, int max_copy);
 // FP32 operators of the inner iterations of the mixed mode (FP64 vectors in and out):
 // P x with the FP32 copies of R and H, and the lumped preconditioner with the FP32
 // copy of the boundary blocks.  gx, hx: coarse work vectors [l].
@@ -215,8 +215,8 @@ void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, 
 // (xfull zeroed by the caller); cbuf[slot] = v[dof] - t[dof] on the copy slots.
 void launch_slots_to_full(const DevMesh& M, const double* w, double* xfull, cudaStream_t st);
 void launch_slots_diff(const DevMesh& M, const double* v, const double* t, double* cbuf, cudaStream_t st);
-void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbt,
-                     double* cbuf, cudaStream_t st);
+void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
+                     cudaStream_t st, int max_copy);
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;

@@ -243,47 +243,42 @@ __global__ void k_gemv(const T* __restrict__ A, long long n, const double* __res
 // K_bb comes from the subdomain's boundary blocks (kbb + kbb_off[p]): its shape's
 // elastic template or its own blocks when it has plastic points.
 // T: FP64 blocks, or their FP32 copy for the inner iterations of the mixed mode.
-// B^T w at every copy slot (one thread per slot).
-__global__ void k_bt_slots(DevMesh M, const double* __restrict__ w, double* cbt) {
-  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (sl < M.n_copy) cbt[sl] = bt_at_slot(M, w, sl);
-}
-
-// Lumped preconditioner, subdomain part: v = K_bb (B^T w) on the interface slots, one
-// thread per slot of all subdomains, with cbt = B^T w from k_bt_slots.  K_bb comes from
-// the subdomain's boundary blocks (kbb + kbb_off[p]): its shape's elastic template or its
-// own blocks when it has plastic points, stored [t][cc][3 b + a] (neighbour t, column cc,
-// row 3 b + a of boundary node b), so that threads of consecutive slots read consecutive
-// values.  T: FP64 blocks, or their FP32 copy for the inner iterations of the mixed mode.
 template <typename T>
-__global__ void k_lumped(DevMesh M, const double* __restrict__ cbt, const T* __restrict__ kbb,
+__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __restrict__ kbb,
                          const long long* __restrict__ kbb_off, double* cbuf) {
-  const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (slot >= M.n_copy) return;
-  const int p = M.slot_sub[slot];
-  const long long copy_off = M.subs[p].copy_off;
-  const long long nr = 3LL * M.subs[p].n_bnd;
-  const int b = M.slot_bnd[slot], a = (int)((slot - copy_off) % 3);
-  const T* kv = kbb + kbb_off[p] + 3LL * b + a;
-  const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
-  int nb[28];
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  T* xs = reinterpret_cast<T*>(xs_raw);
+  const int p = blockIdx.x;
+  const SubDev S = M.subs[p];
+  for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = T(bt_at_slot(M, w, S.copy_off + s));
+  __syncthreads();
+  // blocks stored [t][cc][3 b + a] (neighbour t, column cc, row 3 b + a of boundary node b)
+  const T* kb = kbb + kbb_off[p];
+  const long long nr = 3LL * S.n_bnd;
+  for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
+    const long long slot = S.copy_off + q;
+    const int b = M.slot_bnd[slot], a = q % 3;
+    const T* kv = kb + 3LL * b + a;
+    const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
+    int nb[28];
 #pragma unroll
-  for (int u = 0; u < 7; ++u) {
-    const int4 v = __ldg(nb4 + u);
-    nb[4 * u] = v.x;
-    nb[4 * u + 1] = v.y;
-    nb[4 * u + 2] = v.z;
-    nb[4 * u + 3] = v.w;
-  }
-  T s = T(0);
-#pragma unroll
-  for (int t = 0; t < 27; ++t) {
-    if (nb[t] >= 0) {
-      const double* x = cbt + nb[t];
-      s += kv[(3 * t) * nr] * T(x[0]) + kv[(3 * t + 1) * nr] * T(x[1]) + kv[(3 * t + 2) * nr] * T(x[2]);
+    for (int u = 0; u < 7; ++u) {
+      const int4 v = __ldg(nb4 + u);
+      nb[4 * u] = v.x;
+      nb[4 * u + 1] = v.y;
+      nb[4 * u + 2] = v.z;
+      nb[4 * u + 3] = v.w;
     }
+    T s = T(0);
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      if (nb[t] >= 0) {
+        const int lb = (int)(nb[t] - S.copy_off);
+        s += kv[(3 * t) * nr] * xs[lb] + kv[(3 * t + 1) * nr] * xs[lb + 1] + kv[(3 * t + 2) * nr] * xs[lb + 2];
+      }
+    }
+    cbuf[slot] = double(s);
   }
-  cbuf[slot] = double(s);
 }
 
 // Dirichlet preconditioner: B^T w onto the copy-slot dofs of the full local vectors.
@@ -681,11 +676,12 @@ void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, 
   k_add_R_alpha<<<dim3((unsigned)((max_ndof + 255) / 256), (unsigned)M.n_sub), 256, 0, st>>>(M, v, alpha, out);
 }
 
-void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbt,
-                   double* cbuf, cudaStream_t st) {
-  if (M.n_copy <= 0) return;
-  k_bt_slots<<<blocks_for(M.n_copy, 256), 256, 0, st>>>(M, w, cbt);
-  k_lumped<double><<<blocks_for(M.n_copy, 128), 128, 0, st>>>(M, cbt, kbb, kbb_off, cbuf);
+void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
+                   cudaStream_t st, int max_copy) {
+  const size_t smem = sizeof(double) * (size_t)(max_copy > 0 ? max_copy : 1);
+  static const int lim = dyn_smem_limit((const void*)k_lumped<double>);
+  cudaFuncSetAttribute(k_lumped<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  k_lumped<double><<<M.n_sub, 256, smem, st>>>(M, w, kbb, kbb_off, cbuf);
 }
 
 void launch_slots_to_full(const DevMesh& M, const double* w, double* xfull, cudaStream_t st) {
@@ -696,11 +692,12 @@ void launch_slots_diff(const DevMesh& M, const double* v, const double* t, doubl
   if (M.n_copy > 0) k_slots_diff<<<blocks_for(M.n_copy, 256), 256, 0, st>>>(M, v, t, cbuf);
 }
 
-void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbt,
-                     double* cbuf, cudaStream_t st) {
-  if (M.n_copy <= 0) return;
-  k_bt_slots<<<blocks_for(M.n_copy, 256), 256, 0, st>>>(M, w, cbt);
-  k_lumped<float><<<blocks_for(M.n_copy, 128), 128, 0, st>>>(M, cbt, kbb32, kbb_off, cbuf);
+void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
+                     cudaStream_t st, int max_copy) {
+  const size_t smem = sizeof(float) * (size_t)(max_copy > 0 ? max_copy : 1);
+  static const int lim = dyn_smem_limit((const void*)k_lumped<float>);
+  cudaFuncSetAttribute(k_lumped<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  k_lumped<float><<<M.n_sub, 256, smem, st>>>(M, w, kbb32, kbb_off, cbuf);
 }
 
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st) {
