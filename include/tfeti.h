@@ -180,9 +180,11 @@ int tfeti_return_map(tfeti_ctx* ctx, const double* du, double* dsigma, double* d
  * f^p = df^p - sum_T |T| dsigma_T^T G_T R_T and K^p = sum_T |T| (T^o G_T R_T)^T G_T R_T,
  * then the generalised inverse of every K^p is prepared (banded Cholesky of
  * K_rr; subdomains whose Gauss points are all elastic reuse the shared factor
- * of their shape).  df: device [n_dof]; f_out: device [n_dof], nullable.  The
- * assembled operator stays in the context for tfeti_dual_pcg and the
- * operator calls below.  Errors: TFETI_ERR_NUMERIC. */
+ * of their shape, the others are factorised into a slot of the context's pool of
+ * own factor records, which grows on demand).  df: device [n_dof]; f_out: device
+ * [n_dof], nullable.  The assembled operator stays in the context for
+ * tfeti_dual_pcg and the operator calls below.  Errors: TFETI_ERR_NUMERIC,
+ * TFETI_ERR_OOM (the pool could not grow). */
 int tfeti_assemble_tangent(tfeti_ctx* ctx, const double* du, const double* df, double* f_out);
 
 typedef struct tfeti_pcg_info {
