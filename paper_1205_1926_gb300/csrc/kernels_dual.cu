@@ -81,8 +81,10 @@ template <typename T>
 __device__ __forceinline__ void g_entry(const T* __restrict__ Gv, long long e, T g[6]);
 template <>
 __device__ __forceinline__ void g_entry<double>(const double* __restrict__ Gv, long long e, double g[6]) {
-#pragma unroll
-  for (int c = 0; c < 6; ++c) g[c] = Gv[e * 6 + c];
+  // 6 doubles = 48 bytes per entry: every entry starts on a 16-byte boundary
+  const double2* v = reinterpret_cast<const double2*>(Gv + e * 6);
+  const double2 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2);
+  g[0] = a.x; g[1] = a.y; g[2] = b.x; g[3] = b.y; g[4] = c.x; g[5] = c.y;
 }
 template <>
 __device__ __forceinline__ void g_entry<float>(const float* __restrict__ Gv, long long e, float g[6]) {
@@ -123,13 +125,47 @@ __global__ void k_GT_csr(DevMesh M, const T* __restrict__ GTv, const double* __r
   double s = 0.0;
   for (long long e = M.gt_ptr[row]; e < M.gt_ptr[row + 1]; ++e) {
     const double* hq = h + 6 * (long long)M.gt_p[e];
-    const T* g = GTv + e * 6;
+    T g[6];
+    g_entry<T>(GTv, e, g);
+    double hv[6];
+    if (sizeof(T) == 8) {
+      const double2* h2 = reinterpret_cast<const double2*>(hq);
+      const double2 a = __ldg(h2), b = __ldg(h2 + 1), c = __ldg(h2 + 2);
+      hv[0] = a.x; hv[1] = a.y; hv[2] = b.x; hv[3] = b.y; hv[4] = c.x; hv[5] = c.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) hv[c] = hq[c];
+    }
     T t = T(0);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) t += g[c] * T(hq[c]);
+    for (int c = 0; c < 6; ++c) t += g[c] * T(hv[c]);
     s += double(t);
   }
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
+}
+
+// y = alpha H x in FP64 for even n (rows start on 16-byte boundaries): two rows per warp,
+// double2 loads of H and x (x is small and stays in L1).
+__global__ void k_gemv64(const double* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
+                         double* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long r0 = (blockIdx.x * (long long)(blockDim.x >> 5) + warp) * 2;
+  const long long n2 = n >> 1;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long row = r0 + k;
+    if (row >= n) break;
+    const double2* a2 = reinterpret_cast<const double2*>(A + row * n);
+    double acc = 0.0;
+#pragma unroll 4
+    for (long long j = lane; j < n2; j += 32) {
+      const double2 a = __ldg(a2 + j), v = __ldg(x2 + j);
+      acc += a.x * v.x + a.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = alpha * acc;
+  }
 }
 
 // FP32: out[row] = x[row] - (G^T h)[row] with the padded FP32 values and h8, the FP32
@@ -644,7 +680,9 @@ void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, 
 }
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
-  k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+  if (n <= 0) return;
+  if (n % 2 == 0) k_gemv64<<<blocks_for(n, 16), 256, 0, st>>>(A, n, x, alpha, y);
+  else k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
 }
 
 // FP32 copy of the dense H with rows padded to h32_ld(l) (zeros beyond column l).
