@@ -1236,6 +1236,7 @@ void fill_sizes(const tfeti_ctx* c, tfeti_sizes* out) {
 // the Dirichlet templates; everything the case writes is its own.
 int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   Plan& P = c->plan;
+  cudaGetDevice(&c->device);
   const int ns = (int)P.subs.size();
   c->l = 6LL * ns;
   // subdomain descriptors
@@ -1724,6 +1725,12 @@ int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* c
   }
   std::vector<int> status(n_cases, TFETI_OK);
   auto run = [&](int k) {
+    // a new host thread starts on device 0: make the context's device current
+    if (cudaSetDevice(ctxs[k]->device) != cudaSuccess) {
+      cudaGetLastError();
+      status[k] = fail(ctxs[k], TFETI_ERR_CUDA, "ssn_time_step_cases: cudaSetDevice failed");
+      return;
+    }
     try {
       status[k] = ssn_time_step(ctxs[k], df[k], df_on_host, newton_tol, pcg_rtol, newton_maxit, pcg_maxit,
                                 info ? info + k : nullptr);
@@ -1740,7 +1747,10 @@ int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* c
     for (std::thread& t : threads) t.join();
     return fail(ctxs[0], TFETI_ERR_ARG, "ssn_time_step_cases: could not start a host thread");
   }
+  int prev_device = 0;
+  cudaGetDevice(&prev_device);
   run(0);
+  cudaSetDevice(prev_device);   // the caller's current device is left as it was
   for (std::thread& t : threads) t.join();
   for (int k = 0; k < n_cases; ++k)
     if (status[k] != TFETI_OK) return status[k];

@@ -14,6 +14,7 @@ struct tfeti_ctx {
   tfeti::Plan plan;
   cudaStream_t st = nullptr;
   bool owns_stream = false;          // st was created by the context (case contexts without a stream)
+  int device = 0;                    // CUDA device current at set-up (the context's device)
   // case context (tfeti_setup_case): the context whose read-only set-up this one shares
   tfeti_ctx* base = nullptr;
   std::string err;

@@ -144,30 +144,6 @@ __global__ void k_GT_csr(DevMesh M, const T* __restrict__ GTv, const double* __r
   out[row] = (x ? ax * x[row] : 0.0) + bh * s;
 }
 
-// y = alpha H x in FP64 for even n (rows start on 16-byte boundaries): two rows per warp,
-// double2 loads of H and x (x is small and stays in L1).
-__global__ void k_gemv64(const double* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
-                         double* y) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long r0 = (blockIdx.x * (long long)(blockDim.x >> 5) + warp) * 2;
-  const long long n2 = n >> 1;
-  const double2* x2 = reinterpret_cast<const double2*>(x);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long row = r0 + k;
-    if (row >= n) break;
-    const double2* a2 = reinterpret_cast<const double2*>(A + row * n);
-    double acc = 0.0;
-#pragma unroll 4
-    for (long long j = lane; j < n2; j += 32) {
-      const double2 a = __ldg(a2 + j), v = __ldg(x2 + j);
-      acc += a.x * v.x + a.y * v.y;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[row] = alpha * acc;
-  }
-}
-
 // FP32: out[row] = x[row] - (G^T h)[row] with the padded FP32 values and h8, the FP32
 // copy of h padded to 8 per subdomain (two float4 per entry and subdomain).
 __global__ void k_GT_csr32(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x,
@@ -680,9 +656,7 @@ void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, 
 }
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
-  if (n <= 0) return;
-  if (n % 2 == 0) k_gemv64<<<blocks_for(n, 16), 256, 0, st>>>(A, n, x, alpha, y);
-  else k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+  if (n > 0) k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
 }
 
 // FP32 copy of the dense H with rows padded to h32_ld(l) (zeros beyond column l).

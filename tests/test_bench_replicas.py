@@ -45,3 +45,14 @@ def test_max_over_ranks_and_replica_value_two_gloo_ranks():
 def test_single_process_is_identity():
     assert bench.max_over_ranks([3.5, 1.25]) == [3.5, 1.25]
     assert bench.replica_value(3.4, 17, 1) == pytest.approx(0.2)
+
+
+def test_oracle_sample_on_several_cores_tiny_workload():
+    """The all-core oracle timing runs the same bounded sample in one single-thread process per core
+    and averages their component times (2 processes on a 2-subdomain case here)."""
+    s = bench.oracle_sample_all_cores("tiny2_1x1x2", n_proc=2)
+    assert s is not None and s["cores"] == 2
+    for k in ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s"):
+        assert s[k] > 0.0
+    v = bench.oracle_step_estimate(s, 2.0, 10.0)
+    assert v == pytest.approx(2.0 * (s["assembly_s"] + s["factor_s"] + 3 * s["f_apply_s"]) + 10.0 * s["pcg_iter_s"])
