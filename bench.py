@@ -41,9 +41,9 @@ FP64_PEAK_TFLOPS = 1.207      # measured DFMA throughput of this GB300 pool (see
 # DRAM traffic per launch of the banded F-apply kernel at the 64^3 benchmark size, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_cube64_bench.md gives the command).
 # Valid only while the kernel source is the one measured.
-MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.37e6,
+MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.32e6,
                                     "src": "paper_1205_1926_gb300/csrc/kernels_band.cu",
-                                    "sha256": "24a70d48182d090667377a09b7bd9afe59c74efc36f18a2e84710b76724d6ea4"}}
+                                    "sha256": "01eefbee3c6566592055bea6187a029d8672e1baf076a248e4ff1e348cfe3f00"}}
 
 
 def measured_traffic(kernel, workload):
