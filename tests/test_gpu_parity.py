@@ -807,3 +807,29 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     w = W.SMALL6_RAGGED
     ctx, infos, us, _ = gpu_history(w, 2)
     assert all(i["converged"] for i in infos) and np.isfinite(us[-1]).all()
+
+
+def test_base_context_steps_beside_its_cases():
+    """The base context itself can be one of the concurrently stepped contexts (its own stream, the
+    library's default stream here): base and case give the displacements of separate contexts."""
+    w = W.SMALL6_RAGGED
+    cases = [{"sigma_y": w.material["sigma_y"], "hardening": w.material["hardening"], "traction_dir": w.traction_dir},
+             {"sigma_y": 380.0, "hardening": 4000.0, "traction_dir": (0.0, 1.0, 0.0)}]
+    base = T.Context(w)
+    ctxs = [base, T.Context.case_of(base, cases[1]["sigma_y"], cases[1]["hardening"])]
+    t_ys = [cx.first_yield_traction(c["traction_dir"]) for cx, c in zip(ctxs, cases)]
+    n = base.sizes["n_dof"]
+    dfs = [zeros(n), zeros(n)]
+    u = zeros(n)
+    torch.cuda.synchronize()
+    prev = 0.0
+    for a in w.load_fractions():
+        for cx, c, t_y, df in zip(ctxs, cases, t_ys, dfs):
+            cx.traction_load(tuple((a - prev) * t_y * d for d in c["traction_dir"]), df)
+        prev = a
+        out = T.time_step_cases(ctxs, dfs, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        assert all(o["converged"] for o in out)
+    for k, c in enumerate(cases):
+        ctxs[k].get_state(u=u)
+        _, _, us_k, _ = gpu_history(W.case_workload(w, c), w.n_steps)
+        assert np.array_equal(host(u), us_k[-1]), (k, rel(host(u), us_k[-1]))
