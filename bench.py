@@ -679,7 +679,8 @@ def main():
                     help="the headline (timed, end-to-end) arm; default mixed_learned, the metric's method")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="shorthand: fp64 = --arm fp64, mixed = --arm mixed (or mixed_learned with --learned)")
-    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--inner-rtol", type=float, default=1e-4,
+                    help="relative residual reduction of each inner FP32 PCGP solve of the mixed arms")
     ap.add_argument("--no-mixed", action="store_true", help="time the headline arm only (no other arms)")
     ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")

@@ -262,7 +262,7 @@ int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* c
  * one GEMM per shape and the others running FP32 banded solves with their factors
  * rounded to FP32.  Each correction is projected in FP64 before it is added, so
  * lambda_Ker stays in Ker N.  Each inner solve reduces its projected residual by
- * inner_rtol (0 < inner_rtol < 1, e.g. 1e-3).  The stopping test
+ * inner_rtol (0 < inner_rtol < 1, e.g. 1e-4).  The stopping test
  * ||P r|| <= rtol ||d~|| is applied to the FP64 residual, so both modes reach
  * the same dual residual.  The paper has no mixed-precision variant; this is an
  * implementation choice for GPUs whose FP64 rate is far below their FP32 rate.

@@ -303,7 +303,7 @@ class Context:
             self._check(st, "ssn_time_step")
         return info.as_dict() | {"status": st}
 
-    def set_precision(self, mixed: bool, inner_rtol: float = 1e-3):
+    def set_precision(self, mixed: bool, inner_rtol: float = 1e-4):
         """FP64 dual solve (default) or FP64-refined PCGP with FP32 inner F-applies."""
         return self._check(self.lib.tfeti_set_precision(self.h, 1 if mixed else 0, inner_rtol), "tfeti_set_precision")
 
