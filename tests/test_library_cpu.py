@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(T.SIGNATURES), set(names) ^ set(T.SIGNATURES)
 
 
-@pytest.mark.parametrize("w", [W.TINY_1x1x2, W.SMALL4, W.SMALL6_RAGGED, W.CUBE12,
+@pytest.mark.parametrize("w", [W.TINY_1x1x2, W.SMALL4, W.SMALL6_RAGGED, W.CUBE12, W.CUBE24_IRREGULAR,
                                W.Workload(name="rollers", nel=(3, 2, 4), cuts=((0, 1, 3), (0, 2), (0, 2, 4)),
                                           dirichlet={"x0": 1, "y0": 2, "z0": 4, "x1": 6})])
 def test_plan_maps_bit_exact_with_oracle(w):
@@ -97,3 +97,14 @@ def test_case_entry_points_reject_bad_arguments():
                                    None) == 1
     assert lib.ssn_time_step_cases(C.cast(hs, C.c_void_p), 1, C.cast(ps, C.c_void_p), 0, 1e-6, 1e-8, 30, 100,
                                    None) == 1
+
+
+def test_plan_sizes_of_the_uneven_box_workload():
+    """80^3 bricks in the seeded 9 x 10 x 9 partition: 810 boxes, multipliers by direct count, and the
+    largest half bandwidth (a 12 x 12 box face: 3 (13 * 13 + 13 + 1) + 2)."""
+    from tests.test_oracle_fem import brute_force_multiplier_count
+    w = W.CUBE80_IRREGULAR
+    s = T.Plan(w).sizes()
+    assert s["n_sub"] == 810 == w.n_sub and s["n_coarse"] == 6 * 810
+    assert s["n_mult"] == brute_force_multiplier_count(w)
+    assert s["max_band"] == 3 * (13 * 13 + 13 + 1) + 2
