@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,7 +36,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "time per load step @1e-8 dual res: FP64 vs mixed+learned; F-apply % HBM peak"
 UNIT = "s/load_step"
-FP64_PEAK_TFLOPS = 1.207      # measured DFMA throughput of this GB300 pool
+FP64_PEAK_TFLOPS = 1.207      # FP64 FMA throughput of a GB300 measured by a DFMA probe (nominal 1.25)
 
 
 # DRAM traffic per launch of the banded F-apply kernel at the 64^3 benchmark size, from one ncu capture
@@ -86,7 +87,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to BENCH_CLOCKS_DIR (default: the system's temporary directory)
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
