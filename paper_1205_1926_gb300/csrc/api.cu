@@ -177,15 +177,21 @@ void build_item_list(tfeti_ctx* c, const std::vector<int>& plastic_count, int R,
     }
     if (it.count) items.push_back(it);
   }
+  // template items first, then the subdomains with their own records (each group by cost):
+  // a residual solve can start the first group while the own records are still being
+  // factorised (results do not depend on the order: every item writes its own subdomains)
+  std::vector<SolveItem> own;
   for (int p = 0; p < ns; ++p)
     if (plastic_count[p] > 0) {
       SolveItem it{};
       it.fac = kOwnFac | own_off(c, p);
       it.count = 1;
       it.sub[0] = p;
-      items.push_back(it);
+      own.push_back(it);
     }
   sort_items_by_cost(c, items);
+  sort_items_by_cost(c, own);
+  items.insert(items.end(), own.begin(), own.end());
 }
 
 // Items of the Dirichlet-preconditioner solves: elastic subdomains grouped R to a CTA
@@ -258,6 +264,8 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
     cudaMemcpyAsync(c->d_items_pl, pl.data(), sizeof(SolveItem) * pl.size(), cudaMemcpyHostToDevice, c->st);
   c->n_items = (int)c->h_items.size();
   c->n_items32 = (int)c->h_items32.size();
+  c->n_items_el = 0;
+  for (const SolveItem& it : c->h_items) c->n_items_el += (it.fac & kOwnFac) ? 0 : 1;
   c->g_inner_stale = true;
   if (c->dirichlet) {
     build_dir_item_list(c, plastic_count, R64, c->h_items_d);
@@ -308,6 +316,30 @@ cudaEvent_t timed_begin(tfeti_ctx* c, int kind) {
   c->ev_kind[c->ev_used / 2] = (uint8_t)kind;
   cudaEventRecord(c->ev_pool[c->ev_used++], c->st);
   return c->ev_pool[c->ev_used++];
+}
+
+// The context stream waits for a deferred refactorisation (no host wait).
+void join_factorisation(tfeti_ctx* c) {
+  if (!c->fac_pending) return;
+  cudaStreamWaitEvent(c->st, c->ev_fac_done, 0);
+  c->fac_pending = false;
+}
+
+// After the context stream has been synchronised past the join: the pivots' status and
+// the factorisation time of a deferred refactorisation.
+int check_factorisation(tfeti_ctx* c) {
+  if (!c->fac_check_pending) return TFETI_OK;
+  join_factorisation(c);
+  cudaStreamSynchronize(c->st_fac);
+  c->fac_check_pending = false;
+  if (c->fac_timed) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->fac_e0, c->fac_e1);
+    c->factor_ms += ms;
+    c->fac_timed = false;
+  }
+  if (*c->h_err_fac) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a subdomain factorisation");
+  return TFETI_OK;
 }
 
 void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
@@ -623,8 +655,12 @@ void collect_events(tfeti_ctx* c) {
   c->ev_used = 0;
 }
 
-int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
+int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bool defer = false) {
   const DevMesh& M = c->M;
+  {
+    const int fst = check_factorisation(c);   // a previous deferred one must be finished
+    if (fst != TFETI_OK) return fst;
+  }
   launch_return_map(M, du, c->sig, c->kap, c->dsig, c->dkap, c->plastic, nullptr, c->pa, c->pb, c->pn, c->st);
   cudaMemsetAsync(c->sub_np, 0, sizeof(int) * M.n_sub, c->st);
   GPData gd{c->dsig, c->pa, c->pb, c->pn, c->plastic};
@@ -665,6 +701,36 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out) {
     for (int p : list) max_rows = std::max(max_rows, c->h_subs[p].n_dof);
     launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band_ws, c->d_list_off, 0, max_rows,
                      c->plan.max_bw, c->st);
+    if (defer && !c->dirichlet) {
+      // factorise on st_fac; the residual solve joins before it reads an own record and
+      // the host checks the pivots after its next synchronisation (check_factorisation)
+      cudaEventRecord(c->ev_fac_fork, c->st);
+      cudaStreamWaitEvent(c->st_fac, c->ev_fac_fork, 0);
+      cudaMemsetAsync(c->d_err_fac, 0, sizeof(int), c->st_fac);
+      c->fac_timed = c->events;
+      if (c->fac_timed) cudaEventRecord(c->fac_e0, c->st_fac);
+      launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band_ws, c->d_list_fac, c->fac_own,
+                       c->d_err_fac, c->plan.max_bw, c->n_sm, c->st_fac);
+      if (c->fac_timed) cudaEventRecord(c->fac_e1, c->st_fac);
+      c->launches += 2;
+      c->factor_launches += 1;
+      if (c->precision == TFETI_PRECISION_MIXED) {
+        long long len = 0;
+        for (int p : list) len = std::max<long long>(len, c->plan.subs[p].fac_size);
+        launch_fac_to_f32(c->fac_own, c->fac32_own, c->d_list_fac, (int)list.size(), len, c->st_fac);
+        c->launches += 1;
+      }
+      cudaMemcpyAsync(c->h_err_fac, c->d_err_fac, sizeof(int), cudaMemcpyDeviceToHost, c->st_fac);
+      cudaEventRecord(c->ev_fac_done, c->st_fac);
+      c->fac_pending = c->fac_check_pending = true;
+      launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
+                      c->kbb32, 0, c->st);
+      launch_internal_force(M, c->dsig, df, c->f_full, c->st);
+      c->launches += 2;
+      if (f_out && f_out != c->f_full)
+        cudaMemcpyAsync(f_out, c->f_full, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
+      return cuda_check(c, "assemble");
+    }
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
     cudaEvent_t e0 = c->events ? c->fac_e0 : nullptr, e1 = c->events ? c->fac_e1 : nullptr;
     if (e0) cudaEventRecord(e0, c->st);
@@ -901,7 +967,23 @@ void residual_solve(tfeti_ctx* c, const double* f, const double* lam, double* r_
   a.dst = c->vsol;
   a.in_mode = 1;
   a.out_mode = 3;
-  timed_sub_solve(c, a);
+  if (c->fac_pending && c->n_items_el < c->n_items) {
+    // template items while the own records are factorised on st_fac, then the others; such a
+    // split pass is not among the timed F-apply passes (its span includes the factorisation)
+    SolveArgs e = a;
+    e.n_items = c->n_items_el;
+    launch_sub_solve(c->M, e, c->solve_smem, c->st);
+    join_factorisation(c);
+    SolveArgs o = a;
+    o.items = a.items + c->n_items_el;
+    o.n_items = c->n_items - c->n_items_el;
+    launch_sub_solve(c->M, o, c->solve_smem, c->st);
+    c->launches += 2;
+    c->f_split += 1;
+  } else {
+    join_factorisation(c);
+    timed_sub_solve(c, a);
+  }
   launch_contract(c->M, c->cbuf, r_out, c->st);
   c->launches += 1;
 }
@@ -1092,7 +1174,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   const auto t0 = std::chrono::steady_clock::now();
   const DevMesh& M = c->M;
   const long long m = M.n_mult;
-  const long long f_before = c->f_launches, f32_before = c->f32_launches;
+  const long long f_before = c->f_launches + c->f_split, f32_before = c->f32_launches;
   // e = -R^T f ; lambda_Im = N^T H e = -B R (H e)
   launch_G_apply(M, nullptr, f, c->ev, -1.0, c->st);
   launch_gemv(c->H, c->l, c->ev, 1.0, c->hx, c->st);
@@ -1101,6 +1183,10 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   // d~ = d - F lambda_Im = B K^+(f - B^T lambda_Im) ; r^0 = d~
   residual_solve(c, f, c->lam_im, c->r);
   const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
+  {
+    const int fst = check_factorisation(c);   // pivots of a deferred refactorisation
+    if (fst != TFETI_OK) return fst;
+  }
   cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
   bool v_current = true;   // vsol and r belong to lambda = lambda_Im + lambda_Ker
   int used_l0 = 0;
@@ -1206,7 +1292,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     info->iterations = it;
     info->converged = converged;
     info->used_lambda0 = used_l0;
-    info->f_applies = (int)(c->f_launches - f_before);
+    info->f_applies = (int)(c->f_launches + c->f_split - f_before);
     info->f32_applies = (int)(c->f32_launches - f32_before);
     info->outer_iterations = outer;
     info->r0_norm = r0;
@@ -1620,6 +1706,12 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   cudaEventCreate(&c->fac_e0);
   cudaEventCreate(&c->fac_e1);
   cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&c->st_fac, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&c->ev_fac_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_fac_done, cudaEventDisableTiming);
+  c->d_err_fac = dalloc<int>(c, 1);
+  if (cudaMallocHost(&c->h_err_fac, sizeof(int)) != cudaSuccess) throw std::bad_alloc();
+  *c->h_err_fac = 0;
   cudaStreamCreateWithFlags(&c->st_cap, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
@@ -1761,6 +1853,7 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (!c) return TFETI_OK;
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  if (c->st_fac) cudaStreamSynchronize(c->st_fac);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
@@ -1768,6 +1861,10 @@ int tfeti_destroy(tfeti_ctx* c) {
   destroy_inner_graph(c);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->st_fac) cudaStreamDestroy(c->st_fac);
+  if (c->ev_fac_fork) cudaEventDestroy(c->ev_fac_fork);
+  if (c->ev_fac_done) cudaEventDestroy(c->ev_fac_done);
+  if (c->h_err_fac) cudaFreeHost(c->h_err_fac);
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st_cap) cudaStreamDestroy(c->st_cap);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -1830,7 +1927,7 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
   int status = TFETI_OK;
   double nrm_old = 0.0;
   for (int i = 1; i <= newton_maxit; ++i) {
-    status = assemble(c, c->du, c->df, nullptr);
+    status = assemble(c, c->du, c->df, nullptr, true);
     if (status != TFETI_OK) break;
     if (c->mlp_on) launch_plastic_fraction(M, c->sub_np, c->pf_now, c->st);
     c->newton_idx = i;
@@ -1839,6 +1936,10 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
     tfeti_pcg_info pi{};
     status = dual_pcg(c, c->f_full, c->tn, nullptr, nullptr, pcg_rtol, pcg_maxit, &pi);
     c->newton_idx = 0;
+    {
+      const int fst = check_factorisation(c);   // no-op unless the solve ended before its join
+      if (status == TFETI_OK) status = fst;
+    }
     if (status != TFETI_OK) break;
     const double nd = std::sqrt(dot_host(c, c->tn, c->tn, n));
     launch_axpby(n, 1.0, c->du, 1.0, c->tn, c->du, c->st);

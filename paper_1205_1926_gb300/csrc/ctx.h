@@ -87,6 +87,16 @@ struct tfeti_ctx {
   int n_items_pl = 0;
   tfeti::SolveItem* d_items_s = nullptr;     // column items for forming S
   cudaStream_t st2 = nullptr;
+  // refactorisation of the plastic subdomains inside a load step runs on st_fac while the
+  // elastic items of the next residual solve run on st; st joins at ev_fac_done before the
+  // first item that reads an own record (fac_pending), the host checks the pivots afterwards
+  cudaStream_t st_fac = nullptr;
+  cudaEvent_t ev_fac_fork = nullptr, ev_fac_done = nullptr;
+  bool fac_pending = false, fac_check_pending = false, fac_timed = false;
+  int* d_err_fac = nullptr;
+  int* h_err_fac = nullptr;          // pinned
+  int n_items_el = 0;                // FP64 items on shape templates (they come first in d_items)
+  long long f_split = 0;             // FP64 passes split around a deferred refactorisation (untimed)
   cudaStream_t st_cap = nullptr;     // private stream used only to capture graphs
   // CUDA graph of the mixed-precision inner PCGP: a WHILE node whose body is one iteration
   cudaGraph_t g_inner = nullptr;
