@@ -16,7 +16,11 @@
  *   passes; the context owns everything it allocates and frees it in
  *   tfeti_destroy.  Null is accepted only where a parameter says "nullable".
  * - All device work of a context is enqueued on the CUDA stream given to
- *   tfeti_setup.  Calls that return host data synchronise that stream.
+ *   tfeti_setup (or tfeti_setup_case); the context also owns internal streams
+ *   that it joins to that stream before a call returns.  Calls that return
+ *   host data synchronise that stream.
+ * - A context is used by one host thread at a time; different contexts may be
+ *   used from different threads at once (ssn_time_step_cases does so).
  * - Floating point is IEEE binary64 throughout unless stated.
  *
  * Discretisation and layouts (all shared with the documentation of the CPU
