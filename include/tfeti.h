@@ -386,13 +386,18 @@ int tfeti_apply_K(tfeti_ctx* ctx, const double* x, double* y);
  * library holds until the process exits; it allocates nothing.
  * - Contexts with n_coarse > TFETI_NOALLOC_MAX_COARSE (more than 4096
  *   subdomains) are rejected with TFETI_ERR_ARG.
- * - The first call on a device resolves the array's device address with
- *   cudaGetSymbolAddress while that device is current; make that first call
- *   before any stream capture.
+ * - The call runs on the context's device (the device current at its set-up):
+ *   it makes that device current for its duration and then restores the
+ *   caller's current device.
+ * - The first call for a device resolves the array's device address on that
+ *   device with cudaGetSymbolAddress; make that first call before any stream
+ *   capture.
  * - All calls on a device share the array: calls whose kernels overlap on the
  *   GPU race.  Both work vectors are overwritten before they are read, so no
  *   clearing is needed between calls.
- * - Synchronises the context's stream. */
+ * - It waits for its kernels before it returns (it synchronises the context's
+ *   stream), and reports a failed launch or an earlier asynchronous fault on
+ *   that stream as TFETI_ERR_CUDA. */
 #define TFETI_NOALLOC_MAX_COARSE 24576
 int tfeti_apply_projector_noalloc(tfeti_ctx* ctx, const double* x, double* y);
 
@@ -421,6 +426,15 @@ int tfeti_timing_reset(tfeti_ctx* ctx, int32_t enable_events);
  * returns normally and *gave_up (host) is set to 1 (0 would mean the wait completed).
  * Nothing faults or hangs; the device stays usable.  cuda_stream: nullable. */
 int tfeti_check_bounded_wait(void* cuda_stream, int64_t limit_cycles, int32_t* gave_up);
+
+/* FP64 FMA throughput of the current device (no context needed; the paper has no
+ * counterpart: it is the roofline denominator of the FP64 kernels, whose
+ * arithmetic intensity lies above the FP64 ridge on this hardware).  Every thread
+ * of 4 CTAs x 256 threads per SM runs 8 independent FMA chains for `iters`
+ * iterations after a short warm-up launch; *tflops (host) = 16 x threads x iters /
+ * CUDA-event time of the launch, in TFLOP/s.  cuda_stream: nullable.  Errors:
+ * TFETI_ERR_ARG (iters < 1, null output), TFETI_ERR_CUDA. */
+int tfeti_measure_fp64_fma(void* cuda_stream, int32_t iters, double* tflops);
 
 #ifdef __cplusplus
 }

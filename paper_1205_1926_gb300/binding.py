@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 TFETI_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "non-positive pivot",
-          5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value"}
+          5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value",
+          9: "bounded device wait timed out"}
 PRECOND_NONE, PRECOND_LUMPED, PRECOND_DIRICHLET = 0, 1, 2
 MLP_PARAMS = 4801
 MAX_NEWTON = 64
@@ -109,6 +110,7 @@ SIGNATURES = {
     "tfeti_timing_get": (C.c_int, [_P, C.POINTER(Timing)]),
     "tfeti_timing_reset": (C.c_int, [_P, _I]),
     "tfeti_check_bounded_wait": (C.c_int, [_P, C.c_int64, C.POINTER(_I)]),
+    "tfeti_measure_fp64_fma": (C.c_int, [_P, _I, C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -391,6 +393,15 @@ def time_step_cases(ctxs, dfs, newton_tol, pcg_rtol, newton_maxit=30, pcg_maxit=
         msgs = "; ".join(f"case {k}: {lib.tfeti_last_error(c.h).decode()}" for k, c in enumerate(ctxs))
         raise TfetiError(st, f"ssn_time_step_cases: {msgs}")
     return [infos[k].as_dict() | {"status": st} for k in range(n)]
+
+
+def measure_fp64_fma(stream=None, iters=20000) -> float:
+    """FP64 FMA rate of the current device in TFLOP/s (``tfeti_measure_fp64_fma``)."""
+    out = C.c_double()
+    st = load().tfeti_measure_fp64_fma(_ptr_stream(stream), int(iters), C.byref(out))
+    if st != TFETI_OK:
+        raise TfetiError(st, "tfeti_measure_fp64_fma")
+    return out.value
 
 
 def _ptr_stream(stream):

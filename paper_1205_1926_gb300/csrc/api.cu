@@ -850,12 +850,10 @@ PcgOut pcg_core(tfeti_ctx* c, double* x, double* r, double tol_abs, int maxit, b
       break;
     }
   }
+  // the breakdown flag of the last iteration, read on the context stream
+  cudaMemcpyAsync(c->h_sc + 6, c->sc + 6, sizeof(double), cudaMemcpyDeviceToHost, c->st);
   sync(c);
-  if (o.status == TFETI_OK) {
-    double flag = 0.0;
-    cudaMemcpy(&flag, c->sc + 6, sizeof(double), cudaMemcpyDeviceToHost);
-    if (flag != 0.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
-  }
+  if (o.status == TFETI_OK && c->h_sc[6] != 0.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
   return o;
 }
 
@@ -1965,6 +1963,12 @@ int ssn_time_step(tfeti_ctx* c, const double* df, int32_t df_on_host, double new
       loc.converged = 1;
       break;
     }
+  }
+  {
+    // a refactorisation queued on st_fac by an assembly whose step then failed is joined here, so
+    // that no later call reads own factors (or the list buffers) while it may still run
+    const int fst = check_factorisation(c);
+    if (status == TFETI_OK) status = fst;
   }
   if (c->mlp_on) {
     cudaMemcpyAsync(c->mlp_dfprev, c->df, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);

@@ -55,42 +55,60 @@ int scratch_address(int device, double** out, std::string* why) {
   return TFETI_OK;
 }
 
+int fail_here(tfeti_ctx* c, int code, const std::string& msg) {
+  c->err = "tfeti_apply_projector_noalloc: " + msg;
+  return code;
+}
+
+// Makes the context's device current for the call and puts the caller's device back afterwards.
+struct DeviceScope {
+  int prev = -1;
+  bool switched = false;
+  cudaError_t enter(int device) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return e;
+    if (prev == device) return cudaSuccess;
+    e = cudaSetDevice(device);
+    switched = e == cudaSuccess;
+    return e;
+  }
+  ~DeviceScope() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 extern "C" int tfeti_apply_projector_noalloc(tfeti_ctx* c, const double* x, double* y) {
-  if (!c || !x || !y) {
-    if (c) c->err = "null argument";
-    return TFETI_ERR_ARG;
-  }
-  if (c->l > kMaxCoarse) {
-    c->err = "tfeti_apply_projector_noalloc: coarse size " + std::to_string(c->l) + " exceeds the static limit " +
-             std::to_string(kMaxCoarse) + " (6 x 4096 subdomains); use tfeti_apply_projector";
-    return TFETI_ERR_ARG;
-  }
-  int device = -1;
-  if (cudaGetDevice(&device) != cudaSuccess) {
+  if (!c) return TFETI_ERR_ARG;
+  if (!x || !y) return fail_here(c, TFETI_ERR_ARG, "null argument");
+  if (c->l > kMaxCoarse)
+    return fail_here(c, TFETI_ERR_ARG, "coarse size " + std::to_string(c->l) + " exceeds the static limit " +
+                                           std::to_string(kMaxCoarse) + " (6 x 4096 subdomains); use "
+                                           "tfeti_apply_projector");
+  // the scratch address and the launches belong to the context's device, whichever device the
+  // caller has current
+  DeviceScope scope;
+  cudaError_t e = scope.enter(c->device);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    c->err = "cudaGetDevice failed";
-    return TFETI_ERR_CUDA;
+    return fail_here(c, TFETI_ERR_CUDA, std::string("selecting the context's device: ") + cudaGetErrorString(e));
   }
   double* scratch = nullptr;
   std::string why;
-  const int st = scratch_address(device, &scratch, &why);
-  if (st != TFETI_OK) {
-    c->err = why;
-    return st;
-  }
+  const int st = scratch_address(c->device, &scratch, &why);
+  if (st != TFETI_OK) return fail_here(c, st, why);
   double* gx = scratch;
   double* hx = scratch + kMaxCoarse;
   tfeti::launch_G_apply(c->M, x, nullptr, gx, 1.0, c->st);
   tfeti::launch_gemv(c->H, c->l, gx, 1.0, hx, c->st);
   tfeti::launch_GT_update(c->M, x, 1.0, hx, -1.0, y, c->st);
   c->launches += 3;
-  cudaStreamSynchronize(c->st);
-  const cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();                  // launch errors of these three kernels
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
-    c->err = std::string("tfeti_apply_projector_noalloc: ") + cudaGetErrorString(e);
-    return TFETI_ERR_CUDA;
+    cudaGetLastError();
+    return fail_here(c, TFETI_ERR_CUDA, cudaGetErrorString(e));
   }
   return TFETI_OK;
 }

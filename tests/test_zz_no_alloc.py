@@ -24,6 +24,9 @@ import paper_1205_1926_gb300 as T  # noqa: E402
 
 @pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
 def test_projector_noalloc_matches_allocating_entry_point(w):
+    """Both entry points launch the same three kernels in the same order on the same inputs, so
+    their results are bitwise equal (the tolerance of the projector's parity tests, 1e-11, is
+    checked too, as the weaker statement)."""
     ctx = T.Context(w)
     m = ctx.sizes["n_mult"]
     for seed in (101, 102):
@@ -35,3 +38,21 @@ def test_projector_noalloc_matches_allocating_entry_point(w):
         a, b = y_static.cpu().numpy(), y_ref.cpu().numpy()
         assert np.isfinite(a).all()
         assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
+        assert torch.equal(y_static, y_ref)
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs a second GPU")
+def test_projector_noalloc_from_another_current_device():
+    """Called while another device is current, the call still runs on the context's device and
+    leaves the caller's current device as it was."""
+    w = W.SMALL6_RAGGED
+    ctx = T.Context(w)
+    m = ctx.sizes["n_mult"]
+    x = torch.as_tensor(W.seeded_vector(m, 103)).cuda(0)
+    y_ref = torch.zeros(m, dtype=torch.float64, device="cuda:0")
+    y_static = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda:0")
+    ctx.apply("projector", x, y_ref)
+    with torch.cuda.device(1):
+        ctx.apply_projector_noalloc(x, y_static)
+        assert torch.cuda.current_device() == 1
+    assert torch.equal(y_static, y_ref)
