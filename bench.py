@@ -7,15 +7,19 @@ load steps; eps_PCGP = 1e-8 (dual relative residual), eps_Newton = 1e-6.
 
 One bench step = one load step (ssn_time_step): every Newton iteration runs the
 return mapping, the tangent assembly, the subdomain factorisations, the PCGP
-dual solve with its F-applies and projections, and the recovery.  Warm-up steps
-are the first W load steps of the history; the K timed steps continue it (beyond
-step 20 the ramp continues at the same rate).  Inputs (factors 2.5 GB) are larger
-than L2, so no flush is needed between steps.
+dual solve with its F-applies and projections, and the recovery.  The K timed steps
+are load steps 1..K of the ramp (K = 20: the whole ramp; beyond step 20 the load
+would keep rising at the same rate).  The W warm-up steps run before them on the same
+context as a coarser ramp to the same final load (0 -> 1.5 t_y in W steps, so the
+plastic code paths and pools are warm) and are discarded: the state is reset to zero
+and the start history and network restart.  Inputs (factors 2.5 GB) are larger than
+L2, so no flush is needed between steps.
 
-Arms: default = the CUDA path; ``--impl reference`` = the FP64 CPU oracle on a
-bounded sample of the same workload (see ``oracle_sample``).  For N > 1 (torchrun)
-each rank solves an independent replica of the workload (weak scaling; the solver
-itself runs on one GPU).
+Arms: default = the CUDA path; ``--impl reference`` = the FP64 CPU oracle: one full
+Newton iteration of load step 1 timed live (single core, and concurrently on every core),
+scaled by the oracle's Newton iterations per step (see ``oracle_newton_sample``).  For
+N > 1 (torchrun) each rank solves an independent replica of the workload (weak
+scaling; the solver itself runs on one GPU).
 """
 from __future__ import annotations
 
@@ -36,12 +40,12 @@ import workloads as W  # noqa: E402
 
 METRIC = "time per load step @1e-8 dual res: FP64 vs mixed+learned; F-apply % HBM peak"
 UNIT = "s/load_step"
-FP64_PEAK_TFLOPS = 1.207      # FP64 FMA throughput of a GB300 measured by a DFMA probe (nominal 1.25)
+FP64_NOMINAL_TFLOPS = 1.25    # GB300 FP64 rate as published; the roofline uses the rate measured in the run
 
 
 # DRAM traffic per launch of the banded F-apply kernel at the 64^3 benchmark size, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_cube64_bench.md gives the command).
-# Valid only while the kernel source is the one measured.
+# (dram__bytes_read.sum + dram__bytes_write.sum; the launch-list summary under profiles/ gives the
+# command).  Valid only while the kernel source is the one measured.
 MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.32e6,
                                     "src": "paper_1205_1926_gb300/csrc/kernels_band.cu",
                                     "sha256": "01eefbee3c6566592055bea6187a029d8672e1baf076a248e4ff1e348cfe3f00"}}
@@ -60,6 +64,23 @@ def measured_traffic(kernel, workload):
     return rec["bytes"]
 
 
+def algorithmic_fapply(w):
+    """Algorithmic FP64 work and bytes of one banded F-apply: for every box its factor of n (bw + 1)
+    entries (n dofs, half bandwidth bw of the lexicographic order), read by a forward and a backward
+    sweep at 2 flops per entry; bytes as stored (8 per entry and sweep)."""
+    entries = 0
+    for k in range(len(w.cuts[2]) - 1):
+        for j in range(len(w.cuts[1]) - 1):
+            for i in range(len(w.cuts[0]) - 1):
+                ax = w.cuts[0][i + 1] - w.cuts[0][i]
+                ay = w.cuts[1][j + 1] - w.cuts[1][j]
+                az = w.cuts[2][k + 1] - w.cuts[2][k]
+                n = 3 * (ax + 1) * (ay + 1) * (az + 1)
+                bw = 3 * ((ax + 1) * (ay + 1) + (ax + 1) + 1) + 2
+                entries += n * (bw + 1)
+    return {"flops": 4.0 * entries, "bytes": 16.0 * entries, "factor_entries": entries}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -75,7 +96,9 @@ def workload_config(w, steps, warmup, precond="lumped"):
                         f"{w.n_steps}-step {sched}{w.load_factor} x first-yield x-traction on z=1",
             "newton_tol": w.newton_tol, "pcg_rtol": w.pcg_rtol, "preconditioner": precond,
             "kdag": "fixing-node banded Cholesky (shared elastic factor per box shape)",
-            "load_steps_timed": f"{warmup + 1}..{warmup + steps}",
+            "load_steps_timed": f"1..{steps} of the {w.n_steps}-step schedule",
+            "warmup": f"{warmup} load steps of a coarser ramp to the schedule's peak load on the same context, "
+                      "then the state reset to zero (discarded)",
             "l2": "inputs larger than L2 (subdomain factors 2.5 GB), no flush"}
 
 
@@ -129,75 +152,84 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------------- oracle
-def oracle_sample(w, n_sub_sample=32, n_pcg_sample=2):
-    """Time the FP64 oracle on a bounded sample of the workload (single BLAS thread).
+def oracle_newton_sample(w):
+    """Time one full Newton iteration of the FP64 oracle on load step 1 of the workload.
 
-    Sample: Algorithm 5 and the fixing-node factorisation for ``n_sub_sample`` of the
-    subdomains (scaled to all of them), and ``n_pcg_sample`` full PCGP iterations over all
-    subdomains (F-apply, two projections, lumped preconditioner).  Returns per-component
-    seconds; the model set-up (mesh, B, R, N N^T) is excluded like the GPU's set-up.
+    The sample is the body of Algorithm 4 once, on every subdomain: Algorithm 5 (return map and
+    tangent assembly), the fixing-node factorisations and the coarse matrix (the solver set-up),
+    Algorithm 3 to eps_PCGP with its recovery, and the Newton update; then the commit (the return
+    map at the increment).  The model's mesh, B and R set-up is excluded like the GPU's set-up.
+    The first-yield traction comes from the oracle's record of this workload when it has one.
     """
     import numpy as np
-    from oracle.decomp import FixingNodeInverse
     from oracle.ssn import ElastoplasticModel
     model = ElastoplasticModel(w)
-    n_sub = model.dec.n_sub
-    subset = list(range(0, n_sub, max(1, n_sub // n_sub_sample)))[:n_sub_sample]
-    f1 = model.traction_load(w.traction_dir)
+    t_y = None
+    rec_path = os.path.join(ROOT, "tests", "golden", "cube64_oracle_record.json")
+    if w.name == "cube64_8x8x8" and os.path.exists(rec_path):
+        with open(rec_path) as fh:
+            t_y = json.load(fh)["t_y"]
+    if t_y is None:
+        t_y = model.first_yield_traction(rtol=1e-10)
+    df = w.load_fractions()[0] * t_y * model.traction_load(w.traction_dir)
     du = np.zeros(model.dec.n_dof)
     t0 = time.perf_counter()
-    Kb_sub, _, _ = model.assemble(du, f1, subdomains=set(subset))
-    t_asm = (time.perf_counter() - t0) * n_sub / len(subset)
-    t0 = time.perf_counter()
-    for K, p in zip(Kb_sub, subset):
-        FixingNodeInverse(K, model.fixing[p])
-    t_fac = (time.perf_counter() - t0) * n_sub / len(subset)
-    # a full operator for the PCGP sample: the elastic factor of one box shape repeated
-    kd0 = FixingNodeInverse(Kb_sub[0], model.fixing[subset[0]])
-    solver = model.tfeti([Kb_sub[0]] * n_sub, kdag=[kd0] * n_sub)
-    rng = np.random.default_rng(0)
-    r = rng.standard_normal(model.dec.m)
-    t0 = time.perf_counter()
-    for _ in range(n_pcg_sample):
-        wv = solver.project(r)
-        z = solver.apply_precond(wv)
-        y = solver.project(z)
-        solver.apply_F(y)
-    t_pcg = (time.perf_counter() - t0) / n_pcg_sample
-    t0 = time.perf_counter()
-    solver.apply_F(r)
-    t_fapply = time.perf_counter() - t0
-    return {"assembly_s": t_asm, "factor_s": t_fac, "pcg_iter_s": t_pcg, "f_apply_s": t_fapply, "cores": 1,
-            "sample": f"Algorithm 5 + fixing-node Cholesky on {len(subset)} of {n_sub} subdomains (scaled), "
-                      f"{n_pcg_sample} PCGP iterations over all {n_sub} subdomains; 1 BLAS thread"}
+    K_blocks, f, _ = model.assemble(du, df)
+    t1 = time.perf_counter()
+    solver = model.tfeti(K_blocks)
+    t2 = time.perf_counter()
+    sol = solver.solve(f, rtol=w.pcg_rtol, maxit=w.pcg_maxit)
+    du_new = du + sol["u"]
+    np.linalg.norm(du_new - du) / (np.linalg.norm(du_new) + np.linalg.norm(du))
+    t3 = time.perf_counter()
+    model.return_map(du_new)
+    t4 = time.perf_counter()
+    return {"newton_s": t3 - t0, "assembly_s": t1 - t0, "setup_s": t2 - t1, "solve_s": t3 - t2,
+            "commit_s": t4 - t3, "pcg_iterations": sol["iterations"], "cores": 1}
 
 
 THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
               "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+SAMPLE_KEYS = ("newton_s", "assembly_s", "setup_s", "solve_s", "commit_s")
+
+
+def _single_thread_env():
+    env = dict(os.environ)
+    for k in THREAD_ENV:
+        env[k] = "1"
+    return env
 
 
 def oracle_sample_subprocess(workload_name):
-    """Run oracle_sample in a fresh interpreter whose BLAS/OpenMP pools are limited to one thread."""
-    env = dict(os.environ)
-    for k in THREAD_ENV:
-        env[k] = "1"
+    """oracle_newton_sample in a fresh interpreter whose BLAS/OpenMP pools hold one thread."""
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name],
-                       env=env, capture_output=True, text=True, check=True)
+                       env=_single_thread_env(), capture_output=True, text=True, check=True)
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample_all_cores(workload_name, n_proc=None):
-    """The same sample run as n_proc concurrent single-thread oracle processes (one per host core):
-    their mean per-process result is the oracle's speed per core with every core busy (shared memory
-    bandwidth and caches included).  Dividing a step's time by n_proc estimates the oracle with its
-    subdomain-local work split over all cores, the parallelism of Sec. 4.3 (the coarse problem and the
-    reductions would not split that well, so this is a lower bound on its time)."""
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def oracle_sample_all_cores(workload_name, n_proc=None, bytes_per_proc=8e9):
+    """The same sample run as concurrent single-thread oracle processes, one per host core (fewer if
+    host memory would not hold them): their mean is the oracle's time per core with every core busy.
+    Dividing a step's time by the process count estimates the oracle with its subdomain work split
+    over all cores (the parallelism of Sec. 4.3); the coarse problem and the reductions would not
+    split that well, so this is a lower bound on its time."""
     n_proc = n_proc or os.cpu_count() or 1
-    env = dict(os.environ)
-    for k in THREAD_ENV:
-        env[k] = "1"
+    avail = _mem_available_bytes()
+    if avail is not None:
+        n_proc = max(1, min(n_proc, int(0.8 * avail // bytes_per_proc)))
     procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload_name],
-                              env=env, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                              env=_single_thread_env(), stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
              for _ in range(n_proc)]
     outs = []
     for pr in procs:
@@ -206,25 +238,46 @@ def oracle_sample_all_cores(workload_name, n_proc=None):
             outs.append(json.loads(out.strip().splitlines()[-1]))
     if not outs:
         return None
-    keys = ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s")
-    mean = {k: statistics.mean(o[k] for o in outs) for k in keys}
-    return mean | {"cores": len(outs)}
+    return {k: statistics.mean(o[k] for o in outs) for k in SAMPLE_KEYS} | {"cores": len(outs)}
 
 
-def oracle_step_estimate(s, newton_per_step, pcg_per_step):
-    """Seconds per load step: per Newton iteration assembly + factorisation + 3 set-up/recovery
-    F-applies, plus the PCGP iterations, with the given iteration counts."""
-    return newton_per_step * (s["assembly_s"] + s["factor_s"] + 3 * s["f_apply_s"]) + pcg_per_step * s["pcg_iter_s"]
+def oracle_step_seconds(s, newton_per_step):
+    """Seconds per load step: Newton iterations per step x one full Newton iteration, plus the commit.
+    Every Newton solve of the 64^3 ramp takes about the same number of PCGP iterations (24-25 in the
+    oracle's record of all 20 steps), so a Newton iteration costs about the same in every step."""
+    return newton_per_step * s["newton_s"] + s["commit_s"]
 
 
-def oracle_record_counts(first, last):
+def oracle_record_newton(first, last):
     path = os.path.join(ROOT, "tests", "golden", "cube64_oracle_record.json")
     with open(path) as fh:
         rec = json.load(fh)
     steps = [s for s in rec["steps"] if first <= s["step"] <= last] or rec["steps"]
-    newton = statistics.mean(s["newton"] for s in steps)
-    pcg = statistics.mean(sum(s["pcg"]) for s in steps)
-    return newton, pcg, f"oracle record, load steps {steps[0]['step']}..{steps[-1]['step']}"
+    return statistics.mean(s["newton"] for s in steps), f"oracle record, load steps {steps[0]['step']}..{steps[-1]['step']}"
+
+
+def cpu_baseline_line(w, newton_per_step, counts_src, all_cores=True):
+    """The oracle timed live on this host: one full Newton iteration (single core, then every core at
+    once), scaled to a load step with the given Newton iterations per step."""
+    s = oracle_sample_subprocess(w.name)
+    v = oracle_step_seconds(s, newton_per_step)
+    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one full Newton iteration of load step 1 (Algorithm 5 on all {w.n_sub} subdomains, "
+                     f"their fixing-node factorisations and the coarse matrix, Algorithm 3 to eps_PCGP = "
+                     f"{w.pcg_rtol:g} ({s['pcg_iterations']} PCGP iterations) and the recovery) plus the commit, "
+                     f"timed live on one core with one BLAS thread; x {newton_per_step:.2f} Newton iterations "
+                     f"per load step ({counts_src})",
+           "components_s": {k: s[k] for k in SAMPLE_KEYS}, "pcg_iterations_in_sample": s["pcg_iterations"]}
+    if all_cores:
+        sa = oracle_sample_all_cores(w.name)
+        if sa is not None:
+            va = oracle_step_seconds(sa, newton_per_step)
+            out["all_cores"] = {"value": va / sa["cores"], "unit": UNIT, "cores": sa["cores"],
+                                "per_core_step_s": va, "components_s": {k: sa[k] for k in SAMPLE_KEYS},
+                                "kind": "oracle, one single-thread process per core running the same sample",
+                                "note": "per-core step time with every core busy / cores = the oracle with its "
+                                        "subdomain work split over all cores (a lower bound)"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -233,31 +286,19 @@ def run_reference(args, rank, world):
     w = W.CUBE64
     t_start = time.perf_counter()
     try:
-        newton, pcg, src = oracle_record_counts(args.warmup + 1, args.warmup + args.steps)
+        newton, src = oracle_record_newton(1, args.steps)
     except (OSError, ValueError, KeyError):
-        newton, pcg, src = None, None, None
-    s = oracle_sample_subprocess(w.name)
-    if newton is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration-count record missing"}))
         return
-    v = oracle_step_estimate(s, newton, pcg)
-    sa = oracle_sample_all_cores(w.name) if args.oracle_all_cores else None
-    elapsed = time.perf_counter() - t_start
+    cb = cpu_baseline_line(w, newton, src, all_cores=not args.no_all_cores)
+    cb["wall_s"] = time.perf_counter() - t_start
+    v = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, args.steps, args.warmup),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
-                             "sample": s["sample"] + f"; iteration counts per step from the {src} "
-                                                     f"(Newton {newton:.2f}, PCGP {pcg:.1f})",
-                             "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s")},
-                             "wall_s": elapsed},
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    if sa is not None:
-        va = oracle_step_estimate(sa, newton, pcg)
-        line["cpu_baseline"]["all_cores"] = {"value": va / sa["cores"], "unit": UNIT, "cores": sa["cores"],
-                                             "per_core_step_s": va,
-                                             "kind": "oracle, one single-thread process per core"}
     print(json.dumps(line))
 
 
@@ -317,7 +358,6 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
 
     w = W.WORKLOADS[args.workload]
-    n_total = args.warmup + args.steps
     stream = torch.cuda.Stream(device=dev)
     pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
     main_arm = resolve_arm(args)
@@ -345,11 +385,13 @@ def run_gpu(args, rank, world, local_rank):
             c.set_recycling(min(args.history, 7))
             c.set_learned(True)
 
+    fp64_peak = T.measure_fp64_fma(stream)           # roofline denominator of the FP64 kernels
     ctx = make_ctx(main_arm)
     n = ctx.sizes["n_dof"]
     t_y = ctx.first_yield_traction(w.traction_dir, rtol=1e-10)
     reset_start(ctx, main_arm)
-    fr = w.load_fractions(n_total)
+    fr = w.load_fractions(args.steps)               # timed: load steps 1..K of the schedule
+    peak_level = max(abs(a) for a in w.load_fractions())
     dfs, prev = [], 0.0
     with torch.cuda.stream(stream):
         for a in fr:
@@ -357,13 +399,32 @@ def run_gpu(args, rank, world, local_rank):
             ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), d)
             dfs.append(d)
             prev = a
+        # warm-up increment: W equal steps from 0 to the schedule's largest load level
+        df_warm = torch.zeros(n, dtype=torch.float64, device=dev)
+        ctx.traction_load(tuple(peak_level / max(args.warmup, 1) * t_y * c for c in w.traction_dir), df_warm)
+        zero_u = torch.zeros(n, dtype=torch.float64, device=dev)
+        zero_s = torch.zeros(6 * ctx.sizes["n_gp"], dtype=torch.float64, device=dev)
+        zero_k = torch.zeros(ctx.sizes["n_gp"], dtype=torch.float64, device=dev)
     stream.synchronize()
 
-    def timed_run(c, headline=False):
-        """Warm-up steps, then the K timed steps (inputs resident in HBM, CUDA events on the context
+    def warm_up(c, arm, on_host=None):
+        """W load steps of the coarse warm-up ramp, then back to the zero state with the start
+        history and the network restarted: the timed steps see warm pools, tuned F-apply and loaded
+        code but nothing of the warm-up's solutions."""
+        for _ in range(args.warmup):
+            if on_host is not None:
+                c.time_step(on_host.data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit,
+                            df_on_host=True)
+            else:
+                c.time_step(df_warm, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        c.set_state(u=zero_u, sigma=zero_s, kappa=zero_k)
+        reset_start(c, arm)
+        torch.cuda.synchronize()
+
+    def timed_run(c, arm, headline=False):
+        """Warm-up, then load steps 1..K timed (inputs resident in HBM, CUDA events on the context
         stream, max over ranks); u after every step is kept for the comparisons made afterwards."""
-        for k in range(args.warmup):
-            c.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        warm_up(c, arm)
         snaps = torch.zeros((args.steps, n), dtype=torch.float64, device=dev)
         infos = []
         sampler = ClockSampler(local_rank) if headline else None
@@ -374,9 +435,9 @@ def run_gpu(args, rank, world, local_rank):
         c.timing_reset(headline)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for k in range(args.warmup, n_total):
+        for k in range(args.steps):
             infos.append(c.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
-            c.get_state(u=snaps[k - args.warmup])
+            c.get_state(u=snaps[k])
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -385,7 +446,7 @@ def run_gpu(args, rank, world, local_rank):
         return {"elapsed": elapsed, "infos": infos, "snaps": snaps, "tm": c.timing(), "clocks": clocks,
                 "tuning": c.tuning() if hasattr(c, "tuning") else None}
 
-    main = timed_run(ctx, headline=True)
+    main = timed_run(ctx, main_arm, headline=True)
     ctx.close()
 
     # ---- end-to-end pass of the headline arm through the C ABI with host (pinned) buffers, on a fresh
@@ -393,15 +454,14 @@ def run_gpu(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         ce = make_ctx(main_arm)
-        for k in range(args.warmup):
-            ce.time_step(dfs[k], w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
         dfs_h = [d.cpu().pin_memory() for d in dfs]
+        warm_up(ce, main_arm, on_host=df_warm.cpu().pin_memory())
         u_host = torch.zeros(n, dtype=torch.float64).pin_memory()
         u_dev = torch.zeros(n, dtype=torch.float64, device=dev)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.warmup, n_total):
+        for k in range(args.steps):
             ce.time_step(dfs_h[k].data_ptr(), w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit, df_on_host=True)
             ce.get_state(u=u_dev)
             with torch.cuda.stream(stream):
@@ -422,7 +482,7 @@ def run_gpu(args, rank, world, local_rank):
             if arm == main_arm:
                 continue
             c = make_ctx(arm)
-            runs[arm] = timed_run(c)
+            runs[arm] = timed_run(c, arm)
             c.close()
     ref = runs.get("fp64")
 
@@ -440,35 +500,37 @@ def run_gpu(args, rank, world, local_rank):
     # F-apply kernels: the banded K^+ solves (k_sub_solve: every F-apply of the FP64 arm, the residual
     # solves of the mixed arms) and, with --fapply schur, the FP64 dual-Schur DGEMM.  The roofline object
     # describes the one with the larger share of the headline arm's device time; the other sits beside it.
+    # Both are FP64-FMA-bound on this GPU (0.25 flop/B against a ridge of fp64 / hbm ~ 0.18 flop/B), so the
+    # peak is the FP64 FMA rate measured in this run.
+    algo = algorithmic_fapply(w)
     avg_f_ms = tm["f_apply_ms_total"] / max(tm["f_apply_launches"], 1)
-    flops = tm["f_apply_flops"]
-    byts = tm["f_apply_bytes"]
-    achieved_tf = flops / (avg_f_ms * 1e-3) / 1e12 if avg_f_ms > 0 else None
-    achieved_gbs = byts / (avg_f_ms * 1e-3) / 1e9 if avg_f_ms > 0 else None
-    banded = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None,
-              "traffic": measured_traffic("k_sub_solve", w.name),
+    achieved_tf = algo["flops"] / (avg_f_ms * 1e-3) / 1e12 if avg_f_ms > 0 else None
+    traffic = measured_traffic("k_sub_solve", w.name)
+    dram_gbs = traffic / (avg_f_ms * 1e-3) / 1e9 if (traffic and avg_f_ms > 0) else None
+    peak_kind = (f"FP64 FMA rate measured in this run (tfeti_measure_fp64_fma); nominal {FP64_NOMINAL_TFLOPS}")
+    banded = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+              "frac": achieved_tf / fp64_peak if achieved_tf else None,
+              "traffic": traffic,
               "kernel": "k_sub_solve (banded forward/backward substitution with the factor records, FP64)",
-              "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25",
-              "total_ms": tm["f_apply_ms_total"], "launches": tm["f_apply_launches"],
-              "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": pk["hbm_gbs"],
-                      "frac": achieved_gbs / pk["hbm_gbs"] if achieved_gbs else None,
-                      "bytes_per_launch": byts, "flops_per_launch": flops, "avg_launch_ms": avg_f_ms,
-                      "of": f"{pk_kind} hbm_gbs"}}
+              "peak_kind": peak_kind,
+              "algorithmic": algo | {"note": "per launch: every subdomain's banded factor n (bw + 1) entries, "
+                                             "2 flops per entry and right-hand side, forward and backward sweep"},
+              "total_ms": tm["f_apply_ms_total"], "launches": tm["f_apply_launches"], "avg_launch_ms": avg_f_ms,
+              "executed_flops_per_launch": tm["f_apply_flops"],
+              "hbm": {"dram_gbs": dram_gbs, "peak_gbs": pk["hbm_gbs"],
+                      "frac": dram_gbs / pk["hbm_gbs"] if dram_gbs else None,
+                      "of": f"{pk_kind} hbm_gbs; DRAM bytes per launch from the ncu capture (traffic): the "
+                            "shared elastic factor record stays in L2, so HBM does not bound this kernel"}}
     schur = None
     if tm["schur_launches"] > 0 and tm["schur_ms_total"] > 0:
         s_tf = tm["schur_flops_total"] / (tm["schur_ms_total"] * 1e-3) / 1e12
-        s_gbs = tm["schur_bytes_total"] / (tm["schur_ms_total"] * 1e-3) / 1e9
-        schur = {"bound": "alu", "achieved": s_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": s_tf / FP64_PEAK_TFLOPS, "traffic": None,
+        schur = {"bound": "alu", "achieved": s_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "frac": s_tf / fp64_peak, "traffic": None,
                  "kernel": "k_schur_dgemm (+ gather): Y = X S with the shape's FP64 dual Schur block",
-                 "peak_kind": "measured FP64 FMA throughput (DFMA probe); nominal 1.25",
+                 "peak_kind": peak_kind,
                  "total_ms": tm["schur_ms_total"], "launches": tm["schur_launches"],
-                 "hbm": {"achieved_gbs": s_gbs, "peak_gbs": pk["hbm_gbs"], "frac": s_gbs / pk["hbm_gbs"],
-                         "bytes_per_launch": tm["schur_bytes_total"] / tm["schur_launches"],
-                         "flops_per_launch": tm["schur_flops_total"] / tm["schur_launches"],
-                         "avg_launch_ms": tm["schur_ms_total"] / tm["schur_launches"],
-                         "of": f"{pk_kind} hbm_gbs; bytes: the shared S (L2-resident) and X, Y"}}
+                 "flops_per_launch": tm["schur_flops_total"] / tm["schur_launches"],
+                 "avg_launch_ms": tm["schur_ms_total"] / tm["schur_launches"]}
     if schur is not None and schur["total_ms"] >= banded["total_ms"]:
         roof, other = dict(schur), banded
     else:
@@ -517,24 +579,10 @@ def run_gpu(args, rank, world, local_rank):
         line["speedup_vs_fp64"] = line["fp64_value"] / value
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cube64_8x8x8":
         counts = fp64_run if fp64_run is not None else main
-        s = oracle_sample_subprocess(w.name)
-        v = oracle_step_estimate(s, statistics.mean(x["newton"] for x in counts["infos"]),
-                                 statistics.mean(sum(x["pcg"]) for x in counts["infos"]))
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
-                                "sample": s["sample"] + "; scaled with the FP64 arm's Newton/PCGP counts per step "
-                                                        "(the oracle runs Algorithm 3 as printed)",
-                                "components_s": {k: s[k] for k in ("assembly_s", "factor_s", "pcg_iter_s",
-                                                                   "f_apply_s")}}
-        if args.oracle_all_cores:
-            sa = oracle_sample_all_cores(w.name)
-            if sa is not None:
-                va = oracle_step_estimate(sa, statistics.mean(x["newton"] for x in counts["infos"]),
-                                          statistics.mean(sum(x["pcg"]) for x in counts["infos"]))
-                line["cpu_baseline"]["all_cores"] = {
-                    "value": va / sa["cores"], "unit": UNIT, "cores": sa["cores"], "per_core_step_s": va,
-                    "kind": "oracle, one single-thread process per core",
-                    "note": "the same sample run concurrently on every core; per-core step time / cores = the "
-                            "oracle with its subdomain work split over all cores (lower bound)"}
+        newton = statistics.mean(x["newton"] for x in counts["infos"])
+        line["cpu_baseline"] = cpu_baseline_line(w, newton, "the FP64 arm's Newton iterations per step: the "
+                                                            "oracle runs the same Algorithm 4",
+                                                 all_cores=not args.no_all_cores)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -672,7 +720,7 @@ def run_cases(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=17)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -697,8 +745,8 @@ def main():
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
                     help="cube64_8x8x8 is the benchmark; smaller cases exist for profiler captures")
-    ap.add_argument("--oracle-all-cores", action="store_true",
-                    help="also time the oracle sample on every host core at once (cpu_baseline.all_cores)")
+    ap.add_argument("--no-all-cores", action="store_true",
+                    help="skip timing the oracle sample on every host core at once (cpu_baseline.all_cores)")
     ap.add_argument("--cases", type=int, default=0,
                     help="N > 0: N load cases on one mesh stepped concurrently (case contexts), one JSON line")
     ap.add_argument("--case-set", default="directions", choices=["directions", "seeded"],
@@ -706,7 +754,7 @@ def main():
                          "direction drawn per case")
     args = ap.parse_args()
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(W.WORKLOADS[args.oracle_sample])))
+        print(json.dumps(oracle_newton_sample(W.WORKLOADS[args.oracle_sample])))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

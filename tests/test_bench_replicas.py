@@ -48,11 +48,23 @@ def test_single_process_is_identity():
 
 
 def test_oracle_sample_on_several_cores_tiny_workload():
-    """The all-core oracle timing runs the same bounded sample in one single-thread process per core
-    and averages their component times (2 processes on a 2-subdomain case here)."""
+    """The all-core oracle timing runs the same sample (one full Newton iteration of load step 1) in one
+    single-thread process per core and averages their times (2 processes on a 2-subdomain case here);
+    a load step is Newton iterations x that iteration plus the commit."""
     s = bench.oracle_sample_all_cores("tiny2_1x1x2", n_proc=2)
     assert s is not None and s["cores"] == 2
-    for k in ("assembly_s", "factor_s", "pcg_iter_s", "f_apply_s"):
+    for k in bench.SAMPLE_KEYS:
         assert s[k] > 0.0
-    v = bench.oracle_step_estimate(s, 2.0, 10.0)
-    assert v == pytest.approx(2.0 * (s["assembly_s"] + s["factor_s"] + 3 * s["f_apply_s"]) + 10.0 * s["pcg_iter_s"])
+    assert s["newton_s"] >= s["assembly_s"] + s["setup_s"]
+    v = bench.oracle_step_seconds(s, 2.5)
+    assert v == pytest.approx(2.5 * s["newton_s"] + s["commit_s"])
+
+
+def test_algorithmic_fapply_counts_band_entries():
+    """One 8^3 box: 2187 dofs, half bandwidth 275 -> 2187 x 276 entries, 4 flops and 16 bytes each."""
+    import workloads as W
+    w = W.cube("one_box", 8, 1)
+    a = bench.algorithmic_fapply(w)
+    assert a["factor_entries"] == 2187 * 276
+    assert a["flops"] == 4.0 * 2187 * 276 and a["bytes"] == 16.0 * 2187 * 276
+    assert bench.algorithmic_fapply(W.CUBE64)["factor_entries"] == 512 * 2187 * 276

@@ -207,3 +207,45 @@ CUBE80_IRREGULAR = irregular_cube(80, 0, newton_tol=1e-6, pcg_rtol=1e-8)
 CUBE24_IRREGULAR = irregular_cube(24, 3, n_steps=4)
 WORKLOADS[CUBE80_IRREGULAR.name] = CUBE80_IRREGULAR
 WORKLOADS[CUBE24_IRREGULAR.name] = CUBE24_IRREGULAR
+
+
+def box_dof_offsets(w: Workload) -> list:
+    """Start of each box's block in the decomposed dof vector (boxes in x-fastest order, three dofs per
+    node of a box of (ax+1)(ay+1)(az+1) nodes), plus the total as the last entry."""
+    sx, sy, sz = (len(c) - 1 for c in w.cuts)
+    off = [0]
+    for k in range(sz):
+        for j in range(sy):
+            for i in range(sx):
+                ax = w.cuts[0][i + 1] - w.cuts[0][i]
+                ay = w.cuts[1][j + 1] - w.cuts[1][j]
+                az = w.cuts[2][k + 1] - w.cuts[2][k]
+                off.append(off[-1] + 3 * (ax + 1) * (ay + 1) * (az + 1))
+    return off
+
+
+def seeded_partly_plastic_increment(w: Workload, seed: int, n_hot: int, hot_scale: float = 1.2e-3,
+                                    cold_scale: float = 1e-5):
+    """Seeded displacement increment whose strains exceed first yield only in a few boxes.
+
+    Every decomposed dof draws N(0, (s h)^2) with h the smallest element edge: s = hot_scale in
+    ``n_hot`` boxes picked by the seed (strains of about 1e-3: from a zero state about half of their
+    Gauss points lie beyond first yield with the Sec. 5 material) and s = cold_scale elsewhere (far
+    below yield).  Returns the vector and the sorted list of hot boxes.
+    """
+    import numpy as np
+    off = box_dof_offsets(w)
+    n_sub = len(off) - 1
+    rng = np.random.default_rng(seed)
+    hot = np.sort(rng.choice(n_sub, size=min(n_hot, n_sub), replace=False))
+    h = min(l / n for l, n in zip(w.length, w.nel))
+    du = rng.standard_normal(off[-1]) * (cold_scale * h)
+    for p in hot:
+        du[off[p]:off[p + 1]] *= hot_scale / cold_scale
+    return du, [int(p) for p in hot]
+
+
+def seeded_indices(n: int, k: int, seed: int):
+    """k distinct indices in [0, n), sorted, drawn by the seed (sampled outputs of full-size checks)."""
+    import numpy as np
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
