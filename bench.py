@@ -321,7 +321,7 @@ def replica_value(elapsed_max, steps, world):
 
 
 # --------------------------------------------------------------------------------------- CUDA path
-ARMS = ("fp64", "mixed", "mixed_history", "mixed_learned")
+ARMS = ("fp64", "mixed", "mixed_history", "mixed_learned", "mixed_history_bf16")
 ARM_NOTES = {
     "fp64": "Algorithm 3 in FP64 (banded K^+ applies), the paper's method",
     "mixed": "FP64-refined PCGP: FP32 dual Schur blocks on the tensor cores (elastic) and FP32 banded solves "
@@ -330,6 +330,8 @@ ARM_NOTES = {
                      "solver's last 8 solutions, zero-start fallback",
     "mixed_learned": "the mixed arm with the learned start: the last 7 solutions plus the per-interface MLP "
                      "prediction (trained online on the solver's own lambda histories) as Galerkin vectors",
+    "mixed_history_bf16": "the mixed_history arm with the dual Schur blocks of the inner F-apply stored in BF16 "
+                          "(X split into BF16 hi/lo, FP32 accumulation) instead of TF32 x 3",
 }
 
 
@@ -368,18 +370,20 @@ def run_gpu(args, rank, world, local_rank):
             c.set_fapply(True)
         if arm != "fp64":
             c.set_precision(True, args.inner_rtol)
-        if arm == "mixed_history":
+        if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
         if arm == "mixed_learned":
             c.set_recycling(min(args.history, 7))
             c.set_learned(True)
+        if arm != "fp64" and (arm.endswith("_bf16") or args.schur_format == "bf16"):
+            c.set_schur_format(True)
         if args.no_graphs:
             c.set_graphs(False)
         return c
 
     def reset_start(c, arm):
         # the history and the network start over (the first-yield solve must not seed them)
-        if arm == "mixed_history":
+        if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
         if arm == "mixed_learned":
             c.set_recycling(min(args.history, 7))
@@ -613,7 +617,9 @@ def run_cases(args, rank, world, local_rank):
     def start(c):
         if arm != "fp64":
             c.set_precision(True, args.inner_rtol)
-        if arm == "mixed_history":
+            if arm.endswith("_bf16") or args.schur_format == "bf16":
+                c.set_schur_format(True)
+        if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
         if arm == "mixed_learned":
             c.set_recycling(min(args.history, 7))
@@ -735,6 +741,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="time the headline arm only (no other arms)")
     ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
+    ap.add_argument("--schur-format", default="tf32x3", choices=["tf32x3", "bf16"],
+                    help="operand format of the inner F-apply's dual Schur blocks in every mixed arm")
     ap.add_argument("--precond", default="lumped", choices=["lumped", "dirichlet"],
                     help="PCGP preconditioner of Sec. 4.2 (every arm)")
     ap.add_argument("--learned", action="store_true",

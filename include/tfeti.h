@@ -328,6 +328,26 @@ int tfeti_mlp_train(tfeti_ctx* ctx, const double* la, const double* lb, const do
 #define TFETI_FAPPLY_SCHUR  1
 int tfeti_set_fapply(tfeti_ctx* ctx, int32_t mode);
 
+/* Operand format of the inner (FP32) F-apply's dual Schur blocks in the mixed mode
+ * (an extension; F = B K^+ B^T of eq. (equ:sps3) applied to the subdomains on their
+ * shape's elastic tangent as Y = X S on the tensor cores, FP32 accumulation).
+ * TF32X3 (default): S and X split into TF32 hi/lo parts, three MMAs per step (FP32
+ * accuracy).  BF16: S stored once in BF16 (half the bytes of one FP32 copy), X split
+ * into BF16 hi/lo, two MMAs per step; the product then carries S's BF16 rounding
+ * (~4e-3 relative) and the FP64 refinement of the mixed mode takes correspondingly
+ * more outer passes.  Requires TFETI_PRECISION_MIXED (else TFETI_ERR_ARG); the BF16
+ * tiles are formed at the first switch (a case context shares its base's); the inner
+ * F-apply's threshold is tuned again.  Errors: TFETI_ERR_ARG, TFETI_ERR_OOM. */
+#define TFETI_SCHUR_TF32X3 0
+#define TFETI_SCHUR_BF16   1
+int tfeti_set_schur_format(tfeti_ctx* ctx, int32_t format);
+/* Overrides the autotuned choice of the inner F-apply in the mixed mode: shapes with at
+ * least `threshold` subdomains (and a formed dual Schur block, i.e. at least 4) apply
+ * it on the tensor cores, the others run FP32 banded solves; a later change of the
+ * Schur operand format keeps it.  threshold = 0 tunes again by timing (and lets the
+ * format change re-tune).  Requires TFETI_PRECISION_MIXED (else TFETI_ERR_ARG). */
+int tfeti_set_schur_threshold(tfeti_ctx* ctx, int32_t threshold);
+
 /* Autotuner of the mixed mode's inner F-apply (run when the mixed mode is switched on):
  * shapes with at least kSchurMinCount = 4 subdomains form their dual Schur block; a
  * shape applies it (one tensor-core GEMM over its elastic subdomains) only if it has at
@@ -430,8 +450,8 @@ int tfeti_check_bounded_wait(void* cuda_stream, int64_t limit_cycles, int32_t* g
 /* FP64 FMA throughput of the current device (no context needed; the paper has no
  * counterpart: it is the roofline denominator of the FP64 kernels, whose
  * arithmetic intensity lies above the FP64 ridge on this hardware).  Every thread
- * of 4 CTAs x 256 threads per SM runs 8 independent FMA chains for `iters`
- * iterations after a short warm-up launch; *tflops (host) = 16 x threads x iters /
+ * of 4 CTAs x 256 threads per SM runs 16 independent FMA chains for `iters`
+ * iterations after a short warm-up launch; *tflops (host) = 32 x threads x iters /
  * CUDA-event time of the launch, in TFLOP/s.  cuda_stream: nullable.  Errors:
  * TFETI_ERR_ARG (iters < 1, null output), TFETI_ERR_CUDA. */
 int tfeti_measure_fp64_fma(void* cuda_stream, int32_t iters, double* tflops);

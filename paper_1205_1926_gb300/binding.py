@@ -91,6 +91,8 @@ SIGNATURES = {
     "tfeti_set_precision": (C.c_int, [_P, _I, _D]),
     "tfeti_set_graphs": (C.c_int, [_P, _I]),
     "tfeti_set_fapply": (C.c_int, [_P, _I]),
+    "tfeti_set_schur_format": (C.c_int, [_P, _I]),
+    "tfeti_set_schur_threshold": (C.c_int, [_P, _I]),
     "tfeti_get_tuning": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_recycling": (C.c_int, [_P, _I]),
     "tfeti_set_learned": (C.c_int, [_P, _I, _I, _D]),
@@ -336,6 +338,14 @@ class Context:
     def set_fapply(self, schur: bool):
         """FP64 F-apply of elastic subdomains by their shape's dual Schur block (DGEMM) or banded solves."""
         return self._check(self.lib.tfeti_set_fapply(self.h, 1 if schur else 0), "tfeti_set_fapply")
+
+    def set_schur_format(self, bf16: bool):
+        """Inner Schur apply of the mixed mode with BF16 S (two MMAs per step) or TF32 x 3 (default)."""
+        return self._check(self.lib.tfeti_set_schur_format(self.h, 1 if bf16 else 0), "tfeti_set_schur_format")
+
+    def set_schur_threshold(self, threshold: int):
+        """Shapes with >= threshold subdomains use their Schur block in the inner F-apply (0: tune)."""
+        return self._check(self.lib.tfeti_set_schur_threshold(self.h, int(threshold)), "tfeti_set_schur_threshold")
 
     def tuning(self) -> dict:
         t, n = C.c_int32(), C.c_int32()

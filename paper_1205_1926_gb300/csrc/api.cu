@@ -394,7 +394,7 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
 // With the shapes' dual Schur blocks formed, subdomains on the elastic template are
 // applied as one FP32 GEMM per shape while the subdomains with plastic points run
 // their FP32 banded solves concurrently on the second stream.
-void op_F32(tfeti_ctx* c, const double* x, double* yv) {
+void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract = true) {
   SolveArgs a = solve_args(c, true);
   a.lam = x;
   a.cbuf = c->cbuf;
@@ -417,15 +417,21 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv) {
       const int cnt = c->el_cnt[sh];
       if (!cnt) continue;
       const int n_bd = 3 * c->plan.shapes[sh].n_bnd;
-      launch_schur_gather(c->M, c->d_el + c->el_off[sh], cnt, n_bd, x, c->Xhi, c->Xlo, c->st);
-      launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, c->Xhi, c->Xlo,
-                                c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh], c->cbuf, c->d_err, c->st);
+      const bool bf = c->schur_bf16;
+      launch_schur_gather(c->M, c->d_el + c->el_off[sh], cnt, n_bd, bf, x, c->Xhi, c->Xlo, c->st);
+      const void* s_hi = bf ? static_cast<const void*>(static_cast<const unsigned char*>(c->Sbf) + 2 * c->s_tile_off[sh])
+                            : static_cast<const void*>(c->Shi + c->s_tile_off[sh]);
+      launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, bf, schur_splits(cnt, n_bd, c->n_sm),
+                                c->Xhi, c->Xlo, s_hi, c->Slo + c->s_tile_off[sh], c->s_part, c->s_count, c->cbuf,
+                                c->d_err, c->st);
       c->launches += 2;
     }
     if (c->n_items_pl > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
   }
-  launch_contract(c->M, c->cbuf, yv, c->st);
-  c->launches += 1;
+  if (contract) {
+    launch_contract(c->M, c->cbuf, yv, c->st);
+    c->launches += 1;
+  }
   c->f32_launches += 1;
 }
 
@@ -454,13 +460,27 @@ int form_schur_blocks(tfeti_ctx* c) {
     a.S64 = c->S64;
     a.s_off = c->s_off_c[sh];
     launch_sub_solve(c->M, a, c->solve_smem, c->st);
-    launch_schur_tile_S(c->S32 + c->s_off_c[sh], n_bd, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
+    launch_schur_tile_S(c->S32 + c->s_off_c[sh], n_bd, false, c->Shi + c->s_tile_off[sh], c->Slo + c->s_tile_off[sh],
                         c->st);
     c->launches += 2;
     sync(c);
   }
   c->schur_ready = true;
   return cuda_check(c, "forming dual Schur blocks");
+}
+
+// Per-context work space of the tensor-core Schur apply: the gathered operand tiles and the
+// split-K partial tiles and counters (each context's own: case contexts run concurrently).
+void alloc_schur_work(tfeti_ctx* c, int max_bd) {
+  const int ns = (int)c->h_subs.size();
+  const long long x_tiles = schur_x_tile_elems(ns, max_bd);
+  c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+  c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
+  c->X64 = dalloc<double>(c, (size_t)ns * (size_t)std::max(1, max_bd));
+  c->s_part = dalloc<float>(c, (size_t)std::max(1LL, schur_part_floats(ns, max_bd, 2)));
+  const int tiles = std::max(1, schur_tiles(ns, max_bd));
+  c->s_count = dalloc<int>(c, (size_t)tiles);
+  cudaMemsetAsync(c->s_count, 0, sizeof(int) * tiles, c->st);
 }
 
 // The shapes' dual Schur blocks in FP32 (tensor-core tiles) and FP64, formed once.
@@ -482,10 +502,7 @@ int ensure_schur(tfeti_ctx* c) {
     for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh)
       if (c->schur_formed[sh]) max_bd = std::max(max_bd, 3 * c->plan.shapes[sh].n_bnd);
     try {
-      const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
-      c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-      c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-      c->X64 = dalloc<double>(c, (size_t)c->h_subs.size() * (size_t)std::max(1, max_bd));
+      alloc_schur_work(c, max_bd);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
@@ -510,16 +527,13 @@ int ensure_schur(tfeti_ctx* c) {
       c->s_off_c[sh] = s_tot;
       s_tot += (long long)n_bd * n_bd;
       c->s_tile_off[sh] = s_tiles;
-      s_tiles += schur_s_tile_floats(n_bd);
+      s_tiles += schur_s_tile_elems(n_bd);
     }
     c->S32 = dalloc<float>(c, (size_t)std::max(1LL, s_tot));
     c->S64 = dalloc<double>(c, (size_t)std::max(1LL, s_tot));
     c->Shi = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
     c->Slo = dalloc<float>(c, (size_t)std::max(1LL, s_tiles));
-    const long long x_tiles = schur_x_tile_floats((int)c->h_subs.size(), max_bd);
-    c->Xhi = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-    c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
-    c->X64 = dalloc<double>(c, (size_t)c->h_subs.size() * (size_t)std::max(1, max_bd));
+    alloc_schur_work(c, max_bd);
   } catch (const std::bad_alloc&) {
     return fail(c, TFETI_ERR_OOM, "device allocation failed");
   }
@@ -527,7 +541,35 @@ int ensure_schur(tfeti_ctx* c) {
   return form_schur_blocks(c);
 }
 
-void op_F32(tfeti_ctx* c, const double* x, double* yv);
+// The BF16 copy of the shapes' S tiles (formed once from the FP32 blocks; a case context
+// shares its base's).
+int ensure_schur_bf16(tfeti_ctx* c) {
+  if (c->Sbf) return TFETI_OK;
+  if (c->base) {
+    const int st = ensure_schur_bf16(c->base);
+    if (st != TFETI_OK) return fail(c, st, c->base->err);
+    c->Sbf = c->base->Sbf;
+    return TFETI_OK;
+  }
+  long long s_tiles = 0;
+  for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh)
+    if (c->schur_formed[sh]) s_tiles = std::max(s_tiles, c->s_tile_off[sh] + schur_s_tile_elems(3 * c->plan.shapes[sh].n_bnd));
+  try {
+    c->Sbf = dalloc<uint16_t>(c, (size_t)std::max(1LL, s_tiles));
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed");
+  }
+  for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
+    if (!c->schur_formed[sh]) continue;
+    launch_schur_tile_S(c->S32 + c->s_off_c[sh], 3 * c->plan.shapes[sh].n_bnd, true,
+                        static_cast<unsigned char*>(c->Sbf) + 2 * c->s_tile_off[sh], nullptr, c->st);
+    c->launches += 1;
+  }
+  sync(c);
+  return cuda_check(c, "forming BF16 Schur tiles");
+}
+
+void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract);
 
 // Autotuner of the inner F-apply: a shape uses its dual Schur block (one tensor-core
 // GEMM over its elastic subdomains) only if it has at least T subdomains, the others
@@ -864,21 +906,22 @@ void destroy_inner_graph(tfeti_ctx* c) {
   c->g_inner = nullptr;
 }
 
-// One PCGP iteration on x = dlt, r = rin with FP32 F-applies and device-side scalars;
-// the last kernel sets the WHILE condition `h` of the enclosing graph node.
-void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h) {
+// One PCGP iteration on x = dlt, r = rin with FP32 F-applies and device-side scalars.  The
+// dot products and scalar steps ride in the kernels that produce their vectors (w, y, F p),
+// and the last kernel closes the body run; inside a graph (has_h) it also sets the WHILE
+// condition `h` of the enclosing node.
+void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h, bool has_h) {
   const long long m = c->M.n_mult;
-  op_project32(c, c->rin, c->w);                                 // w = P r
-  op_precond32(c, c->w, c->z);                                   // z = F^-1 w
-  op_project32(c, c->z, c->y);                                   // y = P z
-  launch_dot2(c->w, c->w, c->y, c->w, m, c->partial, c->sc + kWW, c->sc + kYW, c->st);
-  launch_pcg_pre(c->sc, c->st);
-  launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);             // p = y + beta p
-  op_F32(c, c->pdir, c->Fp);                                     // F p
-  launch_dot(c->pdir, c->Fp, m, c->partial, c->sc + kPFP, c->st);
-  launch_pcg_mid(c->sc, c->st);
-  launch_lam_r_update_g(m, c->pdir, c->Fp, c->dlt, c->rin, c->sc, c->st);
-  launch_pcg_post(c->sc, h, c->st);
+  launch_G32_gemv32(c->M, c->H32, c->l, c->rin, c->gx, c->hx, c->hx8, c->st);
+  launch_GT32_dot(c->M, c->rin, c->hx8, c->w, nullptr, 0, c->sc, c->partial, c->d_ctr, c->st);   // w = P r, w.w
+  op_precond32(c, c->w, c->z);                                                                   // z = F^-1 w
+  launch_G32_gemv32(c->M, c->H32, c->l, c->z, c->gx, c->hx, c->hx8, c->st);
+  launch_GT32_dot(c->M, c->z, c->hx8, c->y, c->w, 1, c->sc, c->partial, c->d_ctr + 1, c->st);  // y = P z, y.w
+  launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);                                           // p = y + beta p
+  op_F32(c, c->pdir, c->Fp, false);                                                              // slots of F p
+  launch_contract_dot(c->M, c->cbuf, c->Fp, c->pdir, c->sc, c->partial, c->d_ctr + 2, c->st);  // F p, p.Fp
+  launch_lam_r_update_post(m, c->pdir, c->Fp, c->dlt, c->rin, c->sc, c->d_ctr + 3, h, has_h ? 1 : 0, c->st);
+  c->launches += 8;
 }
 
 int build_inner_graph(tfeti_ctx* c) {
@@ -910,7 +953,7 @@ int build_inner_graph(tfeti_ctx* c) {
   }
   cudaStream_t saved = c->st;
   c->st = c->st_cap;
-  enqueue_inner_iteration(c, (unsigned long long)h);
+  enqueue_inner_iteration(c, (unsigned long long)h, true);
   c->st = saved;
   cudaGraph_t captured = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->st_cap, &captured);
@@ -950,6 +993,30 @@ PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
   if (h[kStatus] == 7.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
   if (h[kStatus] == 8.0) o.status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
   const int st = cuda_check(c, "inner PCGP graph");
+  if (st != TFETI_OK) o.status = st;
+  return o;
+}
+
+// The same inner PCGP launched body by body from the host (no graph): the host reads the
+// device scalars after every body run; used when graphs are off, e.g. for profilers, which
+// do not see into conditional graph bodies.
+PcgOut pcg_inner_eager(tfeti_ctx* c, double tol_abs, int maxit) {
+  PcgOut o;
+  launch_pcg_init(c->sc, tol_abs * tol_abs, maxit, c->st);
+  for (int run = 0; run < 2 * maxit + 4; ++run) {
+    enqueue_inner_iteration(c, 0ULL, false);
+    c->f32_launches += 1;
+    cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, c->st);
+    sync(c);
+    if (c->h_sc[kDone] != 0.0) break;
+  }
+  const double* hs = c->h_sc;
+  o.it = (int)hs[kIter];
+  o.w_norm = std::sqrt(std::max(0.0, hs[kLastWW]));
+  o.converged = hs[kStopAfter] != 0.0 ? 1 : 0;
+  if (hs[kStatus] == 7.0) o.status = fail(c, TFETI_ERR_BREAKDOWN, "p^T F p <= 0 in PCGP");
+  if (hs[kStatus] == 8.0) o.status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
+  const int st = cuda_check(c, "inner PCGP");
   if (st != TFETI_OK) o.status = st;
   return o;
 }
@@ -1229,7 +1296,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         cudaMemcpyAsync(c->rin, c->w, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
         const double tol_in = std::max(c->inner_rtol * wn, 0.5 * rtol * r0);
         PcgOut in = c->use_graphs ? pcg_inner_graph(c, tol_in, std::min(maxit - it, 1000))
-                                  : pcg_core(c, c->dlt, c->rin, tol_in, std::min(maxit - it, 1000), true);
+                                  : pcg_inner_eager(c, tol_in, std::min(maxit - it, 1000));
         it += in.it;
         ++outer;
         if (in.status != TFETI_OK) {
@@ -1562,7 +1629,9 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->f_full = dalloc<double>(c, P.n_dof);
   c->tn = dalloc<double>(c, P.n_dof);
   c->tn2 = dalloc<double>(c, P.n_dof);
-  c->partial = dalloc<double>(c, 2 * kRedBlocks);   // two interleaved reductions (launch_dot2)
+  c->partial = dalloc<double>(c, std::max(2 * kRedBlocks, kFusedBlocks));   // launch_dot2, fused inner kernels
+  c->d_ctr = dalloc<int>(c, 4);                                              // arrival counters of the fused kernels
+  cudaMemsetAsync(c->d_ctr, 0, sizeof(int) * 4, c->st);
   c->sc = dalloc<double>(c, kNumScalars);
   c->d_err = dalloc<int>(c, 1);
   if (cudaMallocHost(&c->h_sc, kNumScalars * sizeof(double)) != cudaSuccess) throw std::bad_alloc();
@@ -2067,6 +2136,41 @@ int tfeti_set_fapply(tfeti_ctx* c, int32_t mode) {
   }
   c->fapply = mode;
   return cuda_check(c, "tfeti_set_fapply");
+}
+
+int tfeti_set_schur_format(tfeti_ctx* c, int32_t format) {
+  if (!c || (format != TFETI_SCHUR_TF32X3 && format != TFETI_SCHUR_BF16))
+    return fail(c, TFETI_ERR_ARG, "bad Schur operand format");
+  if (c->precision != TFETI_PRECISION_MIXED) return fail(c, TFETI_ERR_ARG, "the Schur operand format needs the mixed mode");
+  if (format == TFETI_SCHUR_BF16) {
+    const int st = ensure_schur_bf16(c);
+    if (st != TFETI_OK) return st;
+  }
+  const bool bf = format == TFETI_SCHUR_BF16;
+  if (bf != c->schur_bf16) {
+    c->schur_bf16 = bf;
+    c->g_inner_stale = true;
+    if (!c->schur_manual) {
+      const int st = tune_schur_threshold(c);   // the faster BF16 apply may move the threshold
+      if (st != TFETI_OK) return st;
+    }
+  }
+  return cuda_check(c, "tfeti_set_schur_format");
+}
+
+int tfeti_set_schur_threshold(tfeti_ctx* c, int32_t threshold) {
+  if (!c || threshold < 0) return fail(c, TFETI_ERR_ARG, "bad Schur threshold");
+  if (c->precision != TFETI_PRECISION_MIXED) return fail(c, TFETI_ERR_ARG, "the Schur threshold needs the mixed mode");
+  c->schur_manual = threshold != 0;
+  if (threshold == 0) return tune_schur_threshold(c);
+  const size_t nsh = c->plan.shapes.size();
+  std::vector<int> count(nsh, 0);
+  for (const SubDev& sd : c->h_subs) ++count[sd.shape];
+  c->schur_threshold = threshold;
+  for (size_t sh = 0; sh < nsh; ++sh) c->schur_use[sh] = c->schur_formed[sh] && count[sh] >= threshold;
+  build_items(c, c->h_np.size() == c->h_subs.size() ? c->h_np : std::vector<int>(c->h_subs.size(), 0));
+  c->g_inner_stale = true;
+  return cuda_check(c, "tfeti_set_schur_threshold");
 }
 
 int tfeti_get_tuning(tfeti_ctx* c, int32_t* schur_threshold, int32_t* n_schur_shapes, float* tune_ms) {

@@ -76,9 +76,16 @@ struct tfeti_ctx {
   int n_items_pl64 = 0;
   double g_ms = 0.0, g_flops = 0.0, g_bytes = 0.0;
   long long g_launches = 0;
-  // tensor-core operand tiles (TF32 hi/lo parts): S per shape at s_tile_off[shape],
-  // the gathered interface vectors of one shape's elastic subdomains
+  // tensor-core operand tiles (TF32 hi/lo parts): S per shape at s_tile_off[shape] (elements),
+  // the gathered interface vectors of one shape's elastic subdomains (TF32 hi/lo, or BF16
+  // hi/lo in the same buffers); Sbf: the BF16 copy of the S tiles (same element offsets),
+  // formed when the BF16 format is first chosen
   float *Shi = nullptr, *Slo = nullptr, *Xhi = nullptr, *Xlo = nullptr;
+  void* Sbf = nullptr;
+  bool schur_bf16 = false;                   // inner Schur apply with BF16 S (else TF32 x 3)
+  bool schur_manual = false;                 // threshold set by tfeti_set_schur_threshold (no re-tuning)
+  float* s_part = nullptr;                   // split-K partial tiles of the Schur apply
+  int* s_count = nullptr;                    // split-K arrival counters (zero between launches)
   std::vector<long long> s_tile_off;
   bool schur_ready = false;
   int* d_el = nullptr;                       // elastic subdomains grouped by shape
@@ -168,6 +175,7 @@ struct tfeti_ctx {
   float* hx8 = nullptr;              // FP32 H g padded to 8 per subdomain (FP32 projector)
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;
+  int* d_ctr = nullptr;                      // arrival counters of the fused inner-iteration kernels
   int* d_err = nullptr;
   int max_copy = 0;
   // timing

@@ -168,19 +168,26 @@ void launch_schur_gather64(const DevMesh& M, const int* sub_list, int n_list, in
 void launch_schur_dgemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* X,
                                 const double* S, double* cbuf, cudaStream_t st);
 // Dual Schur block applied to the elastic subdomains of one shape on the tensor
-// cores (3xTF32): X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k]
-// (0 off the interface), split into TF32 hi/lo tiles; then cbuf at the interface
-// slots = (X S)[k][i].  S tiles (hi/lo) are formed once from the FP32 block S32
-// (S32[j * n_bd + i] = S[i][j]).  err: bit 4 set if a bounded wait gives up.
+// cores: X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k] (0 off the
+// interface), split into hi/lo tiles (TF32 floats, or BF16 halves with bf16); then
+// cbuf at the interface slots = (X S)[k][i].  S tiles (TF32 hi/lo, or one BF16 copy)
+// are formed once from the FP32 block S32 (S32[j * n_bd + i] = S[i][j]).  With
+// splits > 1 the K range is split across CTAs whose partial tiles meet in `part`
+// (schur_part_floats) through the per-tile counters `count` (2 x schur_tiles ints,
+// zero at the first launch; each launch leaves them zero).  err: bit 4 set if a
+// bounded wait gives up.
 int schur_nk(int n_bd);
-long long schur_x_tile_floats(int n_list, int n_bd);   // floats of each of Xhi, Xlo
-long long schur_s_tile_floats(int n_bd);               // floats of each of Shi, Slo
-void launch_schur_tile_S(const float* S32, int n_bd, float* Shi, float* Slo, cudaStream_t st);
-void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, float* Xhi,
-                         float* Xlo, cudaStream_t st);
-void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* Xhi,
-                               const float* Xlo, const float* Shi, const float* Slo, double* cbuf, int* err,
-                               cudaStream_t st);
+int schur_tiles(int n_list, int n_bd);
+int schur_splits(int n_list, int n_bd, int n_sm);
+long long schur_x_tile_elems(int n_list, int n_bd);   // elements of each of Xhi, Xlo
+long long schur_s_tile_elems(int n_bd);               // elements of each of Shi, Slo (Slo unused with BF16)
+long long schur_part_floats(int n_list, int n_bd, int splits);
+void launch_schur_tile_S(const float* S32, int n_bd, bool bf16, void* Shi, void* Slo, cudaStream_t st);
+void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, const double* lam,
+                         void* Xhi, void* Xlo, cudaStream_t st);
+void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
+                               const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
+                               int* count, double* cbuf, int* err, cudaStream_t st);
 // dst[i] = (float) src[i], i < n.
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 // FP32 copies of factor records (offsets in entries, same for both pools)
@@ -257,6 +264,21 @@ enum PcgScalar {
 void launch_pcg_init(double* sc, double tol2, int maxit, cudaStream_t st);
 void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, long long n,
                  double* partial, double* out1, double* out2, cudaStream_t st);
+// Fused kernels of the graph-driven inner iteration (grid kFusedBlocks; each dot is summed by the
+// block that arrives last, in block order; ctr: one zeroed int per kernel, left zero; partial:
+// kFusedBlocks doubles).  GT32_dot: out = x - G^T h8 and sc[kWW] = out.out (mode 0) or
+// sc[kYW] = out.v plus the stop test (mode 1).  contract_dot: Fp = B cbuf, sc[kPFP] = p.Fp plus
+// the breakdown test.  lam_r_update_post: the guarded updates, then the body run is closed and,
+// with has_h, the WHILE condition h set.  G32_gemv32: gx = G x and hx = H32 gx (+ padded hx8).
+constexpr int kFusedBlocks = 608;
+void launch_G32_gemv32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
+                       float* hx8, cudaStream_t st);
+void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
+                     double* sc, double* partial, int* ctr, cudaStream_t st);
+void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,
+                         double* partial, int* ctr, cudaStream_t st);
+void launch_lam_r_update_post(long long n, const double* p, const double* Fp, double* lam, double* r, double* sc,
+                              int* ctr, unsigned long long h, int has_h, cudaStream_t st);
 void launch_pcg_pre(double* sc, cudaStream_t st);
 void launch_pcg_mid(double* sc, cudaStream_t st);
 void launch_pcg_post(double* sc, unsigned long long cond_handle, cudaStream_t st);

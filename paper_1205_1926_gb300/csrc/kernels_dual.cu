@@ -411,8 +411,8 @@ __global__ void k_dot2_final(const double* partial, int nparts, double* out1, do
   }
 }
 
-__global__ void k_pcg_pre(double* sc) {
-  if (threadIdx.x || blockIdx.x || sc[kDone] != 0.0) return;
+__device__ void pcg_pre_logic(double* sc) {
+  if (sc[kDone] != 0.0) return;
   const double ww = sc[kWW], yw = sc[kYW];
   sc[kLastWW] = ww;
   if (!isfinite(ww) || !isfinite(yw)) {
@@ -428,16 +428,16 @@ __global__ void k_pcg_pre(double* sc) {
   sc[kStopAfter] = ww <= sc[kTol2] ? 1.0 : 0.0;
 }
 
-__global__ void k_pcg_mid(double* sc) {
-  if (threadIdx.x || blockIdx.x || sc[kDone] != 0.0) return;
+__device__ void pcg_mid_logic(double* sc) {
+  if (sc[kDone] != 0.0) return;
   if (!(sc[kPFP] > 0.0)) {
     sc[kDone] = 1.0;
     sc[kStatus] = 7.0;
   }
 }
 
-__global__ void k_pcg_post(double* sc, cudaGraphConditionalHandle h) {
-  if (threadIdx.x || blockIdx.x) return;
+// Closes one body run; returns whether the WHILE loop goes on.
+__device__ bool pcg_post_logic(double* sc) {
   sc[kBodyRuns] += 1.0;
   if (sc[kDone] == 0.0) {
     sc[kYWPrev] = sc[kYW];
@@ -445,8 +445,135 @@ __global__ void k_pcg_post(double* sc, cudaGraphConditionalHandle h) {
     sc[kFirst] = 0.0;
     if (sc[kStopAfter] != 0.0 || sc[kIter] >= sc[kMaxit]) sc[kDone] = 1.0;
   }
-  const bool more = sc[kDone] == 0.0 && sc[kBodyRuns] < 2.0 * sc[kMaxit] + 4.0;
+  return sc[kDone] == 0.0 && sc[kBodyRuns] < 2.0 * sc[kMaxit] + 4.0;
+}
+
+__global__ void k_pcg_pre(double* sc) {
+  if (threadIdx.x || blockIdx.x) return;
+  pcg_pre_logic(sc);
+}
+
+__global__ void k_pcg_mid(double* sc) {
+  if (threadIdx.x || blockIdx.x) return;
+  pcg_mid_logic(sc);
+}
+
+__global__ void k_pcg_post(double* sc, cudaGraphConditionalHandle h) {
+  if (threadIdx.x || blockIdx.x) return;
+  const bool more = pcg_post_logic(sc);
   cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Fused kernels of the graph-driven inner PCGP iteration.  Each folds a dot product
+// (and the scalar step that follows it) into the kernel that produces the vector:
+// every block writes its partial sum, and the block that arrives last (counted with
+// one atomic per block) sums the partials in block order, so the result is the same
+// whichever block finishes last; that block resets its counter for the next launch.
+// The grid is fixed (kFusedBlocks, grid-stride loops), which fixes the summation order.
+// ---------------------------------------------------------------------------
+__device__ bool grid_sum_last(double s, double* partial, int* ctr, double* red, double* total) {
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    is_last = atomicAdd(ctr, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + i);
+  t = block_reduce_sum(t, red);
+  if (threadIdx.x == 0) {
+    *total = t;
+    *ctr = 0;
+  }
+  return true;   // *total valid in thread 0
+}
+
+// out = x - G^T h (FP32 padded values, h8 the padded FP32 coarse vector) with the fused
+// dot: mode 0 -> sc[kWW] = out.out (w = P r); mode 1 -> sc[kYW] = out.v (y = P z, v = w),
+// then the stop test of the iteration (pcg_pre).
+__global__ void k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x,
+                           const float* __restrict__ h8, double* out, const double* __restrict__ v, int mode,
+                           double* sc, double* partial, int* ctr) {
+  __shared__ double red[32];
+  const float4* g4 = reinterpret_cast<const float4*>(GTv8);
+  const float4* h4 = reinterpret_cast<const float4*>(h8);
+  double acc = 0.0;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M.n_mult;
+       row += (long long)gridDim.x * blockDim.x) {
+    const long long e0 = M.gt_ptr[row], e1 = M.gt_ptr[row + 1];
+    double s = 0.0;
+    for (long long e = e0; e < e1; ++e) {
+      const int q = __ldg(M.gt_p + e);
+      const float4 a = __ldg(g4 + 2 * e), b = __ldg(g4 + 2 * e + 1);
+      const float4 u = __ldg(h4 + 2 * q), w = __ldg(h4 + 2 * q + 1);
+      const float t = a.x * u.x + a.y * u.y + a.z * u.z + a.w * u.w + b.x * w.x + b.y * w.y;
+      s += double(t);
+    }
+    const double o = x[row] - s;
+    out[row] = o;
+    acc += o * (mode == 0 ? o : v[row]);
+  }
+  acc = block_reduce_sum(acc, red);
+  double tot = 0.0;
+  if (grid_sum_last(acc, partial, ctr, red, &tot) && threadIdx.x == 0) {
+    if (mode == 0) {
+      sc[kWW] = tot;
+    } else {
+      sc[kYW] = tot;
+      pcg_pre_logic(sc);
+    }
+  }
+}
+
+// Fp = B cbuf with the fused dot sc[kPFP] = p.Fp, then the breakdown test (pcg_mid).
+__global__ void k_contract_dot(DevMesh M, const double* __restrict__ cbuf, double* Fp, const double* __restrict__ p,
+                               double* sc, double* partial, int* ctr) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M.n_mult;
+       row += (long long)gridDim.x * blockDim.x) {
+    const double y = b_at_row(M, cbuf, row);
+    Fp[row] = y;
+    acc += p[row] * y;
+  }
+  acc = block_reduce_sum(acc, red);
+  double tot = 0.0;
+  if (grid_sum_last(acc, partial, ctr, red, &tot) && threadIdx.x == 0) {
+    sc[kPFP] = tot;
+    pcg_mid_logic(sc);
+  }
+}
+
+// lam += gamma p, r -= gamma Fp (no-op once done); the last block closes the body run
+// (pcg_post) and, inside a graph (has_h), sets the WHILE condition.
+__global__ void k_lam_r_update_post(long long n, const double* __restrict__ p, const double* __restrict__ Fp,
+                                    double* lam, double* r, double* sc, int* ctr, cudaGraphConditionalHandle h,
+                                    int has_h) {
+  __shared__ int is_last;
+  const bool done = sc[kDone] != 0.0;
+  if (!done) {
+    const double gamma = sc[kYW] / sc[kPFP];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      lam[i] += gamma * p[i];
+      r[i] -= gamma * Fp[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(ctr, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    *ctr = 0;
+    const bool more = pcg_post_logic(sc);
+    if (has_h) cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
 }
 
 __global__ void k_p_update_g(long long n, const double* __restrict__ y, double* p, const double* sc) {
@@ -739,6 +866,30 @@ void launch_dot2(const double* x1, const double* y1, const double* x2, const dou
                  double* partial, double* out1, double* out2, cudaStream_t st) {
   k_dot2_partial<<<kRedBlocks, 256, 0, st>>>(x1, y1, x2, y2, n, partial);
   k_dot2_final<<<1, 256, 0, st>>>(partial, kRedBlocks, out1, out2);
+}
+
+void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
+                     double* sc, double* partial, int* ctr, cudaStream_t st) {
+  k_GT32_dot<<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr);
+}
+
+void launch_G32_gemv32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
+                       float* hx8, cudaStream_t st) {
+  k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
+  static const int lim = dyn_smem_limit((const void*)k_gemv32);
+  cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  const long long ld = h32_ld(l);
+  k_gemv32<<<blocks_for(l, 16), 256, sizeof(float) * (size_t)ld, st>>>(H32, l, ld, gx, hx, hx8);
+}
+
+void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,
+                         double* partial, int* ctr, cudaStream_t st) {
+  k_contract_dot<<<kFusedBlocks, 256, 0, st>>>(M, cbuf, Fp, p, sc, partial, ctr);
+}
+
+void launch_lam_r_update_post(long long n, const double* p, const double* Fp, double* lam, double* r, double* sc,
+                              int* ctr, unsigned long long h, int has_h, cudaStream_t st) {
+  k_lam_r_update_post<<<kFusedBlocks, 256, 0, st>>>(n, p, Fp, lam, r, sc, ctr, (cudaGraphConditionalHandle)h, has_h);
 }
 
 void launch_pcg_pre(double* sc, cudaStream_t st) { k_pcg_pre<<<1, 32, 0, st>>>(sc); }

@@ -9,13 +9,20 @@
 // a = a_hi + a_lo, and D += A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps the
 // product at FP32 accuracy (the dropped A_lo B_lo term is ~2^-22 relative).
 //
+// A second operand format stores S in BF16 (half the bytes of one FP32 copy):
+// kind::f16 MMAs with BF16 operands and FP32 accumulation, X split into two BF16
+// parts and D += X_hi S + X_lo S.  The product then carries S's BF16 rounding
+// (~2^-9 relative); the FP64-refined PCGP around the inner solve absorbs it.
+//
 // Operand tiles are stored in global memory already in the shared-memory layout
 // the MMA reads (no swizzle, K-major "core matrices" of 8 rows x 16 bytes), so
-// one pipeline stage is four contiguous 1-D bulk copies:
+// one pipeline stage is a few contiguous 1-D bulk copies:
 //   A (X) tile: 128 rows (subdomains) x 32 columns (dofs), core matrix (kg, mg)
 //               at byte (kg * 16 + mg) * 128;  B (S) tile: kTN = 32 rows x 32 columns,
 //               core matrix (kg, ng) at byte (kg * 4 + ng) * 128;
-// row r of a core matrix holds 4 consecutive K elements (16 bytes).
+// row r of a core matrix holds 16 bytes of consecutive K elements (4 TF32 or 8 BF16).
+#include <cuda_bf16.h>
+
 #include "async_common.cuh"
 #include "dev.h"
 #include "dual_common.cuh"
@@ -24,10 +31,24 @@ namespace tfeti {
 
 namespace {
 
-constexpr int kTM = 128, kTN = 32, kTK = 32, kStages = 4;
-constexpr uint32_t kABytes = kTM * kTK * 4, kBBytes = kTN * kTK * 4;
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr int kTM = 128, kTN = 64, kTK = 32;
 constexpr uint32_t kTmemCols = kTN;  // FP32 accumulator columns (a power of two >= 32)
+
+// Operand format: TF32 x 3 (FP32 operands split into TF32 hi/lo, S hi/lo) or BF16 x 2
+// (X split into BF16 hi/lo, S one BF16 copy).
+template <bool kBf>
+struct Fmt {
+  static constexpr int eb = kBf ? 2 : 4;                       // bytes per element
+  static constexpr int epr = 16 / eb;                          // elements per core-matrix row
+  static constexpr int stages = kBf ? 8 : 4;
+  static constexpr uint32_t a_bytes = kTM * kTK * eb, b_bytes = kTN * kTK * eb;
+  static constexpr uint32_t stage_bytes = 2 * a_bytes + (kBf ? 1 : 2) * b_bytes;
+  static constexpr int k_step = kBf ? 16 : 8;                  // K of one MMA
+  // instruction descriptor: D FP32; A, B TF32 (kind::tf32) or BF16 (kind::f16); K-major; M x N
+  static constexpr uint32_t idesc = (1u << 4) | ((kBf ? 1u : 2u) << 7) | ((kBf ? 1u : 2u) << 10) |
+                                    ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+  static constexpr size_t smem = stages * stage_bytes + (2 * stages + 1) * sizeof(uint64_t) + 3 * sizeof(uint32_t);
+};
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -40,16 +61,23 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = tf32_round(x - hi);
 }
 
-// Offset (floats) of element (row, col) inside an A tile (rows < 128) or a B tile
-// (rows < 64, groups = 8), col < 32.
-__device__ __forceinline__ int tile_off(int row, int col, int groups) {
-  return (((col >> 2) * groups + (row >> 3)) * 8 + (row & 7)) * 4 + (col & 3);
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Offset (elements) of element (row, col) inside an A tile (groups = 16) or a B tile
+// (groups = 4), col < 32, for elements of epr per 16-byte core-matrix row.
+__device__ __forceinline__ int tile_off(int row, int col, int groups, int epr) {
+  return ((col / epr) * groups + (row >> 3)) * (8 * epr) + (row & 7) * epr + col % epr;
 }
 
 // X tiles: Xhi/Xlo[(mt * nk + ks) * 4096 + tile_off(r, c, 16)] for subdomain
-// sub_list[mt * 128 + r] and boundary dof ks * 32 + c (zero beyond n_list, n_bd).
+// sub_list[mt * 128 + r] and boundary dof ks * 32 + c (zero beyond n_list, n_bd);
+// elements TF32-split floats or BF16-split halves.
+template <bool kBf>
 __global__ void k_schur_gather_tc(DevMesh M, const int* __restrict__ sub_list, int n_list, int n_bd, int nk,
-                                  const double* __restrict__ lam, float* Xhi, float* Xlo) {
+                                  const double* __restrict__ lam, void* Xhi, void* Xlo) {
   const long long ncol = (long long)nk * kTK;
   const int n_mt = (n_list + kTM - 1) / kTM;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -62,15 +90,25 @@ __global__ void k_schur_gather_tc(DevMesh M, const int* __restrict__ sub_list, i
     if (sl >= 0) v = (float)bt_at_slot(M, lam, (long long)sl + j % 3);
   }
   const int mt = k / kTM, ks = j / kTK;
-  const long long o = ((long long)mt * nk + ks) * (kTM * kTK) + tile_off(k % kTM, j % kTK, kTM / 8);
-  float hi, lo;
-  split_tf32(v, hi, lo);
-  Xhi[o] = hi;
-  Xlo[o] = lo;
+  const long long o =
+      ((long long)mt * nk + ks) * (kTM * kTK) + tile_off(k % kTM, j % kTK, kTM / 8, Fmt<kBf>::epr);
+  if constexpr (kBf) {
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    static_cast<__nv_bfloat16*>(Xhi)[o] = hi;
+    static_cast<__nv_bfloat16*>(Xlo)[o] = lo;
+  } else {
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    static_cast<float*>(Xhi)[o] = hi;
+    static_cast<float*>(Xlo)[o] = lo;
+  }
 }
 
-// S tiles from the FP32 block S32 (S32[j * n_bd + i] = S[i][j]).
-__global__ void k_schur_tile_S(const float* __restrict__ S32, int n_bd, int nk, float* Shi, float* Slo) {
+// S tiles from the FP32 block S32 (S32[j * n_bd + i] = S[i][j]): TF32 hi/lo parts, or
+// one BF16 copy (Slo unused).
+template <bool kBf>
+__global__ void k_schur_tile_S(const float* __restrict__ S32, int n_bd, int nk, void* Shi, void* Slo) {
   const long long ncol = (long long)nk * kTK;
   const int n_nt = (n_bd + kTN - 1) / kTN;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -78,11 +116,16 @@ __global__ void k_schur_tile_S(const float* __restrict__ S32, int n_bd, int nk, 
   const int i = (int)(idx / ncol), j = (int)(idx % ncol);
   const float v = (i < n_bd && j < n_bd) ? S32[(long long)j * n_bd + i] : 0.0f;
   const int nt = i / kTN, ks = j / kTK;
-  const long long o = ((long long)nt * nk + ks) * (kTN * kTK) + tile_off(i % kTN, j % kTK, kTN / 8);
-  float hi, lo;
-  split_tf32(v, hi, lo);
-  Shi[o] = hi;
-  Slo[o] = lo;
+  const long long o =
+      ((long long)nt * nk + ks) * (kTN * kTK) + tile_off(i % kTN, j % kTK, kTN / 8, Fmt<kBf>::epr);
+  if constexpr (kBf) {
+    static_cast<__nv_bfloat16*>(Shi)[o] = __float2bfloat16_rn(v);
+  } else {
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    static_cast<float*>(Shi)[o] = hi;
+    static_cast<float*>(Slo)[o] = lo;
+  }
 }
 
 // Shared-memory matrix descriptor: no swizzle, K-major; lbo = byte distance of
@@ -92,16 +135,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M x N.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-      : "memory");
+template <bool kBf>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if constexpr (kBf) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(Fmt<true>::idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(Fmt<false>::idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -128,29 +176,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // C = X S for one 128 x kTN output tile (blockIdx.y: subdomain tile, blockIdx.x:
-// boundary-dof tile), written to the copy slots of the interface dofs.  128
-// threads: thread 0 streams the stages, thread 32 issues the MMAs, all four warps
-// read the accumulator (warp w owns TMEM lanes 32w..32w+31 = output rows).
+// boundary-dof tile) over the K stages [ks0, ks1) of split blockIdx.z, written to the
+// copy slots of the interface dofs.  128 threads: thread 0 streams the stages, thread 32
+// issues the MMAs, all four warps read the accumulator (warp w owns TMEM lanes
+// 32w..32w+31 = output rows).
+//
+// With splits of K (gridDim.z > 1, used when the output tiles alone would leave SMs idle)
+// every CTA of a tile stores its FP32 partial tile in `part` and counts itself in
+// `count[tile]`; the one that arrives last sums the partials in split order and scatters,
+// so the result does not depend on the order in which the CTAs finish, and returns the
+// counter to zero for the next launch.  No CTA waits for another.
+template <bool kBf>
 __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __restrict__ sub_list, int n_list,
-                                                     int n_bd, int nk, const float* __restrict__ Xhi,
-                                                     const float* __restrict__ Xlo, const float* __restrict__ Shi,
-                                                     const float* __restrict__ Slo, double* cbuf, int* err) {
+                                                     int n_bd, int nk, const unsigned char* __restrict__ Xhi,
+                                                     const unsigned char* __restrict__ Xlo,
+                                                     const unsigned char* __restrict__ Shi,
+                                                     const unsigned char* __restrict__ Slo, float* part, int* count,
+                                                     double* cbuf, int* err) {
+  using F = Fmt<kBf>;
+  constexpr int kSt = F::stages;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSt * F::stage_bytes);
+  uint64_t* empty = full + kSt;
+  uint64_t* done = empty + kSt;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  int* s_fail = reinterpret_cast<int*>(tmem_slot + 1);
+  int* s_flag = reinterpret_cast<int*>(tmem_slot + 1);   // [0]: a wait gave up, [1]: this CTA is last
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y;
+  const int nt = blockIdx.x, mt = blockIdx.y, splits = gridDim.z;
+  const int ks0 = (int)((long long)blockIdx.z * nk / splits), ks1 = (int)((long long)(blockIdx.z + 1) * nk / splits);
+  const int n_ks = ks1 - ks0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s]);
-      mbar_init(&empty[s]);
+    for (int q = 0; q < kSt; ++q) {
+      mbar_init(&full[q]);
+      mbar_init(&empty[q]);
     }
     mbar_init(done);
-    *s_fail = 0;
+    s_flag[0] = 0;
+    s_flag[1] = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
@@ -166,65 +229,102 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
   const uint32_t tmem = *tmem_slot;
 
   if (threadIdx.x == 0) {
-    // producer: stage ks % kStages, its u-th use waits for the MMAs of use u - 1
+    // producer: stage j % kSt, its u-th use waits for the MMAs of use u - 1
     int issued = 0;
-    for (int ks = 0; ks < nk; ++ks) {
-      const int st = ks % kStages, u = ks / kStages;
+    for (int j = 0; j < n_ks; ++j) {
+      const int st = j % kSt, u = j / kSt, ks = ks0 + j;
       if (u > 0 && !mbar_wait(&empty[st], (uint32_t)((u - 1) & 1))) {
-        atomicOr(s_fail, 1);
+        atomicOr(&s_flag[0], 1);
         break;
       }
-      unsigned char* base = smem + st * kStageBytes;
-      mbar_expect_tx(&full[st], kStageBytes);
-      const long long a_off = ((long long)mt * nk + ks) * (kTM * kTK);
-      const long long b_off = ((long long)nt * nk + ks) * (kTN * kTK);
-      bulk_copy_tx(base, Xhi + a_off, kABytes, &full[st]);
-      bulk_copy_tx(base + kABytes, Xlo + a_off, kABytes, &full[st]);
-      bulk_copy_tx(base + 2 * kABytes, Shi + b_off, kBBytes, &full[st]);
-      bulk_copy_tx(base + 2 * kABytes + kBBytes, Slo + b_off, kBBytes, &full[st]);
+      unsigned char* base = smem + st * F::stage_bytes;
+      mbar_expect_tx(&full[st], F::stage_bytes);
+      const long long a_off = ((long long)mt * nk + ks) * F::a_bytes;
+      const long long b_off = ((long long)nt * nk + ks) * F::b_bytes;
+      bulk_copy_tx(base, Xhi + a_off, F::a_bytes, &full[st]);
+      bulk_copy_tx(base + F::a_bytes, Xlo + a_off, F::a_bytes, &full[st]);
+      bulk_copy_tx(base + 2 * F::a_bytes, Shi + b_off, F::b_bytes, &full[st]);
+      if (!kBf) bulk_copy_tx(base + 2 * F::a_bytes + F::b_bytes, Slo + b_off, F::b_bytes, &full[st]);
       ++issued;
     }
     // every issued copy has landed before the CTA can leave (immediate on the normal path)
-    for (int ks = issued - 1; ks >= 0 && ks >= issued - kStages; --ks)
-      mbar_wait(&full[ks % kStages], (uint32_t)((ks / kStages) & 1));
+    for (int j = issued - 1; j >= 0 && j >= issued - kSt; --j)
+      mbar_wait(&full[j % kSt], (uint32_t)((j / kSt) & 1));
   } else if (threadIdx.x == 32) {
-    // MMA issuer
-    for (int ks = 0; ks < nk; ++ks) {
-      const int st = ks % kStages, u = ks / kStages;
+    // MMA issuer: per stage, kTK / k_step MMA steps of two core matrices along K
+    for (int j = 0; j < n_ks; ++j) {
+      const int st = j % kSt, u = j / kSt;
       if (!mbar_wait(&full[st], (uint32_t)(u & 1))) {
-        atomicOr(s_fail, 1);
+        atomicOr(&s_flag[0], 1);
         break;
       }
       tc_fence_after();
-      const uint32_t a_hi = smem_addr(smem + st * kStageBytes), a_lo = a_hi + kABytes;
-      const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + kBBytes;
+      const uint32_t a_hi = smem_addr(smem + st * F::stage_bytes), a_lo = a_hi + F::a_bytes;
+      const uint32_t b_hi = a_hi + 2 * F::a_bytes, b_lo = b_hi + F::b_bytes;
 #pragma unroll
-      for (int s = 0; s < kTK / 8; ++s) {   // K = 8 per MMA: two core matrices along K
-        const uint64_t dah = smem_desc(a_hi + s * 2 * (kTM / 8) * 128, (kTM / 8) * 128, 128);
-        const uint64_t dal = smem_desc(a_lo + s * 2 * (kTM / 8) * 128, (kTM / 8) * 128, 128);
-        const uint64_t dbh = smem_desc(b_hi + s * 2 * (kTN / 8) * 128, (kTN / 8) * 128, 128);
-        const uint64_t dbl = smem_desc(b_lo + s * 2 * (kTN / 8) * 128, (kTN / 8) * 128, 128);
-        mma_tf32(tmem, dah, dbh, (ks | s) != 0 ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, 1u);
-        mma_tf32(tmem, dal, dbh, 1u);
+      for (int q = 0; q < kTK / F::k_step; ++q) {
+        const uint64_t dah = smem_desc(a_hi + q * 2 * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+        const uint64_t dal = smem_desc(a_lo + q * 2 * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+        const uint64_t dbh = smem_desc(b_hi + q * 2 * (kTN / 8) * 128, (kTN / 8) * 128, 128);
+        mma_issue<kBf>(tmem, dah, dbh, (j | q) != 0 ? 1u : 0u);
+        if (!kBf) {
+          const uint64_t dbl = smem_desc(b_lo + q * 2 * (kTN / 8) * 128, (kTN / 8) * 128, 128);
+          mma_issue<kBf>(tmem, dah, dbl, 1u);
+        }
+        mma_issue<kBf>(tmem, dal, dbh, 1u);
       }
       mma_commit(&empty[st]);   // stage free once these MMAs have read it
     }
     mma_commit(done);           // all MMAs issued by this thread complete
   }
   __syncwarp();
-  if (!mbar_wait(done, 0u)) atomicOr(s_fail, 1);
+  if (!mbar_wait(done, 0u)) atomicOr(&s_flag[0], 1);
   tc_fence_after();
   __syncthreads();
-  const bool good = *s_fail == 0;   // the same for every thread: tcgen05.ld below is warp-collective
-  if (good) {
-    const int row = warp * 32 + lane;
-    const int k = mt * kTM + row;
+  const bool good = s_flag[0] == 0;   // the same for every thread: tcgen05.ld below is warp-collective
+  const int row = warp * 32 + lane;
+  const int k = mt * kTM + row;
+  const long long tile = (long long)mt * gridDim.x + nt;
+  bool last = true;
+  if (splits > 1) {
+    // every split publishes its partial tile (column c of this row at [c * kTM]); the CTA that
+    // arrives last sums the partials in split order and scatters
+    float* mine = part + (tile * splits + blockIdx.z) * (kTM * kTN) + row;
     for (int c0 = 0; c0 < kTN; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (k < n_list) {
-        const SubDev& S = M.subs[sub_list[k]];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) mine[(c0 + q) * kTM] = good ? v[q] : 0.0f;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int old = atomicAdd(&count[tile], 1);
+      s_flag[1] = old == splits - 1 ? 1 : 0;
+      if (old == splits - 1) count[tile] = 0;   // back to zero for the next launch
+    }
+    __syncthreads();
+    last = s_flag[1] != 0;
+    if (last) __threadfence();
+  }
+  if (last) {   // CTA-uniform, so every lane of a warp takes the warp-collective loads together
+    const bool mine_row = k < n_list;
+    const int sub = mine_row ? sub_list[k] : 0;
+    const float* pt = part + tile * splits * (kTM * kTN) + row;
+    for (int c0 = 0; c0 < kTN; c0 += 16) {
+      float v[16];
+      if (splits == 1) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      } else if (mine_row) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          float acc = __ldcg(pt + (c0 + q) * kTM);
+          for (int z = 1; z < splits; ++z) acc += __ldcg(pt + (long long)z * (kTM * kTN) + (c0 + q) * kTM);
+          v[q] = acc;
+        }
+      }
+      if (mine_row && s_flag[0] == 0) {
+        const SubDev& S = M.subs[sub];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int i = nt * kTN + c0 + q;
@@ -236,7 +336,7 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
       }
     }
   }
-  if (threadIdx.x == 0 && !good) atomicOr(err, 4);
+  if (threadIdx.x == 0 && s_flag[0] != 0) atomicOr(err, 4);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -245,40 +345,64 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
   }
 }
 
-constexpr size_t kSmemTc = kStages * kStageBytes + (2 * kStages + 1) * sizeof(uint64_t) + 2 * sizeof(uint32_t);
-
 }  // namespace
 
 int schur_nk(int n_bd) { return (n_bd + kTK - 1) / kTK; }
 
-long long schur_x_tile_floats(int n_list, int n_bd) {
+int schur_tiles(int n_list, int n_bd) { return ((n_list + kTM - 1) / kTM) * ((n_bd + kTN - 1) / kTN); }
+
+long long schur_x_tile_elems(int n_list, int n_bd) {
   return (long long)((n_list + kTM - 1) / kTM) * kTM * schur_nk(n_bd) * kTK;
 }
 
-long long schur_s_tile_floats(int n_bd) {
+long long schur_s_tile_elems(int n_bd) {
   return (long long)((n_bd + kTN - 1) / kTN) * kTN * schur_nk(n_bd) * kTK;
 }
 
-void launch_schur_tile_S(const float* S32, int n_bd, float* Shi, float* Slo, cudaStream_t st) {
-  const long long n = schur_s_tile_floats(n_bd);
-  if (n > 0) k_schur_tile_S<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S32, n_bd, schur_nk(n_bd), Shi, Slo);
+long long schur_part_floats(int n_list, int n_bd, int splits) {
+  return (long long)schur_tiles(n_list, n_bd) * splits * kTM * kTN;
 }
 
-void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const double* lam, float* Xhi,
-                         float* Xlo, cudaStream_t st) {
-  const long long n = schur_x_tile_floats(n_list, n_bd);
-  if (n > 0)
-    k_schur_gather_tc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), lam,
-                                                                     Xhi, Xlo);
+void launch_schur_tile_S(const float* S32, int n_bd, bool bf16, void* Shi, void* Slo, cudaStream_t st) {
+  const long long n = schur_s_tile_elems(n_bd);
+  if (n <= 0) return;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (bf16) k_schur_tile_S<true><<<blocks, 256, 0, st>>>(S32, n_bd, schur_nk(n_bd), Shi, Slo);
+  else k_schur_tile_S<false><<<blocks, 256, 0, st>>>(S32, n_bd, schur_nk(n_bd), Shi, Slo);
 }
 
-void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, const float* Xhi,
-                               const float* Xlo, const float* Shi, const float* Slo, double* cbuf, int* err,
-                               cudaStream_t st) {
+void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, const double* lam,
+                         void* Xhi, void* Xlo, cudaStream_t st) {
+  const long long n = schur_x_tile_elems(n_list, n_bd);
+  if (n <= 0) return;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (bf16) k_schur_gather_tc<true><<<blocks, 256, 0, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), lam, Xhi, Xlo);
+  else k_schur_gather_tc<false><<<blocks, 256, 0, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), lam, Xhi, Xlo);
+}
+
+int schur_splits(int n_list, int n_bd, int n_sm) {
+  // two splits of K when the output tiles alone would leave SMs idle (and K is long enough)
+  return (schur_tiles(n_list, n_bd) < n_sm && schur_nk(n_bd) >= 8) ? 2 : 1;
+}
+
+void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
+                               const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
+                               int* count, double* cbuf, int* err, cudaStream_t st) {
   if (n_list <= 0 || n_bd <= 0) return;
-  cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc);
-  dim3 grid((unsigned)((n_bd + kTN - 1) / kTN), (unsigned)((n_list + kTM - 1) / kTM));
-  k_schur_tc<<<grid, 128, kSmemTc, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), Xhi, Xlo, Shi, Slo, cbuf, err);
+  dim3 grid((unsigned)((n_bd + kTN - 1) / kTN), (unsigned)((n_list + kTM - 1) / kTM), (unsigned)splits);
+  const auto* xh = static_cast<const unsigned char*>(Xhi);
+  const auto* xl = static_cast<const unsigned char*>(Xlo);
+  const auto* sh = static_cast<const unsigned char*>(Shi);
+  const auto* sl = static_cast<const unsigned char*>(Slo);
+  if (bf16) {
+    cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<true>::smem);
+    k_schur_tc<true><<<grid, 128, Fmt<true>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
+                                                          part, count, cbuf, err);
+  } else {
+    cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<false>::smem);
+    k_schur_tc<false><<<grid, 128, Fmt<false>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
+                                                           part, count, cbuf, err);
+  }
 }
 
 }  // namespace tfeti
