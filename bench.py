@@ -364,8 +364,10 @@ def run_gpu(args, rank, world, local_rank):
     pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
     main_arm = resolve_arm(args)
 
+    coarse = {"auto": T.COARSE_AUTO, "dense": T.COARSE_DENSE, "planes": T.COARSE_PLANES}[args.coarse]
+
     def make_ctx(arm):
-        c = T.Context(w, stream=stream, precond=pre)
+        c = T.Context(w, stream=stream, precond=pre, coarse=coarse)
         if args.fapply == "schur":
             c.set_fapply(True)
         if arm != "fp64":
@@ -566,7 +568,8 @@ def run_gpu(args, rank, world, local_rank):
                 "parallelism": "replicas" if world > 1 else "1 GPU", "arm": main_arm,
                 "arm_note": ARM_NOTES[main_arm],
                 "inner_rtol": args.inner_rtol if main_arm != "fp64" else None, "fapply": args.fapply,
-                "inner_pcgp_launch": "kernel by kernel" if args.no_graphs else "one CUDA graph (WHILE node) per inner solve"},
+                "inner_pcgp_launch": "kernel by kernel" if args.no_graphs else "one CUDA graph (WHILE node) per inner solve",
+                "coarse": args.coarse},
             "e2e": e2e,
             "gpu_launches": int(tm["kernel_launches"]),
             "roofline": roof,
@@ -610,7 +613,8 @@ def run_cases(args, rank, world, local_rank):
     n_total = args.warmup + args.steps
     pre = T.PRECOND_DIRICHLET if args.precond == "dirichlet" else T.PRECOND_LUMPED
     main_stream = torch.cuda.Stream(device=dev)
-    base = T.Context(w, stream=main_stream, precond=pre)
+    base = T.Context(w, stream=main_stream, precond=pre,
+                     coarse={"auto": T.COARSE_AUTO, "dense": T.COARSE_DENSE, "planes": T.COARSE_PLANES}[args.coarse])
     streams = [torch.cuda.Stream(device=dev) for _ in cases]
     ctxs = [T.Context.case_of(base, c["sigma_y"], c["hardening"], stream=st) for c, st in zip(cases, streams)]
 
@@ -741,6 +745,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="time the headline arm only (no other arms)")
     ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
+    ap.add_argument("--coarse", default="auto", choices=["auto", "dense", "planes"],
+                    help="coarse solve of the projector: explicit dense inverse, or block LDL^T over the z-planes "
+                         "of subdomains (auto: planes above 6144 coarse unknowns)")
     ap.add_argument("--schur-format", default="tf32x3", choices=["tf32x3", "bf16"],
                     help="operand format of the inner F-apply's dual Schur blocks in every mixed arm")
     ap.add_argument("--precond", default="lumped", choices=["lumped", "dirichlet"],

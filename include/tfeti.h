@@ -100,7 +100,20 @@ typedef struct tfeti_problem {
     int32_t dirichlet[6];      /* per face x0,x1,y0,y1,z0,z1: bit c = component c fixed */
     int32_t traction_face;     /* 0..5 in the same face order: the loaded face          */
     int32_t precond;           /* TFETI_PRECOND_*                                      */
+    int32_t coarse;            /* TFETI_COARSE_*: how H = (G G^T)^-1 is applied         */
 } tfeti_problem;
+
+/* The coarse solve of the projector P_N (Sec. 4.2): AUTO (0) picks DENSE for
+ * n_coarse <= 6144 and PLANES above.  DENSE: the explicit inverse H (n_coarse^2
+ * doubles, 4.8 GB at 4096 subdomains) applied by one GEMV.  PLANES: G G^T is block
+ * tridiagonal over the planes of subdomains with equal z index (a subdomain couples
+ * only to the boxes around it); its block LDL^T with explicit inverses of the pivot
+ * blocks is applied by 2 nz - 1 dependent GEMVs of (6 nx ny)^2, nz planes of nx x ny
+ * subdomains (3 x 16 x 1536^2 doubles = 0.9 GB at 16^3 subdomains).  Both give H g to
+ * rounding. */
+#define TFETI_COARSE_AUTO   0
+#define TFETI_COARSE_DENSE  1
+#define TFETI_COARSE_PLANES 2
 
 typedef struct tfeti_sizes {
     int64_t n_sub;             /* s                                                     */

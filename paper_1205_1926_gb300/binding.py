@@ -20,6 +20,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4
           5: "singular coarse problem", 6: "not converged", 7: "PCGP breakdown", 8: "non-finite value",
           9: "bounded device wait timed out"}
 PRECOND_NONE, PRECOND_LUMPED, PRECOND_DIRICHLET = 0, 1, 2
+COARSE_AUTO, COARSE_DENSE, COARSE_PLANES = 0, 1, 2
 MLP_PARAMS = 4801
 MAX_NEWTON = 64
 FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
@@ -29,7 +30,7 @@ class Problem(C.Structure):
     _fields_ = [("nel", C.c_int32 * 3), ("length", C.c_double * 3), ("nsub", C.c_int32 * 3),
                 ("cuts", C.POINTER(C.c_int32) * 3), ("young", C.c_double), ("poisson", C.c_double),
                 ("sigma_y", C.c_double), ("hardening", C.c_double), ("dirichlet", C.c_int32 * 6),
-                ("traction_face", C.c_int32), ("precond", C.c_int32)]
+                ("traction_face", C.c_int32), ("precond", C.c_int32), ("coarse", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -161,7 +162,7 @@ def _ptr(x):
     raise TypeError(f"cannot pass {type(x)} as a pointer")
 
 
-def make_problem(workload, material: dict | None = None, precond: int = PRECOND_LUMPED):
+def make_problem(workload, material: dict | None = None, precond: int = PRECOND_LUMPED, coarse: int = COARSE_AUTO):
     """Fill a Problem struct from a ``workloads.Workload`` (sizes, cuts, material, masks)."""
     pr = Problem()
     mat = dict(workload.material if material is None else material)
@@ -180,6 +181,7 @@ def make_problem(workload, material: dict | None = None, precond: int = PRECOND_
         pr.dirichlet[f] = m
     pr.traction_face = FACES.index(workload.traction_face)
     pr.precond = precond
+    pr.coarse = coarse
     pr._keep = keep
     return pr
 

@@ -622,9 +622,9 @@ int tune_schur_threshold(tfeti_ctx* c) {
 
 void op_project(tfeti_ctx* c, const double* x, double* out) {
   launch_G_apply(c->M, x, nullptr, c->gx, 1.0, c->st);
-  launch_gemv(c->H, c->l, c->gx, 1.0, c->hx, c->st);
+  coarse_apply(c->coarse, c->gx, 1.0, c->hx, c->st);
   launch_GT_update(c->M, x, 1.0, c->hx, -1.0, out, c->st);
-  c->launches += 3;
+  c->launches += 2 + coarse_launches(c->coarse);
 }
 
 // Dirichlet preconditioner (Sec. 4.2): z = Bbar Sbar Bbar^T w with
@@ -657,8 +657,8 @@ void op_precond_dirichlet(tfeti_ctx* c, const double* w, double* out, bool fp32)
 
 // FP32 projector and preconditioner of the inner iterations of the mixed mode.
 void op_project32(tfeti_ctx* c, const double* x, double* out) {
-  launch_project32(c->M, c->H32, c->l, x, c->gx, c->hx, c->hx8, out, c->st);
-  c->launches += 3;
+  launch_project32(c->M, c->coarse, x, c->gx, c->hx, c->hx8, out, c->st);
+  c->launches += 2 + coarse_launches(c->coarse);
 }
 
 void op_precond32(tfeti_ctx* c, const double* x, double* out) {
@@ -912,16 +912,16 @@ void destroy_inner_graph(tfeti_ctx* c) {
 // condition `h` of the enclosing node.
 void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h, bool has_h) {
   const long long m = c->M.n_mult;
-  launch_G32_gemv32(c->M, c->H32, c->l, c->rin, c->gx, c->hx, c->hx8, c->st);
+  launch_G32_coarse32(c->M, c->coarse, c->rin, c->gx, c->hx, c->hx8, c->st);
   launch_GT32_dot(c->M, c->rin, c->hx8, c->w, nullptr, 0, c->sc, c->partial, c->d_ctr, c->st);   // w = P r, w.w
   op_precond32(c, c->w, c->z);                                                                   // z = F^-1 w
-  launch_G32_gemv32(c->M, c->H32, c->l, c->z, c->gx, c->hx, c->hx8, c->st);
+  launch_G32_coarse32(c->M, c->coarse, c->z, c->gx, c->hx, c->hx8, c->st);
   launch_GT32_dot(c->M, c->z, c->hx8, c->y, c->w, 1, c->sc, c->partial, c->d_ctr + 1, c->st);  // y = P z, y.w
   launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);                                           // p = y + beta p
   op_F32(c, c->pdir, c->Fp, false);                                                              // slots of F p
   launch_contract_dot(c->M, c->cbuf, c->Fp, c->pdir, c->sc, c->partial, c->d_ctr + 2, c->st);  // F p, p.Fp
   launch_lam_r_update_post(m, c->pdir, c->Fp, c->dlt, c->rin, c->sc, c->d_ctr + 3, h, has_h ? 1 : 0, c->st);
-  c->launches += 8;
+  c->launches += 6 + 2 * coarse_launches(c->coarse);
 }
 
 int build_inner_graph(tfeti_ctx* c) {
@@ -1242,7 +1242,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   const long long f_before = c->f_launches + c->f_split, f32_before = c->f32_launches;
   // e = -R^T f ; lambda_Im = N^T H e = -B R (H e)
   launch_G_apply(M, nullptr, f, c->ev, -1.0, c->st);
-  launch_gemv(c->H, c->l, c->ev, 1.0, c->hx, c->st);
+  coarse_apply(c->coarse, c->ev, 1.0, c->hx, c->st);
   launch_GT_update(M, nullptr, 0.0, c->hx, -1.0, c->lam_im, c->st);
   c->launches += 3;
   // d~ = d - F lambda_Im = B K^+(f - B^T lambda_Im) ; r^0 = d~
@@ -1333,7 +1333,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
     history_push(c);
   }
   launch_G_apply(M, c->r, nullptr, c->gx, -1.0, c->st);
-  launch_gemv(c->H, c->l, c->gx, 1.0, c->alpha, c->st);
+  coarse_apply(c->coarse, c->gx, 1.0, c->alpha, c->st);
   c->launches += 2;
   if (u_out) {
     launch_add_R_alpha(M, c->vsol, c->alpha, u_out, (int)c->plan.max_ndof, c->st);
@@ -1619,7 +1619,6 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
                      &c->rin})
     *v = dalloc<double>(c, m);
   c->vsol = dalloc<double>(c, (size_t)P.n_dof);
-  if (!base) c->H = dalloc<double>(c, (size_t)c->l * c->l);
   c->gx = dalloc<double>(c, c->l);
   c->hx = dalloc<double>(c, c->l);
   c->hx8 = dalloc<float>(c, 8 * (size_t)ns);
@@ -1640,24 +1639,60 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   cudaMemsetAsync(c->kap, 0, sizeof(double) * P.n_gp, c->st);
   cudaMemsetAsync(c->elem_np, 0, sizeof(int) * P.n_elem, c->st);
   cudaMemsetAsync(c->sc, 0, sizeof(double) * kNumScalars, c->st);
-  // coarse problem: G G^T assembled once and inverted (G depends only on B and R)
+  // coarse problem: G G^T assembled once and factorised (G depends only on B and R)
   if (base) {
     c->H = base->H;
+    c->cW = base->cW;
+    c->cV = base->cV;
+    c->cU = base->cU;
+    c->coarse = base->coarse;
   } else {
+    const int per_plane = (int)(P.nsub[0] * P.nsub[1]);
+    const int n_planes = (int)P.nsub[2];
+    const int mode = P.prob.coarse == TFETI_COARSE_DENSE ? kCoarseDense
+                     : P.prob.coarse == TFETI_COARSE_PLANES ? kCoarsePlanes
+                     : (c->l > kCoarseDenseMax ? kCoarsePlanes : kCoarseDense);
     int* pp = upload(c, P.pair_p);
     int* pq = upload(c, P.pair_q);
     long long* ps = upload(c, std::vector<long long>(P.pair_start.begin(), P.pair_start.end()));
     int* tg = upload(c, P.trip_group);
     int* ti = upload(c, P.trip_i);
     int* tj = upload(c, P.trip_j);
-    launch_coarse_assemble(M, pp, pq, ps, tg, ti, tj, (long long)P.pair_p.size(), c->H, c->l, c->st);
     double* work = nullptr;
-    if (cudaMalloc(&work, sizeof(double) * dense_inverse_work(c->l)) != cudaSuccess) {
-      cudaGetLastError();
-      throw std::bad_alloc();
-    }
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    dense_cholesky_inverse(c->H, work, c->l, c->d_err, c->st);
+    c->coarse = CoarseOp{};
+    c->coarse.mode = mode;
+    c->coarse.l = c->l;
+    if (mode == kCoarseDense) {
+      c->H = dalloc<double>(c, (size_t)c->l * c->l);
+      launch_coarse_assemble(M, pp, pq, ps, tg, ti, tj, (long long)P.pair_p.size(), c->H, c->l, c->st);
+      if (cudaMalloc(&work, sizeof(double) * dense_inverse_work(c->l)) != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+      }
+      dense_cholesky_inverse(c->H, work, c->l, c->d_err, c->st);
+      c->coarse.H = c->H;
+    } else {
+      const int n_pl = 6 * per_plane;
+      const size_t blk = (size_t)n_pl * n_pl;
+      c->cW = dalloc<double>(c, blk * n_planes);
+      c->cAoff = dalloc<double>(c, blk * n_planes);
+      c->cV = dalloc<double>(c, blk * n_planes);
+      c->cU = dalloc<double>(c, blk * n_planes);
+      launch_coarse_assemble_planes(M, pp, pq, ps, tg, ti, tj, (long long)P.pair_p.size(), c->cW, c->cAoff, per_plane,
+                                    n_pl, n_planes, c->st);
+      if (cudaMalloc(&work, sizeof(double) * (dense_inverse_work(n_pl) + blk)) != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+      }
+      coarse_planes_factor(c->cW, c->cAoff, c->cV, c->cU, n_pl, n_planes, work + dense_inverse_work(n_pl), work,
+                           c->d_err, c->st);
+      c->coarse.n_pl = n_pl;
+      c->coarse.n_planes = n_planes;
+      c->coarse.W = c->cW;
+      c->coarse.V = c->cV;
+      c->coarse.U = c->cU;
+    }
     int herr = 0;
     cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     sync(c);
@@ -2097,18 +2132,33 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
   c->precision = mode;
   c->inner_rtol = inner_rtol;
   c->g_inner_stale = true;
-  if (mode == TFETI_PRECISION_MIXED && !c->H32) {
-    // FP32 copies of H and the boundary blocks for the inner projector and preconditioner
-    // (the FP32 values of G are formed at set-up)
-    // (a case context shares the base's FP32 H, formed here if the base has none)
+  if (mode == TFETI_PRECISION_MIXED && !c->kbb32) {
+    // FP32 copies of the coarse solve and the boundary blocks for the inner projector and
+    // preconditioner (the FP32 values of G are formed at set-up)
+    // (a case context shares the base's FP32 coarse blocks, formed here if the base has none)
     tfeti_ctx* hown = c->base ? c->base : c;
     try {
-      if (!hown->H32) {
+      if (hown->coarse.mode == kCoarseDense && !hown->H32) {
         hown->H32 = dalloc<float>(hown, (size_t)c->l * (size_t)h32_ld(c->l));
-        launch_h_to_f32(c->H, c->l, hown->H32, c->st);
+        launch_h_to_f32(hown->H, c->l, hown->H32, c->st);
+        hown->coarse.H32 = hown->H32;
+        sync(c);
+      }
+      if (hown->coarse.mode == kCoarsePlanes && !hown->cW32) {
+        const long long n = (long long)hown->coarse.n_pl * hown->coarse.n_pl * hown->coarse.n_planes;
+        hown->cW32 = dalloc<float>(hown, (size_t)n);
+        hown->cV32 = dalloc<float>(hown, (size_t)n);
+        hown->cU32 = dalloc<float>(hown, (size_t)n);
+        launch_to_f32(hown->cW, hown->cW32, n, c->st);
+        launch_to_f32(hown->cV, hown->cV32, n, c->st);
+        launch_to_f32(hown->cU, hown->cU32, n, c->st);
+        hown->coarse.W32 = hown->cW32;
+        hown->coarse.V32 = hown->cV32;
+        hown->coarse.U32 = hown->cU32;
         sync(c);
       }
       c->H32 = hown->H32;
+      c->coarse = hown->coarse;
       c->kbb32 = dalloc<float>(c, c->plan.kbb_template_total + c->plan.kbb_total);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");

@@ -174,6 +174,10 @@ struct tfeti_ctx {
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
   float* hx8 = nullptr;              // FP32 H g padded to 8 per subdomain (FP32 projector)
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
+  // coarse solve (dense explicit H or the plane solver's blocks; a case context shares the base's)
+  tfeti::CoarseOp coarse;
+  double *cW = nullptr, *cV = nullptr, *cU = nullptr, *cAoff = nullptr;
+  float *cW32 = nullptr, *cV32 = nullptr, *cU32 = nullptr;
   double *partial = nullptr, *sc = nullptr, *h_sc = nullptr;
   int* d_ctr = nullptr;                      // arrival counters of the fused inner-iteration kernels
   int* d_err = nullptr;

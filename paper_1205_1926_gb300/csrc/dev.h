@@ -205,14 +205,43 @@ void launch_add_R_alpha(const DevMesh& M, const double* v, const double* alpha, 
                        cudaStream_t st);
 void launch_lumped(const DevMesh& M, const double* w, const double* kbb, const long long* kbb_off, double* cbuf,
                    cudaStream_t st, int max_copy);
+// The coarse solve h = H g, H = (G G^T)^-1 (Sec. 4.2's projector).  Dense: the explicit
+// inverse H (l x l, and its FP32 copy H32 with rows padded to h32_ld(l)), one GEMV.  Planes:
+// G G^T is block tridiagonal over the planes of subdomains with equal z index (a subdomain
+// couples only to the 26 boxes around it), n_planes blocks of n_pl = 6 x (subdomains per
+// plane); a block LDL^T with explicit inverses W_k of the pivots and the products V_k, U_k
+// turns the solve into 2 n_planes - 1 dependent GEMVs of n_pl x n_pl (coarse_planes_factor).
+constexpr int kCoarseDense = 0, kCoarsePlanes = 1;
+constexpr long long kCoarseDenseMax = 6144;   // TFETI_COARSE_AUTO: dense H up to this n_coarse
+struct CoarseOp {
+  int mode = kCoarseDense;
+  long long l = 0;
+  const double* H = nullptr;
+  const float* H32 = nullptr;
+  int n_pl = 0, n_planes = 0;
+  const double *W = nullptr, *V = nullptr, *U = nullptr;      // [n_planes][n_pl][n_pl]
+  const float *W32 = nullptr, *V32 = nullptr, *U32 = nullptr;
+};
+// y = alpha H x in FP64 (x and y distinct).
+void coarse_apply(const CoarseOp& C, const double* x, double alpha, double* y, cudaStream_t st);
+// y = H x with the FP32 copies (FP32 products and sums), and y8, its FP32 copy padded to 8
+// values per subdomain.
+void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cudaStream_t st);
+int coarse_launches(const CoarseOp& C);
+void launch_coarse_assemble_planes(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
+                                   const int* trip_group, const int* trip_i, const int* trip_j, long long n_pairs,
+                                   double* Adiag, double* Aoff, int per_plane, int n_pl, int n_planes,
+                                   cudaStream_t st);
+void coarse_planes_factor(double* W, const double* Aoff, double* V, double* U, int n, int np, double* T,
+                          double* work, int* err, cudaStream_t st);
+
 // FP32 operators of the inner iterations of the mixed mode (FP64 vectors in and out):
-// P x with the FP32 copies of R and H, and the lumped preconditioner with the FP32
-// copy of the boundary blocks.  gx, hx: coarse work vectors [l].
+// P x with the FP32 copies of R and of the coarse solve, and the lumped preconditioner with
+// the FP32 copy of the boundary blocks.  gx, hx: coarse work vectors [l].
 // hx8: FP32 copy of H g padded to 8 values per subdomain (entries 6, 7 zero), [n_sub][8].
-// H32: FP32 copy of H, rows padded to h32_ld(l) floats (launch_h_to_f32).  G values in
-// FP32 (M.Gv32, M.GTv32) are stored 8 per entry (6 and two zeros).
-void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                      float* hx8, double* out, cudaStream_t st);
+// G values in FP32 (M.Gv32, M.GTv32) are stored 8 per entry (6 and two zeros).
+void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
+                      double* out, cudaStream_t st);
 inline long long h32_ld(long long l) { return (l + 3) & ~3LL; }
 void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st);
 // Values of the explicit G from R and the (row, slot, coefficient) entries (set-up).
@@ -269,10 +298,10 @@ void launch_dot2(const double* x1, const double* y1, const double* x2, const dou
 // kFusedBlocks doubles).  GT32_dot: out = x - G^T h8 and sc[kWW] = out.out (mode 0) or
 // sc[kYW] = out.v plus the stop test (mode 1).  contract_dot: Fp = B cbuf, sc[kPFP] = p.Fp plus
 // the breakdown test.  lam_r_update_post: the guarded updates, then the body run is closed and,
-// with has_h, the WHILE condition h set.  G32_gemv32: gx = G x and hx = H32 gx (+ padded hx8).
+// with has_h, the WHILE condition h set.  G32_coarse32: gx = G x and hx = H gx in FP32 (+ padded hx8).
 constexpr int kFusedBlocks = 608;
-void launch_G32_gemv32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                       float* hx8, cudaStream_t st);
+void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
+                         cudaStream_t st);
 void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
                      double* sc, double* partial, int* ctr, cudaStream_t st);
 void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,

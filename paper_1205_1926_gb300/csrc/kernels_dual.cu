@@ -629,6 +629,123 @@ __global__ void k_coarse_assemble(DevMesh M, const int* __restrict__ pair_p, con
   if (p != q) A[(6LL * q + b) * l + 6LL * p + a] = s;
 }
 
+// The same blocks into the block-tridiagonal storage of the plane solver: subdomain p lies in
+// plane p / per_plane at local index p % per_plane; Adiag[k] (n_pl x n_pl, both triangles) and
+// Aoff[k] = the block of plane k's rows and plane k-1's columns (p >= q puts q's plane at or
+// below p's, and neighbours differ by at most one plane).
+__global__ void k_coarse_assemble_planes(DevMesh M, const int* __restrict__ pair_p, const int* __restrict__ pair_q,
+                                         const long long* __restrict__ pair_start, const int* __restrict__ trip_group,
+                                         const int* __restrict__ trip_i, const int* __restrict__ trip_j,
+                                         long long n_pairs, double* Adiag, double* Aoff, int per_plane, int n_pl) {
+  const long long pr = blockIdx.x;
+  if (pr >= n_pairs) return;
+  const int e = threadIdx.x;
+  if (e >= 36) return;
+  const int a = e / 6, b = e % 6;
+  const int p = pair_p[pr], q = pair_q[pr];
+  const double* Rp = M.R + M.subs[p].r_off;
+  const double* Rq = M.R + M.subs[q].r_off;
+  double s = 0.0;
+  for (long long t = pair_start[pr]; t < pair_start[pr + 1]; ++t) {
+    const GroupDev& g = M.groups[trip_group[t]];
+    const int i = trip_i[t], j = trip_j[t];
+    double m;
+    if (g.dirichlet) {
+      m = (i == j) ? 1.0 : 0.0;
+    } else {
+      m = 0.0;
+      for (int r = 1; r < g.k; ++r) m += M.helm[r * 8 + i] * M.helm[r * 8 + j];
+    }
+    s += Rp[(long long)M.slot_ldof[g.slot[i]] * 6 + a] * m * Rq[(long long)M.slot_ldof[g.slot[j]] * 6 + b];
+  }
+  const int kp = p / per_plane, kq = q / per_plane;
+  const long long ip = 6LL * (p % per_plane) + a, iq = 6LL * (q % per_plane) + b;
+  const long long blk = (long long)n_pl * n_pl;
+  if (kp == kq) {
+    Adiag[kp * blk + ip * n_pl + iq] = s;
+    if (p != q) Adiag[kp * blk + iq * n_pl + ip] = s;
+  } else {
+    Aoff[kp * blk + ip * n_pl + iq] = s;   // kq = kp - 1
+  }
+}
+
+// Apply of the plane solver (H = (G G^T)^-1 by block LDL^T over the planes):
+// first y_k = alpha W_k x_k for every plane (blockIdx.y = k), then the forward steps
+// y_k -= V_k y_{k-1}, k = 1..np-1, and the backward steps y_k -= U_k y_{k+1}, k = np-2..0.
+// One warp per row, the other plane's segment staged in shared memory.  T: FP64 blocks, or
+// their FP32 copies (FP32 products and sums); y8 (nullable): the padded FP32 copy of the final
+// y written by the last step that touches a plane (final != 0).
+template <typename T>
+__device__ __forceinline__ double plane_row_dot(const T* __restrict__ row, const void* xs, int n);
+template <>
+__device__ __forceinline__ double plane_row_dot<double>(const double* __restrict__ row, const void* xs, int n) {
+  const int lane = threadIdx.x & 31;
+  const double2* r2 = reinterpret_cast<const double2*>(row);
+  const double2* x2 = reinterpret_cast<const double2*>(xs);
+  double acc = 0.0;
+  for (int j = lane; j < (n >> 1); j += 32) {
+    const double2 a = __ldg(r2 + j), v = x2[j];
+    acc += a.x * v.x + a.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  return acc;
+}
+template <>
+__device__ __forceinline__ double plane_row_dot<float>(const float* __restrict__ row, const void* xs, int n) {
+  const int lane = threadIdx.x & 31;
+  const float2* r2 = reinterpret_cast<const float2*>(row);
+  const float2* x2 = reinterpret_cast<const float2*>(xs);
+  float acc = 0.f;
+  for (int j = lane; j < (n >> 1); j += 32) {
+    const float2 a = __ldg(r2 + j), v = x2[j];
+    acc += a.x * v.x + a.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  return double(acc);
+}
+
+template <typename T>
+__device__ __forceinline__ void plane_stage(const double* __restrict__ x, int n, void* xs) {
+  T* t = reinterpret_cast<T*>(xs);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) t[j] = T(x[j]);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void plane_y8(float* y8, long long grow, double v) {
+  if (y8) y8[(grow / 6) * 8 + grow % 6] = float(v);
+}
+
+template <typename T>
+__global__ void k_plane_first(const T* __restrict__ W, int n, const double* __restrict__ x, double alpha, double* y,
+                              float* y8, int final) {
+  extern __shared__ __align__(16) unsigned char plane_xs[];
+  const int k = blockIdx.y;
+  plane_stage<T>(x + (long long)k * n, n, plane_xs);
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const double v = alpha * plane_row_dot<T>(W + ((long long)k * n + r) * n, plane_xs, n);
+  if ((threadIdx.x & 31) == 0) {
+    const long long g = (long long)k * n + r;
+    y[g] = v;
+    if (final) plane_y8(y8, g, v);
+  }
+}
+
+template <typename T>
+__global__ void k_plane_step(const T* __restrict__ Mk, int n, const double* __restrict__ y_other, double* y_k,
+                             long long row0, float* y8, int final) {
+  extern __shared__ __align__(16) unsigned char plane_xs[];
+  plane_stage<T>(y_other, n, plane_xs);
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const double d = plane_row_dot<T>(Mk + (long long)r * n, plane_xs, n);
+  if ((threadIdx.x & 31) == 0) {
+    const double v = y_k[r] - d;
+    y_k[r] = v;
+    if (final) plane_y8(y8, row0 + r, v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Dense FP64 building blocks for the coarse problem (set-up only).
 // ---------------------------------------------------------------------------
@@ -799,13 +916,9 @@ void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st) 
   if (l > 0) k_h_to_f32<<<blocks_for(l * ld, 256), 256, 0, st>>>(H, l, ld, H32);
 }
 
-void launch_project32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                      float* hx8, double* out, cudaStream_t st) {
-  k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
-  static const int lim = dyn_smem_limit((const void*)k_gemv32);
-  cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  const long long ld = h32_ld(l);
-  k_gemv32<<<blocks_for(l, 16), 256, sizeof(float) * (size_t)ld, st>>>(H32, l, ld, gx, hx, hx8);
+void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
+                      double* out, cudaStream_t st) {
+  launch_G32_coarse32(M, C, x, gx, hx, hx8, st);
   if (M.n_mult > 0) k_GT_csr32<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv32, x, hx8, out);
 }
 
@@ -873,13 +986,10 @@ void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double*
   k_GT32_dot<<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr);
 }
 
-void launch_G32_gemv32(const DevMesh& M, const float* H32, long long l, const double* x, double* gx, double* hx,
-                       float* hx8, cudaStream_t st) {
+void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
+                         cudaStream_t st) {
   k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
-  static const int lim = dyn_smem_limit((const void*)k_gemv32);
-  cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  const long long ld = h32_ld(l);
-  k_gemv32<<<blocks_for(l, 16), 256, sizeof(float) * (size_t)ld, st>>>(H32, l, ld, gx, hx, hx8);
+  coarse_apply32(C, gx, hx, hx8, st);
 }
 
 void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,
@@ -960,5 +1070,81 @@ int dense_cholesky_inverse(double* A, double* work, long long l, int* err, cudaS
   dgemm(l, l, 0, l, 1.0, Y, 1, l, Y, l, 1, 0.0, A, l, 0, 1, st);
   return 0;
 }
+
+
+void launch_coarse_assemble_planes(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
+                                   const int* trip_group, const int* trip_i, const int* trip_j, long long n_pairs,
+                                   double* Adiag, double* Aoff, int per_plane, int n_pl, int n_planes,
+                                   cudaStream_t st) {
+  const size_t blk = (size_t)n_pl * n_pl;
+  cudaMemsetAsync(Adiag, 0, sizeof(double) * blk * n_planes, st);
+  cudaMemsetAsync(Aoff, 0, sizeof(double) * blk * n_planes, st);
+  if (n_pairs > 0)
+    k_coarse_assemble_planes<<<(unsigned)n_pairs, 64, 0, st>>>(M, pair_p, pair_q, pair_start, trip_group, trip_i,
+                                                                trip_j, n_pairs, Adiag, Aoff, per_plane, n_pl);
+}
+
+// Block LDL^T of the block-tridiagonal G G^T over the planes, with explicit inverses:
+// D_0 = A_00, D_k = A_kk - A_{k,k-1} W_{k-1} A_{k,k-1}^T, W_k = D_k^-1 (in place of Adiag),
+// V_k = W_k A_{k,k-1} (k >= 1), U_k = W_k A_{k+1,k}^T (k <= np-2).  T: n_pl^2 doubles,
+// work: dense_inverse_work(n_pl) doubles.  A non-positive pivot sets *err (device).
+void coarse_planes_factor(double* W, const double* Aoff, double* V, double* U, int n, int np, double* T,
+                          double* work, int* err, cudaStream_t st) {
+  const long long blk = (long long)n * n;
+  for (int k = 0; k < np; ++k) {
+    double* Wk = W + k * blk;
+    if (k > 0) {
+      const double* Ak = Aoff + k * blk;
+      dgemm(n, n, 0, n, 1.0, Ak, n, 1, W + (k - 1) * blk, n, 1, 0.0, T, n, 0, 0, st);   // T = A_{k,k-1} W_{k-1}
+      dgemm(n, n, 0, n, -1.0, T, n, 1, Ak, 1, n, 1.0, Wk, n, 0, 0, st);                // D_k = A_kk - T A^T
+    }
+    dense_cholesky_inverse(Wk, work, n, err, st);
+  }
+  for (int k = 0; k < np; ++k) {
+    const double* Wk = W + k * blk;
+    if (k > 0) dgemm(n, n, 0, n, 1.0, Wk, n, 1, Aoff + k * blk, n, 1, 0.0, V + k * blk, n, 0, 0, st);
+    if (k + 1 < np) dgemm(n, n, 0, n, 1.0, Wk, n, 1, Aoff + (k + 1) * blk, 1, n, 0.0, U + k * blk, n, 0, 0, st);
+  }
+}
+
+template <typename T>
+static void plane_apply(const T* W, const T* V, const T* U, int n, int np, const double* x, double alpha, double* y,
+                        float* y8, cudaStream_t st) {
+  const unsigned rb = (unsigned)((n + 7) / 8);
+  const size_t smem = sizeof(T) * (size_t)n;
+  const long long blk = (long long)n * n;
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_plane_first<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_plane_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  k_plane_first<T><<<dim3(rb, (unsigned)np), 256, smem, st>>>(W, n, x, alpha, y, y8, np == 1 ? 1 : 0);
+  for (int k = 1; k < np; ++k)
+    k_plane_step<T><<<rb, 256, smem, st>>>(V + k * blk, n, y + (long long)(k - 1) * n, y + (long long)k * n,
+                                           (long long)k * n, y8, k == np - 1 ? 1 : 0);
+  for (int k = np - 2; k >= 0; --k)
+    k_plane_step<T><<<rb, 256, smem, st>>>(U + k * blk, n, y + (long long)(k + 1) * n, y + (long long)k * n,
+                                           (long long)k * n, y8, 1);
+}
+
+void coarse_apply(const CoarseOp& C, const double* x, double alpha, double* y, cudaStream_t st) {
+  if (C.mode == kCoarseDense) {
+    launch_gemv(C.H, C.l, x, alpha, y, st);
+  } else {
+    plane_apply<double>(C.W, C.V, C.U, C.n_pl, C.n_planes, x, alpha, y, nullptr, st);
+  }
+}
+
+void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cudaStream_t st) {
+  if (C.mode == kCoarseDense) {
+    static const int lim = dyn_smem_limit((const void*)k_gemv32);
+    cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    const long long ld = h32_ld(C.l);
+    k_gemv32<<<blocks_for(C.l, 16), 256, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
+  } else {
+    plane_apply<float>(C.W32, C.V32, C.U32, C.n_pl, C.n_planes, x, 1.0, y, y8, st);
+  }
+}
+
+int coarse_launches(const CoarseOp& C) { return C.mode == kCoarseDense ? 1 : 2 * C.n_planes - 1; }
 
 }  // namespace tfeti

@@ -101,9 +101,9 @@ extern "C" int tfeti_apply_projector_noalloc(tfeti_ctx* c, const double* x, doub
   double* gx = scratch;
   double* hx = scratch + kMaxCoarse;
   tfeti::launch_G_apply(c->M, x, nullptr, gx, 1.0, c->st);
-  tfeti::launch_gemv(c->H, c->l, gx, 1.0, hx, c->st);
+  tfeti::coarse_apply(c->coarse, gx, 1.0, hx, c->st);
   tfeti::launch_GT_update(c->M, x, 1.0, hx, -1.0, y, c->st);
-  c->launches += 3;
+  c->launches += 2 + tfeti::coarse_launches(c->coarse);
   e = cudaGetLastError();                  // launch errors of these three kernels
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {

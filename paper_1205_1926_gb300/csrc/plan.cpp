@@ -53,6 +53,8 @@ int plan_build(const tfeti_problem* prob, Plan& plan) {
   if (prob->precond != TFETI_PRECOND_NONE && prob->precond != TFETI_PRECOND_LUMPED &&
       prob->precond != TFETI_PRECOND_DIRICHLET)
     return bad(plan, "bad preconditioner"), TFETI_ERR_ARG;
+  if (prob->coarse < TFETI_COARSE_AUTO || prob->coarse > TFETI_COARSE_PLANES)
+    return bad(plan, "bad coarse mode"), TFETI_ERR_ARG;
 
   const int nx = prob->nel[0], ny = prob->nel[1], nz = prob->nel[2];
   const int64_t nx1 = nx + 1, ny1 = ny + 1, nz1 = nz + 1;

@@ -137,6 +137,57 @@ def test_dual_operators_F_projector_precond_N(w):
     assert rel(host(outl), solver.N @ lam) <= 1e-11
 
 
+# ---------------------------------------------------------------------------- coarse solve by planes
+@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12, ONE_ELEMENT_BOXES])
+def test_plane_coarse_solve_parity(w):
+    """P_N and the FP64 dual solve with H = (G G^T)^-1 applied by the block LDL^T over the z-planes of
+    subdomains, against the oracle's dense Cholesky of N N^T; the mixed mode (FP32 plane blocks
+    inside) reaches the same solution."""
+    m, sig, kap, du = plastic_state(w, seed=33)
+    du = 0.2 * du
+    ctx = T.Context(w, coarse=T.COARSE_PLANES)
+    s = ctx.sizes
+    set_oracle_state(ctx, sig, kap)
+    df = m.traction_load((20.0, 5.0, -8.0))
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), dev(df), f)
+    m.sigma, m.kappa = sig, kap
+    Kb, f_or, _ = m.assemble(du, df)
+    solver = m.tfeti(Kb)
+    lam = W.seeded_vector(s["n_mult"], seed=34)
+    out = zeros(s["n_mult"])
+    ctx.apply("projector", dev(lam), out)
+    assert rel(host(out), solver.project(lam)) <= 1e-11
+    sol = solver.solve(f_or, rtol=1e-12)
+    for mixed in (False, True):
+        ctx.set_precision(mixed, 1e-3)
+        u, lm = zeros(s["n_dof"]), zeros(s["n_mult"])
+        info = ctx.dual_pcg(f, u, lm, rtol=1e-12, maxit=5000)
+        assert rel(host(u), sol["u"]) <= 1e-9, mixed
+        assert rel(host(lm), sol["lam"]) <= 1e-9, mixed
+        if not mixed:
+            assert abs(info["iterations"] - sol["iterations"]) <= 1
+
+
+def test_plane_coarse_solve_equals_dense_cube48():
+    """48^3 in 6 planes of 36 boxes (n_pl = 216): P_N by the plane solver equals the dense explicit
+    inverse to rounding, in FP64 and (inside the mixed mode's FP32 F-apply test of the projector) FP32."""
+    w = W.CUBE48
+    outs = []
+    for coarse in (T.COARSE_DENSE, T.COARSE_PLANES):
+        ctx = T.Context(w, coarse=coarse)
+        s = ctx.sizes
+        lam = dev(W.seeded_vector(s["n_mult"], seed=36))
+        y = zeros(s["n_mult"])
+        ctx.apply("projector", lam, y)
+        yN = zeros(s["n_coarse"])
+        ctx.apply("N", y, yN)
+        outs.append((host(y), np.abs(host(yN)).max() / np.abs(host(y)).max()))
+        ctx.close()
+    assert rel(outs[1][0], outs[0][0]) <= 1e-12
+    assert outs[1][1] <= 1e-12     # N P_N x = 0: the projection lands in Ker N
+
+
 # ---------------------------------------------------------------------------- Algorithm 3
 @pytest.mark.parametrize("w", [W.TINY_1x1x2, ONE_ELEMENT_BOXES, W.SMALL6_RAGGED, W.CUBE12])
 def test_dual_pcg_parity(w):

@@ -22,12 +22,13 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machine
 import paper_1205_1926_gb300 as T  # noqa: E402
 
 
-@pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
-def test_projector_noalloc_matches_allocating_entry_point(w):
-    """Both entry points launch the same three kernels in the same order on the same inputs, so
+@pytest.mark.parametrize("w,coarse", [(W.SMALL6_RAGGED, 0), (W.CUBE12, 0), (W.CUBE12, 2)])
+def test_projector_noalloc_matches_allocating_entry_point(w, coarse):
+    """Both entry points launch the same kernels in the same order on the same inputs, so
     their results are bitwise equal (the tolerance of the projector's parity tests, 1e-11, is
-    checked too, as the weaker statement)."""
-    ctx = T.Context(w)
+    checked too, as the weaker statement).  coarse = 2: the coarse solve by planes, whose
+    intermediate vectors also live in the static array."""
+    ctx = T.Context(w, coarse=coarse)
     m = ctx.sizes["n_mult"]
     for seed in (101, 102):
         x = torch.as_tensor(W.seeded_vector(m, seed)).cuda()
