@@ -321,7 +321,8 @@ def replica_value(elapsed_max, steps, world):
 
 
 # --------------------------------------------------------------------------------------- CUDA path
-ARMS = ("fp64", "mixed", "mixed_history", "mixed_learned", "mixed_history_bf16")
+ARMS = ("fp64", "mixed", "mixed_history", "mixed_learned")
+EXTRA_ARMS = ("mixed_learned_deflated", "mixed_history_bf16")   # measured variants that lose (--extra-arms)
 ARM_NOTES = {
     "fp64": "Algorithm 3 in FP64 (banded K^+ applies), the paper's method",
     "mixed": "FP64-refined PCGP: FP32 dual Schur blocks on the tensor cores (elastic) and FP32 banded solves "
@@ -330,6 +331,8 @@ ARM_NOTES = {
                      "solver's last 8 solutions, zero-start fallback",
     "mixed_learned": "the mixed arm with the learned start: the last 7 solutions plus the per-interface MLP "
                      "prediction (trained online on the solver's own lambda histories) as Galerkin vectors",
+    "mixed_learned_deflated": "the mixed_learned arm with each inner PCGP deflated by 4 vectors: the network's "
+                              "prediction and the most recent stored solutions, projected, A W by the inner operator",
     "mixed_history_bf16": "the mixed_history arm with the dual Schur blocks of the inner F-apply stored in BF16 "
                           "(X split into BF16 hi/lo, FP32 accumulation) instead of TF32 x 3",
 }
@@ -374,11 +377,15 @@ def run_gpu(args, rank, world, local_rank):
             c.set_precision(True, args.inner_rtol)
         if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
-        if arm == "mixed_learned":
+        if arm in ("mixed_learned", "mixed_learned_deflated"):
             c.set_recycling(min(args.history, 7))
             c.set_learned(True)
+        if arm == "mixed_learned_deflated":
+            c.set_deflation(args.deflation)
         if arm != "fp64" and (arm.endswith("_bf16") or args.schur_format == "bf16"):
             c.set_schur_format(True)
+        if arm != "fp64" and args.no_woodbury:
+            c.set_woodbury(False)
         if args.no_graphs:
             c.set_graphs(False)
         return c
@@ -387,9 +394,11 @@ def run_gpu(args, rank, world, local_rank):
         # the history and the network start over (the first-yield solve must not seed them)
         if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
-        if arm == "mixed_learned":
+        if arm in ("mixed_learned", "mixed_learned_deflated"):
             c.set_recycling(min(args.history, 7))
             c.set_learned(True)
+        if arm == "mixed_learned_deflated":
+            c.set_deflation(args.deflation)
 
     fp64_peak = T.measure_fp64_fma(stream)           # roofline denominator of the FP64 kernels
     ctx = make_ctx(main_arm)
@@ -450,7 +459,9 @@ def run_gpu(args, rank, world, local_rank):
         clocks = sampler.stop() if sampler else None
         elapsed = max_over_ranks([e0.elapsed_time(e1) / 1e3], dev)[0]
         return {"elapsed": elapsed, "infos": infos, "snaps": snaps, "tm": c.timing(), "clocks": clocks,
-                "tuning": c.tuning() if hasattr(c, "tuning") else None}
+                "tuning": c.tuning() if hasattr(c, "tuning") else None,
+                "deflation": c.deflation_stats() if arm == "mixed_learned_deflated" else None,
+                "woodbury": c.woodbury_stats() if arm != "fp64" else None}
 
     main = timed_run(ctx, main_arm, headline=True)
     ctx.close()
@@ -484,7 +495,7 @@ def run_gpu(args, rank, world, local_rank):
     # ---- the other arms of the metric on the same load history
     runs = {main_arm: main}
     if not args.no_mixed:
-        for arm in ARMS:
+        for arm in ARMS + (EXTRA_ARMS if args.extra_arms else ()):
             if arm == main_arm:
                 continue
             c = make_ctx(arm)
@@ -557,6 +568,7 @@ def run_gpu(args, rank, world, local_rank):
         v = replica_value(r["elapsed"], args.steps, world)
         d = rel_u_diffs(r)
         arms[arm] = {"value": v, "unit": UNIT, "headline_speedup": v / value, "note": ARM_NOTES[arm],
+                     "deflation": r.get("deflation"), "woodbury": r.get("woodbury"),
                      "max_rel_u_diff_vs_fp64": max(d) if d else None, "rel_u_diff_vs_fp64_per_step": d,
                      "inner_fapply_tuning": r["tuning"] if arm != "fp64" else None} | per_step(r)
     main_d = rel_u_diffs(main)
@@ -575,7 +587,13 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": roof,
             "clocks": main["clocks"],
             "max_rel_u_diff_vs_fp64": max(main_d) if main_d else None,
+            "inner_iteration": {"ms_total": tm["inner_ms_total"], "iterations": tm["inner_iterations"],
+                                "body_runs": tm["inner_body_runs"],
+                                "us_per_body_run": 1e3 * tm["inner_ms_total"] / max(tm["inner_body_runs"], 1),
+                                "note": "device time of the inner FP32 PCGP graph launches (CUDA events) per body "
+                                        "run (one PCGP iteration)"},
             "solver": {"t_y": t_y, "plastic_gp_final": main["infos"][-1]["plastic_committed"],
+                       "woodbury": main.get("woodbury"),
                        "refactored_per_step": [s["refactored"] for s in main["infos"]],
                        "factor_ms_total": tm["factor_ms_total"], "f_apply_ms_total": tm["f_apply_ms_total"],
                        "inner_fapply_tuning": main["tuning"] if main_arm != "fp64" else None,
@@ -625,9 +643,11 @@ def run_cases(args, rank, world, local_rank):
                 c.set_schur_format(True)
         if arm in ("mixed_history", "mixed_history_bf16"):
             c.set_recycling(args.history)
-        if arm == "mixed_learned":
+        if arm in ("mixed_learned", "mixed_learned_deflated"):
             c.set_recycling(min(args.history, 7))
             c.set_learned(True)
+        if arm == "mixed_learned_deflated":
+            c.set_deflation(args.deflation)
 
     for c in ctxs:
         start(c)
@@ -736,7 +756,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", metavar="WORKLOAD", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiler runs)")
-    ap.add_argument("--arm", default=None, choices=list(ARMS),
+    ap.add_argument("--arm", default=None, choices=list(ARMS + EXTRA_ARMS),
                     help="the headline (timed, end-to-end) arm; default mixed_learned, the metric's method")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="shorthand: fp64 = --arm fp64, mixed = --arm mixed (or mixed_learned with --learned)")
@@ -745,6 +765,12 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="time the headline arm only (no other arms)")
     ap.add_argument("--fapply", default="banded", choices=["banded", "schur"],
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
+    ap.add_argument("--extra-arms", action="store_true",
+                    help="also time the deflated learned arm and the BF16 Schur arm (both measured slower)")
+    ap.add_argument("--no-woodbury", action="store_true",
+                    help="mixed arms: plastic subdomains keep FP32 banded solves in the inner F-apply")
+    ap.add_argument("--deflation", type=int, default=4,
+                    help="deflation vectors of the inner PCGP in the mixed_learned_deflated arm (1..8)")
     ap.add_argument("--coarse", default="auto", choices=["auto", "dense", "planes"],
                     help="coarse solve of the projector: explicit dense inverse, or block LDL^T over the z-planes "
                          "of subdomains (auto: planes above 6144 coarse unknowns)")

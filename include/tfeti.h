@@ -318,6 +318,39 @@ int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
  * last layer (the untrained predictor is la).  enable = 0 turns it off. */
 #define TFETI_MLP_PARAMS 4801
 int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr);
+
+/* Inner (FP32) F-apply of subdomains with plastic points in the mixed mode (an extension;
+ * default on).  The plastic tangent of Algorithm 5 differs from the shape's elastic matrix by
+ * the element corrections, K_p = K_el - U U^T with six columns per plastic Gauss point
+ * (sqrt(a |T|) B^T F, F F^T = E_eps, and sqrt(b |T|) B^T n of the Clarke tangent, Sec. 3.1),
+ * so by the Sherman-Morrison-Woodbury identity (K_p^+)_bb = S_el + Z_b C^-1 Z_b^T with
+ * Z_b = (K_el^+)_{b,:} U and C = I - U^T K_el^+ U.  Such a subdomain then joins its shape's
+ * tensor-core GEMM with the elastic subdomains and adds two skinny products, instead of a
+ * banded FP32 solve (a chain of 2 x n / 32 dependent block steps).  Applies to shapes with a
+ * dual Schur block in use and at most 3072 dofs (whose dense K_el^+ is formed once, FP32) and
+ * to subdomains with at most 96 plastic points; the others keep the banded solve.  Set up at
+ * every assembly in the mixed mode; FP64 solves are unchanged.  enable = 0 turns it off from
+ * the next assembly.  Stats: subdomains set up so since the context was made, and set-ups
+ * that fell back to banded solves (a C whose Cholesky failed). */
+int tfeti_set_woodbury(tfeti_ctx* ctx, int32_t enable);
+int tfeti_get_woodbury_stats(tfeti_ctx* ctx, int64_t* subdomains, int64_t* fallbacks);
+
+/* Deflation of the inner PCGP of the mixed mode (an extension; Algorithm 3's projected CG
+ * with the search directions kept conjugate to a deflation space W).  Per dual solve, at its
+ * first inner solve, W holds the network's prediction (when the learned start formed one)
+ * and the most recent stored solutions of the history start, up to k vectors, each
+ * projected by P_N; A W is taken with the inner FP32 operators (P F P) and E = W^T A W is
+ * inverted over its independent columns.  Every inner solve then starts from the Galerkin
+ * correction in span W and each search direction loses its A-conjugate part in span W:
+ * p = y + beta p - W E^-1 (A W)^T y.  If an outer refinement pass with deflation does not
+ * reduce the FP64 residual, the rest of that dual solve runs the plain inner PCGP (fallback).
+ * k = 0 (default) switches it off.  Requires tfeti_set_recycling (else TFETI_ERR_ARG); costs
+ * k FP32 F-applies per dual solve that reaches the inner iterations.  Errors: TFETI_ERR_ARG
+ * (k outside 0..8), TFETI_ERR_OOM. */
+int tfeti_set_deflation(tfeti_ctx* ctx, int32_t k);
+/* Since the last tfeti_set_deflation: deflation spaces formed, their total kept vectors,
+ * and dual solves that fell back to the plain inner PCGP (all nullable). */
+int tfeti_get_deflation_stats(tfeti_ctx* ctx, int64_t* setups, int64_t* vectors, int64_t* fallbacks);
 /* For tests and tools: the FP32 master weights (host float[TFETI_MLP_PARAMS]: W1 [64][8],
  * b1 [64], W2 [64][64], b2 [64], w3 [64], b3), the prediction y (device [n_mult]) for
  * given device inputs la, lb, d [n_mult], pf_now, pf_prev [n_sub] and host scal[4] =
@@ -449,6 +482,11 @@ typedef struct tfeti_timing {
     int64_t schur_launches;
     double schur_flops_total;
     double schur_bytes_total;
+    /* mixed mode: device time of the inner FP32 PCGP solves launched as graphs, their PCGP
+     * iterations and graph body runs (each run is one iteration; the last may stop early) */
+    double inner_ms_total;
+    int64_t inner_iterations;
+    int64_t inner_body_runs;
 } tfeti_timing;
 int tfeti_timing_get(tfeti_ctx* ctx, tfeti_timing* out);
 int tfeti_timing_reset(tfeti_ctx* ctx, int32_t enable_events);

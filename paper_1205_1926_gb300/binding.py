@@ -62,7 +62,8 @@ class Timing(C.Structure):
     _fields_ = [("f_apply_ms_total", C.c_double), ("f_apply_launches", C.c_int64), ("f_apply_bytes", C.c_double),
                 ("f_apply_flops", C.c_double), ("factor_ms_total", C.c_double), ("factor_launches", C.c_int64),
                 ("kernel_launches", C.c_int64), ("schur_ms_total", C.c_double), ("schur_launches", C.c_int64),
-                ("schur_flops_total", C.c_double), ("schur_bytes_total", C.c_double)]
+                ("schur_flops_total", C.c_double), ("schur_bytes_total", C.c_double), ("inner_ms_total", C.c_double),
+                ("inner_iterations", C.c_int64), ("inner_body_runs", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -94,6 +95,10 @@ SIGNATURES = {
     "tfeti_set_fapply": (C.c_int, [_P, _I]),
     "tfeti_set_schur_format": (C.c_int, [_P, _I]),
     "tfeti_set_schur_threshold": (C.c_int, [_P, _I]),
+    "tfeti_set_deflation": (C.c_int, [_P, _I]),
+    "tfeti_set_woodbury": (C.c_int, [_P, _I]),
+    "tfeti_get_woodbury_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "tfeti_get_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tfeti_get_tuning": (C.c_int, [_P, _P, _P, _P]),
     "tfeti_set_recycling": (C.c_int, [_P, _I]),
     "tfeti_set_learned": (C.c_int, [_P, _I, _I, _D]),
@@ -344,6 +349,24 @@ class Context:
     def set_schur_format(self, bf16: bool):
         """Inner Schur apply of the mixed mode with BF16 S (two MMAs per step) or TF32 x 3 (default)."""
         return self._check(self.lib.tfeti_set_schur_format(self.h, 1 if bf16 else 0), "tfeti_set_schur_format")
+
+    def set_woodbury(self, enable: bool):
+        """Inner F-apply of plastic subdomains by the shape's Schur block + a Woodbury correction."""
+        return self._check(self.lib.tfeti_set_woodbury(self.h, 1 if enable else 0), "tfeti_set_woodbury")
+
+    def woodbury_stats(self) -> dict:
+        a, b = C.c_int64(), C.c_int64()
+        self.lib.tfeti_get_woodbury_stats(self.h, C.byref(a), C.byref(b))
+        return {"subdomains": a.value, "fallbacks": b.value}
+
+    def set_deflation(self, k: int):
+        """Deflate the inner PCGP with up to k vectors (network prediction, stored solutions); 0: off."""
+        return self._check(self.lib.tfeti_set_deflation(self.h, int(k)), "tfeti_set_deflation")
+
+    def deflation_stats(self) -> dict:
+        a, b, f = C.c_int64(), C.c_int64(), C.c_int64()
+        self.lib.tfeti_get_deflation_stats(self.h, C.byref(a), C.byref(b), C.byref(f))
+        return {"setups": a.value, "vectors": b.value, "fallbacks": f.value}
 
     def set_schur_threshold(self, threshold: int):
         """Shapes with >= threshold subdomains use their Schur block in the inner F-apply (0: tune)."""

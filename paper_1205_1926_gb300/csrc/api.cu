@@ -240,18 +240,21 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   c->h_np = plastic_count;
   const bool have_use = c->schur_use.size() == c->plan.shapes.size();
   auto uses_schur = [&](int sh) { return have_use && c->schur_use[sh]; };
+  const bool have_wood = c->h_wood.size() == (size_t)ns;
+  auto wood = [&](int p) { return have_wood && c->h_wood[p] && uses_schur(c->h_subs[p].shape); };
   for (size_t sh = 0; sh < c->plan.shapes.size(); ++sh) {
     c->el_off[sh] = (int)c->h_el.size();
     if (uses_schur((int)sh))
       for (int p = 0; p < ns; ++p)
-        if (plastic_count[p] == 0 && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
+        if ((plastic_count[p] == 0 || wood(p)) && c->h_subs[p].shape == (int)sh) c->h_el.push_back(p);
     c->el_cnt[sh] = (int)c->h_el.size() - c->el_off[sh];
   }
-  // banded items beside the Schur GEMMs: subdomains with plastic points and the elastic
-  // subdomains of shapes without a Schur block in use
+  // banded items beside the Schur GEMMs: subdomains with plastic points (unless their inner apply
+  // goes through the Schur block and a Woodbury correction) and the elastic subdomains of shapes
+  // without a Schur block in use
   std::vector<SolveItem> pl, pl64;
   for (const SolveItem& it : c->h_items32)
-    if ((it.fac & kOwnFac) || !uses_schur(c->h_subs[it.sub[0]].shape)) pl.push_back(it);
+    if (((it.fac & kOwnFac) && !wood(it.sub[0])) || !uses_schur(c->h_subs[it.sub[0]].shape)) pl.push_back(it);
   for (const SolveItem& it : c->h_items)
     if ((it.fac & kOwnFac) || !uses_schur(c->h_subs[it.sub[0]].shape)) pl64.push_back(it);
   c->n_items_pl = (int)pl.size();
@@ -426,6 +429,10 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract = true) {
                                 c->d_err, c->st);
       c->launches += 2;
     }
+    if (c->wood.n > 0) {   // plastic subdomains on their shape's block: + Z_b C^-1 Z_b^T x_b
+      launch_wood_apply(c->M, c->wood, x, c->cbuf, c->st);
+      c->launches += 2;
+    }
     if (c->n_items_pl > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
   }
   if (contract) {
@@ -567,6 +574,172 @@ int ensure_schur_bf16(tfeti_ctx* c) {
   }
   sync(c);
   return cuda_check(c, "forming BF16 Schur tiles");
+}
+
+// Dense FP32 K^+ (fixing-dof generalised inverse of the elastic template) of every shape with a
+// formed dual Schur block and at most kWoodMaxN dofs, from unit right-hand sides through the FP64
+// banded solve; formed once (a case context shares its base's).  Used by the Woodbury inner apply.
+int ensure_kinv(tfeti_ctx* c) {
+  if (c->kinv32) return TFETI_OK;
+  if (c->base) {
+    const int st = ensure_kinv(c->base);
+    if (st != TFETI_OK) return fail(c, st, c->base->err);
+    c->kinv32 = c->base->kinv32;
+    c->kinv_off = c->base->kinv_off;
+    c->d_kinv_off = c->base->d_kinv_off;
+    return TFETI_OK;
+  }
+  const Plan& P = c->plan;
+  const size_t nsh = P.shapes.size();
+  c->kinv_off.assign(nsh, -1);
+  long long tot = 0;
+  for (size_t sh = 0; sh < nsh; ++sh) {
+    const int n = (int)P.shapes[sh].n_dof;
+    if (!c->schur_formed[sh] || n > kWoodMaxN) continue;
+    c->kinv_off[sh] = tot;
+    tot += (long long)n * n;
+  }
+  try {
+    c->kinv32 = dalloc<float>(c, (size_t)std::max(1LL, tot));
+    c->d_kinv_off = upload(c, c->kinv_off);
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed");
+  }
+  for (size_t sh = 0; sh < nsh; ++sh) {
+    if (c->kinv_off[sh] < 0) continue;
+    const int n = (int)P.shapes[sh].n_dof;
+    std::vector<SolveItem> items;
+    for (int j = 0; j < n; j += c->rcap) {
+      SolveItem it{};
+      it.fac = c->tmpl_fac_off[sh];
+      for (int r = 0; r < c->rcap && j + r < n; ++r) it.sub[it.count++] = j + r;
+      items.push_back(it);
+    }
+    SolveItem* d_items = nullptr;
+    try {
+      d_items = upload(c, items);
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+    SolveArgs a = solve_args(c);
+    a.items = d_items;
+    a.n_items = (int)items.size();
+    a.in_mode = 5;
+    a.out_mode = 4;
+    a.rep_sub = P.shapes[sh].rep_sub;
+    a.S32 = c->kinv32;
+    a.s_off = c->kinv_off[sh];
+    launch_sub_solve(c->M, a, c->solve_smem, c->st);
+    c->launches += 1;
+    sync(c);
+  }
+  return cuda_check(c, "forming dense K^+ blocks");
+}
+
+// Woodbury set-up of the plastic subdomains chosen in c->h_wood (after an assembly in the mixed
+// mode): their plastic points, C, Z_b^T and Y = C^-1 Z_b^T; pools grown on demand.  A subdomain
+// whose C fails its Cholesky (not expected: C is positive definite) returns to banded solves.
+int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
+  c->wood.n = 0;
+  std::vector<int> list, npts;
+  std::vector<long long> pt_off, c_off, z_off, d_off;
+  long long pts_tot = 0, c_tot = 0, z_tot = 0, d_tot = 0;
+  int max_pts = 0, max_bd = 0;
+  for (size_t p = 0; p < c->h_wood.size(); ++p) {
+    if (!c->h_wood[p]) continue;
+    const int k = np[p], r = 6 * k, n_bd = 3 * c->plan.shapes[c->h_subs[p].shape].n_bnd;
+    list.push_back((int)p);
+    npts.push_back(k);
+    pt_off.push_back(pts_tot);
+    c_off.push_back(c_tot);
+    z_off.push_back(z_tot);
+    d_off.push_back(d_tot);
+    pts_tot += k;
+    c_tot += (long long)r * r;
+    z_tot += (long long)r * n_bd;
+    d_tot += (long long)((r + 31) / 32) * 32 * 32;
+    max_pts = std::max(max_pts, k);
+    max_bd = std::max(max_bd, n_bd);
+  }
+  if (list.empty()) return TFETI_OK;
+  try {
+    const int nl = (int)list.size();
+    if (!c->d_wood_list) {
+      const int ns = (int)c->h_subs.size();
+      c->d_wood_list = dalloc<int>(c, ns);
+      c->d_wood_np = dalloc<int>(c, ns);
+      c->d_wood_pt_off = dalloc<long long>(c, ns);
+      c->d_wood_c_off = dalloc<long long>(c, ns);
+      c->d_wood_z_off = dalloc<long long>(c, ns);
+      c->d_wood_d_off = dalloc<long long>(c, ns);
+    }
+    if (d_tot > c->wood_d_cap) {
+      c->wood_d_cap = std::max(d_tot, 2 * c->wood_d_cap);
+      c->wood_d = dalloc<float>(c, (size_t)c->wood_d_cap);
+    }
+    if (pts_tot > c->wood_pts_cap) {
+      c->wood_pts_cap = std::max(pts_tot, 2 * c->wood_pts_cap);
+      c->d_wood_pts = dalloc<int>(c, (size_t)c->wood_pts_cap);
+    }
+    if (c_tot > c->wood_c_cap) {
+      c->wood_c_cap = std::max(c_tot, 2 * c->wood_c_cap);
+      c->wood_c = dalloc<float>(c, (size_t)c->wood_c_cap);
+    }
+    if (z_tot > c->wood_z_cap) {
+      c->wood_z_cap = std::max(z_tot, 2 * c->wood_z_cap);
+      c->wood_z = dalloc<float>(c, (size_t)c->wood_z_cap);
+      c->wood_y = dalloc<float>(c, (size_t)c->wood_z_cap);
+    }
+    if (!c->wood_t) c->wood_t = dalloc<float>(c, (size_t)c->h_subs.size() * 6 * kWoodMaxPts);
+    cudaMemcpyAsync(c->d_wood_list, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_np, npts.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_pt_off, pt_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_c_off, c_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_z_off, z_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_d_off, d_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed (Woodbury pools)");
+  }
+  WoodArgs& w = c->wood;
+  w.n = (int)list.size();
+  w.max_pts = max_pts;
+  w.max_bd = max_bd;
+  w.list = c->d_wood_list;
+  w.pt_off = c->d_wood_pt_off;
+  w.n_pts = c->d_wood_np;
+  w.pts = c->d_wood_pts;
+  w.plastic = c->plastic;
+  w.pa = c->pa;
+  w.pb = c->pb;
+  w.pn = c->pn;
+  w.kinv = c->kinv32;
+  w.kinv_off = c->d_kinv_off;
+  w.c_off = c->d_wood_c_off;
+  w.c_pool = c->wood_c;
+  w.z_off = c->d_wood_z_off;
+  w.z_pool = c->wood_z;
+  w.y_pool = c->wood_y;
+  w.z_total = z_tot;
+  w.tbuf = c->wood_t;
+  w.d_off = c->d_wood_d_off;
+  w.d_pool = c->wood_d;
+  w.err = c->d_err;
+  cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+  launch_wood_setup(c->M, w, c->st);
+  c->launches += wood_setup_launches(w);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  if (herr & 8) {   // keep the banded solves for this assembly
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    std::fill(c->h_wood.begin(), c->h_wood.end(), 0);
+    c->wood.n = 0;
+    c->wood_fallbacks += 1;
+    build_items(c, np);
+    return cuda_check(c, "Woodbury set-up");
+  }
+  c->wood_subs += w.n;
+  return cuda_check(c, "Woodbury set-up");
 }
 
 void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract);
@@ -733,7 +906,22 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
   }
   cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
   c->last_refactored.push_back((int)list.size());
+  // inner F-apply of the plastic subdomains: their shape's Schur block plus a Woodbury correction
+  // where the shape keeps a dense K^+ and the subdomain has at most kWoodMaxPts plastic points
+  c->h_wood.assign(M.n_sub, 0);
+  c->wood.n = 0;
+  const bool wood_ok = c->wood_on && c->precision == TFETI_PRECISION_MIXED && c->schur_ready && c->kinv32 &&
+                       c->schur_use.size() == c->plan.shapes.size();
+  if (wood_ok)
+    for (int p = 0; p < M.n_sub; ++p) {
+      const int sh = c->h_subs[p].shape;
+      c->h_wood[p] = np[p] > 0 && np[p] <= kWoodMaxPts && c->kinv_off[sh] >= 0 && c->schur_use[sh];
+    }
   build_items(c, np);
+  if (wood_ok) {
+    const int wst = wood_setup(c, np);
+    if (wst != TFETI_OK) return wst;
+  }
   if (!list.empty()) {
     cudaMemcpyAsync(c->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_list_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
@@ -916,8 +1104,9 @@ void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h, bool has_h) {
   launch_GT32_dot(c->M, c->rin, c->hx8, c->w, nullptr, 0, c->sc, c->partial, c->d_ctr, c->st);   // w = P r, w.w
   op_precond32(c, c->w, c->z);                                                                   // z = F^-1 w
   launch_G32_coarse32(c->M, c->coarse, c->z, c->gx, c->hx, c->hx8, c->st);
-  launch_GT32_dot(c->M, c->z, c->hx8, c->y, c->w, 1, c->sc, c->partial, c->d_ctr + 1, c->st);  // y = P z, y.w
-  launch_p_update_g(m, c->y, c->pdir, c->sc, c->st);                                           // p = y + beta p
+  launch_GT32_dot(c->M, c->z, c->hx8, c->y, c->w, 1, c->sc, c->partial, c->d_ctr + 1, c->st,   // y = P z, y.w
+                  c->defl_AW, c->defl_Einv);                                                     // (and mu)
+  launch_p_update_g(m, c->y, c->pdir, c->sc, c->st, c->defl_W);                               // p = y + beta p - W mu
   op_F32(c, c->pdir, c->Fp, false);                                                              // slots of F p
   launch_contract_dot(c->M, c->cbuf, c->Fp, c->pdir, c->sc, c->partial, c->d_ctr + 2, c->st);  // F p, p.Fp
   launch_lam_r_update_post(m, c->pdir, c->Fp, c->dlt, c->rin, c->sc, c->d_ctr + 3, h, has_h ? 1 : 0, c->st);
@@ -981,11 +1170,19 @@ PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
     if (o.status != TFETI_OK) return o;
   }
   launch_pcg_init(c->sc, tol_abs * tol_abs, maxit, c->st);
+  if (c->events) cudaEventRecord(c->in_e0, c->st);
   cudaGraphLaunch(c->g_inner_exec, c->st);
+  if (c->events) cudaEventRecord(c->in_e1, c->st);
   cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, c->st);
   sync(c);
   const double* h = c->h_sc;
   o.it = (int)h[kIter];
+  if (c->events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->in_e0, c->in_e1) == cudaSuccess) c->inner_ms += ms;
+    c->inner_its += o.it;
+    c->inner_runs += (long long)h[kBodyRuns];
+  }
   c->launches += 1 + (long long)c->g_body_kernels * (long long)h[kBodyRuns];
   c->f32_launches += (long long)h[kBodyRuns];
   o.w_norm = std::sqrt(std::max(0.0, h[kLastWW]));
@@ -995,6 +1192,108 @@ PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
   const int st = cuda_check(c, "inner PCGP graph");
   if (st != TFETI_OK) o.status = st;
   return o;
+}
+
+// Deflation space of the inner PCGP for the current dual solve (formed at its first inner
+// solve): the network's prediction when the start formed one, then the most recent stored
+// solutions, up to defl_req vectors; each projected by P_N in FP64 and scaled to unit length,
+// A W = P F P W with the inner FP32 operators, and E = W^T A W inverted on the host over its
+// independent columns (a Cholesky that drops columns whose pivot shows them dependent on those
+// kept, at the accuracy of the FP32 products).
+int deflation_setup(tfeti_ctx* c) {
+  c->defl_formed = true;
+  c->defl_k = 0;
+  const long long m = c->M.n_mult;
+  std::vector<const double*> src;
+  if (c->mlp_slot_valid) src.push_back(c->rec_L + (long long)c->rec_n * m);
+  for (int i = 0; i < c->rec_n && (int)src.size() < c->defl_req; ++i) {
+    const int slot = ((c->rec_head - 1 - i) % c->rec_q + c->rec_q) % c->rec_q;
+    src.push_back(c->rec_L + (long long)slot * m);
+  }
+  const int k = (int)src.size();
+  double zero = 0.0;
+  if (k == 0) {
+    cudaMemcpyAsync(c->sc + kDeflK, &zero, sizeof(double), cudaMemcpyHostToDevice, c->st);
+    sync(c);
+    return cuda_check(c, "deflation set-up");
+  }
+  for (int j = 0; j < k; ++j) {
+    double* Wj = c->defl_W + (long long)j * m;
+    op_project(c, src[j], Wj);
+    const double nrm = std::sqrt(std::max(0.0, dot_host(c, Wj, Wj, m)));
+    launch_axpby(m, nrm > 0.0 ? 1.0 / nrm : 0.0, Wj, 0.0, nullptr, Wj, c->st);   // unit vectors
+    op_F32(c, Wj, c->tm);
+    op_project32(c, c->tm, c->defl_AW + (long long)j * m);
+  }
+  launch_rec_gram(c->defl_W, c->defl_AW, c->defl_W, k, m, c->rec_partial, c->rec_out, c->st);
+  double g[kRecMax * kRecMax + kRecMax];
+  cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  c->launches += 2;
+  // E (symmetrised), its Cholesky over the kept columns, and E^-1 on them (zero elsewhere)
+  std::vector<double> E(k * k), L(k * k, 0.0), Einv(kDeflMax * kDeflMax, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) E[i * k + j] = 0.5 * (g[i * kRecMax + j] + g[j * kRecMax + i]);
+  std::vector<int> kept;
+  for (int j = 0; j < k; ++j) {
+    std::vector<double> row(kept.size());
+    double d = E[j * k + j];
+    for (size_t a = 0; a < kept.size(); ++a) {
+      double v = E[j * k + kept[a]];
+      for (size_t b = 0; b < a; ++b) v -= row[b] * L[a * k + b];
+      row[a] = v / L[a * k + a];
+      d -= row[a] * row[a];
+    }
+    // A W comes from FP32 operators (~1e-7 relative), so a pivot below 1e-4 of its diagonal would
+    // amplify rounding into the search directions: such a vector counts as dependent
+    if (!(d > 1e-4 * E[j * k + j]) || !std::isfinite(d)) continue;
+    const size_t a = kept.size();
+    for (size_t b = 0; b < a; ++b) L[a * k + b] = row[b];
+    L[a * k + a] = std::sqrt(d);
+    kept.push_back(j);
+  }
+  const int kk = (int)kept.size();
+  for (int col = 0; col < kk; ++col) {   // column col of (L L^T)^-1 by two triangular solves
+    std::vector<double> y(kk, 0.0), x(kk, 0.0);
+    for (int a = 0; a < kk; ++a) {
+      double v = a == col ? 1.0 : 0.0;
+      for (int b = 0; b < a; ++b) v -= L[a * k + b] * y[b];
+      y[a] = v / L[a * k + a];
+    }
+    for (int a = kk - 1; a >= 0; --a) {
+      double v = y[a];
+      for (int b = a + 1; b < kk; ++b) v -= L[b * k + a] * x[b];
+      x[a] = v / L[a * k + a];
+    }
+    for (int a = 0; a < kk; ++a) Einv[kept[a] * kDeflMax + kept[col]] = x[a];
+  }
+  cudaMemcpyAsync(c->defl_Einv, Einv.data(), sizeof(double) * Einv.size(), cudaMemcpyHostToDevice, c->st);
+  const double kd = kk > 0 ? (double)k : 0.0;
+  cudaMemcpyAsync(c->sc + kDeflK, &kd, sizeof(double), cudaMemcpyHostToDevice, c->st);
+  sync(c);
+  c->defl_k = kk > 0 ? k : 0;
+  c->defl_setups += 1;
+  c->defl_vectors += kk;
+  return cuda_check(c, "deflation set-up");
+}
+
+// Deflated start of one inner solve on (dlt = 0, rin): dlt = W E^-1 W^T rin, rin -= A W E^-1 W^T rin.
+void deflation_start(tfeti_ctx* c) {
+  const long long m = c->M.n_mult;
+  const int k = c->defl_k;
+  launch_rec_gram(c->defl_W, c->defl_AW, c->rin, k, m, c->rec_partial, c->rec_out, c->st);
+  double g[kRecMax * kRecMax + kRecMax];
+  std::vector<double> Ei(kDeflMax * kDeflMax);
+  cudaMemcpyAsync(g, c->rec_out, sizeof(g), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(Ei.data(), c->defl_Einv, sizeof(double) * Ei.size(), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  std::vector<double> coef(k, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) coef[i] += Ei[i * kDeflMax + j] * g[kRecMax * kRecMax + j];
+  cudaMemcpyAsync(c->rec_c, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->st);
+  launch_rec_combine(c->defl_W, c->rec_c, k, m, nullptr, 1.0, c->dlt, c->st);
+  launch_rec_combine(c->defl_AW, c->rec_c, k, m, c->rin, -1.0, c->rin, c->st);
+  c->launches += 4;
 }
 
 // The same inner PCGP launched body by body from the host (no graph): the host reads the
@@ -1132,6 +1431,7 @@ bool mlp_scalars(tfeti_ctx* c, double r0) {
 int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   const long long m = c->M.n_mult;
   const int n = c->rec_n;
+  c->mlp_slot_valid = false;
   op_project(c, c->r, c->w);
   const double w0 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
   if (w0 <= tol_abs) return 0;   // the zero start already meets the stopping test
@@ -1175,6 +1475,7 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
     coef = coef2;
     nb = n + 1;
     with_mlp = coef2[n] != 0.0;
+    c->mlp_slot_valid = true;
   }
   if (nb == 0 || !(pred < c->rec_accept * w0)) return 0;
   ++c->rec_tried;
@@ -1258,6 +1559,9 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   const bool history = c->rec_q > 0 && m > 0;
   if (history) cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   c->mlp_missed = c->rec_n == 0;   // set by the history start when it runs
+  c->defl_formed = false;          // the deflation space is formed again for this solve
+  c->defl_k = 0;
+  cudaMemsetAsync(c->sc + kDeflK, 0, sizeof(double), c->st);
   if (lambda0) {
     op_project(c, lambda0, c->lamk);
     launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
@@ -1277,10 +1581,18 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
       // FP64 iterative refinement of the dual problem: the true residual
       // r = d~ - F lambda_Ker (FP64 solves) is corrected by inner PCGP solves whose
       // F-applies are FP32; the stopping test is Algorithm 3's, on the FP64 residual.
+      double wn_prev = HUGE_VAL;
       for (outer = 0; outer < 100;) {
         op_project(c, c->r, c->w);
         const double wn = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
         w_norm = wn;
+        if (c->defl_k > 0 && !(wn < wn_prev)) {
+          // a deflated inner solve did not reduce the FP64 residual: plain inner PCGP from here on
+          c->defl_k = 0;
+          c->defl_fallbacks += 1;
+          cudaMemsetAsync(c->sc + kDeflK, 0, sizeof(double), c->st);
+        }
+        wn_prev = wn;
         if (!std::isfinite(wn)) {
           status = fail(c, TFETI_ERR_NONFINITE, "non-finite residual in PCGP");
           break;
@@ -1294,6 +1606,16 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
         // the inner right-hand side is P r (same correction equation: P F P delta = P r), so
         // the FP32 projections inside work relative to ||P r||, not to ||r||
         cudaMemcpyAsync(c->rin, c->w, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+        if (c->defl_req > 0 && history) {
+          if (!c->defl_formed) {
+            const int dst = deflation_setup(c);
+            if (dst != TFETI_OK) {
+              status = dst;
+              break;
+            }
+          }
+          if (c->defl_k > 0) deflation_start(c);
+        }
         const double tol_in = std::max(c->inner_rtol * wn, 0.5 * rtol * r0);
         PcgOut in = c->use_graphs ? pcg_inner_graph(c, tol_in, std::min(maxit - it, 1000))
                                   : pcg_inner_eager(c, tol_in, std::min(maxit - it, 1000));
@@ -1628,7 +1950,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->f_full = dalloc<double>(c, P.n_dof);
   c->tn = dalloc<double>(c, P.n_dof);
   c->tn2 = dalloc<double>(c, P.n_dof);
-  c->partial = dalloc<double>(c, std::max(2 * kRedBlocks, kFusedBlocks));   // launch_dot2, fused inner kernels
+  c->partial = dalloc<double>(c, std::max(2 * kRedBlocks, (1 + kDeflMax) * kFusedBlocks));   // dot2, fused kernels
   c->d_ctr = dalloc<int>(c, 4);                                              // arrival counters of the fused kernels
   cudaMemsetAsync(c->d_ctr, 0, sizeof(int) * 4, c->st);
   c->sc = dalloc<double>(c, kNumScalars);
@@ -1806,6 +2128,8 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   }
   c->launches += 4;
   cudaEventCreate(&c->fac_e0);
+  cudaEventCreate(&c->in_e0);
+  cudaEventCreate(&c->in_e1);
   cudaEventCreate(&c->fac_e1);
   cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
   cudaStreamCreateWithFlags(&c->st_fac, cudaStreamNonBlocking);
@@ -1959,6 +2283,8 @@ int tfeti_destroy(tfeti_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
+  if (c->in_e0) cudaEventDestroy(c->in_e0);
+  if (c->in_e1) cudaEventDestroy(c->in_e1);
   if (c->fac_e1) cudaEventDestroy(c->fac_e1);
   destroy_inner_graph(c);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -2170,6 +2496,10 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     const bool fresh = !c->schur_ready;
     int st = ensure_schur(c);
     if (st != TFETI_OK) return st;
+    if (c->wood_on) {
+      st = ensure_kinv(c);
+      if (st != TFETI_OK) return st;
+    }
     if (fresh || c->schur_threshold == 0) {
       st = tune_schur_threshold(c);
       if (st != TFETI_OK) return st;
@@ -2266,6 +2596,50 @@ int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   c->rec_head = 0;
   c->rec_tried = c->rec_used = 0;
   return cuda_check(c, "tfeti_set_recycling");
+}
+
+int tfeti_set_woodbury(tfeti_ctx* c, int32_t enable) {
+  if (!c) return TFETI_ERR_ARG;
+  c->wood_on = enable != 0;
+  if (c->wood_on && c->precision == TFETI_PRECISION_MIXED && c->schur_ready) {
+    const int st = ensure_kinv(c);
+    if (st != TFETI_OK) return st;
+  }
+  return TFETI_OK;   // takes effect at the next assembly
+}
+
+int tfeti_get_woodbury_stats(tfeti_ctx* c, int64_t* subdomains, int64_t* fallbacks) {
+  if (!c) return TFETI_ERR_ARG;
+  if (subdomains) *subdomains = c->wood_subs;
+  if (fallbacks) *fallbacks = c->wood_fallbacks;
+  return TFETI_OK;
+}
+
+int tfeti_set_deflation(tfeti_ctx* c, int32_t k) {
+  if (!c || k < 0 || k > kDeflMax) return fail(c, TFETI_ERR_ARG, "deflation size must be in 0..8");
+  if (k > 0 && c->rec_q < 1) return fail(c, TFETI_ERR_ARG, "deflation needs the history start (tfeti_set_recycling)");
+  const long long m = c->M.n_mult;
+  if (k > 0 && !c->defl_W) {
+    try {
+      c->defl_W = dalloc<double>(c, (size_t)kDeflMax * (size_t)std::max(1LL, m));
+      c->defl_AW = dalloc<double>(c, (size_t)kDeflMax * (size_t)std::max(1LL, m));
+      c->defl_Einv = dalloc<double>(c, kDeflMax * kDeflMax);
+    } catch (const std::bad_alloc&) {
+      return fail(c, TFETI_ERR_OOM, "device allocation failed");
+    }
+    c->g_inner_stale = true;   // the graph body takes the deflation buffers
+  }
+  c->defl_req = k;
+  c->defl_setups = c->defl_vectors = c->defl_fallbacks = 0;
+  return cuda_check(c, "tfeti_set_deflation");
+}
+
+int tfeti_get_deflation_stats(tfeti_ctx* c, int64_t* setups, int64_t* vectors, int64_t* fallbacks) {
+  if (!c) return TFETI_ERR_ARG;
+  if (setups) *setups = c->defl_setups;
+  if (vectors) *vectors = c->defl_vectors;
+  if (fallbacks) *fallbacks = c->defl_fallbacks;
+  return TFETI_OK;
 }
 
 int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
@@ -2495,6 +2869,9 @@ int tfeti_timing_get(tfeti_ctx* c, tfeti_timing* out) {
   out->schur_launches = c->g_launches;
   out->schur_flops_total = c->g_flops;
   out->schur_bytes_total = c->g_bytes;
+  out->inner_ms_total = c->inner_ms;
+  out->inner_iterations = c->inner_its;
+  out->inner_body_runs = c->inner_runs;
   return TFETI_OK;
 }
 
@@ -2506,6 +2883,8 @@ int tfeti_timing_reset(tfeti_ctx* c, int32_t enable_events) {
   c->f_launches = c->factor_launches = c->launches = 0;
   c->g_ms = c->g_flops = c->g_bytes = 0.0;
   c->g_launches = 0;
+  c->inner_ms = 0.0;
+  c->inner_its = c->inner_runs = 0;
   return TFETI_OK;
 }
 

@@ -84,6 +84,23 @@ struct tfeti_ctx {
   void* Sbf = nullptr;
   bool schur_bf16 = false;                   // inner Schur apply with BF16 S (else TF32 x 3)
   bool schur_manual = false;                 // threshold set by tfeti_set_schur_threshold (no re-tuning)
+  // Woodbury inner F-apply of plastic subdomains (kernels_woodbury.cu): dense FP32 K^+ per shape
+  // (kinv_off[shape] >= 0 where formed; a case context shares the base's), the subdomains
+  // handled that way after the last assembly and their pools (grown on demand)
+  bool wood_on = true;
+  float* kinv32 = nullptr;
+  std::vector<long long> kinv_off;
+  long long* d_kinv_off = nullptr;
+  std::vector<char> h_wood;                  // per subdomain: Woodbury in the inner F-apply
+  tfeti::WoodArgs wood;
+  int* d_wood_list = nullptr;
+  int* d_wood_np = nullptr;
+  long long *d_wood_pt_off = nullptr, *d_wood_c_off = nullptr, *d_wood_z_off = nullptr, *d_wood_d_off = nullptr;
+  int* d_wood_pts = nullptr;
+  float *wood_c = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr;
+  long long wood_pts_cap = 0, wood_c_cap = 0, wood_z_cap = 0, wood_d_cap = 0;
+  float* wood_d = nullptr;
+  long long wood_subs = 0, wood_fallbacks = 0;
   float* s_part = nullptr;                   // split-K partial tiles of the Schur apply
   int* s_count = nullptr;                    // split-K arrival counters (zero between launches)
   std::vector<long long> s_tile_off;
@@ -148,6 +165,14 @@ struct tfeti_ctx {
   // history start (tfeti_set_recycling): ring of the last rec_q solutions lambda_Ker and
   // their products F lambda_Ker, [rec_q][n_mult] each
   int rec_q = 0, rec_n = 0, rec_head = 0;
+  // deflated inner PCGP (tfeti_set_deflation): W (up to kDeflMax vectors in range(P_N)), A W with
+  // the inner FP32 operator, E^-1 = (W^T A W)^-1 over the independent vectors; defl_req: the
+  // requested size, defl_k: the size formed for the current dual solve (0 until its first inner
+  // solve); mlp_slot_valid: the last start formed the network's prediction in slot rec_n
+  int defl_req = 0, defl_k = 0;
+  bool defl_formed = false, mlp_slot_valid = false;
+  double *defl_W = nullptr, *defl_AW = nullptr, *defl_Einv = nullptr;
+  long long defl_setups = 0, defl_vectors = 0, defl_fallbacks = 0;
   double *rec_L = nullptr, *rec_FL = nullptr, *rec_partial = nullptr, *rec_out = nullptr, *rec_c = nullptr;
   double* dtil = nullptr;        // d~ of the current solve (kept when the history start is on)
   double rec_accept = 0.5;       // try the start if the predicted ||P r|| < rec_accept ||P d~||
@@ -188,6 +213,9 @@ struct tfeti_ctx {
   std::vector<uint8_t> ev_kind;             // per event pair: 0 banded F-apply, 1 Schur F-apply
   size_t ev_used = 0;
   cudaEvent_t fac_e0 = nullptr, fac_e1 = nullptr;
+  cudaEvent_t in_e0 = nullptr, in_e1 = nullptr;   // around each inner-solve graph launch (timing on)
+  double inner_ms = 0.0;                           // device time of the timed inner solves
+  long long inner_its = 0, inner_runs = 0;         // their PCGP iterations and body runs
   double f_ms = 0.0, factor_ms = 0.0;
   long long f_launches = 0, factor_launches = 0, launches = 0;
   std::vector<int> last_refactored;

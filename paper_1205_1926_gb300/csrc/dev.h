@@ -146,7 +146,9 @@ struct SolveArgs {
   int rcap;                    // vectors allocated per CTA (>= every item's count)
   // in_mode 2 / out_mode 2 (dual Schur block formation of one shape): item.sub[] hold
   // boundary-dof columns j; the geometry is subdomain rep_sub; column j of
-  // S = (K^+)_{boundary, boundary} goes to S32 + s_off + j * n_bd
+  // S = (K^+)_{boundary, boundary} goes to S32 + s_off + j * n_bd.
+  // in_mode 5 / out_mode 4 (dense K^+ of one shape): item.sub[] hold local dofs j; column j
+  // of K^+ (all n rows, zero at the fixing dofs) goes to S32 + s_off + j * n
   int rep_sub;
   float* S32;
   double* S64;                 // nullable: the same columns in FP64
@@ -188,6 +190,37 @@ void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int 
 void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
                                const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
                                int* count, double* cbuf, int* err, cudaStream_t st);
+// Inner F-apply of plastic subdomains by Woodbury on their shape's elastic dual Schur block
+// (kernels_woodbury.cu).  list: the n subdomains; per subdomain pt_off (into pts), n_pts plastic
+// points, c_off (r x r C, r = 6 n_pts) and z_off (r x n_bd Z_b^T in z_pool, Y = C^{-1} Z_b^T at
+// the same offset in y_pool); kinv: dense FP32 K^+ per shape at kinv_off[shape].  err: bit 8
+// set if a Cholesky pivot of C is not positive.
+constexpr int kWoodMaxN = 3072;    // shapes with at most this many dofs keep a dense K^+
+constexpr int kWoodMaxPts = 96;    // subdomains with more plastic points keep the banded solve
+struct WoodArgs {
+  int n = 0, max_pts = 0, max_bd = 0;
+  const int* list = nullptr;
+  const long long* pt_off = nullptr;
+  const int* n_pts = nullptr;
+  int* pts = nullptr;
+  const uint8_t* plastic = nullptr;
+  const double *pa = nullptr, *pb = nullptr, *pn = nullptr;
+  const float* kinv = nullptr;
+  const long long* kinv_off = nullptr;
+  const long long* c_off = nullptr;
+  float* c_pool = nullptr;
+  const long long* z_off = nullptr;
+  float *z_pool = nullptr, *y_pool = nullptr;
+  long long z_total = 0;
+  float* tbuf = nullptr;             // [n][6 max_pts]: t = Y x_b of the apply
+  const long long* d_off = nullptr;  // inverses of the Cholesky factor's 32 x 32 diagonal blocks
+  float* d_pool = nullptr;
+  int* err = nullptr;
+};
+void launch_wood_setup(const DevMesh& M, const WoodArgs& a, cudaStream_t st);
+int wood_setup_launches(const WoodArgs& a);
+void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, double* cbuf, cudaStream_t st);
+
 // dst[i] = (float) src[i], i < n.
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 // FP32 copies of factor records (offsets in entries, same for both pools)
@@ -288,14 +321,19 @@ void launch_rec_combine(const double* X, const double* c, int q, long long m, co
 enum PcgScalar {
   kYW = 0, kYWPrev = 1, kPFP = 2, kWW = 3,
   kDone = 20, kStatus = 21, kStopAfter = 22, kFirst = 23, kTol2 = 24, kIter = 25, kMaxit = 26, kLastWW = 27,
-  kBodyRuns = 28, kNumScalars = 32
+  kBodyRuns = 28, kDeflK = 29, kMu0 = 32, kNumScalars = 48
 };
+// Deflated inner PCGP: at most kDeflMax deflation vectors W (in range(P)), their products
+// A W with the inner operator, and E^-1 = (W^T A W)^-1 ([kDeflMax][kDeflMax]); the size in
+// use is sc[kDeflK] (0: plain PCGP) and mu = E^-1 (AW)^T y sits at sc[kMu0 ..].
+constexpr int kDeflMax = 8;
 void launch_pcg_init(double* sc, double tol2, int maxit, cudaStream_t st);
 void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, long long n,
                  double* partial, double* out1, double* out2, cudaStream_t st);
 // Fused kernels of the graph-driven inner iteration (grid kFusedBlocks; each dot is summed by the
 // block that arrives last, in block order; ctr: one zeroed int per kernel, left zero; partial:
-// kFusedBlocks doubles).  GT32_dot: out = x - G^T h8 and sc[kWW] = out.out (mode 0) or
+// (1 + kDeflMax) x kFusedBlocks doubles).  With deflation (AW, Einv, W given and sc[kDeflK] > 0)
+// GT32_dot mode 1 also forms mu = E^-1 (AW)^T y and p_update subtracts W mu.  GT32_dot: out = x - G^T h8 and sc[kWW] = out.out (mode 0) or
 // sc[kYW] = out.v plus the stop test (mode 1).  contract_dot: Fp = B cbuf, sc[kPFP] = p.Fp plus
 // the breakdown test.  lam_r_update_post: the guarded updates, then the body run is closed and,
 // with has_h, the WHILE condition h set.  G32_coarse32: gx = G x and hx = H gx in FP32 (+ padded hx8).
@@ -303,7 +341,8 @@ constexpr int kFusedBlocks = 608;
 void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
                          cudaStream_t st);
 void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
-                     double* sc, double* partial, int* ctr, cudaStream_t st);
+                     double* sc, double* partial, int* ctr, cudaStream_t st, const double* AW = nullptr,
+                     const double* Einv = nullptr);
 void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,
                          double* partial, int* ctr, cudaStream_t st);
 void launch_lam_r_update_post(long long n, const double* p, const double* Fp, double* lam, double* r, double* sc,
@@ -312,7 +351,8 @@ void launch_pcg_pre(double* sc, cudaStream_t st);
 void launch_pcg_mid(double* sc, cudaStream_t st);
 void launch_pcg_post(double* sc, unsigned long long cond_handle, cudaStream_t st);
 // guarded updates: no-ops once sc[kDone] is set
-void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st);
+void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st,
+                       const double* W = nullptr);
 void launch_lam_r_update_g(long long n, const double* p, const double* Fp, double* lam, double* r, const double* sc,
                            cudaStream_t st);
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t st);

@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   T* sm = reinterpret_cast<T*>(sm_raw);
   __shared__ int s_fail;
   const SolveItem item = a.items[blockIdx.x];
-  const SubDev& S0 = M.subs[a.in_mode == 2 ? a.rep_sub : item.sub[0]];
+  // unit right-hand sides (in_mode 2, 5) carry dof indices in item.sub[]: the geometry is rep_sub's
+  const SubDev& S0 = M.subs[(a.in_mode == 2 || a.in_mode == 5) ? a.rep_sub : item.sub[0]];
   const int n = S0.n_dof, bw = S0.bw, nb = S0.nb, nblk = S0.nblk, rec = S0.rec;
   const int R = item.count;
   const int npad = a.npad;                       // vector stride (largest n of the launch, even)
@@ -248,16 +249,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
 
   // ---- right-hand sides
   const int n_bd = 3 * S0.n_bnd;
-  if (a.in_mode == 2) {   // unit vectors at boundary dofs item.sub[r]
+  if (a.in_mode == 2 || a.in_mode == 5) {   // unit vectors at boundary dofs (2) or local dofs (5) item.sub[r]
     for (int r = 0; r < R; ++r)
       for (int i = tid; i < n; i += nt) vec[r * npad + i] = T(0);
     __syncthreads();
     if (tid < R) {
       const int j = item.sub[tid];
-      vec[tid * npad + 3 * M.shape_bln[S0.bnd_off + j / 3] + j % 3] = T(1);
+      vec[tid * npad + (a.in_mode == 2 ? 3 * M.shape_bln[S0.bnd_off + j / 3] + j % 3 : j)] = T(1);
     }
   }
-  for (int r = 0; r < R && a.in_mode != 2; ++r) {
+  const bool unit_in = a.in_mode == 2 || a.in_mode == 5;
+  for (int r = 0; r < R && !unit_in; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
     T* x = vec + r * npad;
     if (a.in_mode == 0)
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
       for (int i = tid; i < n; i += nt) x[i] = a.src ? T(a.src[S.dof_off + i]) : T(0);
   }
   __syncthreads();
-  for (int r = 0; r < R && a.in_mode != 2; ++r) {
+  for (int r = 0; r < R && !unit_in; ++r) {
     const SubDev& S = M.subs[item.sub[r]];
     T* x = vec + r * npad;
     if (a.in_mode == 0) {
@@ -406,6 +408,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   __syncthreads();
 
   // ---- outputs
+  if (a.out_mode == 4) {   // column item.sub[r] of the dense K^+ of the geometry rep_sub, FP32
+    for (int r = 0; r < R; ++r) {
+      const long long o = a.s_off + (long long)item.sub[r] * n;
+      for (int i = tid; i < n; i += nt) a.S32[o + i] = (float)vec[r * npad + i];
+    }
+    return;
+  }
   if (a.out_mode == 2) {
     for (int r = 0; r < R; ++r) {
       const long long o = a.s_off + (long long)item.sub[r] * n_bd;

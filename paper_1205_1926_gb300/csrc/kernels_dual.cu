@@ -494,15 +494,23 @@ __device__ bool grid_sum_last(double s, double* partial, int* ctr, double* red, 
 
 // out = x - G^T h (FP32 padded values, h8 the padded FP32 coarse vector) with the fused
 // dot: mode 0 -> sc[kWW] = out.out (w = P r); mode 1 -> sc[kYW] = out.v (y = P z, v = w),
-// then the stop test of the iteration (pcg_pre).
+// then the stop test of the iteration (pcg_pre), and with deflation (k = sc[kDeflK] > 0)
+// also d_j = out.AW_j and mu = E^-1 d -> sc[kMu0 + i].  The partial sums of value j sit at
+// partial[j * gridDim.x + block].
 __global__ void k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x,
                            const float* __restrict__ h8, double* out, const double* __restrict__ v, int mode,
-                           double* sc, double* partial, int* ctr) {
+                           double* sc, double* partial, int* ctr, const double* __restrict__ AW,
+                           const double* __restrict__ Einv) {
   __shared__ double red[32];
+  __shared__ int is_last;
   const float4* g4 = reinterpret_cast<const float4*>(GTv8);
   const float4* h4 = reinterpret_cast<const float4*>(h8);
-  double acc = 0.0;
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M.n_mult;
+  const int kd = (mode == 1 && AW) ? (int)sc[kDeflK] : 0;
+  const long long m = M.n_mult;
+  double acc = 0.0, accd[kDeflMax];
+#pragma unroll
+  for (int j = 0; j < kDeflMax; ++j) accd[j] = 0.0;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < m;
        row += (long long)gridDim.x * blockDim.x) {
     const long long e0 = M.gt_ptr[row], e1 = M.gt_ptr[row + 1];
     double s = 0.0;
@@ -516,15 +524,41 @@ __global__ void k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const doub
     const double o = x[row] - s;
     out[row] = o;
     acc += o * (mode == 0 ? o : v[row]);
+#pragma unroll
+    for (int j = 0; j < kDeflMax; ++j)
+      if (j < kd) accd[j] += o * AW[(long long)j * m + row];
   }
   acc = block_reduce_sum(acc, red);
-  double tot = 0.0;
-  if (grid_sum_last(acc, partial, ctr, red, &tot) && threadIdx.x == 0) {
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  for (int j = 0; j < kd; ++j) {
+    const double t = block_reduce_sum(accd[j], red);
+    if (threadIdx.x == 0) partial[(long long)(1 + j) * gridDim.x + blockIdx.x] = t;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(ctr, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double tot[1 + kDeflMax];
+  for (int j = 0; j <= kd; ++j) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + (long long)j * gridDim.x + i);
+    tot[j] = block_reduce_sum(t, red);
+  }
+  if (threadIdx.x == 0) {
+    *ctr = 0;
     if (mode == 0) {
-      sc[kWW] = tot;
+      sc[kWW] = tot[0];
     } else {
-      sc[kYW] = tot;
+      sc[kYW] = tot[0];
       pcg_pre_logic(sc);
+      for (int i = 0; i < kd; ++i) {
+        double mu = 0.0;
+        for (int j = 0; j < kd; ++j) mu += Einv[i * kDeflMax + j] * tot[1 + j];
+        sc[kMu0 + i] = mu;
+      }
     }
   }
 }
@@ -576,13 +610,19 @@ __global__ void k_lam_r_update_post(long long n, const double* __restrict__ p, c
   }
 }
 
-__global__ void k_p_update_g(long long n, const double* __restrict__ y, double* p, const double* sc) {
+__global__ void k_p_update_g(long long n, const double* __restrict__ y, double* p, const double* sc,
+                             const double* __restrict__ W) {
   if (sc[kDone] != 0.0) return;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool first = sc[kFirst] != 0.0;
   const double beta = first ? 0.0 : sc[kYW] / sc[kYWPrev];
-  p[i] = first ? y[i] : y[i] + beta * p[i];
+  double v = first ? y[i] : y[i] + beta * p[i];
+  if (W) {   // deflated direction: p = y + beta p - W mu
+    const int kd = (int)sc[kDeflK];
+    for (int j = 0; j < kd; ++j) v -= sc[kMu0 + j] * W[(long long)j * n + i];
+  }
+  p[i] = v;
 }
 
 __global__ void k_lam_r_update_g(long long n, const double* __restrict__ p, const double* __restrict__ Fp,
@@ -672,36 +712,52 @@ __global__ void k_coarse_assemble_planes(DevMesh M, const int* __restrict__ pair
 // Apply of the plane solver (H = (G G^T)^-1 by block LDL^T over the planes):
 // first y_k = alpha W_k x_k for every plane (blockIdx.y = k), then the forward steps
 // y_k -= V_k y_{k-1}, k = 1..np-1, and the backward steps y_k -= U_k y_{k+1}, k = np-2..0.
-// One warp per row, the other plane's segment staged in shared memory.  T: FP64 blocks, or
+// Two warps per row, the other plane's segment staged in shared memory.  T: FP64 blocks, or
 // their FP32 copies (FP32 products and sums); y8 (nullable): the padded FP32 copy of the final
 // y written by the last step that touches a plane (final != 0).
+// Rows of a plane block: kPlaneRows rows per 256-thread CTA, two warps per row, each lane
+// keeping four 16- or 8-byte loads in flight; the two warps' sums meet in shared memory.
+constexpr int kPlaneRows = 4;
+
 template <typename T>
-__device__ __forceinline__ double plane_row_dot(const T* __restrict__ row, const void* xs, int n);
+__device__ __forceinline__ double plane_part_dot(const T* __restrict__ row, const void* xs, int n, int sub);
 template <>
-__device__ __forceinline__ double plane_row_dot<double>(const double* __restrict__ row, const void* xs, int n) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ double plane_part_dot<double>(const double* __restrict__ row, const void* xs, int n,
+                                                         int sub) {
   const double2* r2 = reinterpret_cast<const double2*>(row);
   const double2* x2 = reinterpret_cast<const double2*>(xs);
   double acc = 0.0;
-  for (int j = lane; j < (n >> 1); j += 32) {
+#pragma unroll 4
+  for (int j = sub; j < (n >> 1); j += 64) {
     const double2 a = __ldg(r2 + j), v = x2[j];
     acc += a.x * v.x + a.y * v.y;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   return acc;
 }
 template <>
-__device__ __forceinline__ double plane_row_dot<float>(const float* __restrict__ row, const void* xs, int n) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ double plane_part_dot<float>(const float* __restrict__ row, const void* xs, int n, int sub) {
   const float2* r2 = reinterpret_cast<const float2*>(row);
   const float2* x2 = reinterpret_cast<const float2*>(xs);
   float acc = 0.f;
-  for (int j = lane; j < (n >> 1); j += 32) {
+#pragma unroll 4
+  for (int j = sub; j < (n >> 1); j += 64) {
     const float2 a = __ldg(r2 + j), v = x2[j];
     acc += a.x * v.x + a.y * v.y;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   return double(acc);
+}
+
+// Row r of this CTA (r < kPlaneRows) of matrix rows `rows` (n wide): the dot with the staged x,
+// valid in thread (r * 64) of the CTA.
+template <typename T>
+__device__ __forceinline__ double plane_row_dot(const T* __restrict__ rowp, const void* xs, int n, double* red) {
+  const int sub = threadIdx.x & 63, pair = threadIdx.x >> 6, lane = threadIdx.x & 31;
+  double acc = rowp ? plane_part_dot<T>(rowp, xs, n, sub) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0 && sub >= 32) red[pair] = acc;
+  __syncthreads();
+  if (sub == 0) acc += red[pair];
+  return acc;
 }
 
 template <typename T>
@@ -716,30 +772,31 @@ __device__ __forceinline__ void plane_y8(float* y8, long long grow, double v) {
 }
 
 template <typename T>
-__global__ void k_plane_first(const T* __restrict__ W, int n, const double* __restrict__ x, double alpha, double* y,
-                              float* y8, int final) {
+__global__ void __launch_bounds__(256) k_plane_first(const T* __restrict__ W, int n, const double* __restrict__ x,
+                                                     double alpha, double* y, float* y8, int final) {
   extern __shared__ __align__(16) unsigned char plane_xs[];
+  __shared__ double red[kPlaneRows];
   const int k = blockIdx.y;
   plane_stage<T>(x + (long long)k * n, n, plane_xs);
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= n) return;
-  const double v = alpha * plane_row_dot<T>(W + ((long long)k * n + r) * n, plane_xs, n);
-  if ((threadIdx.x & 31) == 0) {
+  const int r = blockIdx.x * kPlaneRows + (threadIdx.x >> 6);
+  const double d = plane_row_dot<T>(r < n ? W + ((long long)k * n + r) * n : nullptr, plane_xs, n, red);
+  if ((threadIdx.x & 63) == 0 && r < n) {
     const long long g = (long long)k * n + r;
+    const double v = alpha * d;
     y[g] = v;
     if (final) plane_y8(y8, g, v);
   }
 }
 
 template <typename T>
-__global__ void k_plane_step(const T* __restrict__ Mk, int n, const double* __restrict__ y_other, double* y_k,
-                             long long row0, float* y8, int final) {
+__global__ void __launch_bounds__(256) k_plane_step(const T* __restrict__ Mk, int n, const double* __restrict__ y_other,
+                                                    double* y_k, long long row0, float* y8, int final) {
   extern __shared__ __align__(16) unsigned char plane_xs[];
+  __shared__ double red[kPlaneRows];
   plane_stage<T>(y_other, n, plane_xs);
-  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (r >= n) return;
-  const double d = plane_row_dot<T>(Mk + (long long)r * n, plane_xs, n);
-  if ((threadIdx.x & 31) == 0) {
+  const int r = blockIdx.x * kPlaneRows + (threadIdx.x >> 6);
+  const double d = plane_row_dot<T>(r < n ? Mk + (long long)r * n : nullptr, plane_xs, n, red);
+  if ((threadIdx.x & 63) == 0 && r < n) {
     const double v = y_k[r] - d;
     y_k[r] = v;
     if (final) plane_y8(y8, row0 + r, v);
@@ -982,8 +1039,8 @@ void launch_dot2(const double* x1, const double* y1, const double* x2, const dou
 }
 
 void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
-                     double* sc, double* partial, int* ctr, cudaStream_t st) {
-  k_GT32_dot<<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr);
+                     double* sc, double* partial, int* ctr, cudaStream_t st, const double* AW, const double* Einv) {
+  k_GT32_dot<<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr, AW, Einv);
 }
 
 void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
@@ -1008,8 +1065,8 @@ void launch_pcg_post(double* sc, unsigned long long h, cudaStream_t st) {
   k_pcg_post<<<1, 32, 0, st>>>(sc, (cudaGraphConditionalHandle)h);
 }
 
-void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st) {
-  if (n > 0) k_p_update_g<<<blocks_for(n, 256), 256, 0, st>>>(n, y, p, sc);
+void launch_p_update_g(long long n, const double* y, double* p, const double* sc, cudaStream_t st, const double* W) {
+  if (n > 0) k_p_update_g<<<blocks_for(n, 256), 256, 0, st>>>(n, y, p, sc, W);
 }
 
 void launch_lam_r_update_g(long long n, const double* p, const double* Fp, double* lam, double* r, const double* sc,
@@ -1110,7 +1167,7 @@ void coarse_planes_factor(double* W, const double* Aoff, double* V, double* U, i
 template <typename T>
 static void plane_apply(const T* W, const T* V, const T* U, int n, int np, const double* x, double alpha, double* y,
                         float* y8, cudaStream_t st) {
-  const unsigned rb = (unsigned)((n + 7) / 8);
+  const unsigned rb = (unsigned)((n + kPlaneRows - 1) / kPlaneRows);
   const size_t smem = sizeof(T) * (size_t)n;
   const long long blk = (long long)n * n;
   if (smem > 48 * 1024) {

@@ -177,9 +177,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // C = X S for one 128 x kTN output tile (blockIdx.y: subdomain tile, blockIdx.x:
 // boundary-dof tile) over the K stages [ks0, ks1) of split blockIdx.z, written to the
-// copy slots of the interface dofs.  128 threads: thread 0 streams the stages, thread 32
-// issues the MMAs, all four warps read the accumulator (warp w owns TMEM lanes
-// 32w..32w+31 = output rows).
+// copy slots of the interface dofs.  256 threads: thread 0 streams the stages, thread 32
+// issues the MMAs, and all eight warps read the accumulator: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (its quadrant: output rows) and columns 32 (w / 4) .. + 31, so the
+// epilogue's gathers of slot indices and scattered stores run on eight warps.
 //
 // With splits of K (gridDim.z > 1, used when the output tiles alone would leave SMs idle)
 // every CTA of a tile stores its FP32 partial tile in `part` and counts itself in
@@ -187,7 +188,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // so the result does not depend on the order in which the CTAs finish, and returns the
 // counter to zero for the next launch.  No CTA waits for another.
 template <bool kBf>
-__global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __restrict__ sub_list, int n_list,
+__global__ void __launch_bounds__(256, 1) k_schur_tc(DevMesh M, const int* __restrict__ sub_list, int n_list,
                                                      int n_bd, int nk, const unsigned char* __restrict__ Xhi,
                                                      const unsigned char* __restrict__ Xlo,
                                                      const unsigned char* __restrict__ Shi,
@@ -282,7 +283,8 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
   tc_fence_after();
   __syncthreads();
   const bool good = s_flag[0] == 0;   // the same for every thread: tcgen05.ld below is warp-collective
-  const int row = warp * 32 + lane;
+  const int quad = warp & 3, cbeg = (warp >> 2) * (kTN / 2), cend = cbeg + kTN / 2;
+  const int row = quad * 32 + lane;
   const int k = mt * kTM + row;
   const long long tile = (long long)mt * gridDim.x + nt;
   bool last = true;
@@ -290,9 +292,9 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
     // every split publishes its partial tile (column c of this row at [c * kTM]); the CTA that
     // arrives last sums the partials in split order and scatters
     float* mine = part + (tile * splits + blockIdx.z) * (kTM * kTN) + row;
-    for (int c0 = 0; c0 < kTN; c0 += 16) {
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) mine[(c0 + q) * kTM] = good ? v[q] : 0.0f;
     }
@@ -311,10 +313,10 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(DevMesh M, const int* __res
     const bool mine_row = k < n_list;
     const int sub = mine_row ? sub_list[k] : 0;
     const float* pt = part + tile * splits * (kTM * kTN) + row;
-    for (int c0 = 0; c0 < kTN; c0 += 16) {
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
       float v[16];
       if (splits == 1) {
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
       } else if (mine_row) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -396,11 +398,11 @@ void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list
   const auto* sl = static_cast<const unsigned char*>(Slo);
   if (bf16) {
     cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<true>::smem);
-    k_schur_tc<true><<<grid, 128, Fmt<true>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
+    k_schur_tc<true><<<grid, 256, Fmt<true>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
                                                           part, count, cbuf, err);
   } else {
     cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<false>::smem);
-    k_schur_tc<false><<<grid, 128, Fmt<false>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
+    k_schur_tc<false><<<grid, 256, Fmt<false>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
                                                            part, count, cbuf, err);
   }
 }

@@ -573,6 +573,42 @@ def test_fp32_F_apply_matches_fp64(w, plastic):
     assert torch.equal(y32, y32b)
 
 
+@pytest.mark.parametrize("hot_scale", [6.5e-4, 7e-4])
+def test_woodbury_inner_F_apply(hot_scale):
+    """Plastic subdomains in the inner F-apply through their shape's Schur block plus the Woodbury
+    correction of the plastic tangent (C = I - U^T K^+ U, Z_b = (K^+)_b U): FP32 accuracy against the
+    FP64 F; with 7e-4 one hot box has more than 96 plastic points and keeps its banded solve while the
+    other takes the correction.  The mixed dual solve then reaches the oracle at eps = 1e-12."""
+    w = W.CUBE12
+    du, hot = W.seeded_partly_plastic_increment(w, 5, 2, hot_scale=hot_scale)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    ctx.set_precision(True, 1e-3)
+    ctx.set_schur_threshold(4)
+    df = zeros(s["n_dof"])
+    ctx.traction_load((20.0, 5.0, -8.0), df)
+    f = zeros(s["n_dof"])
+    ctx.assemble_tangent(dev(du), df, f)
+    assert ctx.woodbury_stats()["subdomains"] >= 1
+    x = dev(W.seeded_vector(s["n_mult"], seed=64))
+    y64, y32 = zeros(s["n_mult"]), zeros(s["n_mult"])
+    ctx.apply("F", x, y64)
+    ctx.apply("F32", x, y32)
+    assert rel(host(y32), host(y64)) <= 1e-5, rel(host(y32), host(y64))
+    u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+    ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+    m = ElastoplasticModel(w)
+    Kb, f_or, _ = m.assemble(du, m.traction_load((20.0, 5.0, -8.0)))
+    sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+    assert rel(host(u), sol["u"]) <= 1e-9
+    assert rel(host(lam), sol["lam"]) <= 1e-9
+    # the same with the correction off: the banded FP32 solves give the same accuracy
+    ctx.set_woodbury(False)
+    ctx.assemble_tangent(dev(du), df, f)
+    ctx.apply("F32", x, y32)
+    assert rel(host(y32), host(y64)) <= 1e-5
+
+
 @pytest.mark.parametrize("w", [W.CUBE12, W.CUBE48, CUBE12_BOXES3])
 def test_bf16_schur_F_apply(w):
     """The inner F-apply with the dual Schur blocks stored in BF16 (X split into BF16 hi/lo, FP32
@@ -702,6 +738,39 @@ def test_history_start_load_history_cube12(mixed):
         assert rel(runs[8][0][k], model.u) <= 1e-9, k
     assert runs[0][2] == 0 and runs[8][2] > 0
     assert runs[8][1] < runs[0][1], (runs[8][1], runs[0][1])
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_deflated_inner_pcgp_history_cube12(learned):
+    """The mixed mode with the inner PCGP deflated by up to 4 vectors (the stored solutions, and the
+    network's prediction when the learned start forms one): the oracle's displacements at every
+    load step of the 12^3 history; deflation spaces are formed."""
+    w = W.CUBE12
+    ctx = T.Context(w)
+    ctx.set_precision(True, 1e-3)
+    ctx.set_recycling(7)
+    if learned:
+        ctx.set_learned(True)
+    ctx.set_deflation(4)
+    t_y = ctx.first_yield_traction(w.traction_dir)
+    ctx.set_recycling(7)
+    if learned:
+        ctx.set_learned(True)
+    ctx.set_deflation(4)
+    model = ElastoplasticModel(w)
+    t_or = model.first_yield_traction()
+    f1 = model.traction_load(w.traction_dir)
+    df, u = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_dof"])
+    prev = 0.0
+    for a in w.load_fractions():
+        ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+        info = ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        model.time_step((a - prev) * t_or * f1, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit)
+        prev = a
+        ctx.get_state(u=u)
+        assert info["converged"] and rel(host(u), model.u) <= 1e-9
+    st = ctx.deflation_stats()
+    assert st["setups"] > 0 and st["vectors"] >= st["setups"]
 
 
 def test_history_start_repeated_rhs():
