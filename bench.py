@@ -386,6 +386,8 @@ def run_gpu(args, rank, world, local_rank):
             c.set_schur_format(True)
         if arm != "fp64" and args.no_woodbury:
             c.set_woodbury(False)
+        if arm != "fp64" and args.schur_threshold > 0:
+            c.set_schur_threshold(args.schur_threshold)
         if args.no_graphs:
             c.set_graphs(False)
         return c
@@ -767,6 +769,9 @@ def main():
                     help="FP64 F-apply of elastic subdomains: shape's dual Schur block (DGEMM) or banded solves")
     ap.add_argument("--extra-arms", action="store_true",
                     help="also time the deflated learned arm and the BF16 Schur arm (both measured slower)")
+    ap.add_argument("--schur-threshold", type=int, default=0,
+                    help="pin the inner F-apply's Schur threshold (0: autotuned; profilers serialise launches, "
+                         "which misleads the tuner)")
     ap.add_argument("--no-woodbury", action="store_true",
                     help="mixed arms: plastic subdomains keep FP32 banded solves in the inner F-apply")
     ap.add_argument("--deflation", type=int, default=4,

@@ -431,7 +431,7 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract = true) {
     }
     if (c->wood.n > 0) {   // plastic subdomains on their shape's block: + Z_b C^-1 Z_b^T x_b
       launch_wood_apply(c->M, c->wood, x, c->cbuf, c->st);
-      c->launches += 2;
+      c->launches += 3;
     }
     if (c->n_items_pl > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
   }
@@ -691,6 +691,10 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
       c->wood_y = dalloc<float>(c, (size_t)c->wood_z_cap);
     }
     if (!c->wood_t) c->wood_t = dalloc<float>(c, (size_t)c->h_subs.size() * 6 * kWoodMaxPts);
+    if ((long long)nl * max_bd > c->wood_x_cap) {
+      c->wood_x_cap = std::max((long long)nl * max_bd, 2 * c->wood_x_cap);
+      c->wood_x = dalloc<float>(c, (size_t)c->wood_x_cap);
+    }
     cudaMemcpyAsync(c->d_wood_list, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_wood_np, npts.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_wood_pt_off, pt_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
@@ -721,6 +725,7 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
   w.y_pool = c->wood_y;
   w.z_total = z_tot;
   w.tbuf = c->wood_t;
+  w.xbuf = c->wood_x;
   w.d_off = c->d_wood_d_off;
   w.d_pool = c->wood_d;
   w.err = c->d_err;

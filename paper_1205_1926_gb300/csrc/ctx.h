@@ -98,7 +98,8 @@ struct tfeti_ctx {
   long long *d_wood_pt_off = nullptr, *d_wood_c_off = nullptr, *d_wood_z_off = nullptr, *d_wood_d_off = nullptr;
   int* d_wood_pts = nullptr;
   float *wood_c = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr;
-  long long wood_pts_cap = 0, wood_c_cap = 0, wood_z_cap = 0, wood_d_cap = 0;
+  long long wood_pts_cap = 0, wood_c_cap = 0, wood_z_cap = 0, wood_d_cap = 0, wood_x_cap = 0;
+  float* wood_x = nullptr;
   float* wood_d = nullptr;
   long long wood_subs = 0, wood_fallbacks = 0;
   float* s_part = nullptr;                   // split-K partial tiles of the Schur apply

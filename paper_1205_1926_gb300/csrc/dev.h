@@ -213,6 +213,7 @@ struct WoodArgs {
   float *z_pool = nullptr, *y_pool = nullptr;
   long long z_total = 0;
   float* tbuf = nullptr;             // [n][6 max_pts]: t = Y x_b of the apply
+  float* xbuf = nullptr;             // [n][max_bd]: x_b of the apply
   const long long* d_off = nullptr;  // inverses of the Cholesky factor's 32 x 32 diagonal blocks
   float* d_pool = nullptr;
   int* err = nullptr;

@@ -16,7 +16,7 @@
 // All of it in FP32, the precision of the inner iterations.  Per subdomain (one CTA each):
 // the plastic points in order (k_wood_points), C and Z_b from the shape's dense K^+ (k_wood_C,
 // k_wood_Zb), the blocked Cholesky factor of C (k_wood_chol_*) and Y by blocked substitution
-// (k_wood_subst); per inner F-apply k_wood_t and k_wood_y.
+// (k_wood_subst); per inner F-apply k_wood_x, k_wood_t and k_wood_y.
 #include "dev.h"
 #include "dual_common.cuh"
 
@@ -368,61 +368,69 @@ __global__ void __launch_bounds__(256) k_wood_subst(const SubDev* __restrict__ s
   }
 }
 
-// Correction of the inner F-apply, in two launches spread over many CTAs (the per-subdomain
+// Correction of the inner F-apply, in three launches spread over many CTAs (the per-subdomain
 // products are a few MB each and one CTA per subdomain would leave them latency-bound):
-// k_wood_t: t = Y x_b for rows blockIdx.y * 32 .. + 31 of subdomain list[blockIdx.x], x_b = B^T lam
-// at the boundary dofs (formed in shared memory by every CTA), one row per warp at a time, into
-// tbuf + w * tstride;  k_wood_y: cbuf[slots] += Z_b t for boundary dofs blockIdx.y * 256 + thread.
-constexpr int kWoodRows = 32;
+// k_wood_x: x_b = B^T lam at the boundary dofs of subdomain list[blockIdx.x] -> xbuf + w * xstride;
+// k_wood_t: t = Y x_b, one row per warp, kWoodRows rows per CTA (blockIdx.y) -> tbuf + w * tstride;
+// k_wood_y: cbuf[slots] += Z_b t for 64 boundary dofs per CTA (blockIdx.y), four threads per dof
+// splitting the sum over the rows, combined in shared memory in a fixed order.
+constexpr int kWoodRows = 8;
 
-__global__ void __launch_bounds__(256) k_wood_t(DevMesh M, const int* __restrict__ list,
-                                                const int* __restrict__ n_pts, const long long* __restrict__ y_off,
-                                                const float* __restrict__ y_pool, const double* __restrict__ lam,
-                                                float* tbuf, int tstride) {
-  extern __shared__ float xb[];
+__global__ void __launch_bounds__(256) k_wood_x(DevMesh M, const int* __restrict__ list, const double* __restrict__ lam,
+                                                float* xbuf, int xstride) {
   const int w = blockIdx.x;
-  const int r = 6 * n_pts[w];
-  const int c0 = blockIdx.y * kWoodRows;
-  if (c0 >= r) return;
   const SubDev S = M.subs[list[w]];
   const int n_bd = 3 * S.n_bnd;
-  for (int k = threadIdx.x; k < n_bd; k += blockDim.x) {
-    const int sl = M.sub_b2s[S.b2s_off + k / 3];
-    xb[k] = sl >= 0 ? (float)bt_at_slot(M, lam, (long long)sl + k % 3) : 0.f;
-  }
-  __syncthreads();
-  const float* Y = y_pool + y_off[w];
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= n_bd) return;
+  const int sl = M.sub_b2s[S.b2s_off + k / 3];
+  xbuf[(long long)w * xstride + k] = sl >= 0 ? (float)bt_at_slot(M, lam, (long long)sl + k % 3) : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_wood_t(const SubDev* __restrict__ subs, const int* __restrict__ list,
+                                                const int* __restrict__ n_pts, const long long* __restrict__ y_off,
+                                                const float* __restrict__ y_pool, const float* __restrict__ xbuf,
+                                                int xstride, float* tbuf, int tstride) {
+  const int w = blockIdx.x;
+  const int r = 6 * n_pts[w];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = c0 + warp; c < min(r, c0 + kWoodRows); c += blockDim.x >> 5) {
-    const float* yr = Y + (long long)c * n_bd;
-    float v = 0.f;
-#pragma unroll 4
-    for (int k = lane; k < n_bd; k += 32) v += yr[k] * xb[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) tbuf[(long long)w * tstride + c] = v;
-  }
+  const int c = blockIdx.y * kWoodRows + warp;
+  if (c >= r) return;
+  const int n_bd = 3 * subs[list[w]].n_bnd;
+  const float* yr = y_pool + y_off[w] + (long long)c * n_bd;
+  const float* xb = xbuf + (long long)w * xstride;
+  float v = 0.f;
+#pragma unroll 8
+  for (int k = lane; k < n_bd; k += 32) v += __ldg(yr + k) * __ldg(xb + k);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) tbuf[(long long)w * tstride + c] = v;
 }
 
 __global__ void __launch_bounds__(256) k_wood_y(DevMesh M, const int* __restrict__ list, const int* __restrict__ n_pts,
                                                 const long long* __restrict__ z_off, const float* __restrict__ z_pool,
                                                 const float* __restrict__ tbuf, int tstride, double* cbuf) {
-  extern __shared__ float ts[];
+  __shared__ float part[4][64];
   const int w = blockIdx.x;
   const int r = 6 * n_pts[w];
   const SubDev S = M.subs[list[w]];
   const int n_bd = 3 * S.n_bnd;
-  const int k = blockIdx.y * blockDim.x + threadIdx.x;
-  if ((int)(blockIdx.y * blockDim.x) >= n_bd) return;
-  for (int c = threadIdx.x; c < r; c += blockDim.x) ts[c] = tbuf[(long long)w * tstride + c];
-  __syncthreads();
-  if (k >= n_bd) return;
-  const int sl = M.sub_b2s[S.b2s_off + k / 3];
-  if (sl < 0) return;
+  const int k0 = blockIdx.y * 64;
+  if (k0 >= n_bd) return;
+  const int kk = threadIdx.x & 63, q = threadIdx.x >> 6, k = k0 + kk;
   const float* Zt = z_pool + z_off[w];
+  const float* t = tbuf + (long long)w * tstride;
   float v = 0.f;
+  if (k < n_bd) {
+    const int c0 = q * ((r + 3) / 4), c1 = min(r, c0 + (r + 3) / 4);
 #pragma unroll 4
-  for (int c = 0; c < r; ++c) v += Zt[(long long)c * n_bd + k] * ts[c];
-  cbuf[(long long)sl + k % 3] += (double)v;
+    for (int c = c0; c < c1; ++c) v += __ldg(Zt + (long long)c * n_bd + k) * __ldg(t + c);
+  }
+  part[q][kk] = v;
+  __syncthreads();
+  if (q == 0 && k < n_bd) {
+    const int sl = M.sub_b2s[S.b2s_off + k / 3];
+    if (sl >= 0) cbuf[(long long)sl + k % 3] += (double)(((part[0][kk] + part[1][kk]) + part[2][kk]) + part[3][kk]);
+  }
 }
 
 }  // namespace
@@ -463,10 +471,11 @@ int wood_setup_launches(const WoodArgs& a) {
 void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, double* cbuf, cudaStream_t st) {
   if (a.n <= 0) return;
   const int rmax = 6 * a.max_pts;
-  k_wood_t<<<dim3((unsigned)a.n, (unsigned)((rmax + kWoodRows - 1) / kWoodRows)), 256, sizeof(float) * a.max_bd,
-             st>>>(M, a.list, a.n_pts, a.z_off, a.y_pool, lam, a.tbuf, rmax);
-  k_wood_y<<<dim3((unsigned)a.n, (unsigned)((a.max_bd + 255) / 256)), 256, sizeof(float) * rmax, st>>>(
-      M, a.list, a.n_pts, a.z_off, a.z_pool, a.tbuf, rmax, cbuf);
+  k_wood_x<<<dim3((unsigned)a.n, (unsigned)((a.max_bd + 255) / 256)), 256, 0, st>>>(M, a.list, lam, a.xbuf, a.max_bd);
+  k_wood_t<<<dim3((unsigned)a.n, (unsigned)((rmax + kWoodRows - 1) / kWoodRows)), 256, 0, st>>>(
+      M.subs, a.list, a.n_pts, a.z_off, a.y_pool, a.xbuf, a.max_bd, a.tbuf, rmax);
+  k_wood_y<<<dim3((unsigned)a.n, (unsigned)((a.max_bd + 63) / 64)), 256, 0, st>>>(M, a.list, a.n_pts, a.z_off,
+                                                                                   a.z_pool, a.tbuf, rmax, cbuf);
 }
 
 }  // namespace tfeti

@@ -155,9 +155,10 @@ def test_cube64_dual_solve_elementwise(rec, ctx64, mixed):
 
 def test_cube64_plastic_load_step_elementwise(rec):
     """One load step of Algorithm 4 from the zero state to 1.5 t_y at (eps_Newton, eps_PCGP) =
-    (1e-10, 1e-12): Newton and PCGP counts, u and the committed kappa and sigma_13 at sampled points,
-    and the plastic Gauss points exactly, except those within |Phi| <= 1e-8 sigma_y of the yield
-    surface at the commit."""
+    (1e-10, 1e-11) (at this size the FP64 dual residual of the full-load step stalls above 1e-12, in the
+    oracle as on the GPU): Newton and PCGP counts, u and the committed kappa and sigma_13 at sampled
+    points, and the plastic Gauss points exactly, except those within |Phi| <= 1e-8 sigma_y of the
+    yield surface at the commit."""
     _, idx_d, idx_g, _, _, _ = inputs(rec)
     r = rec["plastic_step"]
     w = W.CUBE64
