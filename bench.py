@@ -384,8 +384,8 @@ def run_gpu(args, rank, world, local_rank):
             c.set_deflation(args.deflation)
         if arm != "fp64" and (arm.endswith("_bf16") or args.schur_format == "bf16"):
             c.set_schur_format(True)
-        if arm != "fp64" and args.no_woodbury:
-            c.set_woodbury(False)
+        if arm != "fp64":
+            c.set_woodbury(0 if args.no_woodbury else args.woodbury)
         if arm != "fp64" and args.schur_threshold > 0:
             c.set_schur_threshold(args.schur_threshold)
         if args.no_graphs:
@@ -772,8 +772,10 @@ def main():
     ap.add_argument("--schur-threshold", type=int, default=0,
                     help="pin the inner F-apply's Schur threshold (0: autotuned; profilers serialise launches, "
                          "which misleads the tuner)")
-    ap.add_argument("--no-woodbury", action="store_true",
-                    help="mixed arms: plastic subdomains keep FP32 banded solves in the inner F-apply")
+    ap.add_argument("--woodbury", type=int, default=2, choices=[0, 1, 2],
+                    help="mixed arms: plastic subdomains on their shape's elastic factor + a Woodbury correction "
+                         "(1: inner FP32 F-apply only, 2: also the FP64 solves, no refactorisation; 0: off)")
+    ap.add_argument("--no-woodbury", action="store_true", help="same as --woodbury 0")
     ap.add_argument("--deflation", type=int, default=4,
                     help="deflation vectors of the inner PCGP in the mixed_learned_deflated arm (1..8)")
     ap.add_argument("--coarse", default="auto", choices=["auto", "dense", "planes"],

@@ -319,20 +319,27 @@ int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
 #define TFETI_MLP_PARAMS 4801
 int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr);
 
-/* Inner (FP32) F-apply of subdomains with plastic points in the mixed mode (an extension;
- * default on).  The plastic tangent of Algorithm 5 differs from the shape's elastic matrix by
- * the element corrections, K_p = K_el - U U^T with six columns per plastic Gauss point
- * (sqrt(a |T|) B^T F, F F^T = E_eps, and sqrt(b |T|) B^T n of the Clarke tangent, Sec. 3.1),
- * so by the Sherman-Morrison-Woodbury identity (K_p^+)_bb = S_el + Z_b C^-1 Z_b^T with
- * Z_b = (K_el^+)_{b,:} U and C = I - U^T K_el^+ U.  Such a subdomain then joins its shape's
- * tensor-core GEMM with the elastic subdomains and adds two skinny products, instead of a
- * banded FP32 solve (a chain of 2 x n / 32 dependent block steps).  Applies to shapes with a
- * dual Schur block in use and at most 3072 dofs (whose dense K_el^+ is formed once, FP32) and
- * to subdomains with at most 96 plastic points; the others keep the banded solve.  Set up at
- * every assembly in the mixed mode; FP64 solves are unchanged.  enable = 0 turns it off from
- * the next assembly.  Stats: subdomains set up so since the context was made, and set-ups
- * that fell back to banded solves (a C whose Cholesky failed). */
-int tfeti_set_woodbury(tfeti_ctx* ctx, int32_t enable);
+/* Subdomains with few plastic points on their shape's elastic factor in the mixed mode (an
+ * extension; default mode 2).  The plastic tangent of Algorithm 5 differs from the shape's
+ * elastic matrix by the element corrections, K_p = K_el - U U^T with six columns per plastic
+ * Gauss point (sqrt(a |T|) B^T F, F F^T = E_eps, and sqrt(b |T|) B^T n of the Clarke tangent,
+ * Sec. 3.1), so by the Sherman-Morrison-Woodbury identity the fixing-dof generalised inverse
+ * (Remark 1) is K_p^+ = K_el^+ + Z C^-1 Z^T with Z = K_el^+ U and C = I - U^T K_el^+ U (set up in
+ * FP64 at every assembly from the shape's dense FP64 K_el^+, formed once).
+ *   mode 1: the inner FP32 F-apply of such a subdomain joins its shape's tensor-core GEMM with
+ *           the elastic subdomains and adds Z_b (C^-1 Z_b^T x_b) (b: its boundary dofs), instead
+ *           of a banded FP32 solve; its FP64 solves still use its refactorised tangent.
+ *   mode 2: as 1, and its FP64 solves (residual solves, F-applies, K^+ applies) run on the
+ *           shape's elastic factor plus Z C^-1 Z^T v, so it is not refactorised at all (not with
+ *           the Dirichlet preconditioner, whose K_ii factors need the refactorisation).
+ *   mode 0: off.
+ * Applies to shapes with a dual Schur block in use and at most 3072 dofs and to subdomains with
+ * at most 96 plastic points; the others keep the refactorisation and banded solves.  Takes
+ * effect at the next assembly.  A later change of the Schur blocks in use (threshold, format)
+ * first refactorises the subdomains of mode 2.  Errors: TFETI_ERR_ARG (mode not 0..2).
+ * Stats: subdomain set-ups so since the context was made, and set-ups that fell back to the
+ * refactorisation (a C whose Cholesky failed). */
+int tfeti_set_woodbury(tfeti_ctx* ctx, int32_t mode);
 int tfeti_get_woodbury_stats(tfeti_ctx* ctx, int64_t* subdomains, int64_t* fallbacks);
 
 /* Deflation of the inner PCGP of the mixed mode (an extension; Algorithm 3's projected CG

@@ -350,9 +350,12 @@ class Context:
         """Inner Schur apply of the mixed mode with BF16 S (two MMAs per step) or TF32 x 3 (default)."""
         return self._check(self.lib.tfeti_set_schur_format(self.h, 1 if bf16 else 0), "tfeti_set_schur_format")
 
-    def set_woodbury(self, enable: bool):
-        """Inner F-apply of plastic subdomains by the shape's Schur block + a Woodbury correction."""
-        return self._check(self.lib.tfeti_set_woodbury(self.h, 1 if enable else 0), "tfeti_set_woodbury")
+    def set_woodbury(self, mode):
+        """Plastic subdomains on their shape's elastic factor + a Woodbury correction: 0 (or False) off,
+        1 in the inner FP32 F-apply only, 2 (or True, the default) also in the FP64 solves, which
+        leaves them out of the refactorisation."""
+        m = 2 if mode is True else 0 if mode is False else int(mode)
+        return self._check(self.lib.tfeti_set_woodbury(self.h, m), "tfeti_set_woodbury")
 
     def woodbury_stats(self) -> dict:
         a, b = C.c_int64(), C.c_int64()

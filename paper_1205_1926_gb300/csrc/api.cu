@@ -345,10 +345,13 @@ int check_factorisation(tfeti_ctx* c) {
   return TFETI_OK;
 }
 
+void wood_correct_solve(tfeti_ctx* c, const SolveArgs& a, cudaStream_t st);
+
 void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
   cudaEvent_t e1 = timed_begin(c, 0);
   launch_sub_solve(c->M, a, c->solve_smem, c->st);
   if (e1) cudaEventRecord(e1, c->st);
+  wood_correct_solve(c, a, c->st);   // subdomains on their elastic factor + Woodbury correction
   c->launches += 1;
   c->f_launches += 1;
 }
@@ -383,6 +386,7 @@ void op_F(tfeti_ctx* c, const double* x, double* yv) {
       c->g_flops += 2.0 * cnt * (double)n_bd * n_bd;
       c->g_bytes += 8.0 * ((double)n_bd * n_bd + 2.0 * cnt * n_bd);
     }
+    wood_correct_solve(c, a, c->st);   // plastic subdomains on the Schur block + correction
     if (ge1) cudaEventRecord(ge1, c->st);
     c->g_launches += 1;
     if (c->n_items_pl64 > 0) cudaStreamWaitEvent(c->st, c->ev_join, 0);
@@ -576,37 +580,39 @@ int ensure_schur_bf16(tfeti_ctx* c) {
   return cuda_check(c, "forming BF16 Schur tiles");
 }
 
-// Dense FP32 K^+ (fixing-dof generalised inverse of the elastic template) of every shape with a
+// Dense FP64 K^+ (fixing-dof generalised inverse of the elastic template) of every shape with a
 // formed dual Schur block and at most kWoodMaxN dofs, from unit right-hand sides through the FP64
-// banded solve; formed once (a case context shares its base's).  Used by the Woodbury inner apply.
+// banded solve; formed once (a case context shares its base's).  Used by the Woodbury set-up.
 int ensure_kinv(tfeti_ctx* c) {
-  if (c->kinv32) return TFETI_OK;
+  if (c->kinv) return TFETI_OK;
   if (c->base) {
     const int st = ensure_kinv(c->base);
     if (st != TFETI_OK) return fail(c, st, c->base->err);
-    c->kinv32 = c->base->kinv32;
+    c->kinv = c->base->kinv;
     c->kinv_off = c->base->kinv_off;
     c->d_kinv_off = c->base->d_kinv_off;
     return TFETI_OK;
   }
   const Plan& P = c->plan;
   const size_t nsh = P.shapes.size();
-  c->kinv_off.assign(nsh, -1);
+  std::vector<long long> off(nsh, -1);
   long long tot = 0;
   for (size_t sh = 0; sh < nsh; ++sh) {
     const int n = (int)P.shapes[sh].n_dof;
     if (!c->schur_formed[sh] || n > kWoodMaxN) continue;
-    c->kinv_off[sh] = tot;
+    off[sh] = tot;
     tot += (long long)n * n;
   }
+  double* kinv = nullptr;
   try {
-    c->kinv32 = dalloc<float>(c, (size_t)std::max(1LL, tot));
-    c->d_kinv_off = upload(c, c->kinv_off);
+    kinv = dalloc<double>(c, (size_t)std::max(1LL, tot));
+    c->d_kinv_off = upload(c, off);
   } catch (const std::bad_alloc&) {
+    dfree(c, kinv, (size_t)std::max(1LL, tot));
     return fail(c, TFETI_ERR_OOM, "device allocation failed");
   }
   for (size_t sh = 0; sh < nsh; ++sh) {
-    if (c->kinv_off[sh] < 0) continue;
+    if (off[sh] < 0) continue;
     const int n = (int)P.shapes[sh].n_dof;
     std::vector<SolveItem> items;
     for (int j = 0; j < n; j += c->rcap) {
@@ -627,43 +633,64 @@ int ensure_kinv(tfeti_ctx* c) {
     a.in_mode = 5;
     a.out_mode = 4;
     a.rep_sub = P.shapes[sh].rep_sub;
-    a.S32 = c->kinv32;
-    a.s_off = c->kinv_off[sh];
+    a.S64 = kinv;
+    a.s_off = off[sh];
     launch_sub_solve(c->M, a, c->solve_smem, c->st);
     c->launches += 1;
     sync(c);
+    dfree(c, d_items, items.size());
   }
+  c->kinv = kinv;
+  c->kinv_off = off;
   return cuda_check(c, "forming dense K^+ blocks");
 }
 
+// Grows a scratch pool (contents not kept) to at least `need` elements, doubling.
+template <typename T>
+void ensure_cap(tfeti_ctx* c, T*& p, long long& cap, long long need) {
+  if (need <= cap && p) return;
+  sync(c);
+  dfree(c, p, (size_t)std::max(1LL, cap));
+  cap = std::max(need, 2 * cap);
+  p = dalloc<T>(c, (size_t)std::max(1LL, cap));
+}
+
 // Woodbury set-up of the plastic subdomains chosen in c->h_wood (after an assembly in the mixed
-// mode): their plastic points, C, Z_b^T and Y = C^-1 Z_b^T; pools grown on demand.  A subdomain
-// whose C fails its Cholesky (not expected: C is positive definite) returns to banded solves.
-int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
+// mode): their plastic points, U, Z^T, C and its Cholesky factor in FP64, and the inner apply's
+// FP32 Z_b^T and Y = C^-1 Z_b^T.  fp64: the FP64 solves of these subdomains will run on the
+// elastic factor plus the correction (no refactorisation).  If a pivot of some C is not
+// positive (not expected: C is positive definite) no subdomain keeps the correction and the
+// function returns TFETI_OK with c->wood.n == 0 and h_wood cleared.
+int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64) {
   c->wood.n = 0;
   std::vector<int> list, npts;
-  std::vector<long long> pt_off, c_off, z_off, d_off;
-  long long pts_tot = 0, c_tot = 0, z_tot = 0, d_tot = 0;
-  int max_pts = 0, max_bd = 0;
+  std::vector<long long> pt_off, c_off, z_off, d_off, zt_off;
+  long long pts_tot = 0, c_tot = 0, z_tot = 0, d_tot = 0, zt_tot = 0;
+  int max_pts = 0, max_bd = 0, max_n = 0, max_copy = 0;
   for (size_t p = 0; p < c->h_wood.size(); ++p) {
     if (!c->h_wood[p]) continue;
-    const int k = np[p], r = 6 * k, n_bd = 3 * c->plan.shapes[c->h_subs[p].shape].n_bnd;
+    const SubDev& S = c->h_subs[p];
+    const int k = np[p], r = 6 * k, n_bd = 3 * S.n_bnd;
     list.push_back((int)p);
     npts.push_back(k);
     pt_off.push_back(pts_tot);
     c_off.push_back(c_tot);
     z_off.push_back(z_tot);
     d_off.push_back(d_tot);
+    zt_off.push_back(zt_tot);
     pts_tot += k;
     c_tot += (long long)r * r;
     z_tot += (long long)r * n_bd;
     d_tot += (long long)((r + 31) / 32) * 32 * 32;
+    zt_tot += (long long)r * S.n_dof;
     max_pts = std::max(max_pts, k);
     max_bd = std::max(max_bd, n_bd);
+    max_n = std::max(max_n, S.n_dof);
+    max_copy = std::max(max_copy, S.n_copy);
   }
   if (list.empty()) return TFETI_OK;
+  const int nl = (int)list.size();
   try {
-    const int nl = (int)list.size();
     if (!c->d_wood_list) {
       const int ns = (int)c->h_subs.size();
       c->d_wood_list = dalloc<int>(c, ns);
@@ -672,28 +699,24 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
       c->d_wood_c_off = dalloc<long long>(c, ns);
       c->d_wood_z_off = dalloc<long long>(c, ns);
       c->d_wood_d_off = dalloc<long long>(c, ns);
+      c->d_wood_zt_off = dalloc<long long>(c, ns);
+      c->wood_t = dalloc<float>(c, (size_t)ns * 6 * kWoodMaxPts);
+      c->wood_t64 = dalloc<double>(c, (size_t)ns * 6 * kWoodMaxPts);
     }
-    if (d_tot > c->wood_d_cap) {
-      c->wood_d_cap = std::max(d_tot, 2 * c->wood_d_cap);
-      c->wood_d = dalloc<float>(c, (size_t)c->wood_d_cap);
-    }
-    if (pts_tot > c->wood_pts_cap) {
-      c->wood_pts_cap = std::max(pts_tot, 2 * c->wood_pts_cap);
-      c->d_wood_pts = dalloc<int>(c, (size_t)c->wood_pts_cap);
-    }
-    if (c_tot > c->wood_c_cap) {
-      c->wood_c_cap = std::max(c_tot, 2 * c->wood_c_cap);
-      c->wood_c = dalloc<float>(c, (size_t)c->wood_c_cap);
-    }
-    if (z_tot > c->wood_z_cap) {
-      c->wood_z_cap = std::max(z_tot, 2 * c->wood_z_cap);
-      c->wood_z = dalloc<float>(c, (size_t)c->wood_z_cap);
-      c->wood_y = dalloc<float>(c, (size_t)c->wood_z_cap);
-    }
-    if (!c->wood_t) c->wood_t = dalloc<float>(c, (size_t)c->h_subs.size() * 6 * kWoodMaxPts);
-    if ((long long)nl * max_bd > c->wood_x_cap) {
-      c->wood_x_cap = std::max((long long)nl * max_bd, 2 * c->wood_x_cap);
-      c->wood_x = dalloc<float>(c, (size_t)c->wood_x_cap);
+    ensure_cap(c, c->d_wood_pts, c->wood_pts_cap, pts_tot);
+    ensure_cap(c, c->wood_dofs, c->wood_dofs_cap, 24 * pts_tot);
+    ensure_cap(c, c->wood_u, c->wood_u_cap, 144 * pts_tot);
+    ensure_cap(c, c->wood_zt, c->wood_zt_cap, zt_tot);
+    ensure_cap(c, c->wood_c64, c->wood_c64_cap, c_tot);
+    ensure_cap(c, c->wood_d64, c->wood_d64_cap, d_tot);
+    ensure_cap(c, c->wood_c, c->wood_c_cap, c_tot);
+    ensure_cap(c, c->wood_d, c->wood_d_cap, d_tot);
+    ensure_cap(c, c->wood_z, c->wood_z_cap, z_tot);
+    ensure_cap(c, c->wood_y, c->wood_y_cap, z_tot);
+    ensure_cap(c, c->wood_x, c->wood_x_cap, (long long)nl * max_bd);
+    if (fp64) {
+      ensure_cap(c, c->wood_v, c->wood_v_cap, (long long)nl * max_n);
+      ensure_cap(c, c->wood_yb, c->wood_yb_cap, (long long)nl * max_n);
     }
     cudaMemcpyAsync(c->d_wood_list, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_wood_np, npts.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, c->st);
@@ -701,13 +724,18 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
     cudaMemcpyAsync(c->d_wood_c_off, c_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_wood_z_off, z_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_wood_d_off, d_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_wood_zt_off, zt_off.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice, c->st);
   } catch (const std::bad_alloc&) {
     return fail(c, TFETI_ERR_OOM, "device allocation failed (Woodbury pools)");
   }
   WoodArgs& w = c->wood;
-  w.n = (int)list.size();
+  w = WoodArgs{};
+  w.n = nl;
   w.max_pts = max_pts;
   w.max_bd = max_bd;
+  w.max_n = max_n;
+  w.max_copy = max_copy;
+  w.fp64 = fp64;
   w.list = c->d_wood_list;
   w.pt_off = c->d_wood_pt_off;
   w.n_pts = c->d_wood_np;
@@ -716,18 +744,29 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
   w.pa = c->pa;
   w.pb = c->pb;
   w.pn = c->pn;
-  w.kinv = c->kinv32;
+  w.kinv = c->kinv;
   w.kinv_off = c->d_kinv_off;
+  w.u_pool = c->wood_u;
+  w.dof_pool = c->wood_dofs;
+  w.zt_off = c->d_wood_zt_off;
+  w.zt_pool = c->wood_zt;
   w.c_off = c->d_wood_c_off;
-  w.c_pool = c->wood_c;
+  w.c_pool = c->wood_c64;
+  w.c32_pool = c->wood_c;
+  w.c_total = c_tot;
+  w.d_off = c->d_wood_d_off;
+  w.d_pool = c->wood_d64;
+  w.d32_pool = c->wood_d;
+  w.d_total = d_tot;
   w.z_off = c->d_wood_z_off;
   w.z_pool = c->wood_z;
   w.y_pool = c->wood_y;
   w.z_total = z_tot;
   w.tbuf = c->wood_t;
   w.xbuf = c->wood_x;
-  w.d_off = c->d_wood_d_off;
-  w.d_pool = c->wood_d;
+  w.vbuf = c->wood_v;
+  w.tbuf64 = c->wood_t64;
+  w.ybuf = c->wood_yb;
   w.err = c->d_err;
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
   launch_wood_setup(c->M, w, c->st);
@@ -735,16 +774,79 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np) {
   int herr = 0;
   cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
   sync(c);
-  if (herr & 8) {   // keep the banded solves for this assembly
+  if (herr & 8) {   // keep the refactorisation and the banded solves for this assembly
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
     std::fill(c->h_wood.begin(), c->h_wood.end(), 0);
     c->wood.n = 0;
     c->wood_fallbacks += 1;
-    build_items(c, np);
     return cuda_check(c, "Woodbury set-up");
   }
   c->wood_subs += w.n;
+  if (fp64) c->wood_fac_saved += w.n;
   return cuda_check(c, "Woodbury set-up");
+}
+
+// After an FP64 subdomain-solve pass whose items put the Woodbury subdomains on their elastic
+// factor (right-hand side src + sign B^T lam): add Z C^-1 Z^T v to dst and the slots in cbuf.
+void wood_correct64(tfeti_ctx* c, const double* src, const double* lam, double sign, double* cbuf, double* dst,
+                    cudaStream_t st) {
+  if (c->wood.n <= 0 || !c->wood.fp64) return;
+  c->launches += launch_wood_apply64(c->M, c->wood, src, lam, sign, cbuf, dst, st);
+}
+
+// Gives the subdomains that the last assembly put on the FP64 Woodbury correction their own
+// factor records (from the element corrections kept since), so that they no longer depend on
+// the inner apply's Schur block; called before the Schur blocks in use change.
+int wood_materialize(tfeti_ctx* c) {
+  if (c->wood.n <= 0 || !c->wood.fp64) return TFETI_OK;
+  const int fst = check_factorisation(c);
+  if (fst != TFETI_OK) return fst;
+  const DevMesh& M = c->M;
+  const std::vector<int>& np = c->h_np_all;
+  std::vector<int> list;
+  std::vector<long long> offs, facs;
+  try {
+    update_slots(c, np);
+    for (int p = 0; p < M.n_sub; ++p)
+      if (c->h_wood[p]) list.push_back(p);
+    offs = band_workspace(c, list);
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed (own factor records)");
+  }
+  int max_rows = 0;
+  long long len = 0;
+  for (int p : list) {
+    facs.push_back(own_off(c, p));
+    max_rows = std::max(max_rows, c->h_subs[p].n_dof);
+    len = std::max<long long>(len, c->plan.subs[p].fac_size);
+  }
+  cudaMemcpyAsync(c->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->d_list_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
+  cudaMemcpyAsync(c->d_list_fac, facs.data(), sizeof(long long) * facs.size(), cudaMemcpyHostToDevice, c->st);
+  launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band_ws, c->d_list_off, 0, max_rows,
+                   c->plan.max_bw, c->st);
+  cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+  launch_band_chol(M, c->d_list, (int)list.size(), c->d_list_off, c->band_ws, c->d_list_fac, c->fac_own, c->d_err,
+                   c->plan.max_bw, c->n_sm, c->st);
+  launch_fac_to_f32(c->fac_own, c->fac32_own, c->d_list_fac, (int)list.size(), len, c->st);
+  c->launches += 3;
+  c->factor_launches += 1;
+  int herr = 0;
+  cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  sync(c);
+  if (herr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a subdomain factorisation");
+  c->wood.fp64 = false;
+  c->wood_fac_saved -= (long long)list.size();
+  build_items(c, np);
+  return cuda_check(c, "Woodbury subdomains refactorised");
+}
+
+// The same for the outputs of the FP64 solve pass `a` (in_mode 0 or 1; out_mode 0, 1 or 3).
+void wood_correct_solve(tfeti_ctx* c, const SolveArgs& a, cudaStream_t st) {
+  if (a.fp32 || (a.in_mode != 0 && a.in_mode != 1)) return;
+  const bool to_c = a.out_mode == 0 || a.out_mode == 3, to_d = a.out_mode == 1 || a.out_mode == 3;
+  wood_correct64(c, a.in_mode == 1 ? a.src : nullptr, a.lam, a.in_mode == 0 ? 1.0 : -1.0, to_c ? a.cbuf : nullptr,
+                 to_d ? a.dst : nullptr, st);
 }
 
 void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract);
@@ -754,6 +856,10 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract);
 // run FP32 banded solves.  T is picked among a few candidates by timing the FP32
 // F-apply once per distinct choice (after one warm-up application each).
 int tune_schur_threshold(tfeti_ctx* c) {
+  {
+    const int wst = wood_materialize(c);
+    if (wst != TFETI_OK) return wst;
+  }
   const size_t nsh = c->plan.shapes.size();
   std::vector<int> count(nsh, 0);
   for (const SubDev& sd : c->h_subs) ++count[sd.shape];
@@ -889,20 +995,42 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
   std::vector<int> np(M.n_sub);
   cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
   sync(c);
-  std::vector<int> list;
+  c->h_np_all = np;
+  // plastic subdomains on their shape's elastic factor plus a Woodbury correction, where the shape
+  // keeps a dense K^+ and the subdomain has at most kWoodMaxPts plastic points: in the inner FP32
+  // F-apply (through the shape's Schur block) and, with wood_mode 2, in the FP64 solves as well,
+  // which leaves them out of the refactorisation
+  c->h_wood.assign(M.n_sub, 0);
+  c->wood.n = 0;
+  const bool wood_ok = c->wood_mode > 0 && c->precision == TFETI_PRECISION_MIXED && c->schur_ready && c->kinv &&
+                       c->schur_use.size() == c->plan.shapes.size();
+  if (wood_ok) {
+    for (int p = 0; p < M.n_sub; ++p) {
+      const int sh = c->h_subs[p].shape;
+      c->h_wood[p] = np[p] > 0 && np[p] <= kWoodMaxPts && c->kinv_off[sh] >= 0 && c->schur_use[sh];
+    }
+    const int wst = wood_setup(c, np, c->wood_mode >= 2 && !c->dirichlet);
+    if (wst != TFETI_OK) return wst;
+  }
+  std::vector<int> npf = np;   // plastic points of the subdomains that are refactorised
+  if (c->wood.n > 0 && c->wood.fp64)
+    for (int p = 0; p < M.n_sub; ++p)
+      if (c->h_wood[p]) npf[p] = 0;
+  std::vector<int> list, klist;
   std::vector<long long> offs, facs, kbbs;
   try {
-    update_slots(c, np);
+    update_slots(c, npf);
     for (int p = 0; p < M.n_sub; ++p)
-      if (np[p] > 0) list.push_back(p);
+      if (npf[p] > 0) list.push_back(p);
     offs = band_workspace(c, list);
   } catch (const std::bad_alloc&) {
     return fail(c, TFETI_ERR_OOM, "device allocation failed (own factor records)");
   }
   for (int p = 0; p < M.n_sub; ++p) {
     const SubDev& S = c->h_subs[p];
-    if (np[p] > 0) {
-      facs.push_back(own_off(c, p));
+    if (npf[p] > 0) facs.push_back(own_off(c, p));
+    if (np[p] > 0) {   // the lumped preconditioner's K_bb of every plastic subdomain
+      klist.push_back(p);
       kbbs.push_back(c->own_kbb_base + c->plan.subs[p].kbb_off);
       c->h_kbb_off[p] = kbbs.back();
     } else {
@@ -910,28 +1038,16 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
     }
   }
   cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
-  c->last_refactored.push_back((int)list.size());
-  // inner F-apply of the plastic subdomains: their shape's Schur block plus a Woodbury correction
-  // where the shape keeps a dense K^+ and the subdomain has at most kWoodMaxPts plastic points
-  c->h_wood.assign(M.n_sub, 0);
-  c->wood.n = 0;
-  const bool wood_ok = c->wood_on && c->precision == TFETI_PRECISION_MIXED && c->schur_ready && c->kinv32 &&
-                       c->schur_use.size() == c->plan.shapes.size();
-  if (wood_ok)
-    for (int p = 0; p < M.n_sub; ++p) {
-      const int sh = c->h_subs[p].shape;
-      c->h_wood[p] = np[p] > 0 && np[p] <= kWoodMaxPts && c->kinv_off[sh] >= 0 && c->schur_use[sh];
-    }
-  build_items(c, np);
-  if (wood_ok) {
-    const int wst = wood_setup(c, np);
-    if (wst != TFETI_OK) return wst;
+  if (!klist.empty()) {
+    cudaMemcpyAsync(c->d_klist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_list_kbb, kbbs.data(), sizeof(long long) * kbbs.size(), cudaMemcpyHostToDevice, c->st);
   }
+  c->last_refactored.push_back((int)list.size());
+  build_items(c, npf);
   if (!list.empty()) {
     cudaMemcpyAsync(c->d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_list_off, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_list_fac, facs.data(), sizeof(long long) * facs.size(), cudaMemcpyHostToDevice, c->st);
-    cudaMemcpyAsync(c->d_list_kbb, kbbs.data(), sizeof(long long) * kbbs.size(), cudaMemcpyHostToDevice, c->st);
     int max_rows = 0;
     for (int p : list) max_rows = std::max(max_rows, c->h_subs[p].n_dof);
     launch_band_fill(M, c->d_list, (int)list.size(), c->elem_np, c->dKe, c->band_ws, c->d_list_off, 0, max_rows,
@@ -958,7 +1074,7 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
       cudaMemcpyAsync(c->h_err_fac, c->d_err_fac, sizeof(int), cudaMemcpyDeviceToHost, c->st_fac);
       cudaEventRecord(c->ev_fac_done, c->st_fac);
       c->fac_pending = c->fac_check_pending = true;
-      launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
+      launch_kbb_fill(M, c->d_klist, c->d_list_kbb, (int)klist.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
                       c->kbb32, 0, c->st);
       launch_internal_force(M, c->dsig, df, c->f_full, c->st);
       c->launches += 2;
@@ -1010,8 +1126,8 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
       if (derr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a Dirichlet-preconditioner factorisation");
     }
   }
-  if (!list.empty())
-    launch_kbb_fill(M, c->d_list, c->d_list_kbb, (int)list.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
+  if (!klist.empty())
+    launch_kbb_fill(M, c->d_klist, c->d_list_kbb, (int)klist.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
                     c->kbb32, 0, c->st);
   launch_internal_force(M, c->dsig, df, c->f_full, c->st);
   c->launches += 2;
@@ -1347,6 +1463,7 @@ void residual_solve(tfeti_ctx* c, const double* f, const double* lam, double* r_
     o.items = a.items + c->n_items_el;
     o.n_items = c->n_items - c->n_items_el;
     launch_sub_solve(c->M, o, c->solve_smem, c->st);
+    wood_correct_solve(c, a, c->st);
     c->launches += 2;
     c->f_split += 1;
   } else {
@@ -1939,6 +2056,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->d_kbb_off = dalloc<long long>(c, ns);
   c->h_kbb_off.assign(ns, 0);
   c->d_list_kbb = dalloc<long long>(c, ns);
+  c->d_klist = dalloc<int>(c, ns);
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
   c->cbuf = dalloc<double>(c, P.n_copy);
   const size_t m = (size_t)P.n_mult;
@@ -2501,7 +2619,7 @@ int tfeti_set_precision(tfeti_ctx* c, int32_t mode, double inner_rtol) {
     const bool fresh = !c->schur_ready;
     int st = ensure_schur(c);
     if (st != TFETI_OK) return st;
-    if (c->wood_on) {
+    if (c->wood_mode > 0) {
       st = ensure_kinv(c);
       if (st != TFETI_OK) return st;
     }
@@ -2548,6 +2666,10 @@ int tfeti_set_schur_threshold(tfeti_ctx* c, int32_t threshold) {
   if (c->precision != TFETI_PRECISION_MIXED) return fail(c, TFETI_ERR_ARG, "the Schur threshold needs the mixed mode");
   c->schur_manual = threshold != 0;
   if (threshold == 0) return tune_schur_threshold(c);
+  {
+    const int wst = wood_materialize(c);
+    if (wst != TFETI_OK) return wst;
+  }
   const size_t nsh = c->plan.shapes.size();
   std::vector<int> count(nsh, 0);
   for (const SubDev& sd : c->h_subs) ++count[sd.shape];
@@ -2603,10 +2725,11 @@ int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   return cuda_check(c, "tfeti_set_recycling");
 }
 
-int tfeti_set_woodbury(tfeti_ctx* c, int32_t enable) {
+int tfeti_set_woodbury(tfeti_ctx* c, int32_t mode) {
   if (!c) return TFETI_ERR_ARG;
-  c->wood_on = enable != 0;
-  if (c->wood_on && c->precision == TFETI_PRECISION_MIXED && c->schur_ready) {
+  if (mode < 0 || mode > 2) return fail(c, TFETI_ERR_ARG, "Woodbury mode must be 0, 1 or 2");
+  c->wood_mode = mode;
+  if (mode > 0 && c->precision == TFETI_PRECISION_MIXED && c->schur_ready) {
     const int st = ensure_kinv(c);
     if (st != TFETI_OK) return st;
   }
@@ -2840,6 +2963,7 @@ int tfeti_apply_kdag(tfeti_ctx* c, const double* x, double* y) {
   a.in_mode = 1;
   a.out_mode = 1;
   launch_sub_solve(c->M, a, c->solve_smem, c->st);
+  wood_correct_solve(c, a, c->st);
   c->launches += 1;
   sync(c);
   return cuda_check(c, "tfeti_apply_kdag");

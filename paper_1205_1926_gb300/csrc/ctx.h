@@ -84,24 +84,32 @@ struct tfeti_ctx {
   void* Sbf = nullptr;
   bool schur_bf16 = false;                   // inner Schur apply with BF16 S (else TF32 x 3)
   bool schur_manual = false;                 // threshold set by tfeti_set_schur_threshold (no re-tuning)
-  // Woodbury inner F-apply of plastic subdomains (kernels_woodbury.cu): dense FP32 K^+ per shape
-  // (kinv_off[shape] >= 0 where formed; a case context shares the base's), the subdomains
-  // handled that way after the last assembly and their pools (grown on demand)
-  bool wood_on = true;
-  float* kinv32 = nullptr;
+  // Plastic subdomains on their shape's elastic factor plus a Woodbury correction
+  // (kernels_woodbury.cu): dense FP64 K^+ per shape (kinv_off[shape] >= 0 where formed; a case
+  // context shares the base's), the subdomains handled that way after the last assembly and
+  // their pools (grown on demand, contents not kept).  wood_mode: 0 off, 1 the inner FP32
+  // F-apply only (the subdomains are still refactorised for the FP64 solves), 2 also the FP64
+  // solves (no refactorisation).
+  int wood_mode = 2;
+  double* kinv = nullptr;
   std::vector<long long> kinv_off;
   long long* d_kinv_off = nullptr;
-  std::vector<char> h_wood;                  // per subdomain: Woodbury in the inner F-apply
+  std::vector<char> h_wood;                  // per subdomain: on the Woodbury correction
+  std::vector<int> h_np_all;                 // plastic points per subdomain at the last assembly
   tfeti::WoodArgs wood;
   int* d_wood_list = nullptr;
   int* d_wood_np = nullptr;
-  long long *d_wood_pt_off = nullptr, *d_wood_c_off = nullptr, *d_wood_z_off = nullptr, *d_wood_d_off = nullptr;
-  int* d_wood_pts = nullptr;
-  float *wood_c = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr;
-  long long wood_pts_cap = 0, wood_c_cap = 0, wood_z_cap = 0, wood_d_cap = 0, wood_x_cap = 0;
-  float* wood_x = nullptr;
-  float* wood_d = nullptr;
-  long long wood_subs = 0, wood_fallbacks = 0;
+  long long *d_wood_pt_off = nullptr, *d_wood_c_off = nullptr, *d_wood_z_off = nullptr, *d_wood_d_off = nullptr,
+            *d_wood_zt_off = nullptr;
+  int *d_wood_pts = nullptr, *wood_dofs = nullptr;
+  double *wood_u = nullptr, *wood_zt = nullptr, *wood_c64 = nullptr, *wood_d64 = nullptr;
+  double *wood_v = nullptr, *wood_t64 = nullptr, *wood_yb = nullptr;
+  float *wood_c = nullptr, *wood_d = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr,
+        *wood_x = nullptr;
+  long long wood_pts_cap = 0, wood_dofs_cap = 0, wood_u_cap = 0, wood_zt_cap = 0, wood_c64_cap = 0,
+            wood_d64_cap = 0, wood_c_cap = 0, wood_d_cap = 0, wood_z_cap = 0, wood_y_cap = 0, wood_x_cap = 0,
+            wood_v_cap = 0, wood_yb_cap = 0;
+  long long wood_subs = 0, wood_fallbacks = 0, wood_fac_saved = 0;
   float* s_part = nullptr;                   // split-K partial tiles of the Schur apply
   int* s_count = nullptr;                    // split-K arrival counters (zero between launches)
   std::vector<long long> s_tile_off;
@@ -145,6 +153,7 @@ struct tfeti_ctx {
   long long* d_kbb_off = nullptr;      // per subdomain: template or own offset
   std::vector<long long> h_kbb_off;
   long long* d_list_kbb = nullptr;
+  int* d_klist = nullptr;                    // plastic subdomains of the last assembly (K_bb refresh)
   int max_bnd = 0;
   // dual
   double *cbuf = nullptr, *lam = nullptr, *lam_im = nullptr, *lamk = nullptr, *r = nullptr, *w = nullptr,

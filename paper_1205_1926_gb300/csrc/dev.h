@@ -148,7 +148,7 @@ struct SolveArgs {
   // boundary-dof columns j; the geometry is subdomain rep_sub; column j of
   // S = (K^+)_{boundary, boundary} goes to S32 + s_off + j * n_bd.
   // in_mode 5 / out_mode 4 (dense K^+ of one shape): item.sub[] hold local dofs j; column j
-  // of K^+ (all n rows, zero at the fixing dofs) goes to S32 + s_off + j * n
+  // of K^+ (all n rows, zero at the fixing dofs) goes to S64 + s_off + j * n
   int rep_sub;
   float* S32;
   double* S64;                 // nullable: the same columns in FP64
@@ -190,37 +190,60 @@ void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int 
 void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
                                const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
                                int* count, double* cbuf, int* err, cudaStream_t st);
-// Inner F-apply of plastic subdomains by Woodbury on their shape's elastic dual Schur block
-// (kernels_woodbury.cu).  list: the n subdomains; per subdomain pt_off (into pts), n_pts plastic
-// points, c_off (r x r C, r = 6 n_pts) and z_off (r x n_bd Z_b^T in z_pool, Y = C^{-1} Z_b^T at
-// the same offset in y_pool); kinv: dense FP32 K^+ per shape at kinv_off[shape].  err: bit 8
-// set if a Cholesky pivot of C is not positive.
+// Plastic subdomains on their shape's elastic factor plus a Woodbury correction
+// (kernels_woodbury.cu).  list: the n subdomains (r = 6 n_pts[w] correction columns each, n dofs,
+// n_bd boundary dofs).  Per subdomain w: pts + pt_off[w] its plastic points; u_pool +
+// 144 pt_off[w] the r x 24 U and dof_pool + 24 pt_off[w] the points' 24 local dofs; zt_pool +
+// zt_off[w] Z^T = (K^+ U)^T (r x n, FP64); c_pool + c_off[w] C = I - U^T Z, then its lower
+// Cholesky factor (r x r, FP64), d_pool + d_off[w] the inverses of its 32 x 32 diagonal blocks;
+// c32_pool / d32_pool the same rounded to FP32; z_pool + z_off[w] Z_b^T (r x n_bd, FP32) and
+// y_pool + z_off[w] Y = C^-1 Z_b^T.  kinv: dense FP64 K^+ per shape at kinv_off[shape].
+// err: bit 8 set if a Cholesky pivot of C is not positive.
 constexpr int kWoodMaxN = 3072;    // shapes with at most this many dofs keep a dense K^+
 constexpr int kWoodMaxPts = 96;    // subdomains with more plastic points keep the banded solve
 struct WoodArgs {
-  int n = 0, max_pts = 0, max_bd = 0;
+  int n = 0, max_pts = 0, max_bd = 0, max_n = 0, max_copy = 0;
+  bool fp64 = false;                 // the FP64 solves run on the elastic factor + correction
   const int* list = nullptr;
   const long long* pt_off = nullptr;
   const int* n_pts = nullptr;
   int* pts = nullptr;
   const uint8_t* plastic = nullptr;
   const double *pa = nullptr, *pb = nullptr, *pn = nullptr;
-  const float* kinv = nullptr;
+  const double* kinv = nullptr;
   const long long* kinv_off = nullptr;
+  double* u_pool = nullptr;
+  int* dof_pool = nullptr;
+  const long long* zt_off = nullptr;
+  double* zt_pool = nullptr;
   const long long* c_off = nullptr;
-  float* c_pool = nullptr;
+  double* c_pool = nullptr;
+  float* c32_pool = nullptr;
+  long long c_total = 0;
+  const long long* d_off = nullptr;
+  double* d_pool = nullptr;
+  float* d32_pool = nullptr;
+  long long d_total = 0;
   const long long* z_off = nullptr;
   float *z_pool = nullptr, *y_pool = nullptr;
   long long z_total = 0;
-  float* tbuf = nullptr;             // [n][6 max_pts]: t = Y x_b of the apply
-  float* xbuf = nullptr;             // [n][max_bd]: x_b of the apply
-  const long long* d_off = nullptr;  // inverses of the Cholesky factor's 32 x 32 diagonal blocks
-  float* d_pool = nullptr;
+  float* tbuf = nullptr;             // [n][6 max_pts]: t = Y x_b of the inner apply
+  float* xbuf = nullptr;             // [n][max_bd]: x_b of the inner apply
+  double* vbuf = nullptr;            // [n][max_n]: v of the FP64 correction
+  double* tbuf64 = nullptr;          // [n][6 max_pts]: t = Z^T v, then C^-1 t
+  double* ybuf = nullptr;            // [n][max_n]: y = Z C^-1 t
   int* err = nullptr;
 };
 void launch_wood_setup(const DevMesh& M, const WoodArgs& a, cudaStream_t st);
 int wood_setup_launches(const WoodArgs& a);
+// Inner (FP32) F-apply correction: cbuf at the subdomains' interface slots += Z_b Y x_b.
 void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, double* cbuf, cudaStream_t st);
+// FP64 correction after a subdomain solve of the list's subdomains on the elastic factor with
+// right-hand side v = src + sign B^T lam (src, lam nullable; sign -1 for in_mode 1, +1 for in_mode
+// 0): y = Z C^-1 Z^T v is added to dst (the decomposed vector, nullable) and to cbuf at the
+// interface slots (nullable).  Returns the number of launches.
+int launch_wood_apply64(const DevMesh& M, const WoodArgs& a, const double* src, const double* lam, double sign,
+                        double* cbuf, double* dst, cudaStream_t st);
 
 // dst[i] = (float) src[i], i < n.
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);

@@ -408,10 +408,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sub_solve(DevMesh M, SolveArgs 
   __syncthreads();
 
   // ---- outputs
-  if (a.out_mode == 4) {   // column item.sub[r] of the dense K^+ of the geometry rep_sub, FP32
+  if (a.out_mode == 4) {   // column item.sub[r] of the dense K^+ of the geometry rep_sub, FP64
     for (int r = 0; r < R; ++r) {
       const long long o = a.s_off + (long long)item.sub[r] * n;
-      for (int i = tid; i < n; i += nt) a.S32[o + i] = (float)vec[r * npad + i];
+      for (int i = tid; i < n; i += nt) a.S64[o + i] = (double)vec[r * npad + i];
     }
     return;
   }

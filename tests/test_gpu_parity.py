@@ -609,6 +609,88 @@ def test_woodbury_inner_F_apply(hot_scale):
     assert rel(host(y32), host(y64)) <= 1e-5
 
 
+def test_woodbury_fp64_solves_match_refactorisation():
+    """Woodbury mode 2: the two hot subdomains are not refactorised; their FP64 solves run on the
+    shape's elastic factor plus Z C^-1 Z^T v (Z = K^+ U, C = I - U^T Z, set up in FP64).  F, K^+ v and
+    the FP64-refined dual solution against mode 0 (their refactorised tangents) to FP64 rounding, and
+    K^+ v against the oracle.  Changing the Schur blocks in use afterwards refactorises them first:
+    F is unchanged and the inner apply (now banded FP32 solves on the new records) stays accurate."""
+    w = W.CUBE12
+    du, hot = W.seeded_partly_plastic_increment(w, 5, 2, hot_scale=6.5e-4)
+    ctx = T.Context(w)
+    s = ctx.sizes
+    ctx.set_precision(True, 1e-3)
+    ctx.set_schur_threshold(4)
+    df = zeros(s["n_dof"])
+    ctx.traction_load((20.0, 5.0, -8.0), df)
+    f = zeros(s["n_dof"])
+    x = dev(W.seeded_vector(s["n_mult"], seed=65))
+    v = dev(W.seeded_vector(s["n_dof"], seed=66))
+    out = {}
+    for mode in (2, 0):
+        ctx.set_woodbury(mode)
+        before = ctx.woodbury_stats()["subdomains"]
+        ctx.assemble_tangent(dev(du), df, f)
+        assert (ctx.woodbury_stats()["subdomains"] - before >= 1) == (mode == 2)
+        yF, yK = zeros(s["n_mult"]), zeros(s["n_dof"])
+        ctx.apply("F", x, yF)
+        ctx.apply("kdag", v, yK)
+        u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+        ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+        out[mode] = [host(t).copy() for t in (yF, yK, u, lam)]
+    for a, b, tol in zip(out[2], out[0], (1e-13, 1e-13, 1e-10, 1e-10)):
+        assert rel(a, b) <= tol, (rel(a, b), tol)
+    m = ElastoplasticModel(w)
+    Kb, _, _ = m.assemble(du, np.zeros(m.dec.n_dof))
+    assert rel(out[2][1], m.tfeti(Kb).apply_kdag(host(v))) <= 1e-10
+    # back to mode 2, then a threshold that leaves no Schur block in use
+    ctx.set_woodbury(2)
+    ctx.assemble_tangent(dev(du), df, f)
+    ctx.set_schur_threshold(1 << 20)
+    yF, y32 = zeros(s["n_mult"]), zeros(s["n_mult"])
+    ctx.apply("F", x, yF)
+    ctx.apply("F32", x, y32)
+    assert rel(host(yF), out[0][0]) <= 1e-13
+    assert rel(host(y32), out[0][0]) <= 1e-5
+
+
+def test_woodbury_fp64_history_matches_refactorisation():
+    """The 12^3 load history in the mixed mode (Schur blocks in use) with Woodbury mode 2 against mode 0:
+    fewer subdomains refactorised, the same Newton iteration counts, u to 1e-8 (two iterates converged
+    to eps_Newton = 1e-10 and eps_PCGP = 1e-12) and the same plastic Gauss points at the end."""
+    w = W.CUBE12
+    res = {}
+    for mode in (2, 0):
+        ctx = T.Context(w)
+        ctx.set_precision(True, 1e-3)
+        ctx.set_schur_threshold(4)
+        ctx.set_woodbury(mode)
+        t_y = ctx.first_yield_traction(w.traction_dir)
+        prev = 0.0
+        df = zeros(ctx.sizes["n_dof"])
+        u, kap = zeros(ctx.sizes["n_dof"]), zeros(ctx.sizes["n_gp"])
+        infos, us, kaps = [], [], []
+        for a in w.load_fractions(w.n_steps):
+            ctx.traction_load(tuple((a - prev) * t_y * c for c in w.traction_dir), df)
+            prev = a
+            infos.append(ctx.time_step(df, w.newton_tol, w.pcg_rtol, w.newton_maxit, w.pcg_maxit))
+            ctx.get_state(u=u, kappa=kap)
+            us.append(host(u).copy())
+            kaps.append(host(kap).copy())
+        res[mode] = (infos, us, kaps, ctx.woodbury_stats())
+        ctx.close()
+    i2, u2, k2, st2 = res[2]
+    i0, u0, k0, _ = res[0]
+    assert st2["subdomains"] >= 1
+    refac2 = sum(sum(i["refactored"]) for i in i2)
+    refac0 = sum(sum(i["refactored"]) for i in i0)
+    assert refac2 < refac0, (refac2, refac0)
+    assert [i["newton"] for i in i2] == [i["newton"] for i in i0]
+    for a, b in zip(u2, u0):
+        assert rel(a, b) <= 1e-8, rel(a, b)
+    np.testing.assert_array_equal(k2[-1] > 0, k0[-1] > 0)
+
+
 @pytest.mark.parametrize("w", [W.CUBE12, W.CUBE48, CUBE12_BOXES3])
 def test_bf16_schur_F_apply(w):
     """The inner F-apply with the dual Schur blocks stored in BF16 (X split into BF16 hi/lo, FP32
