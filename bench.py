@@ -46,9 +46,9 @@ FP64_NOMINAL_TFLOPS = 1.25    # GB300 FP64 rate as published; the roofline uses 
 # DRAM traffic per launch of the banded F-apply kernel at the 64^3 benchmark size, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; the launch-list summary under profiles/ gives the
 # command).  Valid only while the kernel source is the one measured.
-MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.32e6,
+MEASURED_TRAFFIC = {"k_sub_solve": {"workload": "cube64_8x8x8", "bytes": 34.37e6,
                                     "src": "paper_1205_1926_gb300/csrc/kernels_band.cu",
-                                    "sha256": "01eefbee3c6566592055bea6187a029d8672e1baf076a248e4ff1e348cfe3f00"}}
+                                    "sha256": "5f8f884233206d10cad9c65b326615a3ce4106e7bd603f2808adf1301e97fb6d"}}
 
 
 def measured_traffic(kernel, workload):
@@ -390,6 +390,8 @@ def run_gpu(args, rank, world, local_rank):
             c.set_schur_threshold(args.schur_threshold)
         if args.no_graphs:
             c.set_graphs(False)
+        if args.no_fused:
+            c.set_fused_inner(False)
         return c
 
     def reset_start(c, arm):
@@ -789,6 +791,8 @@ def main():
                     help="with --precision mixed: the learned start (mixed_learned arm)")
     ap.add_argument("--history", type=int, default=8,
                     help="stored dual solutions of the history start in the mixed+learned arm (1..8)")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="mixed arms: the inner PCGP iteration from separate kernels instead of one cooperative launch")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),
