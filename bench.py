@@ -390,8 +390,8 @@ def run_gpu(args, rank, world, local_rank):
             c.set_schur_threshold(args.schur_threshold)
         if args.no_graphs:
             c.set_graphs(False)
-        if args.no_fused:
-            c.set_fused_inner(False)
+        if args.fused:
+            c.set_fused_inner(True)
         return c
 
     def reset_start(c, arm):
@@ -791,8 +791,9 @@ def main():
                     help="with --precision mixed: the learned start (mixed_learned arm)")
     ap.add_argument("--history", type=int, default=8,
                     help="stored dual solutions of the history start in the mixed+learned arm (1..8)")
-    ap.add_argument("--no-fused", action="store_true",
-                    help="mixed arms: the inner PCGP iteration from separate kernels instead of one cooperative launch")
+    ap.add_argument("--fused", action="store_true",
+                    help="mixed arms: the inner PCGP iteration as one cooperative launch between F-applies "
+                         "(measured slower than the separate kernels)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the mixed inner PCGP kernel by kernel instead of as one CUDA graph (for profilers)")
     ap.add_argument("--workload", default="cube64_8x8x8", choices=sorted(W.WORKLOADS),

@@ -342,6 +342,20 @@ int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr)
 int tfeti_set_woodbury(tfeti_ctx* ctx, int32_t mode);
 int tfeti_get_woodbury_stats(tfeti_ctx* ctx, int64_t* subdomains, int64_t* fallbacks);
 
+/* The inner PCGP iteration of the mixed mode as one cooperative launch between two F-applies
+ * (an extension; default off): the contraction of F p and p.Fp, the lambda and r updates, w = P r,
+ * the lumped preconditioner, y = P z and the new search direction run in one kernel with one CTA
+ * per SM and grid barriers between the phases (each wait bounded: one that gives up ends the
+ * dual solve with TFETI_ERR_TIMEOUT).  It applies with the lumped preconditioner, the dense coarse
+ * solve and no deflation, and not inside ssn_time_step_cases with several contexts; otherwise the
+ * iteration runs as separate kernels.  No other cooperative launch of the whole device may run
+ * concurrently with a context's dual solves while it is on.  enable = 1 turns it on (measured
+ * slower than the separate kernels on GB300: every phase is a chain of dependent loads that the
+ * fusion does not shorten).  tfeti_get_fused_inner: *active = 1 if the next inner solve uses it
+ * (mixed mode). */
+int tfeti_set_fused_inner(tfeti_ctx* ctx, int32_t enable);
+int tfeti_get_fused_inner(tfeti_ctx* ctx, int32_t* active);
+
 /* Deflation of the inner PCGP of the mixed mode (an extension; Algorithm 3's projected CG
  * with the search directions kept conjugate to a deflation space W).  Per dual solve, at its
  * first inner solve, W holds the network's prediction (when the learned start formed one)

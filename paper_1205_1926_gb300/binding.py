@@ -97,6 +97,8 @@ SIGNATURES = {
     "tfeti_set_schur_threshold": (C.c_int, [_P, _I]),
     "tfeti_set_deflation": (C.c_int, [_P, _I]),
     "tfeti_set_woodbury": (C.c_int, [_P, _I]),
+    "tfeti_set_fused_inner": (C.c_int, [_P, _I]),
+    "tfeti_get_fused_inner": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "tfeti_get_woodbury_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tfeti_get_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "tfeti_get_tuning": (C.c_int, [_P, _P, _P, _P]),
@@ -356,6 +358,15 @@ class Context:
         leaves them out of the refactorisation."""
         m = 2 if mode is True else 0 if mode is False else int(mode)
         return self._check(self.lib.tfeti_set_woodbury(self.h, m), "tfeti_set_woodbury")
+
+    def set_fused_inner(self, enable: bool):
+        """The inner PCGP iteration as one cooperative launch between two F-applies (default off)."""
+        return self._check(self.lib.tfeti_set_fused_inner(self.h, 1 if enable else 0), "tfeti_set_fused_inner")
+
+    def fused_inner_active(self) -> bool:
+        v = C.c_int32()
+        self._check(self.lib.tfeti_get_fused_inner(self.h, C.byref(v)), "tfeti_get_fused_inner")
+        return bool(v.value)
 
     def woodbury_stats(self) -> dict:
         a, b = C.c_int64(), C.c_int64()

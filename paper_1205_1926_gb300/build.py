@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libtfeti_gb300.so")
-SOURCES = ["plan.cpp", "api.cu", "kernels_fem.cu", "kernels_band.cu", "kernels_dual.cu", "kernels_schur.cu", "kernels_schur64.cu", "kernels_recycle.cu", "kernels_mlp.cu", "kernels_check.cu", "noalloc.cu", "kernels_woodbury.cu"]
+SOURCES = ["plan.cpp", "api.cu", "kernels_fem.cu", "kernels_band.cu", "kernels_dual.cu", "kernels_schur.cu", "kernels_schur64.cu", "kernels_recycle.cu", "kernels_mlp.cu", "kernels_check.cu", "noalloc.cu", "kernels_woodbury.cu", "kernels_inner.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

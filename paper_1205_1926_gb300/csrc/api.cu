@@ -9,11 +9,11 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <new>
 #include <string>
 #include <system_error>
 #include <thread>
-#include <map>
 #include <vector>
 
 #include "../../include/tfeti.h"
@@ -270,6 +270,7 @@ void build_items(tfeti_ctx* c, const std::vector<int>& plastic_count) {
   c->n_items_el = 0;
   for (const SolveItem& it : c->h_items) c->n_items_el += (it.fac & kOwnFac) ? 0 : 1;
   c->g_inner_stale = true;
+  c->lump_stale = true;
   if (c->dirichlet) {
     build_dir_item_list(c, plastic_count, R64, c->h_items_d);
     build_dir_item_list(c, plastic_count, R32, c->h_items_d32);
@@ -996,6 +997,11 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
   cudaMemcpyAsync(np.data(), c->sub_np, sizeof(int) * M.n_sub, cudaMemcpyDeviceToHost, c->st);
   sync(c);
   c->h_np_all = np;
+  {
+    long long npl = 0;
+    for (int v : np) npl += v;
+    c->op_ver = npl == 0 ? 0 : ++c->ver_counter;   // the all-elastic tangent is always the same operator
+  }
   // plastic subdomains on their shape's elastic factor plus a Woodbury correction, where the shape
   // keeps a dense K^+ and the subdomain has at most kWoodMaxPts plastic points: in the inner FP32
   // F-apply (through the shape's Schur block) and, with wood_mode 2, in the FP64 solves as well,
@@ -1219,6 +1225,120 @@ void destroy_inner_graph(tfeti_ctx* c) {
 // dot products and scalar steps ride in the kernels that produce their vectors (w, y, F p),
 // and the last kernel closes the body run; inside a graph (has_h) it also sets the WHILE
 // condition `h` of the enclosing node.
+// Tasks of the fused inner iteration's lumped preconditioner: the subdomains that share their
+// boundary blocks (the elastic ones of a shape share its template), kLumpR to a task in index
+// order; a block's rows are split only when there are fewer such groups than SMs.
+int build_lump_tasks(tfeti_ctx* c) {
+  std::map<long long, std::vector<int>> by;
+  for (size_t p = 0; p < c->h_subs.size(); ++p) by[c->h_kbb_off[p]].push_back((int)p);
+  long long n_grp = 0;
+  for (const auto& kv : by) n_grp += ((long long)kv.second.size() + kLumpR - 1) / kLumpR;
+  const int split = (int)std::max(1LL, std::min(8LL, c->n_sm / std::max(1LL, n_grp)));
+  std::vector<LumpTask> t;
+  int max_nr = 0;
+  for (const auto& kv : by) {
+    const std::vector<int>& v = kv.second;
+    const int nr = 3 * c->h_subs[v[0]].n_bnd;
+    max_nr = std::max(max_nr, nr);
+    const int chunk = ((nr + split - 1) / split + 31) / 32 * 32;
+    for (size_t i0 = 0; i0 < v.size(); i0 += kLumpR)
+      for (int r0 = 0; r0 < nr; r0 += chunk) {
+        LumpTask T{};
+        T.kbb = kv.first;
+        T.count = (int)std::min<size_t>(kLumpR, v.size() - i0);
+        for (int k = 0; k < T.count; ++k) T.sub[k] = v[i0 + k];
+        T.row0 = r0;
+        T.row1 = std::min(nr, r0 + chunk);
+        t.push_back(T);
+      }
+  }
+  try {
+    if ((int)t.size() > c->lump_cap) {
+      sync(c);
+      dfree(c, c->d_lump, (size_t)std::max(1, c->lump_cap));
+      c->lump_cap = std::max((int)t.size(), 2 * c->lump_cap);
+      c->d_lump = dalloc<LumpTask>(c, (size_t)c->lump_cap);
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(c, TFETI_ERR_OOM, "device allocation failed");
+  }
+  cudaMemcpyAsync(c->d_lump, t.data(), sizeof(LumpTask) * t.size(), cudaMemcpyHostToDevice, c->st);
+  c->n_lump = (int)t.size();
+  c->lump_max_nr = max_nr;
+  c->lump_stale = false;
+  return TFETI_OK;
+}
+
+// The fused inner iteration applies to the lumped preconditioner with the dense coarse solve and
+// no deflation, outside ssn_time_step_cases runs with other contexts (two cooperative launches of
+// the whole device must not run at once).
+bool fused_usable(tfeti_ctx* c) {
+  if (!c->fused_req || c->in_cases || c->dirichlet || c->plan.prob.precond != TFETI_PRECOND_LUMPED) return false;
+  if (c->coarse.mode != kCoarseDense || !c->coarse.H32 || c->defl_req > 0) return false;
+  if (c->lump_stale && build_lump_tasks(c) != TFETI_OK) return false;
+  if (c->inner_grid_n < 0) {
+    try {
+      c->xslot = dalloc<float>(c, (size_t)std::max(1LL, c->M.n_copy));
+      c->d_bar = dalloc<unsigned>(c, 2);
+    } catch (const std::bad_alloc&) {
+      c->inner_grid_n = 0;
+      return false;
+    }
+    cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->st);
+    InnerArgs a;
+    a.max_nr = c->lump_max_nr;
+    a.ld = h32_ld(c->coarse.l);
+    c->inner_smem_b = inner_smem(a);
+    c->inner_grid_n = inner_grid(c->n_sm, c->inner_smem_b);
+  }
+  return c->inner_grid_n > 0 && c->n_lump > 0;
+}
+
+InnerArgs inner_args(tfeti_ctx* c, int body, unsigned long long h, bool has_h) {
+  InnerArgs a;
+  a.M = c->M;
+  a.H32 = c->coarse.H32;
+  a.l = c->coarse.l;
+  a.ld = h32_ld(c->coarse.l);
+  a.kbb32 = c->kbb32;
+  a.tasks = c->d_lump;
+  a.n_tasks = c->n_lump;
+  a.max_nr = c->lump_max_nr;
+  a.r = c->rin;
+  a.w = c->w;
+  a.z = c->z;
+  a.y = c->y;
+  a.p = c->pdir;
+  a.Fp = c->Fp;
+  a.lam = c->dlt;
+  a.cbuf = c->cbuf;
+  a.xslot = c->xslot;
+  a.gx = c->gx;
+  a.hx = c->hx;
+  a.hx8 = c->hx8;
+  a.sc = c->sc;
+  a.partial = c->partial;
+  a.bar = c->d_bar;
+  a.err = c->d_err;
+  a.cond = h;
+  a.has_cond = has_h ? 1 : 0;
+  a.body = body;
+  return a;
+}
+
+int launch_inner_fused(tfeti_ctx* c, int body, unsigned long long h, bool has_h) {
+  const cudaError_t e = launch_inner(inner_args(c, body, h, has_h), c->inner_grid_n, c->inner_smem_b, c->st);
+  c->launches += 1;
+  if (e != cudaSuccess) return fail(c, TFETI_ERR_CUDA, cudaGetErrorString(e));
+  return TFETI_OK;
+}
+
+// Body of the fused inner iteration: F p onto the slots, then the fused launch.
+int enqueue_inner_fused_body(tfeti_ctx* c, unsigned long long h, bool has_h) {
+  op_F32(c, c->pdir, c->Fp, false);   // slots of F p
+  return launch_inner_fused(c, 1, h, has_h);
+}
+
 void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h, bool has_h) {
   const long long m = c->M.n_mult;
   launch_G32_coarse32(c->M, c->coarse, c->rin, c->gx, c->hx, c->hx8, c->st);
@@ -1263,10 +1383,23 @@ int build_inner_graph(tfeti_ctx* c) {
   }
   cudaStream_t saved = c->st;
   c->st = c->st_cap;
-  enqueue_inner_iteration(c, (unsigned long long)h, true);
+  const bool fused = fused_usable(c);
+  int fst = TFETI_OK;
+  if (fused) fst = enqueue_inner_fused_body(c, (unsigned long long)h, true);
+  else enqueue_inner_iteration(c, (unsigned long long)h, true);
   c->st = saved;
   cudaGraph_t captured = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->st_cap, &captured);
+  if (fused && (fst != TFETI_OK || e != cudaSuccess)) {
+    // the cooperative launch could not be captured: build the body from separate kernels
+    cudaGetLastError();
+    if (captured) cudaGraphDestroy(captured);
+    cudaGraphDestroy(g);
+    c->launches = before;
+    c->inner_grid_n = 0;
+    return build_inner_graph(c);
+  }
+  c->g_inner_fused = fused;
   c->g_body_kernels = (int)(c->launches - before);
   c->launches = before;
   if (e != cudaSuccess) {
@@ -1286,12 +1419,17 @@ int build_inner_graph(tfeti_ctx* c) {
 // Inner PCGP of the mixed-precision refinement on (dlt, rin), run as one graph launch.
 PcgOut pcg_inner_graph(tfeti_ctx* c, double tol_abs, int maxit) {
   PcgOut o;
-  if (c->g_inner_stale || !c->g_inner_exec) {
+  const bool fused = fused_usable(c);
+  if (c->g_inner_stale || !c->g_inner_exec || c->g_inner_fused != fused) {
     o.status = build_inner_graph(c);
     if (o.status != TFETI_OK) return o;
   }
   launch_pcg_init(c->sc, tol_abs * tol_abs, maxit, c->st);
   if (c->events) cudaEventRecord(c->in_e0, c->st);
+  if (c->g_inner_fused) {   // the first w, z, y and p, before the loop
+    o.status = launch_inner_fused(c, 0, 0ULL, false);
+    if (o.status != TFETI_OK) return o;
+  }
   cudaGraphLaunch(c->g_inner_exec, c->st);
   if (c->events) cudaEventRecord(c->in_e1, c->st);
   cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, c->st);
@@ -1423,8 +1561,18 @@ void deflation_start(tfeti_ctx* c) {
 PcgOut pcg_inner_eager(tfeti_ctx* c, double tol_abs, int maxit) {
   PcgOut o;
   launch_pcg_init(c->sc, tol_abs * tol_abs, maxit, c->st);
+  const bool fused = fused_usable(c);
+  if (fused) {
+    o.status = launch_inner_fused(c, 0, 0ULL, false);
+    if (o.status != TFETI_OK) return o;
+  }
   for (int run = 0; run < 2 * maxit + 4; ++run) {
-    enqueue_inner_iteration(c, 0ULL, false);
+    if (fused) {
+      o.status = enqueue_inner_fused_body(c, 0ULL, false);
+      if (o.status != TFETI_OK) return o;
+    } else {
+      enqueue_inner_iteration(c, 0ULL, false);
+    }
     c->f32_launches += 1;
     cudaMemcpyAsync(c->h_sc, c->sc, sizeof(double) * kNumScalars, cudaMemcpyDeviceToHost, c->st);
     sync(c);
@@ -1605,9 +1753,26 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   op_project(c, c->y, c->lamk);
   launch_axpby(m, 1.0, c->lam_im, 1.0, c->lamk, c->lam, c->st);
   c->launches += 2;
-  residual_solve(c, f, c->lam, c->r);   // r = d~ - F lambda_Ker
-  op_project(c, c->r, c->w);
-  const double w1 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
+  // with every contributing solution stored under the current operator, F and K^+ B^T are linear
+  // in it: r = d~ - sum_j c_j F lambda_j (formed above) and K^+ (f - B^T lambda) = K^+ (f - B^T
+  // lambda_Im) - sum_j c_j w_j replace the residual solve (the stored lambda_j lie in Ker N, so the
+  // projection of their combination changes it only by rounding)
+  bool exact = true;
+  for (int j = 0; j < nb && exact; ++j)
+    if (coef[j] != 0.0) exact = j < n && c->rec_ver[j] == c->op_ver;
+  double w1;
+  if (exact) {
+    const long long nd = c->M.n_dof;
+    launch_rec_combine(c->rec_W, c->rec_c, std::min(nb, n), nd, c->vsol_im, -1.0, c->vsol, c->st);
+    cudaMemcpyAsync(c->r, c->tm, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+    c->launches += 1;
+    ++c->rec_exact;
+    w1 = pred;
+  } else {
+    residual_solve(c, f, c->lam, c->r);   // r = d~ - F lambda_Ker
+    op_project(c, c->r, c->w);
+    w1 = std::sqrt(std::max(0.0, dot_host(c, c->w, c->w, m)));
+  }
   if (!(w1 < w0)) {
     cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
     cudaMemcpyAsync(c->r, c->dtil, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
@@ -1652,7 +1817,11 @@ void history_push(tfeti_ctx* c) {
   double* FLj = c->rec_FL + (long long)c->rec_head * m;
   cudaMemcpyAsync(Lj, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   launch_axpby(m, 1.0, c->dtil, -1.0, c->r, FLj, c->st);
-  c->launches += 1;
+  // w_j = K^+ B^T lambda_Ker = K^+ (f - B^T lambda_Im) - K^+ (f - B^T lambda)
+  const long long nd = c->M.n_dof;
+  launch_axpby(nd, 1.0, c->vsol_im, -1.0, c->vsol, c->rec_W + (long long)c->rec_head * nd, c->st);
+  c->rec_ver[c->rec_head] = c->op_ver;
+  c->launches += 2;
   c->rec_head = (c->rec_head + 1) % c->rec_q;
   c->rec_n = std::min(c->rec_n + 1, c->rec_q);
 }
@@ -1670,6 +1839,8 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   c->launches += 3;
   // d~ = d - F lambda_Im = B K^+(f - B^T lambda_Im) ; r^0 = d~
   residual_solve(c, f, c->lam_im, c->r);
+  if (c->rec_q > 0 && c->vsol_im)
+    cudaMemcpyAsync(c->vsol_im, c->vsol, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
   const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
   {
     const int fst = check_factorisation(c);   // pivots of a deferred refactorisation
@@ -1791,10 +1962,12 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   collect_events(c);
   int cst = cuda_check(c, "tfeti_dual_pcg");
   if (cst != TFETI_OK) return cst;
-  if (herr & 6) {
+  if (herr & 38) {
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    return fail(c, TFETI_ERR_TIMEOUT, (herr & 2) ? "a factor-panel copy did not complete within its time limit"
-                                              : "a Schur-tile copy or MMA did not complete within its time limit");
+    if (herr & 32) cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->st);   // the barrier restarts at zero
+    return fail(c, TFETI_ERR_TIMEOUT, (herr & 2)    ? "a factor-panel copy did not complete within its time limit"
+                                      : (herr & 4) ? "a Schur-tile copy or MMA did not complete within its time limit"
+                                                   : "a grid-barrier wait of the fused inner iteration gave up");
   }
   if (status == TFETI_OK && !converged) status = fail(c, TFETI_ERR_NOT_CONVERGED, "PCGP iteration limit reached");
   if (info) {
@@ -1893,9 +2066,36 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   std::vector<double> helm(64, 0.0);
   for (int r = 1; r < 8; ++r)
     for (int j = 0; j <= r; ++j) helm[r * 8 + j] = helmert_coef(r, j);
+  // B^T by copy slot (CSR): slot j of a free group takes helm[r][j] x[row0 + r - 1] for
+  // r = max(j, 1) .. k - 1, of a Dirichlet group x[row0 + j] (the fused inner iteration gathers with it)
+  std::vector<int> bt_ptr((size_t)P.n_copy + 1, 0), bt_row;
+  std::vector<double> bt_val;
+  for (const Group& g : P.groups)
+    for (int j = 0; j < g.k; ++j)
+      bt_ptr[(size_t)g.slot[j] + 1] = g.nrows == 0 ? 0 : (g.dirichlet ? 1 : g.k - std::max(j, 1));
+  for (size_t i = 0; i < (size_t)P.n_copy; ++i) bt_ptr[i + 1] += bt_ptr[i];
+  bt_row.resize((size_t)bt_ptr[(size_t)P.n_copy]);
+  bt_val.resize(bt_row.size());
+  for (const Group& g : P.groups)
+    for (int j = 0; j < g.k; ++j) {
+      int e = bt_ptr[(size_t)g.slot[j]];
+      if (g.nrows == 0) continue;
+      if (g.dirichlet) {
+        bt_row[e] = (int)g.row0 + j;
+        bt_val[e] = 1.0;
+        continue;
+      }
+      for (int r = std::max(j, 1); r < g.k; ++r, ++e) {
+        bt_row[e] = (int)g.row0 + r - 1;
+        bt_val[e] = helmert_coef(r, j);
+      }
+    }
   M.subs = c->d_subs;
   M.n_sub = ns;
   M.groups = upload(c, gd);
+  M.bt_ptr = upload(c, bt_ptr);
+  M.bt_row = upload(c, bt_row);
+  M.bt_val = upload(c, bt_val);
   M.slot_group = upload(c, P.slot_group);
   M.slot_j = upload(c, P.slot_j);
   M.slot_ldof = upload(c, P.slot_ldof);
@@ -1928,6 +2128,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   M.n_gp = P.n_gp;
   M.n_mult = P.n_mult;
   M.n_copy = P.n_copy;
+  M.n_groups = (long long)gd.size();
   M.n_elem = P.n_elem;
   launch_tables(P.h, lam, mu, dN, Kel, Q, c->st);
   for (const ShapeInfo& sh : P.shapes) launch_rigid_for_shape(c->h_subs[sh.rep_sub], P.h, R + sh.r_off, c->st);
@@ -2365,6 +2566,7 @@ int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* c
       if (ctxs[j] == ctxs[k]) return fail(ctxs[k], TFETI_ERR_ARG, "ssn_time_step_cases: a context appears twice");
   }
   std::vector<int> status(n_cases, TFETI_OK);
+  for (int k = 0; k < n_cases; ++k) ctxs[k]->in_cases = n_cases > 1;
   auto run = [&](int k) {
     // a new host thread starts on device 0: make the context's device current
     if (cudaSetDevice(ctxs[k]->device) != cudaSuccess) {
@@ -2393,6 +2595,7 @@ int ssn_time_step_cases(tfeti_ctx* const* ctxs, int32_t n_cases, const double* c
   run(0);
   cudaSetDevice(prev_device);   // the caller's current device is left as it was
   for (std::thread& t : threads) t.join();
+  for (int k = 0; k < n_cases; ++k) ctxs[k]->in_cases = false;
   for (int k = 0; k < n_cases; ++k)
     if (status[k] != TFETI_OK) return status[k];
   return TFETI_OK;
@@ -2706,8 +2909,14 @@ int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   if (q > 0 && q > c->rec_q) {
     try {
       // one spare slot for the MLP vector of the learned start
+      const long long nd = std::max(1LL, c->M.n_dof);
+      dfree(c, c->rec_L, (size_t)(c->rec_q + 1) * (size_t)std::max(1LL, m));
+      dfree(c, c->rec_FL, (size_t)(c->rec_q + 1) * (size_t)std::max(1LL, m));
+      dfree(c, c->rec_W, (size_t)(c->rec_q + 1) * (size_t)nd);
       c->rec_L = dalloc<double>(c, (size_t)(q + 1) * (size_t)std::max(1LL, m));
       c->rec_FL = dalloc<double>(c, (size_t)(q + 1) * (size_t)std::max(1LL, m));
+      c->rec_W = dalloc<double>(c, (size_t)(q + 1) * (size_t)nd);
+      if (!c->vsol_im) c->vsol_im = dalloc<double>(c, (size_t)nd);
       if (!c->rec_partial) {
         c->rec_partial = dalloc<double>(c, (size_t)kRedBlocks * (kRecMax * kRecMax + kRecMax));
         c->rec_out = dalloc<double>(c, kRecMax * kRecMax + kRecMax);
@@ -2721,7 +2930,8 @@ int tfeti_set_recycling(tfeti_ctx* c, int32_t q) {
   c->rec_q = q;
   c->rec_n = 0;
   c->rec_head = 0;
-  c->rec_tried = c->rec_used = 0;
+  c->rec_tried = c->rec_used = c->rec_exact = 0;
+  c->rec_ver.assign((size_t)q + 1, -1);
   return cuda_check(c, "tfeti_set_recycling");
 }
 
@@ -2734,6 +2944,18 @@ int tfeti_set_woodbury(tfeti_ctx* c, int32_t mode) {
     if (st != TFETI_OK) return st;
   }
   return TFETI_OK;   // takes effect at the next assembly
+}
+
+int tfeti_set_fused_inner(tfeti_ctx* c, int32_t enable) {
+  if (!c) return TFETI_ERR_ARG;
+  c->fused_req = enable != 0;
+  return TFETI_OK;   // the inner graph is rebuilt at the next inner solve if the choice changes
+}
+
+int tfeti_get_fused_inner(tfeti_ctx* c, int32_t* active) {
+  if (!c || !active) return TFETI_ERR_ARG;
+  *active = c->precision == TFETI_PRECISION_MIXED && fused_usable(c) ? 1 : 0;
+  return cuda_check(c, "tfeti_get_fused_inner");
 }
 
 int tfeti_get_woodbury_stats(tfeti_ctx* c, int64_t* subdomains, int64_t* fallbacks) {

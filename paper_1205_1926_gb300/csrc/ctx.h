@@ -110,6 +110,17 @@ struct tfeti_ctx {
             wood_d64_cap = 0, wood_c_cap = 0, wood_d_cap = 0, wood_z_cap = 0, wood_y_cap = 0, wood_x_cap = 0,
             wood_v_cap = 0, wood_yb_cap = 0;
   long long wood_subs = 0, wood_fallbacks = 0, wood_fac_saved = 0;
+  // fused inner iteration (kernels_inner.cu): one cooperative launch between two F-applies
+  bool fused_req = false;                    // tfeti_set_fused_inner
+  bool g_inner_fused = false;                // the built graph body uses it
+  bool in_cases = false;                     // inside ssn_time_step_cases with other contexts
+  tfeti::LumpTask* d_lump = nullptr;
+  int n_lump = 0, lump_cap = 0, lump_max_nr = 0;
+  bool lump_stale = true;
+  float* xslot = nullptr;
+  unsigned* d_bar = nullptr;
+  int inner_grid_n = -1;                     // CTAs of the fused launch (0: not possible, -1: not asked)
+  size_t inner_smem_b = 0;
   float* s_part = nullptr;                   // split-K partial tiles of the Schur apply
   int* s_count = nullptr;                    // split-K arrival counters (zero between launches)
   std::vector<long long> s_tile_off;
@@ -186,7 +197,15 @@ struct tfeti_ctx {
   double *rec_L = nullptr, *rec_FL = nullptr, *rec_partial = nullptr, *rec_out = nullptr, *rec_c = nullptr;
   double* dtil = nullptr;        // d~ of the current solve (kept when the history start is on)
   double rec_accept = 0.5;       // try the start if the predicted ||P r|| < rec_accept ||P d~||
-  long long rec_tried = 0, rec_used = 0;
+  long long rec_tried = 0, rec_used = 0, rec_exact = 0;
+  // operator versions: 0 for the all-elastic tangent, a new number for every other assembly; a stored
+  // solution whose version equals the current one has its exact FP64 products F lambda_j and
+  // w_j = K^+ B^T lambda_j ([rec_q + 1][n_dof] in rec_W), so a start built from such solutions alone
+  // gets its residual and primal vector by linear combination instead of a residual solve
+  long long op_ver = 0, ver_counter = 0;
+  std::vector<long long> rec_ver;
+  double* rec_W = nullptr;
+  double* vsol_im = nullptr;                 // K^+ (f - B^T lambda_Im) of the current dual solve
   // per-interface MLP of the learned start (tfeti_set_learned): FP32 master weights and
   // Adam moments, FP16 copy for inference, the first-Newton-solve solutions of the last
   // two load steps, per-subdomain plastic fractions, the previous load increment

@@ -57,6 +57,9 @@ struct DevMesh {
   const int* sub_b2s;       // boundary index -> first copy slot or -1, per subdomain
   const int* slot_bnd;      // copy slot -> boundary index of its node
   const int* sub_nbr;       // [interface node][28] first slot of each stencil neighbour or -1
+  const int* bt_ptr;        // B^T by copy slot (CSR over multiplier rows): bt_ptr[n_copy + 1],
+  const int* bt_row;        //   rows bt_row[e] and coefficients bt_val[e]
+  const double* bt_val;
   const int* elem_sub;     // subdomain of every element
   const double* R;         // rigid-body bases per shape, [n_dof][6] row-major
   const double* dN;        // [8 g][8 a][3] physical shape-function gradients
@@ -80,6 +83,7 @@ struct DevMesh {
   double wdet;
   double lam, mu, sigma_y, H;
   long long n_dof, n_gp, n_mult, n_copy, n_elem;
+  long long n_groups;
 };
 
 // Per-Newton-iterate Gauss-point data used by the assembly.
@@ -310,6 +314,42 @@ void launch_slots_to_full(const DevMesh& M, const double* w, double* xfull, cuda
 void launch_slots_diff(const DevMesh& M, const double* v, const double* t, double* cbuf, cudaStream_t st);
 void launch_lumped32(const DevMesh& M, const double* w, const float* kbb32, const long long* kbb_off, double* cbuf,
                      cudaStream_t st, int max_copy);
+
+// The inner PCGP iteration between two F-applies as one cooperative launch (kernels_inner.cu):
+// contraction of F p and p.Fp, the lambda and r updates (body launches), then w = P r, the lumped
+// preconditioner, y = P z and the new search direction, with grid barriers between the phases.
+// The lumped preconditioner runs by tasks: up to kLumpR subdomains that share their boundary
+// blocks (kbb32 + kbb; the elastic subdomains of a shape share its template) and a range
+// [row0, row1) of those blocks' rows.
+constexpr int kLumpR = 4;
+struct LumpTask {
+  long long kbb;
+  int count, row0, row1, pad;
+  int sub[kLumpR];
+};
+struct InnerArgs {
+  DevMesh M;
+  const float* H32 = nullptr;        // dense FP32 H, rows padded to ld
+  long long l = 0, ld = 0;
+  const float* kbb32 = nullptr;
+  const LumpTask* tasks = nullptr;
+  int n_tasks = 0, max_nr = 0;       // max_nr: largest 3 n_bnd of the tasks' shapes
+  double *r = nullptr, *w = nullptr, *z = nullptr, *y = nullptr, *p = nullptr, *Fp = nullptr, *lam = nullptr;
+  double* cbuf = nullptr;
+  float* xslot = nullptr;            // [n_copy]: B^T w at the copy slots
+  double *gx = nullptr, *hx = nullptr;
+  float* hx8 = nullptr;
+  double* sc = nullptr;
+  double* partial = nullptr;         // [3][grid]
+  unsigned* bar = nullptr;           // grid barrier (count, generation), count zero between launches
+  int* err = nullptr;                // bit 32: a grid-barrier wait gave up
+  unsigned long long cond = 0;       // WHILE handle of the graph body (has_cond)
+  int has_cond = 0;
+  int body = 0;                      // 1: starts with the contraction and the updates
+};
+size_t inner_smem(const InnerArgs& a);
+int inner_grid(int n_sm, size_t smem);   // CTAs of the launch (one per SM), 0 if it cannot run
+cudaError_t launch_inner(const InnerArgs& a, int grid, size_t smem, cudaStream_t st);
 
 // Deterministic reductions and PCG vector updates
 constexpr int kRedBlocks = 304;

@@ -29,4 +29,44 @@ __device__ __forceinline__ double b_at_row(const DevMesh& M, const double* __res
   return s;
 }
 
+// Scalar logic of the inner PCGP (state in sc, see PcgScalar): pre -- after y.w of the
+// iteration: the finiteness and stop tests; mid -- after p.Fp: the breakdown test; post -- at the
+// end of a body run: the counters and the done flag; returns whether another body run follows.
+__device__ __forceinline__ void pcg_pre_logic(double* sc) {
+  if (sc[kDone] != 0.0) return;
+  const double ww = sc[kWW], yw = sc[kYW];
+  sc[kLastWW] = ww;
+  if (!isfinite(ww) || !isfinite(yw)) {
+    sc[kDone] = 1.0;
+    sc[kStatus] = 8.0;
+    return;
+  }
+  if (sc[kFirst] != 0.0 && !(ww > 0.0)) {   // w^0 = 0: nothing to do
+    sc[kDone] = 1.0;
+    sc[kStopAfter] = 1.0;
+    return;
+  }
+  sc[kStopAfter] = ww <= sc[kTol2] ? 1.0 : 0.0;
+}
+
+__device__ __forceinline__ void pcg_mid_logic(double* sc) {
+  if (sc[kDone] != 0.0) return;
+  if (!(sc[kPFP] > 0.0)) {
+    sc[kDone] = 1.0;
+    sc[kStatus] = 7.0;
+  }
+}
+
+// Closes one body run; returns whether the WHILE loop goes on.
+__device__ __forceinline__ bool pcg_post_logic(double* sc) {
+  sc[kBodyRuns] += 1.0;
+  if (sc[kDone] == 0.0) {
+    sc[kYWPrev] = sc[kYW];
+    sc[kIter] += 1.0;
+    sc[kFirst] = 0.0;
+    if (sc[kStopAfter] != 0.0 || sc[kIter] >= sc[kMaxit]) sc[kDone] = 1.0;
+  }
+  return sc[kDone] == 0.0 && sc[kBodyRuns] < 2.0 * sc[kMaxit] + 4.0;
+}
+
 }  // namespace tfeti

@@ -411,43 +411,6 @@ __global__ void k_dot2_final(const double* partial, int nparts, double* out1, do
   }
 }
 
-__device__ void pcg_pre_logic(double* sc) {
-  if (sc[kDone] != 0.0) return;
-  const double ww = sc[kWW], yw = sc[kYW];
-  sc[kLastWW] = ww;
-  if (!isfinite(ww) || !isfinite(yw)) {
-    sc[kDone] = 1.0;
-    sc[kStatus] = 8.0;
-    return;
-  }
-  if (sc[kFirst] != 0.0 && !(ww > 0.0)) {   // w^0 = 0: nothing to do
-    sc[kDone] = 1.0;
-    sc[kStopAfter] = 1.0;
-    return;
-  }
-  sc[kStopAfter] = ww <= sc[kTol2] ? 1.0 : 0.0;
-}
-
-__device__ void pcg_mid_logic(double* sc) {
-  if (sc[kDone] != 0.0) return;
-  if (!(sc[kPFP] > 0.0)) {
-    sc[kDone] = 1.0;
-    sc[kStatus] = 7.0;
-  }
-}
-
-// Closes one body run; returns whether the WHILE loop goes on.
-__device__ bool pcg_post_logic(double* sc) {
-  sc[kBodyRuns] += 1.0;
-  if (sc[kDone] == 0.0) {
-    sc[kYWPrev] = sc[kYW];
-    sc[kIter] += 1.0;
-    sc[kFirst] = 0.0;
-    if (sc[kStopAfter] != 0.0 || sc[kIter] >= sc[kMaxit]) sc[kDone] = 1.0;
-  }
-  return sc[kDone] == 0.0 && sc[kBodyRuns] < 2.0 * sc[kMaxit] + 4.0;
-}
-
 __global__ void k_pcg_pre(double* sc) {
   if (threadIdx.x || blockIdx.x) return;
   pcg_pre_logic(sc);

@@ -744,6 +744,53 @@ def test_bf16_mixed_dual_pcg_reaches_fp64_accuracy():
     assert rel(host(lam), sol["lam"]) <= 1e-9
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("w,plastic", [(W.CUBE12, False), (W.CUBE12, True), (W.SMALL6_RAGGED, True),
+                                       (W.CUBE48, False), (CUBE12_BOXES3, True)])
+def test_fused_inner_iteration_matches_separate_kernels(w, plastic, graphs):
+    """The inner PCGP iteration as one cooperative launch between two F-applies (contraction, updates,
+    both projections with the dense coarse solve, the lumped preconditioner by tasks of subdomains
+    sharing their boundary blocks) against the same iteration from separate kernels, in the graph's
+    WHILE loop and launched from the host: inner and outer iteration counts within two and one, the
+    FP64-refined solution to 1e-10, and both at the oracle's solution (eps = 1e-12) to 1e-9."""
+    with_oracle = w is not W.CUBE48     # the oracle's 48^3 solve takes minutes
+    if with_oracle:
+        m, sig, kap, du = plastic_state(w, seed=71)
+        if not plastic:
+            du = np.zeros_like(du)
+            sig, kap = np.zeros_like(sig), np.zeros_like(kap)
+    res = {}
+    for fused in (True, False):
+        ctx = T.Context(w)
+        s = ctx.sizes
+        if with_oracle:
+            set_oracle_state(ctx, sig, kap)
+        else:
+            du = np.zeros(s["n_dof"])
+        ctx.set_precision(True, 1e-3)
+        ctx.set_schur_threshold(4)
+        ctx.set_graphs(graphs)
+        ctx.set_fused_inner(fused)
+        df = zeros(s["n_dof"])
+        ctx.traction_load((20.0, 5.0, -8.0), df)
+        f = zeros(s["n_dof"])
+        ctx.assemble_tangent(dev(du), df, f)
+        assert ctx.fused_inner_active() == fused
+        u, lam = zeros(s["n_dof"]), zeros(s["n_mult"])
+        info = ctx.dual_pcg(f, u, lam, rtol=1e-12, maxit=5000)
+        res[fused] = (host(u).copy(), host(lam).copy(), info)
+        ctx.close()
+    (uf, lf, inf), (us, ls, ins) = res[True], res[False]
+    assert abs(inf["iterations"] - ins["iterations"]) <= 2, (inf["iterations"], ins["iterations"])
+    assert abs(inf["outer_iterations"] - ins["outer_iterations"]) <= 1
+    assert rel(uf, us) <= 1e-10 and rel(lf, ls) <= 1e-10, (rel(uf, us), rel(lf, ls))
+    if with_oracle:
+        m.sigma, m.kappa = sig, kap
+        Kb, f_or, _ = m.assemble(du, m.traction_load((20.0, 5.0, -8.0)))
+        sol = m.tfeti(Kb).solve(f_or, rtol=1e-12)
+        assert rel(uf, sol["u"]) <= 1e-9 and rel(lf, sol["lam"]) <= 1e-9
+
+
 @pytest.mark.parametrize("w", [W.SMALL6_RAGGED, W.CUBE12])
 def test_mixed_precision_dual_pcg_reaches_fp64_accuracy(w):
     """FP32 inner F-applies corrected by FP64 residuals reach the oracle's solution at eps = 1e-12."""
@@ -820,6 +867,41 @@ def test_history_start_load_history_cube12(mixed):
         assert rel(runs[8][0][k], model.u) <= 1e-9, k
     assert runs[0][2] == 0 and runs[8][2] > 0
     assert runs[8][1] < runs[0][1], (runs[8][1], runs[0][1])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_history_start_exact_on_unchanged_operator(mixed):
+    """On an unchanged (all-elastic) tangent the stored solutions carry exact products F lambda_j and
+    K^+ B^T lambda_j, so the start built from them takes its residual and primal vector by linear
+    combination: for f_b = 2 f_a after a solve with f_a, in the mixed mode one FP64 subdomain pass
+    (d~) and no PCGP iteration at eps = 1e-11 (the start's residual is twice the first solve's, below 1e-12 of its own
+    d~), u_b = 2 u_a to rounding, and equal to the zero-start solution at eps = 1e-12."""
+    w = W.CUBE12
+    out = {}
+    for q in (4, 0):
+        ctx = T.Context(w)
+        s = ctx.sizes
+        if mixed:
+            ctx.set_precision(True, 1e-3)
+        ctx.set_recycling(q)
+        fa = zeros(s["n_dof"])
+        ctx.traction_load((20.0, 5.0, -8.0), fa)
+        f = zeros(s["n_dof"])
+        ctx.assemble_tangent(zeros(s["n_dof"]), fa, f)
+        ua, ub = zeros(s["n_dof"]), zeros(s["n_dof"])
+        ctx.dual_pcg(f, ua, rtol=1e-12, maxit=5000)
+        ctx.assemble_tangent(zeros(s["n_dof"]), 2.0 * fa, f)   # the same elastic operator again
+        ib = ctx.dual_pcg(f, ub, rtol=1e-11 if q else 1e-12, maxit=5000)
+        out[q] = (host(ua).copy(), host(ub).copy(), ib)
+        ctx.close()
+    ua, ub, ib = out[4]
+    # the mixed mode tests the start before any inner solve; Algorithm 3 (FP64) runs one iteration
+    # (its stopping test follows the updates): d~, F p and the recovery instead of four passes
+    want = (0, 1) if mixed else (1, 3)
+    assert ib["used_lambda0"] == 2 and (ib["iterations"], ib["f_applies"]) == want, ib
+    assert rel(ub, 2.0 * ua) <= 1e-11
+    assert rel(ub, out[0][1]) <= 1e-9
+    assert out[0][2]["f_applies"] >= 2
 
 
 @pytest.mark.parametrize("learned", [False, True])
