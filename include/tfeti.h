@@ -312,10 +312,15 @@ int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
  * 8 -> 64 -> 64 -> 1 with ReLU, FP16 weights, FP32 accumulation.  Where the stored
  * solutions alone do not meet the stopping test, the projected prediction joins them
  * as one more vector of the Galerkin start (its product by one F-apply, FP32 in the
- * mixed mode; the zero start stays the fallback).  After each such solve the network
- * takes `epochs` Adam steps (learning rate lr, FP32 master weights) on 64 x 128 rows
- * of the solve against its lambda_Ker.  Weights start from a fixed seed with a zero
- * last layer (the untrained predictor is la).  enable = 0 turns it off. */
+ * mixed mode; the zero start stays the fallback).  A solve where the network's vector
+ * lowers the predicted residual by less than 10 % counts against it; after two such
+ * solves in a row at a Newton index it is consulted there only every fourth time.
+ * After each solve the stored solutions could not start well the network takes
+ * `epochs` Adam steps (learning rate lr, FP32 master weights) on 64 x 128 rows of the
+ * solve against its lambda_Ker, on a low-priority stream of its own beside the next
+ * Newton iteration (the next prediction waits for it).  Weights start from a fixed
+ * seed with a zero last layer (the untrained predictor is la).  enable = 0 turns it
+ * off. */
 #define TFETI_MLP_PARAMS 4801
 int tfeti_set_learned(tfeti_ctx* ctx, int32_t enable, int32_t epochs, double lr);
 

@@ -1674,7 +1674,15 @@ float* pf_prev_of(tfeti_ctx* c) { return c->pf_prev + (long long)(c->newton_idx 
 // Scalars of the MLP features: 1/s, 1/s_d, rho, s, index feature, with s the RMS of
 // the previous step's lambda_Ker at this Newton iteration and s_d the RMS of d~
 // (||d~|| = r0).  False if s = 0.
+// The context stream waits for the network's last training (no host wait).
+void mlp_join(tfeti_ctx* c) {
+  if (!c->mlp_pending) return;
+  cudaStreamWaitEvent(c->st, c->ev_mlp_done, 0);
+  c->mlp_pending = false;
+}
+
 bool mlp_scalars(tfeti_ctx* c, double r0) {
+  mlp_join(c);
   const long long m = c->M.n_mult;
   const double s = std::sqrt(std::max(0.0, dot_host(c, mlp_la_of(c), mlp_la_of(c), m)) / (double)m);
   const double sd = r0 / std::sqrt((double)m);
@@ -1730,7 +1738,14 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   // the MLP vector joins only where the stored solutions alone miss the stopping test
   // (there the start is refined anyway, so the mixed mode takes its product in FP32)
   c->mlp_missed = pred > tol_abs;
-  if (pred > tol_abs && mlp_ready(c) && mlp_scalars(c, r0)) {
+  // the network's own judge: a solve where its vector lowered the predicted residual by less than
+  // 10 % counts against it, and after two such solves in a row at this Newton index it is consulted
+  // only every fourth time (it keeps training meanwhile)
+  bool consult = true;
+  if (mlp_index_ok(c) && c->mlp_nogain[c->newton_idx - 1] >= 2) consult = (c->mlp_probe++ % 4) == 0;
+  if (pred > tol_abs && mlp_ready(c) && !consult) ++c->mlp_skipped;
+  if (pred > tol_abs && mlp_ready(c) && consult && mlp_scalars(c, r0)) {
+    const double pred0 = pred;
     double* Ln = c->rec_L + (long long)n * m;   // slot n is free: rec_q solutions in rec_q + 1 slots
     double* FLn = c->rec_FL + (long long)n * m;
     launch_mlp_infer(c->M, c->mlp_w16, mlp_la_of(c), mlp_lb_of(c), c->r, c->pf_now, pf_prev_of(c), c->mlp_scal,
@@ -1746,6 +1761,8 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
     nb = n + 1;
     with_mlp = coef2[n] != 0.0;
     c->mlp_slot_valid = true;
+    int& ng = c->mlp_nogain[c->newton_idx - 1];
+    ng = pred > 0.9 * pred0 ? ng + 1 : 0;
   }
   if (nb == 0 || !(pred < c->rec_accept * w0)) return 0;
   ++c->rec_tried;
@@ -1793,19 +1810,30 @@ void mlp_train(tfeti_ctx* c, double r0) {
   if (!mlp_index_ok(c)) return;
   const long long m = c->M.n_mult;
   // training only after solves that the stored solutions alone could not start well
-  if (c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0))) {
+  const bool train =
+      c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0));
+  // the next Newton iteration overwrites d~, lambda_Ker and the plastic fractions on the context stream
+  cudaMemcpyAsync(c->mlp_d, c->dtil, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->mlp_tgt, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->mlp_pf, c->pf_now, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->mlp_scal_t, c->mlp_scal, sizeof(float) * 8, cudaMemcpyDeviceToDevice, c->st);
+  cudaEventRecord(c->ev_mlp_fork, c->st);
+  cudaStreamWaitEvent(c->st_mlp, c->ev_mlp_fork, 0);
+  if (train) {
     for (int e = 0; e < c->mlp_epochs; ++e) {
       ++c->mlp_t;
       const long long start = (104729LL * c->mlp_t + 7919LL * e) % m;
-      launch_mlp_train_step(c->M, c->mlp_w, mlp_la_of(c), mlp_lb_of(c), c->dtil, c->pf_now, pf_prev_of(c),
-                            c->mlp_scal, c->lamk, start, 7919, c->mlp_blocks, c->mlp_partial, c->mlp_w, c->mlp_m1,
-                            c->mlp_m2, c->mlp_w16, c->mlp_lr, c->mlp_t, c->st);
+      launch_mlp_train_step(c->M, c->mlp_w, mlp_la_of(c), mlp_lb_of(c), c->mlp_d, c->mlp_pf, pf_prev_of(c),
+                            c->mlp_scal_t, c->mlp_tgt, start, 7919, c->mlp_blocks, c->mlp_partial, c->mlp_w,
+                            c->mlp_m1, c->mlp_m2, c->mlp_w16, c->mlp_lr, c->mlp_t, c->st_mlp);
       c->launches += 2;
     }
   }
-  cudaMemcpyAsync(mlp_lb_of(c), mlp_la_of(c), sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(mlp_la_of(c), c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(pf_prev_of(c), c->pf_now, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(mlp_lb_of(c), mlp_la_of(c), sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st_mlp);
+  cudaMemcpyAsync(mlp_la_of(c), c->mlp_tgt, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st_mlp);
+  cudaMemcpyAsync(pf_prev_of(c), c->mlp_pf, sizeof(float) * c->M.n_sub, cudaMemcpyDeviceToDevice, c->st_mlp);
+  cudaEventRecord(c->ev_mlp_done, c->st_mlp);
+  c->mlp_pending = true;
   c->mlp_scal_valid = false;
   ++c->mlp_seen[c->newton_idx - 1];
 }
@@ -2606,6 +2634,7 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   if (c->st_fac) cudaStreamSynchronize(c->st_fac);
+  if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
@@ -2620,6 +2649,9 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->ev_fac_done) cudaEventDestroy(c->ev_fac_done);
   if (c->h_err_fac) cudaFreeHost(c->h_err_fac);
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->st_mlp) cudaStreamDestroy(c->st_mlp);
+  if (c->ev_mlp_fork) cudaEventDestroy(c->ev_mlp_fork);
+  if (c->ev_mlp_done) cudaEventDestroy(c->ev_mlp_done);
   if (c->st_cap) cudaStreamDestroy(c->st_cap);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   if (c->owns_stream && c->st) cudaStreamDestroy(c->st);
@@ -3010,10 +3042,21 @@ int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
       c->mlp_dfprev = dalloc<double>(c, (size_t)std::max(1LL, c->M.n_dof));
       c->pf_now = dalloc<float>(c, c->M.n_sub);
       c->pf_prev = dalloc<float>(c, (size_t)kMlpIdx * c->M.n_sub);
+      c->mlp_d = dalloc<double>(c, (size_t)std::max(1LL, m));
+      c->mlp_tgt = dalloc<double>(c, (size_t)std::max(1LL, m));
+      c->mlp_pf = dalloc<float>(c, (size_t)std::max(1, c->M.n_sub));
+      c->mlp_scal_t = dalloc<float>(c, 8);
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      cudaStreamCreateWithPriority(&c->st_mlp, cudaStreamNonBlocking, lo);
+      cudaEventCreateWithFlags(&c->ev_mlp_fork, cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&c->ev_mlp_done, cudaEventDisableTiming);
     } catch (const std::bad_alloc&) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
   }
+  if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);   // no training in flight while the network is reset
+  c->mlp_pending = false;
   if (enable) {
     // seeded initialisation: uniform(-a, a), a = sqrt(6 / (fan_in + fan_out)) for the two
     // hidden layers, zero biases and a zero last layer (the untrained predictor is the
@@ -3043,7 +3086,8 @@ int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
   c->mlp_lr = (float)lr;
   c->mlp_t = 0;
   for (int& v : c->mlp_seen) v = 0;
-  c->mlp_used = 0;
+  c->mlp_used = c->mlp_skipped = c->mlp_probe = 0;
+  for (int& v : c->mlp_nogain) v = 0;
   c->have_dfprev = false;
   return cuda_check(c, "tfeti_set_learned");
 }
@@ -3055,6 +3099,7 @@ int tfeti_mlp_predict(tfeti_ctx* c, const double* la, const double* lb, const do
   const float sc[5] = {scal[0], scal[1], scal[2], scal[3], 0.0f};
   cudaMemcpyAsync(c->mlp_scal, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st);
   sync(c);
+  mlp_join(c);
   launch_mlp_infer(c->M, c->mlp_w16, la, lb, d, pf_now, pf_prev, c->mlp_scal, y, c->st);
   c->launches += 1;
   sync(c);

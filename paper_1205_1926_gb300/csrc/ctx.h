@@ -222,7 +222,16 @@ struct tfeti_ctx {
   double mlp_rho = 1.0;
   float h_scal[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   bool mlp_scal_valid = false;
-  long long mlp_used = 0;
+  // training runs on its own low-priority stream, beside the next Newton iteration: the inputs that
+  // the next solve overwrites (d~, lambda_Ker, the plastic fractions, the scalings) are copied first,
+  // and every later reader of the network's weights or histories waits for ev_mlp_done
+  cudaStream_t st_mlp = nullptr;
+  cudaEvent_t ev_mlp_fork = nullptr, ev_mlp_done = nullptr;
+  bool mlp_pending = false;
+  double *mlp_d = nullptr, *mlp_tgt = nullptr;
+  float *mlp_pf = nullptr, *mlp_scal_t = nullptr;
+  long long mlp_used = 0, mlp_skipped = 0, mlp_probe = 0;
+  int mlp_nogain[tfeti::kMlpIdx] = {0, 0, 0, 0};   // consecutive solves where the network added < 10 %
   // FP32 copies for the inner iterations of the mixed mode (allocated by tfeti_set_precision)
   float *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
