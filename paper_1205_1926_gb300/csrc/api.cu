@@ -347,6 +347,7 @@ int check_factorisation(tfeti_ctx* c) {
 }
 
 void wood_correct_solve(tfeti_ctx* c, const SolveArgs& a, cudaStream_t st);
+void wood_join(tfeti_ctx* c);
 
 void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
   cudaEvent_t e1 = timed_begin(c, 0);
@@ -435,6 +436,7 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract = true) {
       c->launches += 2;
     }
     if (c->wood.n > 0) {   // plastic subdomains on their shape's block: + Z_b C^-1 Z_b^T x_b
+      wood_join(c);
       launch_wood_apply(c->M, c->wood, x, c->cbuf, c->st);
       c->launches += 3;
     }
@@ -662,7 +664,8 @@ void ensure_cap(tfeti_ctx* c, T*& p, long long& cap, long long need) {
 // elastic factor plus the correction (no refactorisation).  If a pivot of some C is not
 // positive (not expected: C is positive definite) no subdomain keeps the correction and the
 // function returns TFETI_OK with c->wood.n == 0 and h_wood cleared.
-int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64) {
+int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64, bool async = false) {
+  wood_join(c);   // an earlier set-up still in flight finishes before its pools are reused
   c->wood.n = 0;
   std::vector<int> list, npts;
   std::vector<long long> pt_off, c_off, z_off, d_off, zt_off;
@@ -768,6 +771,32 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64) {
   w.vbuf = c->wood_v;
   w.tbuf64 = c->wood_t64;
   w.ybuf = c->wood_yb;
+  if (async) {
+    // beside the first residual solve of the Newton iteration (its template items do not need it)
+    if (!c->st_wood) {
+      try {
+        c->d_err_wood = dalloc<int>(c, 1);
+      } catch (const std::bad_alloc&) {
+        return fail(c, TFETI_ERR_OOM, "device allocation failed");
+      }
+      if (cudaMallocHost(&c->h_err_wood, sizeof(int)) != cudaSuccess) return fail(c, TFETI_ERR_OOM, "host allocation failed");
+      cudaStreamCreateWithFlags(&c->st_wood, cudaStreamNonBlocking);
+      cudaEventCreateWithFlags(&c->ev_wood_fork, cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&c->ev_wood_done, cudaEventDisableTiming);
+    }
+    w.err = c->d_err_wood;
+    cudaEventRecord(c->ev_wood_fork, c->st);
+    cudaStreamWaitEvent(c->st_wood, c->ev_wood_fork, 0);
+    cudaMemsetAsync(c->d_err_wood, 0, sizeof(int), c->st_wood);
+    launch_wood_setup(c->M, w, c->st_wood);
+    cudaMemcpyAsync(c->h_err_wood, c->d_err_wood, sizeof(int), cudaMemcpyDeviceToHost, c->st_wood);
+    cudaEventRecord(c->ev_wood_done, c->st_wood);
+    c->launches += wood_setup_launches(w);
+    c->wood_pending = c->wood_check_pending = true;
+    c->wood_subs += w.n;
+    if (fp64) c->wood_fac_saved += w.n;
+    return cuda_check(c, "Woodbury set-up");
+  }
   w.err = c->d_err;
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
   launch_wood_setup(c->M, w, c->st);
@@ -789,9 +818,17 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64) {
 
 // After an FP64 subdomain-solve pass whose items put the Woodbury subdomains on their elastic
 // factor (right-hand side src + sign B^T lam): add Z C^-1 Z^T v to dst and the slots in cbuf.
+// The context stream waits for an asynchronous Woodbury set-up (no host wait).
+void wood_join(tfeti_ctx* c) {
+  if (!c->wood_pending) return;
+  cudaStreamWaitEvent(c->st, c->ev_wood_done, 0);
+  c->wood_pending = false;
+}
+
 void wood_correct64(tfeti_ctx* c, const double* src, const double* lam, double sign, double* cbuf, double* dst,
                     cudaStream_t st) {
   if (c->wood.n <= 0 || !c->wood.fp64) return;
+  wood_join(c);
   c->launches += launch_wood_apply64(c->M, c->wood, src, lam, sign, cbuf, dst, st);
 }
 
@@ -800,6 +837,7 @@ void wood_correct64(tfeti_ctx* c, const double* src, const double* lam, double s
 // the inner apply's Schur block; called before the Schur blocks in use change.
 int wood_materialize(tfeti_ctx* c) {
   if (c->wood.n <= 0 || !c->wood.fp64) return TFETI_OK;
+  wood_join(c);
   const int fst = check_factorisation(c);
   if (fst != TFETI_OK) return fst;
   const DevMesh& M = c->M;
@@ -840,6 +878,27 @@ int wood_materialize(tfeti_ctx* c) {
   c->wood_fac_saved -= (long long)list.size();
   build_items(c, np);
   return cuda_check(c, "Woodbury subdomains refactorised");
+}
+
+// After a synchronisation of the context stream that followed wood_join: the pivots of an
+// asynchronous set-up.  A failed Cholesky (not expected: C is positive definite) drops the correction
+// for this assembly: its subdomains get their own factor records, and *redo = 1 tells the caller to
+// repeat the residual solve it made with the correction.
+int wood_check(tfeti_ctx* c, int* redo) {
+  *redo = 0;
+  if (!c->wood_check_pending) return TFETI_OK;
+  c->wood_check_pending = false;
+  if (!(*c->h_err_wood & 8)) return TFETI_OK;
+  c->wood_fallbacks += 1;
+  if (c->wood.fp64) {
+    const int st = wood_materialize(c);
+    if (st != TFETI_OK) return st;
+  }
+  std::fill(c->h_wood.begin(), c->h_wood.end(), 0);
+  c->wood.n = 0;
+  build_items(c, c->h_np_all);
+  *redo = 1;
+  return cuda_check(c, "Woodbury set-up");
 }
 
 // The same for the outputs of the FP64 solve pass `a` (in_mode 0 or 1; out_mode 0, 1 or 3).
@@ -1015,7 +1074,7 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
       const int sh = c->h_subs[p].shape;
       c->h_wood[p] = np[p] > 0 && np[p] <= kWoodMaxPts && c->kinv_off[sh] >= 0 && c->schur_use[sh];
     }
-    const int wst = wood_setup(c, np, c->wood_mode >= 2 && !c->dirichlet);
+    const int wst = wood_setup(c, np, c->wood_mode >= 2 && !c->dirichlet, defer && !c->dirichlet);
     if (wst != TFETI_OK) return wst;
   }
   std::vector<int> npf = np;   // plastic points of the subdomains that are refactorised
@@ -1867,13 +1926,21 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   c->launches += 3;
   // d~ = d - F lambda_Im = B K^+(f - B^T lambda_Im) ; r^0 = d~
   residual_solve(c, f, c->lam_im, c->r);
-  if (c->rec_q > 0 && c->vsol_im)
-    cudaMemcpyAsync(c->vsol_im, c->vsol, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
-  const double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
+  wood_join(c);   // the inner solves read the set-up's FP32 part
+  double r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
   {
     const int fst = check_factorisation(c);   // pivots of a deferred refactorisation
     if (fst != TFETI_OK) return fst;
+    int redo = 0;
+    const int wst = wood_check(c, &redo);      // pivots of an asynchronous Woodbury set-up
+    if (wst != TFETI_OK) return wst;
+    if (redo) {
+      residual_solve(c, f, c->lam_im, c->r);
+      r0 = std::sqrt(std::max(0.0, dot_host(c, c->r, c->r, m)));
+    }
   }
+  if (c->rec_q > 0 && c->vsol_im)
+    cudaMemcpyAsync(c->vsol_im, c->vsol, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
   cudaMemsetAsync(c->lamk, 0, sizeof(double) * m, c->st);
   bool v_current = true;   // vsol and r belong to lambda = lambda_Im + lambda_Ker
   int used_l0 = 0;
@@ -2635,6 +2702,7 @@ int tfeti_destroy(tfeti_ctx* c) {
   else cudaDeviceSynchronize();
   if (c->st_fac) cudaStreamSynchronize(c->st_fac);
   if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);
+  if (c->st_wood) cudaStreamSynchronize(c->st_wood);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
@@ -2650,6 +2718,10 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->h_err_fac) cudaFreeHost(c->h_err_fac);
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st_mlp) cudaStreamDestroy(c->st_mlp);
+  if (c->st_wood) cudaStreamDestroy(c->st_wood);
+  if (c->ev_wood_fork) cudaEventDestroy(c->ev_wood_fork);
+  if (c->ev_wood_done) cudaEventDestroy(c->ev_wood_done);
+  if (c->h_err_wood) cudaFreeHost(c->h_err_wood);
   if (c->ev_mlp_fork) cudaEventDestroy(c->ev_mlp_fork);
   if (c->ev_mlp_done) cudaEventDestroy(c->ev_mlp_done);
   if (c->st_cap) cudaStreamDestroy(c->st_cap);
@@ -3055,7 +3127,8 @@ int tfeti_set_learned(tfeti_ctx* c, int32_t enable, int32_t epochs, double lr) {
       return fail(c, TFETI_ERR_OOM, "device allocation failed");
     }
   }
-  if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);   // no training in flight while the network is reset
+  if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);
+  if (c->st_wood) cudaStreamSynchronize(c->st_wood);   // no training in flight while the network is reset
   c->mlp_pending = false;
   if (enable) {
     // seeded initialisation: uniform(-a, a), a = sqrt(6 / (fan_in + fan_out)) for the two

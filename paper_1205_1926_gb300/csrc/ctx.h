@@ -110,6 +110,14 @@ struct tfeti_ctx {
             wood_d64_cap = 0, wood_c_cap = 0, wood_d_cap = 0, wood_z_cap = 0, wood_y_cap = 0, wood_x_cap = 0,
             wood_v_cap = 0, wood_yb_cap = 0;
   long long wood_subs = 0, wood_fallbacks = 0, wood_fac_saved = 0;
+  // set-up inside a load step: on st_wood beside the first residual solve; the context stream waits
+  // for ev_wood_done before the first use (wood_pending) and the host reads the pivots' status at its
+  // next synchronisation (wood_check_pending)
+  cudaStream_t st_wood = nullptr;
+  cudaEvent_t ev_wood_fork = nullptr, ev_wood_done = nullptr;
+  int* d_err_wood = nullptr;
+  int* h_err_wood = nullptr;
+  bool wood_pending = false, wood_check_pending = false;
   // fused inner iteration (kernels_inner.cu): one cooperative launch between two F-applies
   bool fused_req = false;                    // tfeti_set_fused_inner
   bool g_inner_fused = false;                // the built graph body uses it

@@ -172,32 +172,24 @@ __global__ void k_gemv32(const float* __restrict__ A, long long n, long long ld,
   extern __shared__ __align__(16) float xs[];
   for (long long j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = j < n ? float(x[j]) : 0.f;
   __syncthreads();
+  // one row per warp (16 per 512-thread block), eight float4 loads of the row in flight per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long r0 = (blockIdx.x * (long long)(blockDim.x >> 5) + warp) * 2;
+  const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + warp;
+  if (row >= n) return;
   const long long n4 = ld >> 2;
   const float4* x4 = reinterpret_cast<const float4*>(xs);
-  float s[2] = {0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const long long row = r0 + k;
-    if (row >= n) break;
-    const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
-    float acc = 0.f;
-#pragma unroll 4
-    for (long long j = lane; j < n4; j += 32) {
-      const float4 a = __ldg(a4 + j), v = x4[j];
-      acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    s[k] = acc;
+  const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
+  float acc = 0.f;
+#pragma unroll 8
+  for (long long j = lane; j < n4; j += 32) {
+    const float4 a = __ldg(a4 + j), v = x4[j];
+    acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
   }
-  if (lane == 0)
-    for (int k = 0; k < 2; ++k) {
-      const long long row = r0 + k;
-      if (row >= n) break;
-      y[row] = double(s[k]);
-      h8[(row / 6) * 8 + row % 6] = s[k];
-    }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    y[row] = double(acc);
+    h8[(row / 6) * 8 + row % 6] = acc;
+  }
 }
 
 // Entry values of G: e' runs over the row-ordered entries, e = gt_e[e'] is the same
@@ -1159,7 +1151,7 @@ void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cu
     static const int lim = dyn_smem_limit((const void*)k_gemv32);
     cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     const long long ld = h32_ld(C.l);
-    k_gemv32<<<blocks_for(C.l, 16), 256, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
+    k_gemv32<<<blocks_for(C.l, 16), 512, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
   } else {
     plane_apply<float>(C.W32, C.V32, C.U32, C.n_pl, C.n_planes, x, 1.0, y, y8, st);
   }
