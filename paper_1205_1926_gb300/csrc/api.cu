@@ -1141,8 +1141,8 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
       c->fac_pending = c->fac_check_pending = true;
       launch_kbb_fill(M, c->d_klist, c->d_list_kbb, (int)klist.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
                       c->kbb32, 0, c->st);
-      launch_internal_force(M, c->dsig, df, c->f_full, c->st);
-      c->launches += 2;
+      launch_internal_force(M, c->dsig, df, c->fe, c->f_full, c->st);
+      c->launches += 2 + (klist.empty() ? 0 : 1);
       if (f_out && f_out != c->f_full)
         cudaMemcpyAsync(f_out, c->f_full, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
       return cuda_check(c, "assemble");
@@ -1191,10 +1191,12 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
       if (derr) return fail(c, TFETI_ERR_NUMERIC, "non-positive pivot in a Dirichlet-preconditioner factorisation");
     }
   }
-  if (!klist.empty())
+  if (!klist.empty()) {
     launch_kbb_fill(M, c->d_klist, c->d_list_kbb, (int)klist.size(), c->max_bnd, c->elem_np, c->dKe, c->kbb,
                     c->kbb32, 0, c->st);
-  launch_internal_force(M, c->dsig, df, c->f_full, c->st);
+    c->launches += 1;
+  }
+  launch_internal_force(M, c->dsig, df, c->fe, c->f_full, c->st);
   c->launches += 2;
   if (f_out && f_out != c->f_full)
     cudaMemcpyAsync(f_out, c->f_full, sizeof(double) * M.n_dof, cudaMemcpyDeviceToDevice, c->st);
@@ -2219,6 +2221,10 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   M.sigma_y = pr.sigma_y;
   M.H = pr.hardening;
   M.wdet = P.h[0] * P.h[1] * P.h[2] / 8.0;
+  for (int d = 0; d < 3; ++d) {
+    M.ga[d] = 0.5 * (1.0 + 1.0 / std::sqrt(3.0)) / P.h[d];
+    M.gb[d] = 0.5 * (1.0 - 1.0 / std::sqrt(3.0)) / P.h[d];
+  }
   M.n_dof = P.n_dof;
   M.n_gp = P.n_gp;
   M.n_mult = P.n_mult;
@@ -2294,6 +2300,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->du = dalloc<double>(c, P.n_dof);
   c->df = dalloc<double>(c, P.n_dof);
   c->dsig = dalloc<double>(c, 6 * P.n_gp);
+  c->fe = dalloc<double>(c, 3 * P.n_gp);
   c->dkap = dalloc<double>(c, P.n_gp);
   c->pa = dalloc<double>(c, P.n_gp);
   c->pb = dalloc<double>(c, P.n_gp);

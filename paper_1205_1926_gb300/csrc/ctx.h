@@ -29,6 +29,7 @@ struct tfeti_ctx {
   double *u = nullptr, *sig = nullptr, *kap = nullptr;
   // Newton iterate
   double *du = nullptr, *df = nullptr, *dsig = nullptr, *dkap = nullptr, *pa = nullptr, *pb = nullptr, *pn = nullptr;
+  double* fe = nullptr;   // [n_elem][8][3] element parts of the internal force
   uint8_t* plastic = nullptr;
   int *elem_np = nullptr, *sub_np = nullptr;
   double* dKe = nullptr;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 namespace tfeti {
@@ -40,6 +41,8 @@ struct GroupDev {
   int slot[8];
   int sub[8];
 };
+// kernels read the header (row0, k, nrows, dirichlet) of a group as one 16-byte load
+static_assert(sizeof(GroupDev) % 16 == 0 && offsetof(GroupDev, dirichlet) == 12, "GroupDev header layout");
 
 // Everything a kernel needs to know about the mesh and the decomposition.
 struct DevMesh {
@@ -81,6 +84,10 @@ struct DevMesh {
   const float* GTv32;
   long long n_gpairs;
   double wdet;
+  // trilinear gradient weights on the uniform bricks: ga[d] = (1 + 1/sqrt 3) / (2 h_d) and
+  // gb[d] = (1 - 1/sqrt 3) / (2 h_d), the nodal weights of a Gauss point on the same and on the
+  // other side of the element along direction d, divided by h_d
+  double ga[3], gb[3];
   double lam, mu, sigma_y, H;
   long long n_dof, n_gp, n_mult, n_copy, n_elem;
   long long n_groups;
@@ -100,6 +107,10 @@ void launch_tables(const double* h, double lam, double mu, double* dN, double* K
 void launch_rigid_for_shape(const SubDev& S, const double* h, double* R_shape, cudaStream_t st);
 void launch_traction(const DevMesh& M, int face, const int* nel, const double* t, const double* h, double* f,
                      cudaStream_t st);
+// Internal force f = df - F(dsig) of eq. (F_def): element contributions into fe
+// ([element][8 nodes, bit order x + 2y + 4z][3]), then gathered per dof in a fixed order.
+void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* fe, double* f,
+                           cudaStream_t st);
 void launch_return_map(const DevMesh& M, const double* du, const double* sig_k, const double* kap_k,
                        double* dsig, double* dkap, uint8_t* plastic, double* Dtan, double* pa, double* pb,
                        double* pn, cudaStream_t st);
@@ -114,7 +125,6 @@ void launch_band_fill(const DevMesh& M, const int* sub_list, int n_list, const i
 void launch_kbb_fill(const DevMesh& M, const int* sub_list, const long long* dst_off, int n_list, int max_bnd,
                      const int* elem_np, const double* dKe, double* kbb, float* kbb32, int elastic_only,
                      cudaStream_t st);
-void launch_internal_force(const DevMesh& M, const double* dsig, const double* df, double* f, cudaStream_t st);
 void launch_apply_K(const DevMesh& M, const int* elem_np, const double* dKe, const double* x, double* y,
                     cudaStream_t st);
 void launch_commit(const DevMesh& M, const double* du, const double* dsig, const double* dkap, double* u,

@@ -18,6 +18,49 @@ __device__ __forceinline__ double bt_at_slot(const DevMesh& M, const double* __r
   return s;
 }
 
+// (B^T x) at U copy slots at once (slot < 0 gives 0), each value summed as bt_at_slot sums it.
+// The loads run stage by stage over the U slots (their groups, the groups' headers, then each
+// value's first Helmert term), so that the U chains of dependent loads overlap; the further
+// terms (copies shared by more than two subdomains) follow in a loop.
+template <int U>
+__device__ __forceinline__ void bt_at_slots(const DevMesh& M, const double* __restrict__ x, const long long* slot,
+                                            double* out) {
+  int g[U], j[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    g[k] = slot[k] >= 0 ? __ldg(M.slot_group + slot[k]) : -1;
+    j[k] = slot[k] >= 0 ? __ldg(M.slot_j + slot[k]) : 0;
+  }
+  int4 hd[U];   // GroupDev header: row0, k, nrows, dirichlet
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    hd[k] = g[k] >= 0 ? __ldg(reinterpret_cast<const int4*>(M.groups + g[k])) : make_int4(0, 0, 0, 0);
+  double xv[U], hv[U];
+  int r0[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    r0[k] = hd[k].w ? j[k] : (j[k] > 1 ? j[k] : 1);
+    const bool any = hd[k].z != 0 && (hd[k].w || r0[k] < hd[k].y);
+    xv[k] = any ? x[hd[k].x + r0[k] - (hd[k].w ? 0 : 1)] : 0.0;
+    hv[k] = any && !hd[k].w ? __ldg(M.helm + r0[k] * 8 + j[k]) : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    if (hd[k].z == 0) {
+      out[k] = 0.0;
+    } else if (hd[k].w) {
+      out[k] = xv[k];
+    } else {
+      double s = 0.0;
+      if (r0[k] < hd[k].y) {
+        s += hv[k] * xv[k];
+        for (int r = r0[k] + 1; r < hd[k].y; ++r) s += M.helm[r * 8 + j[k]] * x[hd[k].x + r - 1];
+      }
+      out[k] = s;
+    }
+  }
+}
+
 // (B v)[row] for copy-slot values v.
 __device__ __forceinline__ double b_at_row(const DevMesh& M, const double* __restrict__ v, long long row) {
   const GroupDev& g = M.groups[M.row_group[row]];

@@ -93,19 +93,36 @@ __device__ __forceinline__ void g_entry<float>(const float* __restrict__ Gv, lon
   g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w; g[4] = b.x; g[5] = b.y;
 }
 
+// entries per thread with their loads in flight together (FP32 / FP64 values)
 template <typename T>
-__global__ void k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x, double* gx,
+constexpr int g_batch() { return sizeof(T) == 4 ? 4 : 2; }
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x, double* gx,
                         double scale) {
   __shared__ double red[6 * 32];
   const int p = blockIdx.x;
   const long long e0 = M.gp_ptr[p], e1 = M.gp_ptr[p + 1];
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const T v = T(x[M.gp_row[e]]);
-    T g[6];
-    g_entry<T>(Gv, e, g);
+  // a thread's entries e0 + tid + k blockDim in k order, g_batch<T>() of them with all their
+  // loads in flight together (the row index, then x at the row, is a chain of two dependent loads)
+  constexpr int kGU = g_batch<T>();
+  const long long bd = blockDim.x;
+  for (long long eb = e0 + threadIdx.x; eb < e1; eb += kGU * bd) {
+    int row[kGU];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] += g[c] * v;
+    for (int k = 0; k < kGU; ++k) row[k] = eb + k * bd < e1 ? __ldg(M.gp_row + eb + k * bd) : -1;
+    T g[kGU][6];
+#pragma unroll
+    for (int k = 0; k < kGU; ++k)
+      if (row[k] >= 0) g_entry<T>(Gv, eb + k * bd, g[k]);
+    T v[kGU];
+#pragma unroll
+    for (int k = 0; k < kGU; ++k) v[k] = row[k] >= 0 ? T(__ldg(x + row[k])) : T(0);
+#pragma unroll
+    for (int k = 0; k < kGU; ++k)
+      if (row[k] >= 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += g[k][c] * v[k];
   }
   double s[6];
 #pragma unroll
@@ -165,30 +182,38 @@ __global__ void k_GT_csr32(DevMesh M, const float* __restrict__ GTv8, const doub
 }
 
 // y = H x with the FP32 copy of H (n x n, rows padded with zeros to ld, a multiple of 4),
-// x rounded to FP32 in shared memory; two rows per warp, float4 loads; writes y (FP64)
-// and its padded FP32 copy h8.
-__global__ void k_gemv32(const float* __restrict__ A, long long n, long long ld, const double* __restrict__ x,
-                         double* y, float* h8) {
+// x rounded to FP32 in shared memory; writes y (FP64) and its padded FP32 copy h8.  Two warps
+// per row (kGemvRows rows per 512-thread block), each taking every other 32-float4 segment of
+// the row, so that a lane has about a dozen float4 loads in flight at 64^3; the two halves are
+// added in warp order.
+constexpr int kGemvRows = 8;
+__global__ void __launch_bounds__(512, 3) k_gemv32(const float* __restrict__ A, long long n, long long ld,
+                                                   const double* __restrict__ x, double* y, float* h8) {
   extern __shared__ __align__(16) float xs[];
+  __shared__ float half[16];
   for (long long j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = j < n ? float(x[j]) : 0.f;
   __syncthreads();
-  // one row per warp (16 per 512-thread block), eight float4 loads of the row in flight per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + warp;
-  if (row >= n) return;
-  const long long n4 = ld >> 2;
-  const float4* x4 = reinterpret_cast<const float4*>(xs);
-  const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
+  const long long row = blockIdx.x * (long long)kGemvRows + (warp >> 1);
+  const int hf = warp & 1;
   float acc = 0.f;
-#pragma unroll 8
-  for (long long j = lane; j < n4; j += 32) {
-    const float4 a = __ldg(a4 + j), v = x4[j];
-    acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
+  if (row < n) {
+    const long long n4 = ld >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(xs);
+    const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
+#pragma unroll 6
+    for (long long j = 32 * hf + lane; j < n4; j += 64) {
+      const float4 a = __ldg(a4 + j), v = x4[j];
+      acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) {
-    y[row] = double(acc);
-    h8[(row / 6) * 8 + row % 6] = acc;
+  if (lane == 0) half[warp] = acc;
+  __syncthreads();
+  if (hf == 0 && lane == 0 && row < n) {
+    const float t = half[warp] + half[warp + 1];
+    y[row] = double(t);
+    h8[(row / 6) * 8 + row % 6] = t;
   }
 }
 
@@ -247,39 +272,58 @@ __global__ void k_gemv(const T* __restrict__ A, long long n, const double* __res
 // K_bb comes from the subdomain's boundary blocks (kbb + kbb_off[p]): its shape's
 // elastic template or its own blocks when it has plastic points.
 // T: FP64 blocks, or their FP32 copy for the inner iterations of the mixed mode.
+constexpr int kXU = 4;       // copy slots per thread with their B^T gathers in flight together
+// stencil neighbours per batch of block loads in the lumped apply (FP32 / FP64 blocks)
 template <typename T>
-__global__ void k_lumped(DevMesh M, const double* __restrict__ w, const T* __restrict__ kbb,
-                         const long long* __restrict__ kbb_off, double* cbuf) {
+constexpr int nb_batch() { return sizeof(T) == 4 ? 9 : 3; }
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_lumped(DevMesh M, const double* __restrict__ w, const T* __restrict__ kbb,
+                                                   const long long* __restrict__ kbb_off, double* cbuf) {
   extern __shared__ __align__(16) unsigned char xs_raw[];
   T* xs = reinterpret_cast<T*>(xs_raw);
   const int p = blockIdx.x;
   const SubDev S = M.subs[p];
-  for (int s = threadIdx.x; s < S.n_copy; s += blockDim.x) xs[s] = T(bt_at_slot(M, w, S.copy_off + s));
+  for (int s0 = threadIdx.x; s0 < S.n_copy; s0 += kXU * blockDim.x) {
+    long long sl[kXU];
+    double v[kXU];
+#pragma unroll
+    for (int k = 0; k < kXU; ++k) sl[k] = s0 + k * (int)blockDim.x < S.n_copy ? S.copy_off + s0 + k * blockDim.x : -1;
+    bt_at_slots<kXU>(M, w, sl, v);
+#pragma unroll
+    for (int k = 0; k < kXU; ++k)
+      if (sl[k] >= 0) xs[s0 + k * blockDim.x] = T(v[k]);
+  }
   __syncthreads();
-  // blocks stored [t][cc][3 b + a] (neighbour t, column cc, row 3 b + a of boundary node b)
+  // blocks stored [t][cc][3 b + a] (neighbour t, column cc, row 3 b + a of boundary node b), all 27
+  // neighbours present in the storage (zero where the stencil has none); the neighbours are
+  // visited in order, nb_batch<T>() of them with their slot and block loads issued together
   const T* kb = kbb + kbb_off[p];
   const long long nr = 3LL * S.n_bnd;
   for (int q = threadIdx.x; q < S.n_copy; q += blockDim.x) {
     const long long slot = S.copy_off + q;
     const int b = M.slot_bnd[slot], a = q % 3;
     const T* kv = kb + 3LL * b + a;
-    const int4* nb4 = reinterpret_cast<const int4*>(M.sub_nbr + (slot / 3) * 28);
-    int nb[28];
-#pragma unroll
-    for (int u = 0; u < 7; ++u) {
-      const int4 v = __ldg(nb4 + u);
-      nb[4 * u] = v.x;
-      nb[4 * u + 1] = v.y;
-      nb[4 * u + 2] = v.z;
-      nb[4 * u + 3] = v.w;
-    }
+    const int* nbp = M.sub_nbr + (slot / 3) * 28;
     T s = T(0);
+    constexpr int NB = nb_batch<T>();
 #pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      if (nb[t] >= 0) {
-        const int lb = (int)(nb[t] - S.copy_off);
-        s += kv[(3 * t) * nr] * xs[lb] + kv[(3 * t + 1) * nr] * xs[lb + 1] + kv[(3 * t + 2) * nr] * xs[lb + 2];
+    for (int t0 = 0; t0 < 27; t0 += NB) {
+      int nb[NB];
+      T k0[NB], k1[NB], k2[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int t = t0 + u;
+        nb[u] = __ldg(nbp + t);
+        k0[u] = __ldg(kv + (3 * t) * nr);
+        k1[u] = __ldg(kv + (3 * t + 1) * nr);
+        k2[u] = __ldg(kv + (3 * t + 2) * nr);
       }
+#pragma unroll
+      for (int u = 0; u < NB; ++u)
+        if (nb[u] >= 0) {
+          const int lb = (int)(nb[u] - S.copy_off);
+          s += k0[u] * xs[lb] + k1[u] * xs[lb + 1] + k2[u] * xs[lb + 2];
+        }
     }
     cbuf[slot] = double(s);
   }
@@ -451,41 +495,78 @@ __device__ bool grid_sum_last(double s, double* partial, int* ctr, double* red, 
 // dot: mode 0 -> sc[kWW] = out.out (w = P r); mode 1 -> sc[kYW] = out.v (y = P z, v = w),
 // then the stop test of the iteration (pcg_pre), and with deflation (k = sc[kDeflK] > 0)
 // also d_j = out.AW_j and mu = E^-1 d -> sc[kMu0 + i].  The partial sums of value j sit at
-// partial[j * gridDim.x + block].
-__global__ void k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x,
-                           const float* __restrict__ h8, double* out, const double* __restrict__ v, int mode,
-                           double* sc, double* partial, int* ctr, const double* __restrict__ AW,
-                           const double* __restrict__ Einv) {
+// partial[j * gridDim.x + block].  kDefl: the instance that carries the deflation sums (AW given).
+template <bool kDefl>
+__global__ void __launch_bounds__(256, 4)
+    k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const double* __restrict__ x, const float* __restrict__ h8,
+               double* out, const double* __restrict__ v, int mode, double* sc, double* partial, int* ctr,
+               const double* __restrict__ AW, const double* __restrict__ Einv) {
   __shared__ double red[32];
   __shared__ int is_last;
   const float4* g4 = reinterpret_cast<const float4*>(GTv8);
   const float4* h4 = reinterpret_cast<const float4*>(h8);
-  const int kd = (mode == 1 && AW) ? (int)sc[kDeflK] : 0;
+  const int kd = (kDefl && mode == 1 && AW) ? (int)sc[kDeflK] : 0;
   const long long m = M.n_mult;
-  double acc = 0.0, accd[kDeflMax];
+  constexpr int KD = kDefl ? kDeflMax : 1;
+  double acc = 0.0, accd[KD];
 #pragma unroll
-  for (int j = 0; j < kDeflMax; ++j) accd[j] = 0.0;
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < m;
-       row += (long long)gridDim.x * blockDim.x) {
-    const long long e0 = M.gt_ptr[row], e1 = M.gt_ptr[row + 1];
-    double s = 0.0;
-    for (long long e = e0; e < e1; ++e) {
-      const int q = __ldg(M.gt_p + e);
-      const float4 a = __ldg(g4 + 2 * e), b = __ldg(g4 + 2 * e + 1);
-      const float4 u = __ldg(h4 + 2 * q), w = __ldg(h4 + 2 * q + 1);
-      const float t = a.x * u.x + a.y * u.y + a.z * u.z + a.w * u.w + b.x * w.x + b.y * w.y;
-      s += double(t);
+  for (int j = 0; j < KD; ++j) accd[j] = 0.0;
+  // a thread's rows row0 + i stride in i order, two at a time with their loads interleaved
+  // (row range, then the entries' subdomains, then h at those: three dependent loads)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long row0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; row0 < m; row0 += 2 * stride) {
+    const long long row1 = row0 + stride;
+    const bool has1 = row1 < m;
+    const long long e0 = M.gt_ptr[row0], e1 = M.gt_ptr[row0 + 1];
+    const long long f0 = has1 ? M.gt_ptr[row1] : 0, f1 = has1 ? M.gt_ptr[row1 + 1] : 0;
+    const double x0 = x[row0], x1 = has1 ? x[row1] : 0.0;
+    const double v0 = mode == 0 ? 0.0 : v[row0], v1 = (mode == 0 || !has1) ? 0.0 : v[row1];
+    double s0 = 0.0, s1 = 0.0;
+    for (long long k = 0; e0 + k < e1 || f0 + k < f1; ++k) {
+      const bool a0 = e0 + k < e1, a1 = f0 + k < f1;
+      int q0 = 0, q1 = 0;
+      float4 ga0, gb0, ga1, gb1;
+      if (a0) {
+        q0 = __ldg(M.gt_p + e0 + k);
+        ga0 = __ldg(g4 + 2 * (e0 + k));
+        gb0 = __ldg(g4 + 2 * (e0 + k) + 1);
+      }
+      if (a1) {
+        q1 = __ldg(M.gt_p + f0 + k);
+        ga1 = __ldg(g4 + 2 * (f0 + k));
+        gb1 = __ldg(g4 + 2 * (f0 + k) + 1);
+      }
+      if (a0) {
+        const float4 u = __ldg(h4 + 2 * q0), w = __ldg(h4 + 2 * q0 + 1);
+        s0 += double(ga0.x * u.x + ga0.y * u.y + ga0.z * u.z + ga0.w * u.w + gb0.x * w.x + gb0.y * w.y);
+      }
+      if (a1) {
+        const float4 u = __ldg(h4 + 2 * q1), w = __ldg(h4 + 2 * q1 + 1);
+        s1 += double(ga1.x * u.x + ga1.y * u.y + ga1.z * u.z + ga1.w * u.w + gb1.x * w.x + gb1.y * w.y);
+      }
     }
-    const double o = x[row] - s;
-    out[row] = o;
-    acc += o * (mode == 0 ? o : v[row]);
+    const double o0 = x0 - s0;
+    out[row0] = o0;
+    acc += o0 * (mode == 0 ? o0 : v0);
+    if constexpr (kDefl) {
 #pragma unroll
-    for (int j = 0; j < kDeflMax; ++j)
-      if (j < kd) accd[j] += o * AW[(long long)j * m + row];
+      for (int j = 0; j < KD; ++j)
+        if (j < kd) accd[j] += o0 * AW[(long long)j * m + row0];
+    }
+    if (has1) {
+      const double o1 = x1 - s1;
+      out[row1] = o1;
+      acc += o1 * (mode == 0 ? o1 : v1);
+      if constexpr (kDefl) {
+#pragma unroll
+        for (int j = 0; j < KD; ++j)
+          if (j < kd) accd[j] += o1 * AW[(long long)j * m + row1];
+      }
+    }
   }
   acc = block_reduce_sum(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-  for (int j = 0; j < kd; ++j) {
+  for (int j = 0; j < kd && j < KD; ++j) {
     const double t = block_reduce_sum(accd[j], red);
     if (threadIdx.x == 0) partial[(long long)(1 + j) * gridDim.x + blockIdx.x] = t;
   }
@@ -496,8 +577,8 @@ __global__ void k_GT32_dot(DevMesh M, const float* __restrict__ GTv8, const doub
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  double tot[1 + kDeflMax];
-  for (int j = 0; j <= kd; ++j) {
+  double tot[1 + KD];
+  for (int j = 0; j <= kd && j <= KD; ++j) {
     double t = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + (long long)j * gridDim.x + i);
     tot[j] = block_reduce_sum(t, red);
@@ -523,11 +604,20 @@ __global__ void k_contract_dot(DevMesh M, const double* __restrict__ cbuf, doubl
                                double* sc, double* partial, int* ctr) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < M.n_mult;
-       row += (long long)gridDim.x * blockDim.x) {
-    const double y = b_at_row(M, cbuf, row);
-    Fp[row] = y;
-    acc += p[row] * y;
+  // a thread's rows in order, two at a time (their gathers from cbuf overlap)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long row0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; row0 < M.n_mult; row0 += 2 * stride) {
+    const long long row1 = row0 + stride;
+    const bool has1 = row1 < M.n_mult;
+    const double p0 = p[row0], p1 = has1 ? p[row1] : 0.0;
+    const double y0 = b_at_row(M, cbuf, row0);
+    const double y1 = has1 ? b_at_row(M, cbuf, row1) : 0.0;
+    Fp[row0] = y0;
+    acc += p0 * y0;
+    if (has1) {
+      Fp[row1] = y1;
+      acc += p1 * y1;
+    }
   }
   acc = block_reduce_sum(acc, red);
   double tot = 0.0;
@@ -546,9 +636,19 @@ __global__ void k_lam_r_update_post(long long n, const double* __restrict__ p, c
   const bool done = sc[kDone] != 0.0;
   if (!done) {
     const double gamma = sc[kYW] / sc[kPFP];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      lam[i] += gamma * p[i];
-      r[i] -= gamma * Fp[i];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+      const long long i1 = i + stride;
+      const bool has1 = i1 < n;
+      const double l0 = lam[i], p0 = p[i], r0 = r[i], f0 = Fp[i];
+      const double l1 = has1 ? lam[i1] : 0.0, p1 = has1 ? p[i1] : 0.0, r1 = has1 ? r[i1] : 0.0,
+                   f1 = has1 ? Fp[i1] : 0.0;
+      lam[i] = l0 + gamma * p0;
+      r[i] = r0 - gamma * f0;
+      if (has1) {
+        lam[i1] = l1 + gamma * p1;
+        r[i1] = r1 - gamma * f1;
+      }
     }
   }
   __syncthreads();
@@ -995,7 +1095,8 @@ void launch_dot2(const double* x1, const double* y1, const double* x2, const dou
 
 void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
                      double* sc, double* partial, int* ctr, cudaStream_t st, const double* AW, const double* Einv) {
-  k_GT32_dot<<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr, AW, Einv);
+  if (AW) k_GT32_dot<true><<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr, AW, Einv);
+  else k_GT32_dot<false><<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr, AW, Einv);
 }
 
 void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
@@ -1151,7 +1252,7 @@ void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cu
     static const int lim = dyn_smem_limit((const void*)k_gemv32);
     cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     const long long ld = h32_ld(C.l);
-    k_gemv32<<<blocks_for(C.l, 16), 512, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
+    k_gemv32<<<blocks_for(C.l, kGemvRows), 512, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
   } else {
     plane_apply<float>(C.W32, C.V32, C.U32, C.n_pl, C.n_planes, x, 1.0, y, y8, st);
   }
