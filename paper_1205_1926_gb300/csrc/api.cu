@@ -431,9 +431,8 @@ void op_F32(tfeti_ctx* c, const double* x, double* yv, bool contract = true) {
       const void* s_hi = bf ? static_cast<const void*>(static_cast<const unsigned char*>(c->Sbf) + 2 * c->s_tile_off[sh])
                             : static_cast<const void*>(c->Shi + c->s_tile_off[sh]);
       launch_schur_gemm_scatter(c->M, c->d_el + c->el_off[sh], cnt, n_bd, bf, schur_splits(cnt, n_bd, c->n_sm),
-                                c->Xhi, c->Xlo, s_hi, c->Slo + c->s_tile_off[sh], c->s_part, c->s_count, c->cbuf,
-                                c->d_err, c->st);
-      c->launches += 2;
+                                c->Xhi, c->Xlo, s_hi, c->Slo + c->s_tile_off[sh], c->s_part, c->cbuf, c->d_err, c->st);
+      c->launches += 3;
     }
     if (c->wood.n > 0) {   // plastic subdomains on their shape's block: + Z_b C^-1 Z_b^T x_b
       wood_join(c);
@@ -484,7 +483,7 @@ int form_schur_blocks(tfeti_ctx* c) {
 }
 
 // Per-context work space of the tensor-core Schur apply: the gathered operand tiles and the
-// split-K partial tiles and counters (each context's own: case contexts run concurrently).
+// output tiles of the K splits (each context's own: case contexts run concurrently).
 void alloc_schur_work(tfeti_ctx* c, int max_bd) {
   const int ns = (int)c->h_subs.size();
   const long long x_tiles = schur_x_tile_elems(ns, max_bd);
@@ -492,9 +491,6 @@ void alloc_schur_work(tfeti_ctx* c, int max_bd) {
   c->Xlo = dalloc<float>(c, (size_t)std::max(1LL, x_tiles));
   c->X64 = dalloc<double>(c, (size_t)ns * (size_t)std::max(1, max_bd));
   c->s_part = dalloc<float>(c, (size_t)std::max(1LL, schur_part_floats(ns, max_bd, 2)));
-  const int tiles = std::max(1, schur_tiles(ns, max_bd));
-  c->s_count = dalloc<int>(c, (size_t)tiles);
-  cudaMemsetAsync(c->s_count, 0, sizeof(int) * tiles, c->st);
 }
 
 // The shapes' dual Schur blocks in FP32 (tensor-core tiles) and FP64, formed once.
@@ -1009,7 +1005,7 @@ void op_precond32(tfeti_ctx* c, const double* x, double* out) {
   if (c->dirichlet) {
     op_precond_dirichlet(c, x, out, true);
   } else if (c->plan.prob.precond == TFETI_PRECOND_LUMPED) {
-    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off, c->cbuf, c->st, c->max_copy);
+    launch_lumped32(c->M, x, c->kbb32, c->d_kbb_off32, c->cbuf, c->st, c->max_copy);
     launch_contract(c->M, c->cbuf, out, c->st);
     c->launches += 2;
   } else {
@@ -1103,6 +1099,15 @@ int assemble(tfeti_ctx* c, const double* du, const double* df, double* f_out, bo
     }
   }
   cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
+  // The inner FP32 iterations precondition the subdomains on the Woodbury path with their shape's
+  // elastic K_bb: their few plastic points change K_bb only by the terms of U U^T at the box
+  // boundary, and an inner preconditioner need only be symmetric positive definite (the FP64
+  // residual and stopping test, and the FP64 preconditioner, keep the tangent's K_bb).  The
+  // template stays in L2 where the own blocks (about 1 MB each for an 8^3 box) would stream from
+  // HBM at every inner iteration.
+  for (int p = 0; p < M.n_sub; ++p)
+    c->h_kbb_off32[p] = (c->wood.n > 0 && c->h_wood[p]) ? c->plan.shapes[c->h_subs[p].shape].kbb_off : c->h_kbb_off[p];
+  cudaMemcpyAsync(c->d_kbb_off32, c->h_kbb_off32.data(), sizeof(long long) * M.n_sub, cudaMemcpyHostToDevice, c->st);
   if (!klist.empty()) {
     cudaMemcpyAsync(c->d_klist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_list_kbb, kbbs.data(), sizeof(long long) * kbbs.size(), cudaMemcpyHostToDevice, c->st);
@@ -1291,7 +1296,7 @@ void destroy_inner_graph(tfeti_ctx* c) {
 // order; a block's rows are split only when there are fewer such groups than SMs.
 int build_lump_tasks(tfeti_ctx* c) {
   std::map<long long, std::vector<int>> by;
-  for (size_t p = 0; p < c->h_subs.size(); ++p) by[c->h_kbb_off[p]].push_back((int)p);
+  for (size_t p = 0; p < c->h_subs.size(); ++p) by[c->h_kbb_off32[p]].push_back((int)p);
   long long n_grp = 0;
   for (const auto& kv : by) n_grp += ((long long)kv.second.size() + kLumpR - 1) / kLumpR;
   const int split = (int)std::max(1LL, std::min(8LL, c->n_sm / std::max(1LL, n_grp)));
@@ -2358,6 +2363,8 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
     cudaMemcpyAsync(c->kbb, base->kbb, sizeof(double) * P.kbb_template_total, cudaMemcpyDeviceToDevice, c->st);
   c->d_kbb_off = dalloc<long long>(c, ns);
   c->h_kbb_off.assign(ns, 0);
+  c->d_kbb_off32 = dalloc<long long>(c, ns);
+  c->h_kbb_off32.assign(ns, 0);
   c->d_list_kbb = dalloc<long long>(c, ns);
   c->d_klist = dalloc<int>(c, ns);
   for (const ShapeInfo& sh : P.shapes) c->max_bnd = std::max(c->max_bnd, sh.n_bnd);
@@ -2549,8 +2556,9 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
     } else {
       build_items(c, std::vector<int>(ns, 0));
     }
-    for (int p = 0; p < ns; ++p) c->h_kbb_off[p] = P.shapes[c->h_subs[p].shape].kbb_off;
+    for (int p = 0; p < ns; ++p) c->h_kbb_off[p] = c->h_kbb_off32[p] = P.shapes[c->h_subs[p].shape].kbb_off;
     cudaMemcpyAsync(c->d_kbb_off, c->h_kbb_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->d_kbb_off32, c->h_kbb_off32.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, c->st);
   }
   c->launches += 4;
   cudaEventCreate(&c->fac_e0);

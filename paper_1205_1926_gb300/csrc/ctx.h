@@ -130,8 +130,7 @@ struct tfeti_ctx {
   unsigned* d_bar = nullptr;
   int inner_grid_n = -1;                     // CTAs of the fused launch (0: not possible, -1: not asked)
   size_t inner_smem_b = 0;
-  float* s_part = nullptr;                   // split-K partial tiles of the Schur apply
-  int* s_count = nullptr;                    // split-K arrival counters (zero between launches)
+  float* s_part = nullptr;                   // output tiles of the Schur apply, one set per K split
   std::vector<long long> s_tile_off;
   bool schur_ready = false;
   int* d_el = nullptr;                       // elastic subdomains grouped by shape
@@ -172,6 +171,8 @@ struct tfeti_ctx {
   long long own_kbb_base = 0;
   long long* d_kbb_off = nullptr;      // per subdomain: template or own offset
   std::vector<long long> h_kbb_off;
+  long long* d_kbb_off32 = nullptr;    // the same for the inner FP32 lumped preconditioner: the template
+  std::vector<long long> h_kbb_off32;  //   for subdomains on the Woodbury path
   long long* d_list_kbb = nullptr;
   int* d_klist = nullptr;                    // plastic subdomains of the last assembly (K_bb refresh)
   int max_bnd = 0;

@@ -187,11 +187,10 @@ void launch_schur_dgemm_scatter(const DevMesh& M, const int* sub_list, int n_lis
 // cores: X[k][i] = (B^T lam) at boundary dof i of subdomain sub_list[k] (0 off the
 // interface), split into hi/lo tiles (TF32 floats, or BF16 halves with bf16); then
 // cbuf at the interface slots = (X S)[k][i].  S tiles (TF32 hi/lo, or one BF16 copy)
-// are formed once from the FP32 block S32 (S32[j * n_bd + i] = S[i][j]).  With
-// splits > 1 the K range is split across CTAs whose partial tiles meet in `part`
-// (schur_part_floats) through the per-tile counters `count` (2 x schur_tiles ints,
-// zero at the first launch; each launch leaves them zero).  err: bit 4 set if a
-// bounded wait gives up.
+// are formed once from the FP32 block S32 (S32[j * n_bd + i] = S[i][j]).  The GEMM's
+// output tiles (with splits > 1, one partial per split of the K range) go to `part`
+// (schur_part_floats), from which a second kernel sums the splits in order and writes
+// the slots.  err: bit 4 set if a bounded wait gives up.
 int schur_nk(int n_bd);
 int schur_tiles(int n_list, int n_bd);
 int schur_splits(int n_list, int n_bd, int n_sm);
@@ -203,7 +202,7 @@ void launch_schur_gather(const DevMesh& M, const int* sub_list, int n_list, int 
                          void* Xhi, void* Xlo, cudaStream_t st);
 void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
                                const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
-                               int* count, double* cbuf, int* err, cudaStream_t st);
+                               double* cbuf, int* err, cudaStream_t st);
 // Plastic subdomains on their shape's elastic factor plus a Woodbury correction
 // (kernels_woodbury.cu).  list: the n subdomains (r = 6 n_pts[w] correction columns each, n dofs,
 // n_bd boundary dofs).  Per subdomain w: pts + pt_off[w] its plastic points; u_pool +

@@ -53,6 +53,26 @@ __device__ void block_reduce_sum6(double v[6], double* red) {
   }
 }
 
+// block_reduce_sum6 in FP32: red holds 6 x 32 floats.
+__device__ void block_reduce_sum6f(float v[6], float* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  if (l == 0)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) red[c * 32 + w] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float s = threadIdx.x < nw ? red[c * 32 + threadIdx.x] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[c] = s;
+    }
+  }
+}
+
 // gx[6p+c] = scale * (R_p^T x_p)_c over all dofs of subdomain p (set-up: e = -R^T f).
 // One CTA per subdomain.
 __global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* gx, double scale) {
@@ -125,9 +145,17 @@ __global__ void __launch_bounds__(256, 4) k_G_csr(DevMesh M, const T* __restrict
         for (int c = 0; c < 6; ++c) acc[c] += g[k][c] * v[k];
   }
   double s[6];
+  if constexpr (sizeof(T) == 4) {
+    // the FP32 instance sums its block in FP32 (the FP64 pipe is narrow), in the order of
+    // block_reduce_sum6, and rounds the sums to FP64 at the end
+    block_reduce_sum6f(acc, reinterpret_cast<float*>(red));
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s[c] = double(acc[c]);
-  block_reduce_sum6(s, red);
+    for (int c = 0; c < 6; ++c) s[c] = double(acc[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] = double(acc[c]);
+    block_reduce_sum6(s, red);
+  }
   if (threadIdx.x == 0)
 #pragma unroll
     for (int c = 0; c < 6; ++c) gx[6 * (long long)p + c] = scale * s[c];
@@ -181,12 +209,14 @@ __global__ void k_GT_csr32(DevMesh M, const float* __restrict__ GTv8, const doub
   out[row] = x[row] - s;
 }
 
+constexpr int kGemvRows = 8;   // rows per 512-thread block of the coarse GEMVs (two warps per row)
+constexpr int kGemv32B = 4;    // float4 loads per lane in flight in the FP32 coarse GEMV
+
 // y = H x with the FP32 copy of H (n x n, rows padded with zeros to ld, a multiple of 4),
 // x rounded to FP32 in shared memory; writes y (FP64) and its padded FP32 copy h8.  Two warps
 // per row (kGemvRows rows per 512-thread block), each taking every other 32-float4 segment of
 // the row, so that a lane has about a dozen float4 loads in flight at 64^3; the two halves are
 // added in warp order.
-constexpr int kGemvRows = 8;
 __global__ void __launch_bounds__(512, 3) k_gemv32(const float* __restrict__ A, long long n, long long ld,
                                                    const double* __restrict__ x, double* y, float* h8) {
   extern __shared__ __align__(16) float xs[];
@@ -201,10 +231,21 @@ __global__ void __launch_bounds__(512, 3) k_gemv32(const float* __restrict__ A, 
     const long long n4 = ld >> 2;
     const float4* x4 = reinterpret_cast<const float4*>(xs);
     const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
-#pragma unroll 6
-    for (long long j = 32 * hf + lane; j < n4; j += 64) {
-      const float4 a = __ldg(a4 + j), v = x4[j];
-      acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
+    for (long long j0 = 32 * hf + lane; j0 < n4; j0 += 64 * kGemv32B) {
+      float4 a[kGemv32B];   // the batch's loads issued before their products are summed
+#pragma unroll
+      for (int u = 0; u < kGemv32B; ++u) {
+        const long long j = j0 + 64 * u;
+        a[u] = j < n4 ? __ldg(a4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kGemv32B; ++u) {
+        const long long j = j0 + 64 * u;
+        if (j < n4) {
+          const float4 v = x4[j];
+          acc += a[u].x * v.x + a[u].y * v.y + a[u].z * v.z + a[u].w * v.w;
+        }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   }
@@ -253,19 +294,43 @@ __global__ void k_add_R_alpha(DevMesh M, const double* __restrict__ v, const dou
   out[S.dof_off + i] = s;
 }
 
-// y = alpha * A x, A dense n x n row-major (T: FP64, or its FP32 copy); one warp per row.
-template <typename T>
-__global__ void k_gemv(const T* __restrict__ A, long long n, const double* __restrict__ x, double alpha,
-                       double* y) {
-  const long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const T* a = A + row * n;
-  T s = T(0);
-#pragma unroll 4
-  for (long long j = lane; j < n; j += 32) s += a[j] * T(x[j]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = alpha * double(s);
+// y = alpha * A x, A dense n x n row-major FP64.  Two warps per row (kGemvRows rows per
+// 512-thread block), each taking every other 32-double2 segment of the row (16-byte loads: n is
+// even, 6 coarse unknowns per subdomain) with kGemv64B of its loads issued before their products
+// are summed; the halves are added in warp order.
+constexpr int kGemv64B = 6;
+__global__ void __launch_bounds__(512, 3) k_gemv64(const double* __restrict__ A, long long n,
+                                                   const double* __restrict__ x, double alpha, double* y) {
+  __shared__ double half[16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long row = blockIdx.x * (long long)kGemvRows + (warp >> 1);
+  const int hf = warp & 1;
+  double acc = 0.0;
+  if (row < n) {
+    const long long n2 = n >> 1;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    const double2* a2 = reinterpret_cast<const double2*>(A + row * n);
+    for (long long j0 = 32 * hf + lane; j0 < n2; j0 += 64 * kGemv64B) {
+      double2 a[kGemv64B];
+#pragma unroll
+      for (int u = 0; u < kGemv64B; ++u) {
+        const long long j = j0 + 64 * u;
+        a[u] = j < n2 ? __ldg(a2 + j) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < kGemv64B; ++u) {
+        const long long j = j0 + 64 * u;
+        if (j < n2) {
+          const double2 v = __ldg(x2 + j);
+          acc += a[u].x * v.x + a[u].y * v.y;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  }
+  if (lane == 0) half[warp] = acc;
+  __syncthreads();
+  if (hf == 0 && lane == 0 && row < n) y[row] = alpha * (half[warp] + half[warp + 1]);
 }
 
 // Lumped preconditioner, subdomain part: v = K_bb (B^T w) on the interface slots.
@@ -521,7 +586,7 @@ __global__ void __launch_bounds__(256, 4)
     const long long f0 = has1 ? M.gt_ptr[row1] : 0, f1 = has1 ? M.gt_ptr[row1 + 1] : 0;
     const double x0 = x[row0], x1 = has1 ? x[row1] : 0.0;
     const double v0 = mode == 0 ? 0.0 : v[row0], v1 = (mode == 0 || !has1) ? 0.0 : v[row1];
-    double s0 = 0.0, s1 = 0.0;
+    float s0 = 0.f, s1 = 0.f;   // a row's few FP32 products summed in FP32
     for (long long k = 0; e0 + k < e1 || f0 + k < f1; ++k) {
       const bool a0 = e0 + k < e1, a1 = f0 + k < f1;
       int q0 = 0, q1 = 0;
@@ -538,14 +603,14 @@ __global__ void __launch_bounds__(256, 4)
       }
       if (a0) {
         const float4 u = __ldg(h4 + 2 * q0), w = __ldg(h4 + 2 * q0 + 1);
-        s0 += double(ga0.x * u.x + ga0.y * u.y + ga0.z * u.z + ga0.w * u.w + gb0.x * w.x + gb0.y * w.y);
+        s0 += ga0.x * u.x + ga0.y * u.y + ga0.z * u.z + ga0.w * u.w + gb0.x * w.x + gb0.y * w.y;
       }
       if (a1) {
         const float4 u = __ldg(h4 + 2 * q1), w = __ldg(h4 + 2 * q1 + 1);
-        s1 += double(ga1.x * u.x + ga1.y * u.y + ga1.z * u.z + ga1.w * u.w + gb1.x * w.x + gb1.y * w.y);
+        s1 += ga1.x * u.x + ga1.y * u.y + ga1.z * u.z + ga1.w * u.w + gb1.x * w.x + gb1.y * w.y;
       }
     }
-    const double o0 = x0 - s0;
+    const double o0 = x0 - double(s0);
     out[row0] = o0;
     acc += o0 * (mode == 0 ? o0 : v0);
     if constexpr (kDefl) {
@@ -554,7 +619,7 @@ __global__ void __launch_bounds__(256, 4)
         if (j < kd) accd[j] += o0 * AW[(long long)j * m + row0];
     }
     if (has1) {
-      const double o1 = x1 - s1;
+      const double o1 = x1 - double(s1);
       out[row1] = o1;
       acc += o1 * (mode == 0 ? o1 : v1);
       if constexpr (kDefl) {
@@ -633,9 +698,13 @@ __global__ void k_lam_r_update_post(long long n, const double* __restrict__ p, c
                                     double* lam, double* r, double* sc, int* ctr, cudaGraphConditionalHandle h,
                                     int has_h) {
   __shared__ int is_last;
+  __shared__ double s_gamma;
   const bool done = sc[kDone] != 0.0;
   if (!done) {
-    const double gamma = sc[kYW] / sc[kPFP];
+    // one FP64 division per block (the FP64 pipe is narrow): gamma for all its threads
+    if (threadIdx.x == 0) s_gamma = sc[kYW] / sc[kPFP];
+    __syncthreads();
+    const double gamma = s_gamma;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
       const long long i1 = i + stride;
@@ -667,11 +736,14 @@ __global__ void k_lam_r_update_post(long long n, const double* __restrict__ p, c
 
 __global__ void k_p_update_g(long long n, const double* __restrict__ y, double* p, const double* sc,
                              const double* __restrict__ W) {
-  if (sc[kDone] != 0.0) return;
+  __shared__ double s_beta;
+  if (sc[kDone] != 0.0) return;   // the same for every thread
+  const bool first = sc[kFirst] != 0.0;
+  if (threadIdx.x == 0) s_beta = first ? 0.0 : sc[kYW] / sc[kYWPrev];   // one division per block
+  __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const bool first = sc[kFirst] != 0.0;
-  const double beta = first ? 0.0 : sc[kYW] / sc[kYWPrev];
+  const double beta = s_beta;
   double v = first ? y[i] : y[i] + beta * p[i];
   if (W) {   // deflated direction: p = y + beta p - W mu
     const int kd = (int)sc[kDeflK];
@@ -682,10 +754,13 @@ __global__ void k_p_update_g(long long n, const double* __restrict__ y, double* 
 
 __global__ void k_lam_r_update_g(long long n, const double* __restrict__ p, const double* __restrict__ Fp,
                                  double* lam, double* r, const double* sc) {
-  if (sc[kDone] != 0.0) return;
+  __shared__ double s_gamma;
+  if (sc[kDone] != 0.0) return;   // the same for every thread
+  if (threadIdx.x == 0) s_gamma = sc[kYW] / sc[kPFP];   // one division per block
+  __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double gamma = sc[kYW] / sc[kPFP];
+  const double gamma = s_gamma;
   lam[i] += gamma * p[i];
   r[i] -= gamma * Fp[i];
 }
@@ -1012,7 +1087,7 @@ void launch_fill_G(const DevMesh& M, const int* gp_slot, const double* gp_coef, 
 }
 
 void launch_gemv(const double* A, long long n, const double* x, double alpha, double* y, cudaStream_t st) {
-  if (n > 0) k_gemv<double><<<blocks_for(n, 8), 256, 0, st>>>(A, n, x, alpha, y);
+  if (n > 0) k_gemv64<<<blocks_for(n, kGemvRows), 512, 0, st>>>(A, n, x, alpha, y);
 }
 
 // FP32 copy of the dense H with rows padded to h32_ld(l) (zeros beyond column l).

@@ -32,6 +32,7 @@ namespace tfeti {
 namespace {
 
 constexpr int kTM = 128, kTN = 64, kTK = 32;
+constexpr int kSU = 4;   // elements per thread of the scatter kernel, their loads in flight together
 constexpr uint32_t kTmemCols = kTN;  // FP32 accumulator columns (a power of two >= 32)
 
 // Operand format: TF32 x 3 (FP32 operands split into TF32 hi/lo, S hi/lo) or BF16 x 2
@@ -102,6 +103,45 @@ __global__ void k_schur_gather_tc(DevMesh M, const int* __restrict__ sub_list, i
     split_tf32(v, hi, lo);
     static_cast<float*>(Xhi)[o] = hi;
     static_cast<float*>(Xlo)[o] = lo;
+  }
+}
+
+// cbuf at the interface slots of subdomain sub_list[k] = the sum over the K splits, in split
+// order, of the GEMM's partial outputs part[z][k][i] (boundary dof i; row pitch n_nt * kTN).
+// Consecutive threads take consecutive dofs of a subdomain (coalesced slot tables and stores);
+// kSU elements per thread with their loads in flight together.
+__global__ void k_schur_scatter(DevMesh M, const int* __restrict__ sub_list, int n_list, int n_bd, int n_mt, int n_nt,
+                                int splits, const float* __restrict__ part, double* cbuf) {
+  const long long ldp = (long long)n_nt * kTN, zs = (long long)n_mt * kTM * ldp;
+  const long long n = (long long)n_list * n_bd, stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < n; b += kSU * stride) {
+    int k[kSU], i[kSU], sub[kSU];
+#pragma unroll
+    for (int u = 0; u < kSU; ++u) {
+      const long long id = b + u * stride;
+      k[u] = id < n ? (int)(id / n_bd) : -1;
+      i[u] = id < n ? (int)(id % n_bd) : 0;
+      sub[u] = k[u] >= 0 ? __ldg(sub_list + k[u]) : 0;
+    }
+    long long b2s[kSU];
+    float v[kSU];
+#pragma unroll
+    for (int u = 0; u < kSU; ++u) {
+      b2s[u] = k[u] >= 0 ? M.subs[sub[u]].b2s_off : 0;
+      float acc = 0.f;
+      if (k[u] >= 0) {
+        const float* pk = part + (long long)k[u] * ldp + i[u];
+        acc = __ldg(pk);
+        for (int z = 1; z < splits; ++z) acc += __ldg(pk + z * zs);
+      }
+      v[u] = acc;
+    }
+    int sl[kSU];
+#pragma unroll
+    for (int u = 0; u < kSU; ++u) sl[u] = k[u] >= 0 ? __ldg(M.sub_b2s + b2s[u] + i[u] / 3) : -1;
+#pragma unroll
+    for (int u = 0; u < kSU; ++u)
+      if (sl[u] >= 0) cbuf[(long long)sl[u] + i[u] % 3] = (double)v[u];
   }
 }
 
@@ -176,24 +216,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // C = X S for one 128 x kTN output tile (blockIdx.y: subdomain tile, blockIdx.x:
-// boundary-dof tile) over the K stages [ks0, ks1) of split blockIdx.z, written to the
-// copy slots of the interface dofs.  256 threads: thread 0 streams the stages, thread 32
-// issues the MMAs, and all eight warps read the accumulator: warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 (its quadrant: output rows) and columns 32 (w / 4) .. + 31, so the
-// epilogue's gathers of slot indices and scattered stores run on eight warps.
-//
-// With splits of K (gridDim.z > 1, used when the output tiles alone would leave SMs idle)
-// every CTA of a tile stores its FP32 partial tile in `part` and counts itself in
-// `count[tile]`; the one that arrives last sums the partials in split order and scatters,
-// so the result does not depend on the order in which the CTAs finish, and returns the
-// counter to zero for the next launch.  No CTA waits for another.
+// boundary-dof tile) over the K stages [ks0, ks1) of split blockIdx.z (gridDim.z > 1 when the
+// output tiles alone would leave SMs idle), stored row-major in `part` for k_schur_scatter.
+// 256 threads: thread 0 streams the stages, thread 32 issues the MMAs, and all eight warps
+// read the accumulator: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its quadrant: output
+// rows) and columns 32 (w / 4) .. + 31.  No CTA waits for another.
 template <bool kBf>
-__global__ void __launch_bounds__(256, 1) k_schur_tc(DevMesh M, const int* __restrict__ sub_list, int n_list,
-                                                     int n_bd, int nk, const unsigned char* __restrict__ Xhi,
+__global__ void __launch_bounds__(256, 1) k_schur_tc(int nk, const unsigned char* __restrict__ Xhi,
                                                      const unsigned char* __restrict__ Xlo,
                                                      const unsigned char* __restrict__ Shi,
-                                                     const unsigned char* __restrict__ Slo, float* part, int* count,
-                                                     double* cbuf, int* err) {
+                                                     const unsigned char* __restrict__ Slo, float* part, int* err) {
   using F = Fmt<kBf>;
   constexpr int kSt = F::stages;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -201,7 +233,7 @@ __global__ void __launch_bounds__(256, 1) k_schur_tc(DevMesh M, const int* __res
   uint64_t* empty = full + kSt;
   uint64_t* done = empty + kSt;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  int* s_flag = reinterpret_cast<int*>(tmem_slot + 1);   // [0]: a wait gave up, [1]: this CTA is last
+  int* s_flag = reinterpret_cast<int*>(tmem_slot + 1);   // [0]: a wait gave up
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = blockIdx.x, mt = blockIdx.y, splits = gridDim.z;
   const int ks0 = (int)((long long)blockIdx.z * nk / splits), ks1 = (int)((long long)(blockIdx.z + 1) * nk / splits);
@@ -214,7 +246,6 @@ __global__ void __launch_bounds__(256, 1) k_schur_tc(DevMesh M, const int* __res
     }
     mbar_init(done);
     s_flag[0] = 0;
-    s_flag[1] = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
@@ -283,60 +314,20 @@ __global__ void __launch_bounds__(256, 1) k_schur_tc(DevMesh M, const int* __res
   tc_fence_after();
   __syncthreads();
   const bool good = s_flag[0] == 0;   // the same for every thread: tcgen05.ld below is warp-collective
+  // this split's output tile, row-major in part[split][m row][n column] (row pitch gridDim.x * kTN):
+  // each lane holds one row of the accumulator and stores it as 16-float runs
   const int quad = warp & 3, cbeg = (warp >> 2) * (kTN / 2), cend = cbeg + kTN / 2;
   const int row = quad * 32 + lane;
-  const int k = mt * kTM + row;
-  const long long tile = (long long)mt * gridDim.x + nt;
-  bool last = true;
-  if (splits > 1) {
-    // every split publishes its partial tile (column c of this row at [c * kTM]); the CTA that
-    // arrives last sums the partials in split order and scatters
-    float* mine = part + (tile * splits + blockIdx.z) * (kTM * kTN) + row;
-    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+  const long long ldp = (long long)gridDim.x * kTN;
+  float* dst = part + (long long)blockIdx.z * ((long long)gridDim.y * kTM * ldp) + ((long long)mt * kTM + row) * ldp +
+               (long long)nt * kTN;
+  for (int c0 = cbeg; c0 < cend; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+    float4* d4 = reinterpret_cast<float4*>(dst + c0);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) mine[(c0 + q) * kTM] = good ? v[q] : 0.0f;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int old = atomicAdd(&count[tile], 1);
-      s_flag[1] = old == splits - 1 ? 1 : 0;
-      if (old == splits - 1) count[tile] = 0;   // back to zero for the next launch
-    }
-    __syncthreads();
-    last = s_flag[1] != 0;
-    if (last) __threadfence();
-  }
-  if (last) {   // CTA-uniform, so every lane of a warp takes the warp-collective loads together
-    const bool mine_row = k < n_list;
-    const int sub = mine_row ? sub_list[k] : 0;
-    const float* pt = part + tile * splits * (kTM * kTN) + row;
-    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-      float v[16];
-      if (splits == 1) {
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-      } else if (mine_row) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          float acc = __ldcg(pt + (c0 + q) * kTM);
-          for (int z = 1; z < splits; ++z) acc += __ldcg(pt + (long long)z * (kTM * kTN) + (c0 + q) * kTM);
-          v[q] = acc;
-        }
-      }
-      if (mine_row && s_flag[0] == 0) {
-        const SubDev& S = M.subs[sub];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int i = nt * kTN + c0 + q;
-          if (i < n_bd) {
-            const int sl = M.sub_b2s[S.b2s_off + i / 3];
-            if (sl >= 0) cbuf[(long long)sl + i % 3] = (double)v[q];
-          }
-        }
-      }
-    }
+    for (int q = 0; q < 4; ++q)
+      d4[q] = good ? make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (threadIdx.x == 0 && s_flag[0] != 0) atomicOr(err, 4);
   tc_fence_before();
@@ -389,22 +380,24 @@ int schur_splits(int n_list, int n_bd, int n_sm) {
 
 void launch_schur_gemm_scatter(const DevMesh& M, const int* sub_list, int n_list, int n_bd, bool bf16, int splits,
                                const void* Xhi, const void* Xlo, const void* Shi, const void* Slo, float* part,
-                               int* count, double* cbuf, int* err, cudaStream_t st) {
+                               double* cbuf, int* err, cudaStream_t st) {
   if (n_list <= 0 || n_bd <= 0) return;
-  dim3 grid((unsigned)((n_bd + kTN - 1) / kTN), (unsigned)((n_list + kTM - 1) / kTM), (unsigned)splits);
+  const int n_nt = (n_bd + kTN - 1) / kTN, n_mt = (n_list + kTM - 1) / kTM;
+  dim3 grid((unsigned)n_nt, (unsigned)n_mt, (unsigned)splits);
   const auto* xh = static_cast<const unsigned char*>(Xhi);
   const auto* xl = static_cast<const unsigned char*>(Xlo);
   const auto* sh = static_cast<const unsigned char*>(Shi);
   const auto* sl = static_cast<const unsigned char*>(Slo);
   if (bf16) {
     cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<true>::smem);
-    k_schur_tc<true><<<grid, 256, Fmt<true>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
-                                                          part, count, cbuf, err);
+    k_schur_tc<true><<<grid, 256, Fmt<true>::smem, st>>>(schur_nk(n_bd), xh, xl, sh, sl, part, err);
   } else {
     cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fmt<false>::smem);
-    k_schur_tc<false><<<grid, 256, Fmt<false>::smem, st>>>(M, sub_list, n_list, n_bd, schur_nk(n_bd), xh, xl, sh, sl,
-                                                           part, count, cbuf, err);
+    k_schur_tc<false><<<grid, 256, Fmt<false>::smem, st>>>(schur_nk(n_bd), xh, xl, sh, sl, part, err);
   }
+  const long long n = (long long)n_list * n_bd;
+  const unsigned blocks = (unsigned)((n + 256LL * kSU - 1) / (256LL * kSU));
+  k_schur_scatter<<<blocks, 256, 0, st>>>(M, sub_list, n_list, n_bd, n_mt, n_nt, splits, part, cbuf);
 }
 
 }  // namespace tfeti
