@@ -713,7 +713,6 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64, bool async =
     ensure_cap(c, c->wood_d, c->wood_d_cap, d_tot);
     ensure_cap(c, c->wood_z, c->wood_z_cap, z_tot);
     ensure_cap(c, c->wood_y, c->wood_y_cap, z_tot);
-    ensure_cap(c, c->wood_x, c->wood_x_cap, (long long)nl * max_bd);
     if (fp64) {
       ensure_cap(c, c->wood_v, c->wood_v_cap, (long long)nl * max_n);
       ensure_cap(c, c->wood_yb, c->wood_yb_cap, (long long)nl * max_n);
@@ -763,7 +762,6 @@ int wood_setup(tfeti_ctx* c, const std::vector<int>& np, bool fp64, bool async =
   w.y_pool = c->wood_y;
   w.z_total = z_tot;
   w.tbuf = c->wood_t;
-  w.xbuf = c->wood_x;
   w.vbuf = c->wood_v;
   w.tbuf64 = c->wood_t64;
   w.ybuf = c->wood_yb;
@@ -997,7 +995,7 @@ void op_precond_dirichlet(tfeti_ctx* c, const double* w, double* out, bool fp32)
 
 // FP32 projector and preconditioner of the inner iterations of the mixed mode.
 void op_project32(tfeti_ctx* c, const double* x, double* out) {
-  launch_project32(c->M, c->coarse, x, c->gx, c->hx, c->hx8, out, c->st);
+  launch_project32(c->M, c->coarse, x, c->gx, c->gx32, c->hx, c->hx8, out, c->st);
   c->launches += 2 + coarse_launches(c->coarse);
 }
 
@@ -1407,10 +1405,10 @@ int enqueue_inner_fused_body(tfeti_ctx* c, unsigned long long h, bool has_h) {
 
 void enqueue_inner_iteration(tfeti_ctx* c, unsigned long long h, bool has_h) {
   const long long m = c->M.n_mult;
-  launch_G32_coarse32(c->M, c->coarse, c->rin, c->gx, c->hx, c->hx8, c->st);
+  launch_G32_coarse32(c->M, c->coarse, c->rin, c->gx, c->gx32, c->hx, c->hx8, c->st);
   launch_GT32_dot(c->M, c->rin, c->hx8, c->w, nullptr, 0, c->sc, c->partial, c->d_ctr, c->st);   // w = P r, w.w
   op_precond32(c, c->w, c->z);                                                                   // z = F^-1 w
-  launch_G32_coarse32(c->M, c->coarse, c->z, c->gx, c->hx, c->hx8, c->st);
+  launch_G32_coarse32(c->M, c->coarse, c->z, c->gx, c->gx32, c->hx, c->hx8, c->st);
   launch_GT32_dot(c->M, c->z, c->hx8, c->y, c->w, 1, c->sc, c->partial, c->d_ctr + 1, c->st,   // y = P z, y.w
                   c->defl_AW, c->defl_Einv);                                                     // (and mu)
   launch_p_update_g(m, c->y, c->pdir, c->sc, c->st, c->defl_W);                               // p = y + beta p - W mu
@@ -2377,6 +2375,7 @@ int setup_impl(tfeti_ctx* c, tfeti_ctx* base = nullptr) {
   c->gx = dalloc<double>(c, c->l);
   c->hx = dalloc<double>(c, c->l);
   c->hx8 = dalloc<float>(c, 8 * (size_t)ns);
+  c->gx32 = dalloc<float>(c, (size_t)std::max(1LL, c->l));
   cudaMemsetAsync(c->hx8, 0, sizeof(float) * 8 * (size_t)ns, c->st);
   c->ev = dalloc<double>(c, c->l);
   c->alpha = dalloc<double>(c, c->l);

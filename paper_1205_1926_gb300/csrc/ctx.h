@@ -105,10 +105,9 @@ struct tfeti_ctx {
   int *d_wood_pts = nullptr, *wood_dofs = nullptr;
   double *wood_u = nullptr, *wood_zt = nullptr, *wood_c64 = nullptr, *wood_d64 = nullptr;
   double *wood_v = nullptr, *wood_t64 = nullptr, *wood_yb = nullptr;
-  float *wood_c = nullptr, *wood_d = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr,
-        *wood_x = nullptr;
+  float *wood_c = nullptr, *wood_d = nullptr, *wood_z = nullptr, *wood_y = nullptr, *wood_t = nullptr;
   long long wood_pts_cap = 0, wood_dofs_cap = 0, wood_u_cap = 0, wood_zt_cap = 0, wood_c64_cap = 0,
-            wood_d64_cap = 0, wood_c_cap = 0, wood_d_cap = 0, wood_z_cap = 0, wood_y_cap = 0, wood_x_cap = 0,
+            wood_d64_cap = 0, wood_c_cap = 0, wood_d_cap = 0, wood_z_cap = 0, wood_y_cap = 0,
             wood_v_cap = 0, wood_yb_cap = 0;
   long long wood_subs = 0, wood_fallbacks = 0, wood_fac_saved = 0;
   // set-up inside a load step: on st_wood beside the first residual solve; the context stream waits
@@ -246,6 +245,7 @@ struct tfeti_ctx {
   float *H32 = nullptr, *kbb32 = nullptr;
   double *H = nullptr, *gx = nullptr, *hx = nullptr, *ev = nullptr, *alpha = nullptr;
   float* hx8 = nullptr;              // FP32 H g padded to 8 per subdomain (FP32 projector)
+  float* gx32 = nullptr;             // FP32 G x of the FP32 projector (the coarse GEMV's input)
   double *f_full = nullptr, *tn = nullptr, *tn2 = nullptr;
   // coarse solve (dense explicit H or the plane solver's blocks; a case context shares the base's)
   tfeti::CoarseOp coarse;

@@ -241,7 +241,6 @@ struct WoodArgs {
   float *z_pool = nullptr, *y_pool = nullptr;
   long long z_total = 0;
   float* tbuf = nullptr;             // [n][6 max_pts]: t = Y x_b of the inner apply
-  float* xbuf = nullptr;             // [n][max_bd]: x_b of the inner apply
   double* vbuf = nullptr;            // [n][max_n]: v of the FP64 correction
   double* tbuf64 = nullptr;          // [n][6 max_pts]: t = Z^T v, then C^-1 t
   double* ybuf = nullptr;            // [n][max_n]: y = Z C^-1 t
@@ -296,7 +295,8 @@ struct CoarseOp {
 void coarse_apply(const CoarseOp& C, const double* x, double alpha, double* y, cudaStream_t st);
 // y = H x with the FP32 copies (FP32 products and sums), and y8, its FP32 copy padded to 8
 // values per subdomain.
-void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cudaStream_t st);
+// x32 (nullable): x already rounded to FP32 (the dense GEMV then reads it instead of converting x).
+void coarse_apply32(const CoarseOp& C, const double* x, const float* x32, double* y, float* y8, cudaStream_t st);
 int coarse_launches(const CoarseOp& C);
 void launch_coarse_assemble_planes(const DevMesh& M, const int* pair_p, const int* pair_q, const long long* pair_start,
                                    const int* trip_group, const int* trip_i, const int* trip_j, long long n_pairs,
@@ -310,8 +310,8 @@ void coarse_planes_factor(double* W, const double* Aoff, double* V, double* U, i
 // the FP32 copy of the boundary blocks.  gx, hx: coarse work vectors [l].
 // hx8: FP32 copy of H g padded to 8 values per subdomain (entries 6, 7 zero), [n_sub][8].
 // G values in FP32 (M.Gv32, M.GTv32) are stored 8 per entry (6 and two zeros).
-void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
-                      double* out, cudaStream_t st);
+void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, float* gx32, double* hx,
+                      float* hx8, double* out, cudaStream_t st);
 inline long long h32_ld(long long l) { return (l + 3) & ~3LL; }
 void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st);
 // Values of the explicit G from R and the (row, slot, coefficient) entries (set-up).
@@ -411,8 +411,8 @@ void launch_dot2(const double* x1, const double* y1, const double* x2, const dou
 // the breakdown test.  lam_r_update_post: the guarded updates, then the body run is closed and,
 // with has_h, the WHILE condition h set.  G32_coarse32: gx = G x and hx = H gx in FP32 (+ padded hx8).
 constexpr int kFusedBlocks = 608;
-void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
-                         cudaStream_t st);
+void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, float* gx32, double* hx,
+                         float* hx8, cudaStream_t st);
 void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double* out, const double* v, int mode,
                      double* sc, double* partial, int* ctr, cudaStream_t st, const double* AW = nullptr,
                      const double* Einv = nullptr);

@@ -93,7 +93,7 @@ __global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* g
   }
 }
 
-// gx[6p+c] = scale * (G x)[6p+c] = scale * sum over the entries of subdomain p of
+// gx[6p+c] = scale * (G x)[6p+c] (and its FP32 rounding in gx32, nullable) = scale * sum over the entries of subdomain p of
 // G[entry][c] x[row].  One CTA per subdomain.  T: FP64 values, or their FP32 copy
 // (products and per-thread sums in T) for the inner iterations of the mixed mode.
 // FP64 values: 6 per entry; FP32 values: 8 per entry (6 and two zeros), read as two float4.
@@ -117,8 +117,8 @@ __device__ __forceinline__ void g_entry<float>(const float* __restrict__ Gv, lon
 template <typename T>
 constexpr int g_batch() { return sizeof(T) == 4 ? 4 : 2; }
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x, double* gx,
-                        double scale) {
+__global__ void __launch_bounds__(256, 4) k_G_csr(DevMesh M, const T* __restrict__ Gv, const double* __restrict__ x,
+                                                  double* gx, double scale, float* gx32 = nullptr) {
   __shared__ double red[6 * 32];
   const int p = blockIdx.x;
   const long long e0 = M.gp_ptr[p], e1 = M.gp_ptr[p + 1];
@@ -158,7 +158,10 @@ __global__ void __launch_bounds__(256, 4) k_G_csr(DevMesh M, const T* __restrict
   }
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int c = 0; c < 6; ++c) gx[6 * (long long)p + c] = scale * s[c];
+    for (int c = 0; c < 6; ++c) {
+      gx[6 * (long long)p + c] = scale * s[c];
+      if (gx32) gx32[6 * (long long)p + c] = (float)(scale * s[c]);
+    }
 }
 
 // out[row] = ax * x[row] + bh * (G^T h)[row]   (x nullable); T as in k_G_csr.
@@ -218,10 +221,12 @@ constexpr int kGemv32B = 4;    // float4 loads per lane in flight in the FP32 co
 // the row, so that a lane has about a dozen float4 loads in flight at 64^3; the two halves are
 // added in warp order.
 __global__ void __launch_bounds__(512, 3) k_gemv32(const float* __restrict__ A, long long n, long long ld,
-                                                   const double* __restrict__ x, double* y, float* h8) {
+                                                   const double* __restrict__ x, const float* __restrict__ x32,
+                                                   double* y, float* h8) {
   extern __shared__ __align__(16) float xs[];
   __shared__ float half[16];
-  for (long long j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = j < n ? float(x[j]) : 0.f;
+  // x rounded to FP32: from x32 when the producer wrote that copy (no FP64 conversions here)
+  for (long long j = threadIdx.x; j < ld; j += blockDim.x) xs[j] = j < n ? (x32 ? x32[j] : float(x[j])) : 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long row = blockIdx.x * (long long)kGemvRows + (warp >> 1);
@@ -1103,9 +1108,9 @@ void launch_h_to_f32(const double* H, long long l, float* H32, cudaStream_t st) 
   if (l > 0) k_h_to_f32<<<blocks_for(l * ld, 256), 256, 0, st>>>(H, l, ld, H32);
 }
 
-void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
-                      double* out, cudaStream_t st) {
-  launch_G32_coarse32(M, C, x, gx, hx, hx8, st);
+void launch_project32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, float* gx32, double* hx,
+                      float* hx8, double* out, cudaStream_t st) {
+  launch_G32_coarse32(M, C, x, gx, gx32, hx, hx8, st);
   if (M.n_mult > 0) k_GT_csr32<<<blocks_for(M.n_mult, 256), 256, 0, st>>>(M, M.GTv32, x, hx8, out);
 }
 
@@ -1174,10 +1179,10 @@ void launch_GT32_dot(const DevMesh& M, const double* x, const float* h8, double*
   else k_GT32_dot<false><<<kFusedBlocks, 256, 0, st>>>(M, M.GTv32, x, h8, out, v, mode, sc, partial, ctr, AW, Einv);
 }
 
-void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, double* hx, float* hx8,
-                         cudaStream_t st) {
-  k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0);
-  coarse_apply32(C, gx, hx, hx8, st);
+void launch_G32_coarse32(const DevMesh& M, const CoarseOp& C, const double* x, double* gx, float* gx32, double* hx,
+                         float* hx8, cudaStream_t st) {
+  k_G_csr<float><<<M.n_sub, 256, 0, st>>>(M, M.Gv32, x, gx, 1.0, gx32);
+  coarse_apply32(C, gx, gx32, hx, hx8, st);
 }
 
 void launch_contract_dot(const DevMesh& M, const double* cbuf, double* Fp, const double* p, double* sc,
@@ -1322,12 +1327,12 @@ void coarse_apply(const CoarseOp& C, const double* x, double alpha, double* y, c
   }
 }
 
-void coarse_apply32(const CoarseOp& C, const double* x, double* y, float* y8, cudaStream_t st) {
+void coarse_apply32(const CoarseOp& C, const double* x, const float* x32, double* y, float* y8, cudaStream_t st) {
   if (C.mode == kCoarseDense) {
     static const int lim = dyn_smem_limit((const void*)k_gemv32);
     cudaFuncSetAttribute(k_gemv32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     const long long ld = h32_ld(C.l);
-    k_gemv32<<<blocks_for(C.l, kGemvRows), 512, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, y, y8);
+    k_gemv32<<<blocks_for(C.l, kGemvRows), 512, sizeof(float) * (size_t)ld, st>>>(C.H32, C.l, ld, x, x32, y, y8);
   } else {
     plane_apply<float>(C.W32, C.V32, C.U32, C.n_pl, C.n_planes, x, 1.0, y, y8, st);
   }

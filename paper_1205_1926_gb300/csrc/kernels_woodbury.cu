@@ -18,7 +18,7 @@
 // From these, for the FP32 inner F-apply: L rounded to FP32, Z_b^T (the boundary columns of Z^T)
 // in FP32 and Y = C^{-1} Z_b^T by blocked FP32 substitution (k_wood_subst), so that on the box
 // boundary S_p = S_el + Z_b Y: the subdomain's slots come from the shape's tensor-core GEMM (as
-// for elastic subdomains) plus Z_b (Y x_b) (k_wood_x, k_wood_t, k_wood_y).
+// for elastic subdomains) plus Z_b (Y x_b) (k_wood_t with the gather of x_b, then k_wood_y).
 //
 // FP64 subdomain solves (residual solves, F-applies, K^+ applies) of these subdomains run on the
 // shape's elastic factor and the correction Z C^{-1} Z^T v is added after them: k_wood_v64 forms
@@ -347,38 +347,47 @@ __global__ void __launch_bounds__(256) k_wood_subst(const SubDev* __restrict__ s
 
 // Correction of the inner F-apply, in three launches spread over many CTAs (the per-subdomain
 // products are a few MB each and one CTA per subdomain would leave them latency-bound):
-// k_wood_x: x_b = B^T lam at the boundary dofs of subdomain list[blockIdx.x] -> xbuf + w * xstride;
-// k_wood_t: t = Y x_b, one row per warp, kWoodRows rows per CTA (blockIdx.y) -> tbuf + w * tstride;
+// k_wood_t: t = Y x_b for the rows kWoodRows blockIdx.y .. + kWoodRows - 1 of subdomain list[blockIdx.x],
+// one row per warp, -> tbuf + w * tstride; each CTA with rows first gathers x_b = B^T lam at the
+// subdomain's boundary dofs into shared memory (kXU dofs per thread with their loads in flight).
 // k_wood_y: cbuf[slots] += Z_b t for 64 boundary dofs per CTA (blockIdx.y), four threads per dof
 // splitting the sum over the rows, combined in shared memory in a fixed order.
 constexpr int kWoodRows = 8;
+constexpr int kXU = 4;
 
-__global__ void __launch_bounds__(256) k_wood_x(DevMesh M, const int* __restrict__ list, const double* __restrict__ lam,
-                                                float* xbuf, int xstride) {
-  const int w = blockIdx.x;
-  const SubDev S = M.subs[list[w]];
-  const int n_bd = 3 * S.n_bnd;
-  const int k = blockIdx.y * blockDim.x + threadIdx.x;
-  if (k >= n_bd) return;
-  const int sl = M.sub_b2s[S.b2s_off + k / 3];
-  xbuf[(long long)w * xstride + k] = sl >= 0 ? (float)bt_at_slot(M, lam, (long long)sl + k % 3) : 0.f;
-}
-
-__global__ void __launch_bounds__(256) k_wood_t(const SubDev* __restrict__ subs, const int* __restrict__ list,
+__global__ void __launch_bounds__(256) k_wood_t(DevMesh M, const int* __restrict__ list, const double* __restrict__ lam,
                                                 const int* __restrict__ n_pts, const long long* __restrict__ y_off,
-                                                const float* __restrict__ y_pool, const float* __restrict__ xbuf,
-                                                int xstride, float* tbuf, int tstride) {
+                                                const float* __restrict__ y_pool, float* tbuf, int tstride) {
+  extern __shared__ __align__(16) float xb[];
   const int w = blockIdx.x;
   const int r = 6 * n_pts[w];
+  if ((int)blockIdx.y * kWoodRows >= r) return;   // the same for the whole CTA
+  const SubDev S = M.subs[list[w]];
+  const int n_bd = 3 * S.n_bnd;
+  for (int k0 = threadIdx.x; k0 < n_bd; k0 += kXU * blockDim.x) {
+    long long slot[kXU];
+    double v[kXU];
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int k = k0 + u * (int)blockDim.x;
+      const int sl = k < n_bd ? __ldg(M.sub_b2s + S.b2s_off + k / 3) : -1;
+      slot[u] = sl >= 0 ? (long long)sl + k % 3 : -1;
+    }
+    bt_at_slots<kXU>(M, lam, slot, v);
+#pragma unroll
+    for (int u = 0; u < kXU; ++u) {
+      const int k = k0 + u * (int)blockDim.x;
+      if (k < n_bd) xb[k] = (float)v[u];
+    }
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.y * kWoodRows + warp;
   if (c >= r) return;
-  const int n_bd = 3 * subs[list[w]].n_bnd;
   const float* yr = y_pool + y_off[w] + (long long)c * n_bd;
-  const float* xb = xbuf + (long long)w * xstride;
   float v = 0.f;
 #pragma unroll 8
-  for (int k = lane; k < n_bd; k += 32) v += __ldg(yr + k) * __ldg(xb + k);
+  for (int k = lane; k < n_bd; k += 32) v += __ldg(yr + k) * xb[k];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane == 0) tbuf[(long long)w * tstride + c] = v;
 }
@@ -574,9 +583,10 @@ int wood_setup_launches(const WoodArgs& a) {
 void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, double* cbuf, cudaStream_t st) {
   if (a.n <= 0) return;
   const int rmax = 6 * a.max_pts;
-  k_wood_x<<<dim3((unsigned)a.n, (unsigned)((a.max_bd + 255) / 256)), 256, 0, st>>>(M, a.list, lam, a.xbuf, a.max_bd);
-  k_wood_t<<<dim3((unsigned)a.n, (unsigned)((rmax + kWoodRows - 1) / kWoodRows)), 256, 0, st>>>(
-      M.subs, a.list, a.n_pts, a.z_off, a.y_pool, a.xbuf, a.max_bd, a.tbuf, rmax);
+  static const int lim = dyn_smem_limit((const void*)k_wood_t);
+  cudaFuncSetAttribute(k_wood_t, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  k_wood_t<<<dim3((unsigned)a.n, (unsigned)((rmax + kWoodRows - 1) / kWoodRows)), 256, sizeof(float) * (size_t)a.max_bd,
+             st>>>(M, a.list, lam, a.n_pts, a.z_off, a.y_pool, a.tbuf, rmax);
   k_wood_y<<<dim3((unsigned)a.n, (unsigned)((a.max_bd + 63) / 64)), 256, 0, st>>>(M, a.list, a.n_pts, a.z_off,
                                                                                    a.z_pool, a.tbuf, rmax, cbuf);
 }
