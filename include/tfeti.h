@@ -314,7 +314,8 @@ int tfeti_set_recycling(tfeti_ctx* ctx, int32_t q);
  * as one more vector of the Galerkin start (its product by one F-apply, FP32 in the
  * mixed mode; the zero start stays the fallback).  A solve where the network's vector
  * lowers the predicted residual by less than 10 % counts against it; after two such
- * solves in a row at a Newton index it is consulted there only every fourth time.
+ * solves in a row at a Newton index it is consulted there only every fourth time, and
+ * trains there only after the solves that consulted it.
  * After each solve the stored solutions could not start well the network takes
  * `epochs` Adam steps (learning rate lr, FP32 master weights) on 64 x 128 rows of the
  * solve against its lambda_Ker, on a low-priority stream of its own beside the next

@@ -1825,6 +1825,7 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
     nb = n + 1;
     with_mlp = coef2[n] != 0.0;
     c->mlp_slot_valid = true;
+    c->mlp_consulted = true;
     int& ng = c->mlp_nogain[c->newton_idx - 1];
     ng = pred > 0.9 * pred0 ? ng + 1 : 0;
   }
@@ -1873,9 +1874,12 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
 void mlp_train(tfeti_ctx* c, double r0) {
   if (!mlp_index_ok(c)) return;
   const long long m = c->M.n_mult;
-  // training only after solves that the stored solutions alone could not start well
-  const bool train =
-      c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 && (c->mlp_scal_valid || mlp_scalars(c, r0));
+  // training only after solves that the stored solutions alone could not start well, and while the
+  // judge has the network benched at this Newton index (two solves in a row where it added less than
+  // 10 %) only after the solves that consulted it
+  const bool benched = c->mlp_nogain[c->newton_idx - 1] >= 2 && !c->mlp_consulted;
+  const bool train = !benched && c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 &&
+                     (c->mlp_scal_valid || mlp_scalars(c, r0));
   // the next Newton iteration overwrites d~, lambda_Ker and the plastic fractions on the context stream
   cudaMemcpyAsync(c->mlp_d, c->dtil, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   cudaMemcpyAsync(c->mlp_tgt, c->lamk, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
@@ -1952,6 +1956,7 @@ int dual_pcg(tfeti_ctx* c, const double* f, double* u_out, double* lambda_out, c
   const bool history = c->rec_q > 0 && m > 0;
   if (history) cudaMemcpyAsync(c->dtil, c->r, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->st);
   c->mlp_missed = c->rec_n == 0;   // set by the history start when it runs
+  c->mlp_consulted = false;
   c->defl_formed = false;          // the deflation space is formed again for this solve
   c->defl_k = 0;
   cudaMemsetAsync(c->sc + kDeflK, 0, sizeof(double), c->st);

@@ -201,6 +201,7 @@ struct tfeti_ctx {
   // solve); mlp_slot_valid: the last start formed the network's prediction in slot rec_n
   int defl_req = 0, defl_k = 0;
   bool defl_formed = false, mlp_slot_valid = false;
+  bool mlp_consulted = false;   // this solve's start consulted the network
   double *defl_W = nullptr, *defl_AW = nullptr, *defl_Einv = nullptr;
   long long defl_setups = 0, defl_vectors = 0, defl_fallbacks = 0;
   double *rec_L = nullptr, *rec_FL = nullptr, *rec_partial = nullptr, *rec_out = nullptr, *rec_c = nullptr;
