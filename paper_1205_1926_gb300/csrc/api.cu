@@ -349,11 +349,39 @@ int check_factorisation(tfeti_ctx* c) {
 void wood_correct_solve(tfeti_ctx* c, const SolveArgs& a, cudaStream_t st);
 void wood_join(tfeti_ctx* c);
 
+// FP64 Woodbury correction of a subdomain-solve pass in two halves: y = Z C^-1 Z^T v from the
+// pass's inputs on st_wc, launched before the pass so that it runs beside it, and its addition
+// to the pass's outputs on the context stream afterwards.  Returns whether a correction is pending.
+bool wood_correct_begin(tfeti_ctx* c, const SolveArgs& a) {
+  if (a.fp32 || (a.in_mode != 0 && a.in_mode != 1) || c->wood.n <= 0 || !c->wood.fp64) return false;
+  if (!c->st_wc) {
+    cudaStreamCreateWithFlags(&c->st_wc, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&c->ev_wc_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_wc_done, cudaEventDisableTiming);
+  }
+  cudaEventRecord(c->ev_wc_fork, c->st);
+  cudaStreamWaitEvent(c->st_wc, c->ev_wc_fork, 0);
+  if (c->wood_pending) cudaStreamWaitEvent(c->st_wc, c->ev_wood_done, 0);   // the set-up's data
+  c->launches += launch_wood_corr64(c->M, c->wood, a.in_mode == 1 ? a.src : nullptr, a.lam,
+                                    a.in_mode == 0 ? 1.0 : -1.0, c->st_wc);
+  cudaEventRecord(c->ev_wc_done, c->st_wc);
+  return true;
+}
+
+void wood_correct_end(tfeti_ctx* c, const SolveArgs& a) {
+  const bool to_c = a.out_mode == 0 || a.out_mode == 3, to_d = a.out_mode == 1 || a.out_mode == 3;
+  wood_join(c);
+  cudaStreamWaitEvent(c->st, c->ev_wc_done, 0);
+  c->launches += launch_wood_add64(c->M, c->wood, to_c ? a.cbuf : nullptr, to_d ? a.dst : nullptr, c->st);
+}
+
 void timed_sub_solve(tfeti_ctx* c, const SolveArgs& a) {
+  // subdomains on their elastic factor + Woodbury correction
+  const bool corr = wood_correct_begin(c, a);
   cudaEvent_t e1 = timed_begin(c, 0);
   launch_sub_solve(c->M, a, c->solve_smem, c->st);
   if (e1) cudaEventRecord(e1, c->st);
-  wood_correct_solve(c, a, c->st);   // subdomains on their elastic factor + Woodbury correction
+  if (corr) wood_correct_end(c, a);
   c->launches += 1;
   c->f_launches += 1;
 }
@@ -2722,6 +2750,7 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->st_fac) cudaStreamSynchronize(c->st_fac);
   if (c->st_mlp) cudaStreamSynchronize(c->st_mlp);
   if (c->st_wood) cudaStreamSynchronize(c->st_wood);
+  if (c->st_wc) cudaStreamSynchronize(c->st_wc);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fac_e0) cudaEventDestroy(c->fac_e0);
@@ -2738,6 +2767,9 @@ int tfeti_destroy(tfeti_ctx* c) {
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st_mlp) cudaStreamDestroy(c->st_mlp);
   if (c->st_wood) cudaStreamDestroy(c->st_wood);
+  if (c->st_wc) cudaStreamDestroy(c->st_wc);
+  if (c->ev_wc_fork) cudaEventDestroy(c->ev_wc_fork);
+  if (c->ev_wc_done) cudaEventDestroy(c->ev_wc_done);
   if (c->ev_wood_fork) cudaEventDestroy(c->ev_wood_fork);
   if (c->ev_wood_done) cudaEventDestroy(c->ev_wood_done);
   if (c->h_err_wood) cudaFreeHost(c->h_err_wood);

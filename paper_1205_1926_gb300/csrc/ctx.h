@@ -115,6 +115,10 @@ struct tfeti_ctx {
   // next synchronisation (wood_check_pending)
   cudaStream_t st_wood = nullptr;
   cudaEvent_t ev_wood_fork = nullptr, ev_wood_done = nullptr;
+  // the FP64 Woodbury correction of a timed subdomain-solve pass runs on st_wc beside the pass (it
+  // reads only the pass's inputs); the context stream waits for ev_wc_done before adding it
+  cudaStream_t st_wc = nullptr;
+  cudaEvent_t ev_wc_fork = nullptr, ev_wc_done = nullptr;
   int* d_err_wood = nullptr;
   int* h_err_wood = nullptr;
   bool wood_pending = false, wood_check_pending = false;

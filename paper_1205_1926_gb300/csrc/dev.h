@@ -256,6 +256,13 @@ void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, d
 // interface slots (nullable).  Returns the number of launches.
 int launch_wood_apply64(const DevMesh& M, const WoodArgs& a, const double* src, const double* lam, double sign,
                         double* cbuf, double* dst, cudaStream_t st);
+// The same correction in two parts, so that the first can run beside the subdomain solve (it
+// reads only the solve's inputs): launch_wood_corr64 forms y = Z C^-1 Z^T v in ybuf;
+// launch_wood_add64 then adds it to dst and to cbuf at the copy slots (each nullable).
+// Both return their launch counts.
+int launch_wood_corr64(const DevMesh& M, const WoodArgs& a, const double* src, const double* lam, double sign,
+                       cudaStream_t st);
+int launch_wood_add64(const DevMesh& M, const WoodArgs& a, double* cbuf, double* dst, cudaStream_t st);
 
 // dst[i] = (float) src[i], i < n.
 void launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);

@@ -591,6 +591,40 @@ void launch_wood_apply(const DevMesh& M, const WoodArgs& a, const double* lam, d
                                                                                    a.z_pool, a.tbuf, rmax, cbuf);
 }
 
+// dst += y at the dofs of subdomain list[blockIdx.x] (y from k_wood_y64 in ybuf).
+__global__ void __launch_bounds__(256) k_wood_add64(DevMesh M, WoodArgs a, double* dst) {
+  const int w = blockIdx.x;
+  const SubDev S = M.subs[a.list[w]];
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= S.n_dof) return;
+  dst[S.dof_off + k] += a.ybuf[(long long)w * a.max_n + k];
+}
+
+int launch_wood_corr64(const DevMesh& M, const WoodArgs& a, const double* src, const double* lam, double sign,
+                       cudaStream_t st) {
+  if (a.n <= 0) return 0;
+  const int rmax = 6 * a.max_pts;
+  k_wood_v64<<<a.n, 256, 0, st>>>(M, a, src, lam, sign);
+  k_wood_t64<<<dim3((unsigned)a.n, (unsigned)((rmax + kWoodRows - 1) / kWoodRows)), 256, 0, st>>>(M.subs, a);
+  k_wood_s64<<<a.n, 256, 0, st>>>(a);
+  k_wood_y64<<<dim3((unsigned)a.n, (unsigned)((a.max_n + 63) / 64)), 256, 0, st>>>(M, a, nullptr);
+  return 4;
+}
+
+int launch_wood_add64(const DevMesh& M, const WoodArgs& a, double* cbuf, double* dst, cudaStream_t st) {
+  if (a.n <= 0) return 0;
+  int n = 0;
+  if (dst) {
+    k_wood_add64<<<dim3((unsigned)a.n, (unsigned)((a.max_n + 255) / 256)), 256, 0, st>>>(M, a, dst);
+    ++n;
+  }
+  if (cbuf) {
+    k_wood_cb64<<<dim3((unsigned)a.n, (unsigned)((a.max_copy + 255) / 256)), 256, 0, st>>>(M, a, cbuf);
+    ++n;
+  }
+  return n;
+}
+
 int launch_wood_apply64(const DevMesh& M, const WoodArgs& a, const double* src, const double* lam, double sign,
                         double* cbuf, double* dst, cudaStream_t st) {
   if (a.n <= 0) return 0;
