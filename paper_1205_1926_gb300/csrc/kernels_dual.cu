@@ -93,10 +93,11 @@ __global__ void k_G_full(DevMesh M, const double* __restrict__ x_full, double* g
   }
 }
 
-// gx[6p+c] = scale * (G x)[6p+c] (and its FP32 rounding in gx32, nullable) = scale * sum over the entries of subdomain p of
-// G[entry][c] x[row].  One CTA per subdomain.  T: FP64 values, or their FP32 copy
-// (products and per-thread sums in T) for the inner iterations of the mixed mode.
-// FP64 values: 6 per entry; FP32 values: 8 per entry (6 and two zeros), read as two float4.
+// gx[6p+c] = scale * (G x)[6p+c] = scale * sum over the entries of subdomain p of G[entry][c] x[row]
+// (and, with gx32, its FP32 rounding for the FP32 coarse GEMV).  One CTA per subdomain.  T: FP64
+// values, or their FP32 copy (products, per-thread and block sums in T) for the inner iterations of
+// the mixed mode.  FP64 values: 6 per entry; FP32 values: 8 per entry (6 and two zeros), read as two
+// float4.
 template <typename T>
 __device__ __forceinline__ void g_entry(const T* __restrict__ Gv, long long e, T g[6]);
 template <>
