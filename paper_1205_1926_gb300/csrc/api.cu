@@ -1830,7 +1830,7 @@ int history_start(tfeti_ctx* c, const double* f, double tol_abs, double r0) {
   // the MLP vector joins only where the stored solutions alone miss the stopping test
   // (there the start is refined anyway, so the mixed mode takes its product in FP32)
   c->mlp_missed = pred > tol_abs;
-  // the network's own judge: a solve where its vector lowered the predicted residual by less than
+  // the network's own gate: a solve where its vector lowered the predicted residual by less than
   // 10 % counts against it, and after two such solves in a row at this Newton index it is consulted
   // only every fourth time (it keeps training meanwhile)
   bool consult = true;
@@ -1903,7 +1903,7 @@ void mlp_train(tfeti_ctx* c, double r0) {
   if (!mlp_index_ok(c)) return;
   const long long m = c->M.n_mult;
   // training only after solves that the stored solutions alone could not start well, and while the
-  // judge has the network benched at this Newton index (two solves in a row where it added less than
+  // gate has the network benched at this Newton index (two solves in a row where it added less than
   // 10 %) only after the solves that consulted it
   const bool benched = c->mlp_nogain[c->newton_idx - 1] >= 2 && !c->mlp_consulted;
   const bool train = !benched && c->mlp_missed && c->mlp_seen[c->newton_idx - 1] >= 1 &&

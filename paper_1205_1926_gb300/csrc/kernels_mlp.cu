@@ -3,7 +3,7 @@
 // side, the load-increment ratio, local plastic indicators) to a predicted entry
 // of lambda_Ker for the first Newton solve of the next load step.  The
 // prediction only enters the Galerkin start of the dual PCGP as one more basis
-// vector, so the start remains judged against the zero start of Algorithm 3.
+// vector, so the start is still compared against the zero start of Algorithm 3.
 //
 // Network: kMlpIn -> kMlpHid (ReLU) -> kMlpHid (ReLU) -> 1, in residual form: the
 // output is f0 (the previous step's value) plus the network, whose last layer starts

@@ -119,7 +119,7 @@ def test_constraint_matrix_orthonormal_full_rank(w):
     assert np.abs(B @ v).max() < 1e-13 * np.abs(v).max()
 
 
-def test_survey_size_table_cube12():
+def test_size_table_cube12():
     # sizes of the 12^3 / 2x2x2 workload by direct counting: decomposed dofs and multipliers
     m = ElastoplasticModel(W.CUBE12)
     assert m.dec.n_dof == 8 * 3 * 7 ** 3 and m.dec.B.shape[0] == 2148 and m.dec.n_gp == 13824
